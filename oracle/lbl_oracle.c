@@ -1,0 +1,200 @@
+/*
+ * ORACLE — test infrastructure only.  Plain, slow, obviously correct CPU
+ * definition of the labeling path of arXiv 1810.02612 (Paden, Liu, Cullen,
+ * "Accelerated Labeling of Discrete Abstractions for Planning Under LTL
+ * Specifications").  Only the test suite, the smoke check and the benchmark's
+ * CPU-baseline leg may load this library; the product path never does.
+ *
+ * It shares no code, header, table or constant with the CUDA library.
+ *
+ * Functions and the passage each follows:
+ *   orc_morton / orc_cell_index  z-order cell index, Sec. 4.1 (Algorithm 1 and
+ *                                the bit-interleaving equivalence stated with it)
+ *   orc_frame_coeffs             fixed-point affine map of the equivariance step,
+ *   orc_frame_transform          Sec. 5 (eq. 13): the roadmap lives in the agent
+ *                                frame; the perceived world grids are re-expressed
+ *                                there at the planning pose
+ *   orc_label / orc_label_rows   Boolean matrix product L = M.P over the CSR
+ *                                rows of M, eq. 10 with Algorithm 2's loop nest
+ *                                (proposition, row, nonzero)
+ *   orc_monitor                  safety-monitor transition delta(q, L(e)) for every
+ *                                monitor state, Sec. 3.2
+ *
+ * Readings of the paper used here (the paper is silent or garbled at these
+ * points):
+ *   - CSR: row pointer r and column indices c as in eq. 11 and Algorithm 2.
+ *   - z-order: x bit i goes to index bit 2i+1, y bit i to bit 2i (axis 0 split
+ *     first, at the most significant level).
+ *   - Agent grid cell (ix,iy) has its centre at (x0+(ix+.5)res, y0+(iy+.5)res)
+ *     in the agent frame; the world point under it is (X,Y)+R(theta)*centre.
+ *     The world cell is the floor of ((p - corner)/res_w), evaluated as a Q32.32
+ *     fixed-point affine map of (ix,iy) whose six coefficients are rounded once
+ *     (half to even) from double; outside the world grid reads as false.
+ *   - Label bits at positions >= P are zero.
+ *   - Monitor: deterministic table delta[q][letter] with an explicit reject
+ *     state; the letter is formed from m <= 8 selected proposition bits.
+ *
+ * Build: gcc -O2 -fPIC -shared -fopenmp -ffp-contract=off (no contraction, so the
+ * double arithmetic of orc_frame_coeffs is evaluated exactly as written).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_ROWMAJOR 0
+#define ORC_MORTON 1
+
+/* ------------------------------------------------------------ cell index */
+
+/* z-order index: interleave the bits of ix and iy one at a time. */
+uint64_t orc_morton(uint32_t ix, uint32_t iy) {
+  uint64_t n = 0;
+  for (int i = 0; i < 32; i++) {
+    uint64_t xb = (ix >> i) & 1u;
+    uint64_t yb = (iy >> i) & 1u;
+    n |= xb << (2 * i + 1);
+    n |= yb << (2 * i);
+  }
+  return n;
+}
+
+int64_t orc_cell_index(int32_t order, int32_t w, int32_t ix, int32_t iy) {
+  if (order == ORC_MORTON) return (int64_t)orc_morton((uint32_t)ix, (uint32_t)iy);
+  return (int64_t)iy * w + ix;
+}
+
+/* --------------------------------------------------------- frame transform */
+
+/* floor(v / 2^32) for any signed v, written without relying on shifts of
+   negative numbers. */
+static int64_t floor_q32(int64_t v) {
+  const int64_t one = (int64_t)1 << 32;
+  int64_t q = v / one;
+  if (v % one != 0 && v < 0) q -= 1;
+  return q;
+}
+
+static int64_t to_q32(double a) {
+  /* a * 2^32 is exact in double; nearbyint rounds half to even */
+  return (int64_t)nearbyint(a * 4294967296.0);
+}
+
+/*
+ * Coefficients of the map (ix,iy) -> continuous world-cell coordinates (u,v):
+ *   u = a00*ix + a01*iy + b0,   v = a10*ix + a11*iy + b1
+ * out = {A00, A01, B0, A10, A11, B1} in Q32.32.
+ */
+void orc_frame_coeffs(double wres, double wx0, double wy0, double ares, double ax0, double ay0, double X, double Y,
+                      double theta, int64_t *out) {
+  double c = cos(theta);
+  double s = sin(theta);
+  double k = ares / wres;
+  double a00 = c * k;
+  double a01 = -(s * k);
+  double a10 = s * k;
+  double a11 = c * k;
+  double xa = ax0 + 0.5 * ares; /* centre of agent cell (0,0), agent frame */
+  double ya = ay0 + 0.5 * ares;
+  double b0 = ((X + ((c * xa) - (s * ya))) - wx0) / wres;
+  double b1 = ((Y + ((s * xa) + (c * ya))) - wy0) / wres;
+  out[0] = to_q32(a00);
+  out[1] = to_q32(a01);
+  out[2] = to_q32(b0);
+  out[3] = to_q32(a10);
+  out[4] = to_q32(a11);
+  out[5] = to_q32(b1);
+}
+
+/*
+ * O[cell_index(ix,iy)] bit p = planes[p][wy][wx] != 0 at the world cell under
+ * the agent cell's centre; 0 when that world cell is outside the world grid.
+ * planes: uint8[P][wh][ww] row-major.  O: uint64[aw*ah].
+ */
+int orc_frame_transform(int32_t ww, int32_t wh, double wres, double wx0, double wy0, const uint8_t *planes, int32_t P,
+                        double X, double Y, double theta, int32_t aw, int32_t ah, double ares, double ax0, double ay0,
+                        int32_t aorder, uint64_t *O) {
+  if (P < 0 || P > 64) return -1;
+  int64_t q[6];
+  orc_frame_coeffs(wres, wx0, wy0, ares, ax0, ay0, X, Y, theta, q);
+  for (int32_t iy = 0; iy < ah; iy++) {
+    for (int32_t ix = 0; ix < aw; ix++) {
+      int64_t u = q[0] * ix + q[1] * iy + q[2];
+      int64_t v = q[3] * ix + q[4] * iy + q[5];
+      int64_t wxc = floor_q32(u);
+      int64_t wyc = floor_q32(v);
+      uint64_t word = 0;
+      if (wxc >= 0 && wxc < ww && wyc >= 0 && wyc < wh) {
+        for (int32_t p = 0; p < P; p++) {
+          uint8_t occ = planes[(size_t)p * ww * wh + (size_t)wyc * ww + (size_t)wxc];
+          if (occ != 0) word |= (uint64_t)1 << p;
+        }
+      }
+      O[orc_cell_index(aorder, aw, ix, iy)] = word;
+    }
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------ labels */
+
+/*
+ * L(e, p) = OR over the nonzeros k of row e of bit p of O[colidx[k]].
+ * Loop nest as in Algorithm 2: propositions outermost, then rows, then the
+ * row's nonzeros.  No early exit.  Rows are independent, so the row loop may be
+ * split across n_threads OpenMP threads without changing any result.
+ */
+void orc_label(int64_t n_edges, const int64_t *rowptr, const int32_t *colidx, const uint64_t *O, int32_t P,
+               uint64_t *L, int32_t n_threads) {
+  for (int64_t e = 0; e < n_edges; e++) L[e] = 0;
+  for (int32_t p = 0; p < P; p++) {
+#pragma omp parallel for schedule(dynamic, 256) num_threads(n_threads > 0 ? n_threads : 1)
+    for (int64_t e = 0; e < n_edges; e++) {
+      uint64_t hit = 0;
+      for (int64_t k = rowptr[e]; k < rowptr[e + 1]; k++) hit |= (O[colidx[k]] >> p) & 1u;
+      L[e] |= hit << p;
+    }
+  }
+}
+
+/* The same definition for a list of rows (for spot checks of large inputs). */
+void orc_label_rows(int64_t n_rows, const int64_t *rows, const int64_t *rowptr, const int32_t *colidx,
+                    const uint64_t *O, int32_t P, uint64_t *L) {
+  for (int64_t i = 0; i < n_rows; i++) {
+    int64_t e = rows[i];
+    uint64_t word = 0;
+    for (int32_t p = 0; p < P; p++) {
+      uint64_t hit = 0;
+      for (int64_t k = rowptr[e]; k < rowptr[e + 1]; k++) hit |= (O[colidx[k]] >> p) & 1u;
+      word |= hit << p;
+    }
+    L[i] = word;
+  }
+}
+
+/* ----------------------------------------------------------------- monitor */
+
+/*
+ * For every edge e and monitor state q < n_states:
+ *   letter = sum_j bit(L[e], relbits[j]) << j,   q' = delta[q][letter]
+ * next[e] holds q' in bits [4q, 4q+4); viol[e] bit q is set iff q' == reject.
+ * delta: uint8[n_states][2^m].
+ */
+int orc_monitor(int32_t n_states, int32_t m, const uint8_t *relbits, const uint8_t *delta, int32_t reject,
+                const uint64_t *L, int64_t n, uint64_t *next, uint16_t *viol) {
+  if (n_states < 1 || n_states > 16 || m < 0 || m > 8) return -1;
+  for (int64_t e = 0; e < n; e++) {
+    uint32_t letter = 0;
+    for (int32_t j = 0; j < m; j++) letter |= (uint32_t)((L[e] >> relbits[j]) & 1u) << j;
+    uint64_t word = 0;
+    uint16_t v = 0;
+    for (int32_t q = 0; q < n_states; q++) {
+      uint32_t qn = delta[(size_t)q * ((size_t)1 << m) + letter];
+      word |= (uint64_t)(qn & 15u) << (4 * q);
+      if ((int32_t)qn == reject) v |= (uint16_t)(1u << q);
+    }
+    next[e] = word;
+    viol[e] = v;
+  }
+  return 0;
+}
