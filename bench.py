@@ -1,0 +1,394 @@
+"""Benchmark of the labeling hot path: edge x proposition labels per second.
+
+One step = one planning query on one frame: resample the world proposition
+planes at the agent pose (frame transform), label every roadmap edge (the
+Boolean product of eq. 10) and, where the workload has one, run the safety
+monitor fused into the labeling kernel.
+
+  value  device-timed steps, inputs resident in HBM (CUDA events per step,
+         L2 flushed before every step)
+  e2e    the same steps through lbl_session_run with pinned host buffers:
+         host->device copy of the planes and device->host copy of the labels
+         (and monitor outputs) are inside the timed region
+
+Multi-GPU (torchrun): every rank labels its own independent frames against
+its own roadmap (weak scaling); ranks only meet at the barrier and the
+max-over-ranks of the timings.
+
+``--impl reference`` times the CPU oracle instead (rank 0 only), on a bounded
+sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "edge*prop labels/s"
+UNIT = "labels/s"
+
+WORKLOADS = {
+    "large": "1,000,000 constant-curvature arcs swept on a 512x512 agent grid at 0.2 m (z-order), 64 propositions, "
+             "world planes resampled at a random pose, 16-state safety monitor over 8 label bits fused",
+    "driving": "100,000 arcs on a 256x256 agent grid at 0.25 m (z-order), 32 propositions, world planes resampled "
+               "at a random pose",
+    "plain": "2,000 arcs on a 64x64 grid at 0.5 m (z-order), 4 disc propositions",
+    "paper": "1,097,702 short arcs on a 2048x1024 row-major grid at 0.1 m (2^21 cells), 2 propositions at ~1 % and "
+             "~90 % fill",
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS))
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--algo", default="auto", choices=["auto", "csr", "bittile"])
+    ap.add_argument("--lanes", type=int, default=0)
+    ap.add_argument("--early-exit", type=int, default=-1)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--edges", type=int, default=None, help="shrink the workload (not for reported numbers)")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# --------------------------------------------------------------------- clocks
+
+CLOCK_FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+class ClockSampler:
+    def __init__(self, index: int, enabled: bool = True):
+        self.proc = None
+        self.path = None
+        if not enabled:
+            return
+        try:
+            out = os.path.join(ROOT, "gpurun_out")
+            os.makedirs(out, exist_ok=True)
+            self.path = os.path.join(out, f"clocks_gpu{index}.csv")
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={CLOCK_FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self, t0: float, t1: float):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                ts = time.mktime(time.strptime(parts[0].split(".")[0], "%Y/%m/%d %H:%M:%S"))
+                rows.append((ts, float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        inside = [r for r in rows if t0 - 1.0 <= r[0] <= t1 + 1.0] or rows
+        if not inside:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in inside for i, v in enumerate(r[3]) if v.lower() == "active"})
+        return {"sm_mhz": float(np.median([r[1] for r in inside])), "sm_max_mhz": max(r[2] for r in inside),
+                "reasons": reasons, "samples": len(inside)}
+
+
+# ------------------------------------------------------------------- roofline
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return None
+
+
+def label_bytes(wl, algo: str, n_bt: int | None, with_monitor: bool) -> int:
+    """Algorithmic HBM bytes of one labeling launch (each array read or written
+    once; O and the bit planes counted once although they are re-read from L2)."""
+    E = wl.n_edges
+    out = 8 * E + (10 * E if with_monitor else 0)
+    if algo == "bittile":
+        blocks = (wl.agent.cells + 63) // 64
+        return 12 * n_bt + 8 * (E + 1) + 8 * wl.agent.cells + 8 * wl.P * blocks + out
+    return 4 * wl.nnz + 8 * (E + 1) + 8 * wl.agent.cells + out
+
+
+def committed_traffic(kernel_src: str, workload: str, algo: str):
+    """Per-launch DRAM bytes from the committed ncu summary, if it was taken on
+    the current kernel source (matching hash) and scaled to this workload."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+    for line in open(path):
+        t = line.split()
+        if len(t) >= 4 and t[0] == workload and t[1] == algo and t[2] == h:
+            return float(t[3])
+    return None
+
+
+# ------------------------------------------------------------------ reference
+
+def cpu_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_step_rate(wl, n_sample: int, threads: int):
+    """Oracle time for one frame on a sample of the workload's edges: frame
+    transform of the whole grid, labels of the first n_sample edges, monitor."""
+    import oracle
+    rp = wl.rowptr[: n_sample + 1]
+    ci = wl.colidx[: int(rp[-1])]
+    t = time.perf_counter()
+    O = oracle.frame_transform(wl.world, wl.planes, wl.pose, wl.agent)
+    Lw = oracle.label(rp, ci, O, wl.P, threads=threads)
+    if wl.monitor is not None:
+        m = wl.monitor
+        oracle.monitor(m.n_states, m.m, m.relbits, m.delta, m.reject, Lw)
+    return time.perf_counter() - t
+
+
+def calibrate_sample(wl, seconds: float, threads: int) -> int:
+    n = min(wl.n_edges, 2000)
+    dt = oracle_step_rate(wl, n, threads)
+    n = int(min(wl.n_edges, max(1000, n * seconds / max(dt, 1e-3))))
+    return n
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    wl = synth.make(args.workload, seed=args.seed, edges=args.edges, threads=cpu_cores())
+    threads = cpu_cores()
+    per_step = max(0.5, min(6.0, 120.0 / max(args.steps + args.warmup, 1)))
+    n = calibrate_sample(wl, per_step, threads)
+    for _ in range(args.warmup):
+        oracle_step_rate(wl, n, threads)
+    times = [oracle_step_rate(wl, n, threads) for _ in range(args.steps)]
+    tot = sum(times)
+    value = n * wl.P * args.steps / tot
+    sample = f"first {n} of {wl.n_edges} edges per step (whole-grid frame transform), {args.steps} steps"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.workload], "name": args.workload},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------ ours
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        if world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("gloo")
+        run_reference(args, rank, world)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import paper_1810_02612_gb300 as L
+    from paper_1810_02612_gb300.lbl import lbl_config
+
+    # ---- inputs: every rank its own independent roadmap and frame
+    t_gen = time.perf_counter()
+    wl = synth.make(args.workload, seed=args.seed + 1000 * rank, edges=args.edges, threads=cpu_cores())
+    t_gen = time.perf_counter() - t_gen
+    algo = {"auto": L.LBL_ALGO_AUTO, "csr": L.LBL_ALGO_CSR, "bittile": L.LBL_ALGO_BITTILE}[args.algo]
+    want_bt = args.algo in ("auto", "bittile")
+    stream = torch.cuda.Stream()
+    rm = L.lbl_roadmap_upload(wl.agent, wl.rowptr, wl.colidx, flags=L.LBL_UPLOAD_BITTILE if want_bt else 0,
+                              stream=stream)
+    mon = None
+    if wl.monitor is not None:
+        m = wl.monitor
+        mon = L.lbl_monitor_create(m.n_states, m.m, m.relbits, m.delta, m.reject)
+    E, P = wl.n_edges, wl.P
+    cfg = lbl_config(algo, args.lanes, args.early_exit, 0)
+    with torch.cuda.stream(stream):
+        d_planes = torch.from_numpy(wl.planes).to("cuda", non_blocking=False)
+        d_O = torch.empty(wl.agent.cells, dtype=torch.uint64, device="cuda")
+        d_L = torch.empty(E, dtype=torch.uint64, device="cuda")
+        d_next = torch.empty(E, dtype=torch.uint64, device="cuda") if mon else None
+        d_viol = torch.empty(E, dtype=torch.uint16, device="cuda") if mon else None
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+
+    def step():
+        L.lbl_frame_transform(wl.world, d_planes, P, wl.pose, wl.agent, d_O, stream=stream)
+        L.lbl_label(rm, d_O, P, d_L, mon, d_next, d_viol, cfg, stream=stream)
+
+    # resolve what AUTO picked (for the roofline accounting)
+    used = args.algo
+    if used == "auto":
+        used = "bittile" if (want_bt and P <= 16) else "csr"
+    launches_per_step = 2 + (1 if used == "bittile" else 0)
+
+    # ---- warm-up
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- device-timed steps (L2 flushed before each)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local, enabled=not args.no_clocks and rank == 0)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.time()
+    for i in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(i & 255)
+        ev[i][0].record(stream)
+        L.lbl_frame_transform(wl.world, d_planes, P, wl.pose, wl.agent, d_O, stream=stream)
+        ev[i][1].record(stream)
+        L.lbl_label(rm, d_O, P, d_L, mon, d_next, d_viol, cfg, stream=stream)
+        ev[i][2].record(stream)
+    torch.cuda.synchronize()
+    t1 = time.time()
+    if dist:
+        dist.barrier()
+    step_ms = np.array([a.elapsed_time(c) for a, b, c in ev])
+    frame_ms = np.array([a.elapsed_time(b) for a, b, c in ev])
+    label_ms = np.array([b.elapsed_time(c) for a, b, c in ev])
+    clk = clocks.stop(t0, t1)
+    total_ms = float(step_ms.sum())
+    if dist:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * E * P * args.steps / (total_ms / 1e3)
+
+    # ---- end to end through the session API with pinned host buffers
+    ss = L.lbl_session_create(rm, wl.world, P, mon, cfg)
+    h_planes = torch.from_numpy(wl.planes).pin_memory()
+    h_L = torch.empty(E, dtype=torch.uint64).pin_memory()
+    h_next = torch.empty(E, dtype=torch.uint64).pin_memory() if mon else None
+    h_viol = torch.empty(E, dtype=torch.uint16).pin_memory() if mon else None
+    for _ in range(args.warmup):
+        L.lbl_session_run(ss, h_planes, wl.pose, h_L, h_next, h_viol, stream=stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for i in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(i & 255)
+        e_ev[i][0].record(stream)
+        L.lbl_session_run(ss, h_planes, wl.pose, h_L, h_next, h_viol, stream=stream)
+        e_ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    e2e_ms_steps = np.array([a.elapsed_time(b) for a, b in e_ev])
+    e2e_ms = float(e2e_ms_steps.sum())
+    if dist:
+        t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = world * E * P * args.steps / (e2e_ms / 1e3)
+    h2d = int(wl.planes.nbytes)
+    d2h = 8 * E + ((8 + 2) * E if mon else 0)
+    L.lbl_session_free(ss)
+
+    # ---- roofline of the dominant kernel (labeling)
+    n_bt = L.lbl_roadmap_info(rm)[2]
+    lb = label_bytes(wl, used, n_bt, mon is not None)
+    label_avg_s = float(label_ms.mean()) / 1e3
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    achieved = lb / label_avg_s / 1e9
+    traffic = committed_traffic(os.path.join(ROOT, "paper_1810_02612_gb300", "csrc", "k_label.cu"),
+                                args.workload, used)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        threads = cpu_cores()
+        n = calibrate_sample(wl, args.cpu_seconds, threads)
+        dt = oracle_step_rate(wl, n, threads)
+        cpu = {"value": n * P / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"one frame: whole-grid frame transform + labels of the first {n} of {E} edges"
+                         + (" + monitor" if mon else "") + f" ({dt:.1f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.workload], "name": args.workload, "edges": E, "nnz": wl.nnz,
+                       "props": P, "grid": f"{wl.agent.w}x{wl.agent.h}", "algo": used,
+                       "monitor": bool(mon), "l2": "flushed before every step (256 MiB write); CSR "
+                       f"{(4 * wl.nnz) / 1e9:.2f} GB > L2", "parallelism": f"replicas x{world}"},
+            "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
+                           "frame_transform_avg": float(frame_ms.mean()), "label_avg": float(label_ms.mean()),
+                           "e2e_p50": float(np.percentile(e2e_ms_steps, 50)),
+                           "e2e_p99": float(np.percentile(e2e_ms_steps, 99))},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches_per_step * args.steps,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": f"label_{used}", "algorithmic_bytes_per_launch": lb,
+                         "peak_source": "measured" if peaks else "fallback"},
+            "cpu_baseline": cpu,
+            "clocks": clk,
+            "setup_s": {"generate": t_gen},
+        }
+        print(json.dumps(line), flush=True)
+
+    if mon:
+        L.lbl_monitor_free(mon)
+    L.lbl_roadmap_free(rm)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,226 @@
+/*
+ * lbl.h — C ABI of liblbl: GPU labeling of a fixed discrete abstraction with
+ * atomic propositions (arXiv 1810.02612, Paden, Liu & Cullen, "Accelerated
+ * Labeling of Discrete Abstractions for Planning Under LTL Specifications").
+ *
+ * The method (Sec. 4): every edge e of a precomputed roadmap is stored as the
+ * set of workspace cells its swept footprint covers (a row of the Boolean
+ * trajectory matrix M, eq. 10, stored in CSR form as in eq. 11).  The perceived
+ * scene is a Boolean matrix P with one column per atomic proposition.  The edge
+ * labels are the Boolean product  L(e, p) = OR_k M(e, k) AND P(k, p)  (eq. 10),
+ * i.e. proposition p labels edge e iff its region meets the swept cells
+ * (eq. 7).  Because the dynamics are equivariant to planar motions (Sec. 5,
+ * eq. 13), one roadmap built in the agent frame is re-used at every planning
+ * pose by resampling the world-frame proposition grids into the agent frame.
+ * A safety monitor (Sec. 3.2) then reads each label.
+ *
+ * Conventions for every entry point:
+ *   - The return value is a status code (LBL_OK or a negative LBL_E*).  On
+ *     failure lbl_last_error() returns a message for the calling thread.
+ *   - "d_" pointers are CUDA device pointers owned by the caller; "h_" pointers
+ *     are host pointers owned by the caller.  The library owns only the objects
+ *     behind its opaque handles and frees them in the matching *_free call.
+ *   - Work is enqueued asynchronously on the caller's stream (NULL = the legacy
+ *     default stream); outputs are valid once that stream has completed.
+ *     Calls on different streams that write the same outputs race.
+ *   - Proposition words are uint64: bit p is proposition p, bits >= n_props are
+ *     zero.  At most 64 propositions.
+ *   - No C++ exception crosses this interface; nothing here calls exit().
+ *   - The library computes on the CUDA device current on the calling thread
+ *     when the handle was created; it never falls back to the CPU.
+ */
+#ifndef LBL_H_
+#define LBL_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t. */
+typedef struct CUstream_st *lbl_stream;
+
+/* ----------------------------------------------------------- status codes */
+#define LBL_OK 0
+#define LBL_EINVAL (-1)      /* bad argument, limit exceeded, malformed CSR */
+#define LBL_ENOMEM (-2)      /* device or host allocation failed */
+#define LBL_ECUDA (-3)       /* a CUDA runtime call or kernel launch failed */
+#define LBL_ETIMEOUT (-4)    /* a bounded wait ran out */
+#define LBL_EUNSUPPORTED (-5)/* valid request this build does not implement */
+
+/* ------------------------------------------------------------ cell order */
+#define LBL_ORDER_ROWMAJOR 0 /* index = iy * w + ix */
+#define LBL_ORDER_MORTON 1   /* z-order (Sec. 4.1, Alg. 1): bit i of ix -> bit 2i+1,
+                                bit i of iy -> bit 2i; needs w == h, a power of two */
+
+/*
+ * Occupancy grid (Sec. 4.1): w x h square cells of side res metres.  Cell
+ * (ix, iy) covers [x0 + ix*res, x0 + (ix+1)*res) x [y0 + iy*res, y0 + (iy+1)*res)
+ * in the grid's own frame (world frame for perception grids, agent frame for
+ * the roadmap grid).  `order` numbers the cells (LBL_ORDER_*).
+ * Limits: 1 <= w, h <= 32768; w*h <= 2^31 - 1; res > 0.
+ */
+typedef struct {
+  int32_t w, h;
+  double res, x0, y0;
+  int32_t order;
+} lbl_grid;
+
+/* Agent pose in the world frame: position (x, y) in metres, heading theta in
+   radians (the agent frame's +x axis points along theta). */
+typedef struct {
+  double x, y, theta;
+} lbl_pose;
+
+/* Labeling algorithm (Sec. 4.3: both compute eq. 10 exactly). */
+#define LBL_ALGO_AUTO 0    /* pick from the roadmap's shape and n_props */
+#define LBL_ALGO_CSR 1     /* gather-OR over the CSR cell lists */
+#define LBL_ALGO_BITTILE 2 /* AND over per-edge 64-cell block masks */
+
+typedef struct {
+  int32_t algo;           /* LBL_ALGO_* */
+  int32_t lanes_per_edge; /* CSR: lanes that share one edge, 0 = auto, else 4/8/16/32 */
+  int32_t early_exit;     /* 1 = stop a row once every proposition is set (Sec. 5,
+                             early termination); 0 = off; -1 = auto */
+  int32_t ctas_per_sm;    /* persistent grid size per SM, 0 = auto */
+} lbl_config;
+
+typedef struct lbl_roadmap_s *lbl_roadmap;
+typedef struct lbl_monitor_s *lbl_monitor;
+typedef struct lbl_session_s *lbl_session;
+
+/* Message describing the last failure on the calling thread ("" if none).
+   The pointer stays valid until the thread's next lbl_* call. */
+const char *lbl_last_error(void);
+
+/* ABI version of this header (major * 10000 + minor * 100 + patch). */
+int lbl_version(void);
+
+/* --------------------------------------------------------------- roadmap */
+
+#define LBL_UPLOAD_DEVICE_PTRS 1u /* rowptr/colidx are device pointers (default: host) */
+#define LBL_UPLOAD_BITTILE 2u     /* also derive the 64-cell block form used by
+                                     LBL_ALGO_BITTILE (costs ~12 B per touched block) */
+
+/*
+ * lbl_roadmap_upload — make a roadmap resident on the device.
+ * The trajectory matrix M of eq. 10 in the CSR layout of eq. 11: row e (edge e)
+ * holds the cells swept by X(e) (eq. 7 discretised on `agent`, Sec. 4.1).
+ *   agent   grid of the roadmap, agent frame (its `order` numbers colidx)
+ *   rowptr  int64[n_edges + 1], rowptr[0] = 0, non-decreasing, rowptr[n_edges] = nnz
+ *   colidx  int32[nnz], each row strictly increasing, 0 <= colidx < w*h
+ *   flags   LBL_UPLOAD_*; host arrays may be pageable or pinned
+ *   s       stream for the copies and derivation kernels
+ * The call copies both arrays into library-owned device memory, checks them on
+ * the device (LBL_EINVAL if malformed), derives the structures the kernels use
+ * and synchronises `s` before returning.  The caller's arrays may be freed
+ * afterwards.  n_edges = 0 is allowed.
+ */
+int lbl_roadmap_upload(const lbl_grid *agent, const int64_t *rowptr, const int32_t *colidx, int64_t n_edges,
+                       int64_t nnz, uint32_t flags, lbl_stream s, lbl_roadmap *out);
+
+/* Release a roadmap (synchronises the device first). NULL is accepted. */
+int lbl_roadmap_free(lbl_roadmap rm);
+
+/* Shape of a roadmap: edges, nonzeros, (block, mask) entries of the block form
+   (0 without LBL_UPLOAD_BITTILE) and device bytes held.  Any out pointer may be
+   NULL. */
+int lbl_roadmap_info(lbl_roadmap rm, int64_t *n_edges, int64_t *nnz, int64_t *n_block_entries,
+                     int64_t *device_bytes);
+
+/* ------------------------------------------------------- frame transform */
+
+/*
+ * lbl_frame_transform — equivariant re-use of the roadmap (Sec. 5, eq. 13).
+ * For every cell (ix, iy) of `agent`, take its centre c in the agent frame,
+ * move it to the world point q = (pose.x, pose.y) + R(pose.theta) c, and set
+ * bit p of d_O[index(ix, iy)] iff d_planes[p] is non-zero at the world cell
+ * containing q; world points outside `world` read as 0.
+ * Exactness: the map (ix, iy) -> world cell coordinates is affine; its six
+ * coefficients are computed once in double on the host and rounded (half to
+ * even) to Q32.32 fixed point; the map is then evaluated exactly in 64-bit
+ * integers and floored, so every device and every run give the same cells.
+ *   world     grid of the planes (row-major planes, its `order` is ignored)
+ *   d_planes  uint8[n_props][world.h][world.w], non-zero = occupied
+ *   n_props   0..64
+ *   agent     roadmap grid; d_O is written in agent.order
+ *   d_O       uint64[agent.w * agent.h]
+ * Errors: LBL_EINVAL for bad grids, n_props > 64, or a pose whose fixed-point
+ * map could overflow 64 bits.
+ */
+int lbl_frame_transform(const lbl_grid *world, const uint8_t *d_planes, int32_t n_props, lbl_pose pose,
+                        const lbl_grid *agent, uint64_t *d_O, lbl_stream s);
+
+/* --------------------------------------------------------------- monitor */
+
+/*
+ * lbl_monitor_create — deterministic safety monitor (Sec. 3.2: the automaton
+ * whose rejected words are the bad prefixes of an LTL safety formula), given as
+ * a table.  A label word is read as the letter
+ *   letter = sum_j bit(L, relbits[j]) << j,  j < m
+ * and state q moves to delta[q * 2^m + letter].
+ *   n_states  1..16       m  0..8       relbits  uint8[m], each < 64
+ *   delta     uint8[n_states << m], each < n_states      reject  state id or -1
+ * The table is copied; the host arrays may be freed afterwards.
+ */
+int lbl_monitor_create(int32_t n_states, int32_t m, const uint8_t *relbits, const uint8_t *delta, int32_t reject,
+                       lbl_monitor *out);
+int lbl_monitor_free(lbl_monitor mon);
+
+/*
+ * lbl_monitor_step — for each of n labels and every state q < n_states:
+ *   d_next[i] bits [4q, 4q+4) = delta(q, letter(d_L[i])),
+ *   d_viol[i] bit q           = (that state == reject).
+ * Fields of states >= n_states are zero.  d_next/d_viol: uint64[n] / uint16[n].
+ */
+int lbl_monitor_step(lbl_monitor mon, const uint64_t *d_L, int64_t n, uint64_t *d_next, uint16_t *d_viol,
+                     lbl_stream s);
+
+/* ---------------------------------------------------------------- labels */
+
+/*
+ * lbl_label — the labeling operation (eq. 7) as the Boolean product of eq. 10:
+ *   d_L[e] = (OR over cells k of row e of d_O[k]) & (2^n_props - 1)
+ * in the caller's edge order.  With `mon` non-NULL the monitor step above is
+ * fused into the same kernel and d_next/d_viol (uint64[E] / uint16[E]) are
+ * written too; with `mon` NULL they are ignored.
+ *   d_O      uint64[agent cells] in the roadmap grid's order (lbl_frame_transform)
+ *   n_props  0..64
+ *   d_L      uint64[n_edges]
+ *   cfg      NULL = defaults (LBL_ALGO_AUTO)
+ * LBL_ALGO_BITTILE needs a roadmap uploaded with LBL_UPLOAD_BITTILE
+ * (LBL_EUNSUPPORTED otherwise).  The roadmap holds per-launch working memory,
+ * so two lbl_label calls on the same roadmap must not overlap on the device.
+ */
+int lbl_label(lbl_roadmap rm, const uint64_t *d_O, int32_t n_props, uint64_t *d_L, lbl_monitor mon, uint64_t *d_next,
+              uint16_t *d_viol, const lbl_config *cfg, lbl_stream s);
+
+/* --------------------------------------------------------------- session */
+
+/*
+ * A session bundles one roadmap, one world grid shape and the device buffers of
+ * a whole planning query, so a frame can be run from host memory in one call:
+ * copy the world planes in, transform them to the agent frame, label (with the
+ * monitor, if any) and copy the results out.
+ *   lbl_session_create  allocates the device buffers (planes, O, labels,
+ *                       monitor outputs) for `world` and n_props.
+ *   lbl_session_run     enqueues H2D(h_planes) -> transform -> label -> D2H on
+ *                       `s`.  h_planes: uint8[n_props][world.h][world.w];
+ *                       h_L: uint64[E]; h_next/h_viol: uint64[E]/uint16[E] or
+ *                       NULL.  Host buffers should be pinned for asynchronous
+ *                       copies.  Results are valid after `s` completes; a
+ *                       session runs one frame at a time.
+ */
+int lbl_session_create(lbl_roadmap rm, const lbl_grid *world, int32_t n_props, lbl_monitor mon,
+                       const lbl_config *cfg, lbl_session *out);
+int lbl_session_run(lbl_session ss, const uint8_t *h_planes, lbl_pose pose, uint64_t *h_L, uint64_t *h_next,
+                    uint16_t *h_viol, lbl_stream s);
+int lbl_session_free(lbl_session ss);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBL_H_ */

@@ -1,0 +1,93 @@
+// Roadmap preparation at upload time: row checks and the 64-cell block form of
+// the trajectory matrix (derived once, Sec. 4.3's dense bit-packed variant).
+#include "lbl_internal.cuh"
+
+namespace lbl {
+namespace {
+
+// One thread per row.  A row is bad unless 0 <= rowptr[e] <= rowptr[e+1] <= nnz
+// and its indices are strictly increasing inside [0, cells).  The row pointer is
+// checked before any column index is read, so every access stays inside the
+// arrays.  bt_count[e] (optional) = number of distinct 64-cell blocks of row e.
+__global__ void __launch_bounds__(256) k_scan_rows(const int64_t *__restrict__ rowptr,
+                                                   const int32_t *__restrict__ colidx, int64_t E, int64_t nnz,
+                                                   int64_t cells, unsigned long long *n_bad, int32_t *bt_count) {
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < E; e += stride) {
+    const int64_t beg = rowptr[e], end = rowptr[e + 1];
+    bool bad = !(beg >= 0 && beg <= end && end <= nnz);
+    int32_t blocks = 0;
+    if (!bad) {
+      int64_t prev = -1, prev_block = -1;
+      for (int64_t k = beg; k < end; ++k) {
+        const int64_t c = colidx[k];
+        if (c < 0 || c >= cells || c <= prev) {
+          bad = true;
+          break;
+        }
+        if ((c >> 6) != prev_block) {
+          ++blocks;
+          prev_block = c >> 6;
+        }
+        prev = c;
+      }
+    }
+    if (bad) atomicAdd(n_bad, 1ull);
+    if (bt_count) bt_count[e] = bad ? 0 : blocks;
+  }
+}
+
+// One thread per row: write the (block, mask) entries of row e at bt_rowptr[e].
+__global__ void __launch_bounds__(256) k_bt_fill(const int64_t *__restrict__ rowptr,
+                                                 const int32_t *__restrict__ colidx, int64_t E,
+                                                 const int64_t *__restrict__ bt_rowptr, uint32_t *__restrict__ bt_block,
+                                                 uint64_t *__restrict__ bt_mask) {
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < E; e += stride) {
+    int64_t out = bt_rowptr[e];
+    int64_t cur = -1;
+    uint64_t m = 0;
+    for (int64_t k = rowptr[e]; k < rowptr[e + 1]; ++k) {
+      const int64_t c = colidx[k];
+      const int64_t b = c >> 6;
+      if (b != cur) {
+        if (cur >= 0) {
+          bt_block[out] = static_cast<uint32_t>(cur);
+          bt_mask[out] = m;
+          ++out;
+        }
+        cur = b;
+        m = 0;
+      }
+      m |= 1ull << (c & 63);
+    }
+    if (cur >= 0) {
+      bt_block[out] = static_cast<uint32_t>(cur);
+      bt_mask[out] = m;
+    }
+  }
+}
+
+unsigned blocks_for(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  if (b > 65535LL * 8) b = 65535LL * 8;
+  return static_cast<unsigned>(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+cudaError_t launch_scan_rows(const int64_t *rowptr, const int32_t *colidx, int64_t E, int64_t nnz, int64_t cells,
+                             unsigned long long *n_bad, int32_t *bt_count, cudaStream_t s) {
+  if (E == 0) return cudaSuccess;
+  k_scan_rows<<<blocks_for(E), 256, 0, s>>>(rowptr, colidx, E, nnz, cells, n_bad, bt_count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bt_fill(const int64_t *rowptr, const int32_t *colidx, int64_t E, const int64_t *bt_rowptr,
+                           uint32_t *bt_block, uint64_t *bt_mask, cudaStream_t s) {
+  if (E == 0) return cudaSuccess;
+  k_bt_fill<<<blocks_for(E), 256, 0, s>>>(rowptr, colidx, E, bt_rowptr, bt_block, bt_mask);
+  return cudaGetLastError();
+}
+
+}  // namespace lbl

@@ -1,0 +1,587 @@
+// C ABI of liblbl (declared in include/lbl.h): argument checks, handles,
+// device memory of roadmaps and sessions, and kernel dispatch.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "lbl_internal.cuh"
+
+namespace lbl {
+
+namespace {
+thread_local std::string g_err;
+
+int device_sms(int dev) {
+  static int cache[64] = {0};
+  if (dev >= 0 && dev < 64 && cache[dev]) return cache[dev];
+  int n = 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 1;
+  if (dev >= 0 && dev < 64) cache[dev] = n;
+  return n;
+}
+
+bool valid_grid(const lbl_grid *g, const char *name, bool need_order) {
+  if (!g) {
+    set_error("%s: grid pointer is NULL", name);
+    return false;
+  }
+  if (g->w < 1 || g->h < 1 || g->w > 32768 || g->h > 32768 ||
+      static_cast<int64_t>(g->w) * g->h > 2147483647LL) {
+    set_error("%s: grid size %d x %d outside 1..32768 per side / 2^31-1 cells", name, g->w, g->h);
+    return false;
+  }
+  if (!(g->res > 0.0) || !std::isfinite(g->res) || !std::isfinite(g->x0) || !std::isfinite(g->y0)) {
+    set_error("%s: resolution must be positive and the corner finite", name);
+    return false;
+  }
+  if (need_order) {
+    if (g->order != LBL_ORDER_ROWMAJOR && g->order != LBL_ORDER_MORTON) {
+      set_error("%s: unknown cell order %d", name, g->order);
+      return false;
+    }
+    if (g->order == LBL_ORDER_MORTON && (g->w != g->h || (g->w & (g->w - 1)) != 0)) {
+      set_error("%s: z-order needs a square power-of-two grid (got %d x %d)", name, g->w, g->h);
+      return false;
+    }
+  }
+  return true;
+}
+
+bool same_device(int dev) {
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) {
+    set_error("cudaGetDevice failed");
+    return false;
+  }
+  if (cur != dev) {
+    set_error("handle belongs to device %d but device %d is current", dev, cur);
+    return false;
+  }
+  return true;
+}
+
+// Q32.32 coefficients of (ix, iy) -> continuous world-cell coordinates:
+//   u = a00*ix + a01*iy + b0,  v = a10*ix + a11*iy + b1,
+// from world point q = (X, Y) + R(theta) * centre(ix, iy) (Sec. 5, eq. 13).
+// The double expressions are evaluated exactly as written (the library is built
+// without floating-point contraction) and each is rounded half to even.
+bool frame_map(const lbl_grid &W, const lbl_grid &A, const lbl_pose &p, FrameMap *out) {
+  if (!std::isfinite(p.x) || !std::isfinite(p.y) || !std::isfinite(p.theta)) {
+    set_error("frame transform: pose must be finite");
+    return false;
+  }
+  const double c = std::cos(p.theta);
+  const double s = std::sin(p.theta);
+  const double k = A.res / W.res;
+  const double a00 = c * k;
+  const double a01 = -(s * k);
+  const double a10 = s * k;
+  const double a11 = c * k;
+  const double xa = A.x0 + 0.5 * A.res;
+  const double ya = A.y0 + 0.5 * A.res;
+  const double b0 = ((p.x + ((c * xa) - (s * ya))) - W.x0) / W.res;
+  const double b1 = ((p.y + ((s * xa) + (c * ya))) - W.y0) / W.res;
+  // |a| <= 2^14 and |b| <= 2^28 keep a*ix + a*iy + b (ix, iy < 2^15) inside int64
+  const double lim_a = 16384.0, lim_b = 268435456.0;
+  if (!(std::fabs(a00) <= lim_a && std::fabs(a01) <= lim_a && std::fabs(b0) <= lim_b && std::fabs(b1) <= lim_b)) {
+    set_error("frame transform: pose or resolution ratio out of the fixed-point range");
+    return false;
+  }
+  auto q = [](double v) { return static_cast<int64_t>(std::nearbyint(v * 4294967296.0)); };
+  out->A00 = q(a00);
+  out->A01 = q(a01);
+  out->B0 = q(b0);
+  out->A10 = q(a10);
+  out->A11 = q(a11);
+  out->B1 = q(b1);
+  return true;
+}
+
+template <typename T>
+cudaError_t dev_alloc(T **p, size_t count, int64_t *bytes) {
+  const size_t b = count * sizeof(T);
+  cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), b ? b : 16);
+  if (e == cudaSuccess && bytes) *bytes += static_cast<int64_t>(b);
+  return e;
+}
+
+void free_roadmap(Roadmap *rm) {
+  if (!rm) return;
+  cudaFree(rm->rowptr);
+  cudaFree(rm->colidx);
+  cudaFree(rm->bt_rowptr);
+  cudaFree(rm->bt_block);
+  cudaFree(rm->bt_mask);
+  cudaFree(rm->planes);
+  delete rm;
+}
+
+int resolve_lpe(const Roadmap &rm, const lbl_config *cfg) {
+  int lpe = cfg ? cfg->lanes_per_edge : 0;
+  if (lpe == 4 || lpe == 8 || lpe == 16 || lpe == 32) return lpe;
+  const double avg = rm.E ? static_cast<double>(rm.nnz) / static_cast<double>(rm.E) : 0.0;
+  lpe = 4;
+  while (lpe < 32 && lpe * 16 < avg) lpe *= 2;
+  return lpe;
+}
+
+}  // namespace
+
+void set_error(const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+  set_error("%s: %s", what, cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? LBL_ENOMEM : LBL_ECUDA;
+}
+
+}  // namespace lbl
+
+using namespace lbl;
+
+struct lbl_roadmap_s : Roadmap {};
+struct lbl_monitor_s : Monitor {};
+struct lbl_session_s {
+  int device = 0;
+  lbl_roadmap rm = nullptr;
+  lbl_monitor mon = nullptr;
+  lbl_grid world{};
+  int32_t P = 0;
+  lbl_config cfg{};
+  bool has_cfg = false;
+  uint8_t *planes = nullptr;
+  uint64_t *O = nullptr, *L = nullptr, *next = nullptr;
+  uint16_t *viol = nullptr;
+};
+
+extern "C" {
+
+const char *lbl_last_error(void) { return g_err.c_str(); }
+
+int lbl_version(void) { return 10000; }
+
+int lbl_roadmap_upload(const lbl_grid *agent, const int64_t *rowptr, const int32_t *colidx, int64_t n_edges,
+                       int64_t nnz, uint32_t flags, lbl_stream s, lbl_roadmap *out) {
+  g_err.clear();
+  if (!out) {
+    set_error("roadmap upload: out is NULL");
+    return LBL_EINVAL;
+  }
+  *out = nullptr;
+  if (!valid_grid(agent, "roadmap upload", true)) return LBL_EINVAL;
+  if (n_edges < 0 || nnz < 0 || nnz > 2147483647LL * 4) {
+    set_error("roadmap upload: negative or oversized n_edges/nnz");
+    return LBL_EINVAL;
+  }
+  if (!rowptr || (nnz > 0 && !colidx)) {
+    set_error("roadmap upload: rowptr/colidx is NULL");
+    return LBL_EINVAL;
+  }
+  if (flags & ~(LBL_UPLOAD_DEVICE_PTRS | LBL_UPLOAD_BITTILE)) {
+    set_error("roadmap upload: unknown flags 0x%x", flags);
+    return LBL_EINVAL;
+  }
+  const bool dev_in = flags & LBL_UPLOAD_DEVICE_PTRS;
+  lbl_roadmap_s *rm = new (std::nothrow) lbl_roadmap_s();
+  if (!rm) {
+    set_error("roadmap upload: out of host memory");
+    return LBL_ENOMEM;
+  }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(s);
+  cudaError_t e = cudaGetDevice(&rm->device);
+  if (e != cudaSuccess) {
+    delete rm;
+    return cuda_fail(e, "roadmap upload: cudaGetDevice");
+  }
+  rm->num_sms = device_sms(rm->device);
+  rm->agent = *agent;
+  rm->E = n_edges;
+  rm->nnz = nnz;
+  rm->cells = static_cast<int64_t>(agent->w) * agent->h;
+  const int64_t padded = ((nnz + 3) / 4) * 4 + 4;  // whole 16-byte vectors, plus one
+  unsigned long long *d_bad = nullptr;
+  int32_t *d_cnt = nullptr;
+  int rc = LBL_OK;
+  auto fail = [&](int code) {
+    cudaStreamSynchronize(st);
+    cudaFree(d_bad);
+    cudaFree(d_cnt);
+    free_roadmap(rm);
+    return code;
+  };
+  if ((e = dev_alloc(&rm->rowptr, static_cast<size_t>(n_edges + 1), &rm->bytes)) != cudaSuccess)
+    return fail(cuda_fail(e, "roadmap upload: rowptr"));
+  if ((e = dev_alloc(&rm->colidx, static_cast<size_t>(padded), &rm->bytes)) != cudaSuccess)
+    return fail(cuda_fail(e, "roadmap upload: colidx"));
+  const cudaMemcpyKind kind = dev_in ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if ((e = cudaMemcpyAsync(rm->rowptr, rowptr, sizeof(int64_t) * (n_edges + 1), kind, st)) != cudaSuccess)
+    return fail(cuda_fail(e, "roadmap upload: copy rowptr"));
+  if (nnz > 0 && (e = cudaMemcpyAsync(rm->colidx, colidx, sizeof(int32_t) * nnz, kind, st)) != cudaSuccess)
+    return fail(cuda_fail(e, "roadmap upload: copy colidx"));
+  if ((e = cudaMemsetAsync(rm->colidx + nnz, 0, sizeof(int32_t) * (padded - nnz), st)) != cudaSuccess)
+    return fail(cuda_fail(e, "roadmap upload: pad colidx"));
+  // row pointer end points
+  int64_t ends[2] = {0, 0};
+  if ((e = cudaMemcpyAsync(&ends[0], rm->rowptr, sizeof(int64_t), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(&ends[1], rm->rowptr + n_edges, sizeof(int64_t), cudaMemcpyDeviceToHost, st)) !=
+          cudaSuccess ||
+      (e = cudaStreamSynchronize(st)) != cudaSuccess)
+    return fail(cuda_fail(e, "roadmap upload: read row pointer"));
+  if (ends[0] != 0 || ends[1] != nnz) {
+    set_error("roadmap upload: rowptr[0] = %lld and rowptr[E] = %lld, expected 0 and nnz = %lld",
+              static_cast<long long>(ends[0]), static_cast<long long>(ends[1]), static_cast<long long>(nnz));
+    return fail(LBL_EINVAL);
+  }
+  const bool want_bt = flags & LBL_UPLOAD_BITTILE;
+  if ((e = dev_alloc(&d_bad, 1, nullptr)) != cudaSuccess) return fail(cuda_fail(e, "roadmap upload: scratch"));
+  if (want_bt && (e = dev_alloc(&d_cnt, static_cast<size_t>(n_edges), nullptr)) != cudaSuccess)
+    return fail(cuda_fail(e, "roadmap upload: block counts"));
+  if ((e = cudaMemsetAsync(d_bad, 0, sizeof(unsigned long long), st)) != cudaSuccess ||
+      (e = launch_scan_rows(rm->rowptr, rm->colidx, n_edges, nnz, rm->cells, d_bad, d_cnt, st)) != cudaSuccess)
+    return fail(cuda_fail(e, "roadmap upload: row check"));
+  unsigned long long bad = 0;
+  if ((e = cudaMemcpyAsync(&bad, d_bad, sizeof(bad), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(st)) != cudaSuccess)
+    return fail(cuda_fail(e, "roadmap upload: row check"));
+  if (bad) {
+    set_error("roadmap upload: %llu malformed rows (row pointer decreasing or out of range, or column indices "
+              "not strictly increasing inside [0, %lld))",
+              bad, static_cast<long long>(rm->cells));
+    return fail(LBL_EINVAL);
+  }
+  if (want_bt) {
+    std::vector<int32_t> cnt(static_cast<size_t>(n_edges));
+    std::vector<int64_t> brow(static_cast<size_t>(n_edges + 1));
+    if (n_edges &&
+        ((e = cudaMemcpyAsync(cnt.data(), d_cnt, sizeof(int32_t) * n_edges, cudaMemcpyDeviceToHost, st)) !=
+             cudaSuccess ||
+         (e = cudaStreamSynchronize(st)) != cudaSuccess))
+      return fail(cuda_fail(e, "roadmap upload: block counts"));
+    brow[0] = 0;
+    for (int64_t i = 0; i < n_edges; ++i) brow[i + 1] = brow[i] + cnt[i];
+    rm->n_bt = brow[n_edges];
+    rm->n_blocks = (rm->cells + 63) / 64;
+    if ((e = dev_alloc(&rm->bt_rowptr, static_cast<size_t>(n_edges + 1), &rm->bytes)) != cudaSuccess ||
+        (e = dev_alloc(&rm->bt_block, static_cast<size_t>(rm->n_bt), &rm->bytes)) != cudaSuccess ||
+        (e = dev_alloc(&rm->bt_mask, static_cast<size_t>(rm->n_bt), &rm->bytes)) != cudaSuccess ||
+        (e = dev_alloc(&rm->planes, static_cast<size_t>(rm->n_blocks * 64), &rm->bytes)) != cudaSuccess)
+      return fail(cuda_fail(e, "roadmap upload: block form"));
+    if ((e = cudaMemcpyAsync(rm->bt_rowptr, brow.data(), sizeof(int64_t) * (n_edges + 1), cudaMemcpyHostToDevice,
+                             st)) != cudaSuccess ||
+        (e = launch_bt_fill(rm->rowptr, rm->colidx, n_edges, rm->bt_rowptr, rm->bt_block, rm->bt_mask, st)) !=
+            cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+      return fail(cuda_fail(e, "roadmap upload: block form"));
+    rm->has_bt = true;
+  }
+  cudaFree(d_bad);
+  cudaFree(d_cnt);
+  *out = rm;
+  return rc;
+}
+
+int lbl_roadmap_free(lbl_roadmap rm) {
+  g_err.clear();
+  if (!rm) return LBL_OK;
+  cudaDeviceSynchronize();
+  free_roadmap(rm);
+  return LBL_OK;
+}
+
+int lbl_roadmap_info(lbl_roadmap rm, int64_t *n_edges, int64_t *nnz, int64_t *n_block_entries,
+                     int64_t *device_bytes) {
+  g_err.clear();
+  if (!rm) {
+    set_error("roadmap info: NULL roadmap");
+    return LBL_EINVAL;
+  }
+  if (n_edges) *n_edges = rm->E;
+  if (nnz) *nnz = rm->nnz;
+  if (n_block_entries) *n_block_entries = rm->n_bt;
+  if (device_bytes) *device_bytes = rm->bytes;
+  return LBL_OK;
+}
+
+int lbl_frame_transform(const lbl_grid *world, const uint8_t *d_planes, int32_t n_props, lbl_pose pose,
+                        const lbl_grid *agent, uint64_t *d_O, lbl_stream s) {
+  g_err.clear();
+  if (!valid_grid(world, "frame transform (world)", false) || !valid_grid(agent, "frame transform (agent)", true))
+    return LBL_EINVAL;
+  if (n_props < 0 || n_props > 64) {
+    set_error("frame transform: n_props = %d outside 0..64", n_props);
+    return LBL_EINVAL;
+  }
+  if (!d_O || (n_props > 0 && !d_planes)) {
+    set_error("frame transform: NULL buffer");
+    return LBL_EINVAL;
+  }
+  FrameMap m;
+  if (!frame_map(*world, *agent, pose, &m)) return LBL_EINVAL;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "frame transform: cudaGetDevice");
+  e = launch_frame_transform(m, d_planes, world->w, world->h, n_props, agent->w, agent->h, agent->order, d_O,
+                             device_sms(dev), reinterpret_cast<cudaStream_t>(s));
+  if (e != cudaSuccess) return cuda_fail(e, "frame transform: launch");
+  return LBL_OK;
+}
+
+int lbl_monitor_create(int32_t n_states, int32_t m, const uint8_t *relbits, const uint8_t *delta, int32_t reject,
+                       lbl_monitor *out) {
+  g_err.clear();
+  if (!out) {
+    set_error("monitor create: out is NULL");
+    return LBL_EINVAL;
+  }
+  *out = nullptr;
+  if (n_states < 1 || n_states > 16 || m < 0 || m > 8 || reject < -1 || reject >= n_states) {
+    set_error("monitor create: need 1 <= n_states <= 16, 0 <= m <= 8, -1 <= reject < n_states");
+    return LBL_EINVAL;
+  }
+  if (!delta || (m > 0 && !relbits)) {
+    set_error("monitor create: NULL table");
+    return LBL_EINVAL;
+  }
+  for (int j = 0; j < m; ++j)
+    if (relbits[j] >= 64) {
+      set_error("monitor create: relbits[%d] = %d >= 64", j, relbits[j]);
+      return LBL_EINVAL;
+    }
+  const int letters = 1 << m;
+  for (int i = 0; i < n_states * letters; ++i)
+    if (delta[i] >= n_states) {
+      set_error("monitor create: delta[%d] = %d is not a state", i, delta[i]);
+      return LBL_EINVAL;
+    }
+  lbl_monitor_s *mon = new (std::nothrow) lbl_monitor_s();
+  if (!mon) {
+    set_error("monitor create: out of host memory");
+    return LBL_ENOMEM;
+  }
+  mon->n_states = n_states;
+  mon->m = m;
+  mon->reject = reject;
+  for (int j = 0; j < m; ++j) mon->rel[j] = relbits[j];
+  // Per letter: the next state of every monitor state packed in 4-bit fields,
+  // and which of those next states is the reject state.
+  for (int letter = 0; letter < letters; ++letter) {
+    uint64_t t = 0;
+    uint16_t v = 0;
+    for (int q = 0; q < n_states; ++q) {
+      const uint32_t nq = delta[q * letters + letter];
+      t |= static_cast<uint64_t>(nq) << (4 * q);
+      if (static_cast<int32_t>(nq) == reject) v |= static_cast<uint16_t>(1u << q);
+    }
+    mon->hT[letter] = t;
+    mon->hV[letter] = v;
+  }
+  cudaError_t e = cudaGetDevice(&mon->device);
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&mon->T), sizeof(mon->hT));
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&mon->V), sizeof(mon->hV));
+  if (e == cudaSuccess) e = cudaMemcpy(mon->T, mon->hT, sizeof(mon->hT), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(mon->V, mon->hV, sizeof(mon->hV), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(mon->T);
+    cudaFree(mon->V);
+    delete mon;
+    return cuda_fail(e, "monitor create");
+  }
+  *out = mon;
+  return LBL_OK;
+}
+
+int lbl_monitor_free(lbl_monitor mon) {
+  g_err.clear();
+  if (!mon) return LBL_OK;
+  cudaDeviceSynchronize();
+  cudaFree(mon->T);
+  cudaFree(mon->V);
+  delete mon;
+  return LBL_OK;
+}
+
+static MonitorTables tables_of(const Monitor &mon, uint64_t *next, uint16_t *viol) {
+  MonitorTables t{};
+  t.T = mon.T;
+  t.V = mon.V;
+  t.next = next;
+  t.viol = viol;
+  t.m = mon.m;
+  for (int j = 0; j < 8; ++j) t.rel[j] = mon.rel[j];
+  return t;
+}
+
+int lbl_monitor_step(lbl_monitor mon, const uint64_t *d_L, int64_t n, uint64_t *d_next, uint16_t *d_viol,
+                     lbl_stream s) {
+  g_err.clear();
+  if (!mon || n < 0 || (n > 0 && (!d_L || !d_next || !d_viol))) {
+    set_error("monitor step: NULL monitor/buffer or negative n");
+    return LBL_EINVAL;
+  }
+  if (!same_device(mon->device)) return LBL_EINVAL;
+  MonitorTables t = tables_of(*mon, d_next, d_viol);
+  cudaError_t e = launch_monitor_step(t, d_L, n, device_sms(mon->device), reinterpret_cast<cudaStream_t>(s));
+  if (e != cudaSuccess) return cuda_fail(e, "monitor step: launch");
+  return LBL_OK;
+}
+
+static int label_impl(lbl_roadmap rm, const uint64_t *d_O, int32_t n_props, uint64_t *d_L, lbl_monitor mon,
+                      uint64_t *d_next, uint16_t *d_viol, const lbl_config *cfg, cudaStream_t st) {
+  if (!rm) {
+    set_error("label: NULL roadmap");
+    return LBL_EINVAL;
+  }
+  if (n_props < 0 || n_props > 64) {
+    set_error("label: n_props = %d outside 0..64", n_props);
+    return LBL_EINVAL;
+  }
+  if (rm->E > 0 && (!d_O || !d_L)) {
+    set_error("label: NULL O or L");
+    return LBL_EINVAL;
+  }
+  if (mon && rm->E > 0 && (!d_next || !d_viol)) {
+    set_error("label: monitor given but next/viol is NULL");
+    return LBL_EINVAL;
+  }
+  if (!same_device(rm->device)) return LBL_EINVAL;
+  if (mon && mon->device != rm->device) {
+    set_error("label: monitor and roadmap live on different devices");
+    return LBL_EINVAL;
+  }
+  int algo = cfg ? cfg->algo : LBL_ALGO_AUTO;
+  if (algo < LBL_ALGO_AUTO || algo > LBL_ALGO_BITTILE) {
+    set_error("label: unknown algo %d", algo);
+    return LBL_EINVAL;
+  }
+  if (algo == LBL_ALGO_BITTILE && !rm->has_bt) {
+    set_error("label: LBL_ALGO_BITTILE needs a roadmap uploaded with LBL_UPLOAD_BITTILE");
+    return LBL_EUNSUPPORTED;
+  }
+  if (algo == LBL_ALGO_AUTO) algo = (rm->has_bt && n_props <= 16) ? LBL_ALGO_BITTILE : LBL_ALGO_CSR;
+  int ee = cfg ? cfg->early_exit : -1;
+  const bool early = ee < 0 ? (n_props <= 4) : (ee != 0);
+  const int ctas = cfg ? cfg->ctas_per_sm : 0;
+  MonitorTables t{};
+  if (mon) t = tables_of(*mon, d_next, d_viol);
+  cudaError_t e;
+  if (algo == LBL_ALGO_BITTILE)
+    e = launch_label_bittile(*rm, d_O, n_props, d_L, mon ? &t : nullptr, early, ctas, st);
+  else
+    e = launch_label_csr(*rm, d_O, n_props, d_L, mon ? &t : nullptr, resolve_lpe(*rm, cfg), early, ctas, st);
+  if (e != cudaSuccess) return cuda_fail(e, "label: launch");
+  return LBL_OK;
+}
+
+int lbl_label(lbl_roadmap rm, const uint64_t *d_O, int32_t n_props, uint64_t *d_L, lbl_monitor mon, uint64_t *d_next,
+              uint16_t *d_viol, const lbl_config *cfg, lbl_stream s) {
+  g_err.clear();
+  return label_impl(rm, d_O, n_props, d_L, mon, d_next, d_viol, cfg, reinterpret_cast<cudaStream_t>(s));
+}
+
+int lbl_session_create(lbl_roadmap rm, const lbl_grid *world, int32_t n_props, lbl_monitor mon,
+                       const lbl_config *cfg, lbl_session *out) {
+  g_err.clear();
+  if (!out) {
+    set_error("session create: out is NULL");
+    return LBL_EINVAL;
+  }
+  *out = nullptr;
+  if (!rm) {
+    set_error("session create: NULL roadmap");
+    return LBL_EINVAL;
+  }
+  if (!valid_grid(world, "session create (world)", false)) return LBL_EINVAL;
+  if (n_props < 0 || n_props > 64) {
+    set_error("session create: n_props = %d outside 0..64", n_props);
+    return LBL_EINVAL;
+  }
+  if (!same_device(rm->device)) return LBL_EINVAL;
+  lbl_session_s *ss = new (std::nothrow) lbl_session_s();
+  if (!ss) {
+    set_error("session create: out of host memory");
+    return LBL_ENOMEM;
+  }
+  ss->device = rm->device;
+  ss->rm = rm;
+  ss->mon = mon;
+  ss->world = *world;
+  ss->P = n_props;
+  if (cfg) {
+    ss->cfg = *cfg;
+    ss->has_cfg = true;
+  }
+  const size_t plane_bytes = static_cast<size_t>(n_props) * world->w * world->h;
+  cudaError_t e = dev_alloc(&ss->planes, plane_bytes, nullptr);
+  if (e == cudaSuccess) e = dev_alloc(&ss->O, static_cast<size_t>(rm->cells), nullptr);
+  if (e == cudaSuccess) e = dev_alloc(&ss->L, static_cast<size_t>(rm->E), nullptr);
+  if (e == cudaSuccess && mon) e = dev_alloc(&ss->next, static_cast<size_t>(rm->E), nullptr);
+  if (e == cudaSuccess && mon) e = dev_alloc(&ss->viol, static_cast<size_t>(rm->E), nullptr);
+  if (e != cudaSuccess) {
+    cudaFree(ss->planes);
+    cudaFree(ss->O);
+    cudaFree(ss->L);
+    cudaFree(ss->next);
+    cudaFree(ss->viol);
+    delete ss;
+    return cuda_fail(e, "session create");
+  }
+  *out = ss;
+  return LBL_OK;
+}
+
+int lbl_session_run(lbl_session ss, const uint8_t *h_planes, lbl_pose pose, uint64_t *h_L, uint64_t *h_next,
+                    uint16_t *h_viol, lbl_stream s) {
+  g_err.clear();
+  if (!ss) {
+    set_error("session run: NULL session");
+    return LBL_EINVAL;
+  }
+  const Roadmap &rm = *ss->rm;
+  if ((ss->P > 0 && !h_planes) || (rm.E > 0 && !h_L)) {
+    set_error("session run: NULL host buffer");
+    return LBL_EINVAL;
+  }
+  if (!same_device(ss->device)) return LBL_EINVAL;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(s);
+  const size_t plane_bytes = static_cast<size_t>(ss->P) * ss->world.w * ss->world.h;
+  cudaError_t e = cudaSuccess;
+  if (plane_bytes) e = cudaMemcpyAsync(ss->planes, h_planes, plane_bytes, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "session run: copy planes");
+  int rc = lbl_frame_transform(&ss->world, ss->planes, ss->P, pose, &rm.agent, ss->O, s);
+  if (rc != LBL_OK) return rc;
+  rc = label_impl(ss->rm, ss->O, ss->P, ss->L, ss->mon, ss->next, ss->viol, ss->has_cfg ? &ss->cfg : nullptr, st);
+  if (rc != LBL_OK) return rc;
+  if (rm.E > 0) {
+    e = cudaMemcpyAsync(h_L, ss->L, sizeof(uint64_t) * rm.E, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && ss->mon && h_next)
+      e = cudaMemcpyAsync(h_next, ss->next, sizeof(uint64_t) * rm.E, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && ss->mon && h_viol)
+      e = cudaMemcpyAsync(h_viol, ss->viol, sizeof(uint16_t) * rm.E, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_fail(e, "session run: copy results");
+  }
+  return LBL_OK;
+}
+
+int lbl_session_free(lbl_session ss) {
+  g_err.clear();
+  if (!ss) return LBL_OK;
+  cudaDeviceSynchronize();
+  cudaFree(ss->planes);
+  cudaFree(ss->O);
+  cudaFree(ss->L);
+  cudaFree(ss->next);
+  cudaFree(ss->viol);
+  delete ss;
+  return LBL_OK;
+}
+
+}  // extern "C"

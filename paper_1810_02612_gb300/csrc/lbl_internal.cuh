@@ -1,0 +1,90 @@
+// Internal declarations of liblbl (not part of the C ABI).
+//
+// Device layouts (all in HBM, all library-owned unless noted):
+//   rowptr  int64[E+1]            CSR row pointer of M (eq. 11)
+//   colidx  int32[nnz + pad]      CSR column indices, padded to a multiple of 4
+//                                 plus 4 so 16-byte vector loads never leave the
+//                                 allocation
+//   O       uint64[cells]         caller-owned proposition word per agent cell
+//   bt_*                          64-cell block form of M: per edge a list of
+//                                 (block id, 64-bit cell mask) entries, block b =
+//                                 cells [64b, 64b+64) in the grid's cell order
+//   planes  uint64[blocks][P]     bit-plane re-layout of O for the block form:
+//                                 bit i of planes[b][p] = bit p of O[64b + i]
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/lbl.h"
+
+namespace lbl {
+
+constexpr int kThreads = 256;  // threads per CTA of every labeling kernel
+
+struct MonitorTables {
+  const uint64_t *T;  // T[letter]: packed next states of all monitor states
+  const uint16_t *V;  // V[letter]: violation mask
+  uint64_t *next;
+  uint16_t *viol;
+  int32_t m;
+  uint8_t rel[8];
+};
+
+struct Roadmap {
+  int device = 0;
+  int num_sms = 0;
+  lbl_grid agent{};
+  int64_t E = 0, nnz = 0, cells = 0;
+  int64_t *rowptr = nullptr;
+  int32_t *colidx = nullptr;
+  // block form (optional)
+  bool has_bt = false;
+  int64_t n_bt = 0;        // entries
+  int64_t n_blocks = 0;    // ceil(cells / 64)
+  int64_t *bt_rowptr = nullptr;
+  uint32_t *bt_block = nullptr;
+  uint64_t *bt_mask = nullptr;
+  uint64_t *planes = nullptr;  // n_blocks * 64 words of working memory
+  int64_t bytes = 0;
+};
+
+struct Monitor {
+  int device = 0;
+  int32_t n_states = 0, m = 0, reject = -1;
+  uint8_t rel[8] = {0};
+  uint64_t hT[256] = {0};
+  uint16_t hV[256] = {0};
+  uint64_t *T = nullptr;
+  uint16_t *V = nullptr;
+};
+
+// ---------------------------------------------------------------- errors
+void set_error(const char *fmt, ...);
+int cuda_fail(cudaError_t e, const char *what);
+
+// --------------------------------------------------------------- kernels
+struct FrameMap {
+  int64_t A00, A01, B0, A10, A11, B1;  // Q32.32
+};
+
+cudaError_t launch_frame_transform(const FrameMap &m, const uint8_t *planes, int32_t ww, int32_t wh, int32_t P,
+                                   int32_t aw, int32_t ah, int32_t order, uint64_t *O, int num_sms, cudaStream_t s);
+
+cudaError_t launch_label_csr(const Roadmap &rm, const uint64_t *O, int32_t P, uint64_t *L, const MonitorTables *mon,
+                             int lanes_per_edge, bool early_exit, int ctas_per_sm, cudaStream_t s);
+
+cudaError_t launch_label_bittile(const Roadmap &rm, const uint64_t *O, int32_t P, uint64_t *L,
+                                 const MonitorTables *mon, bool early_exit, int ctas_per_sm, cudaStream_t s);
+
+cudaError_t launch_monitor_step(const MonitorTables &mon, const uint64_t *L, int64_t n, int num_sms, cudaStream_t s);
+
+// roadmap preparation: row checks, block counts, block fill
+cudaError_t launch_scan_rows(const int64_t *rowptr, const int32_t *colidx, int64_t E, int64_t nnz, int64_t cells,
+                             unsigned long long *n_bad, int32_t *bt_count, cudaStream_t s);
+cudaError_t launch_bt_fill(const int64_t *rowptr, const int32_t *colidx, int64_t E, const int64_t *bt_rowptr,
+                           uint32_t *bt_block, uint64_t *bt_mask, cudaStream_t s);
+
+}  // namespace lbl

@@ -1,0 +1,267 @@
+"""Python binding of liblbl (include/lbl.h): argument marshalling only.
+
+Every function carries the C name and forwards to the shared library; all
+computation happens in the CUDA kernels behind it.  Device buffers are torch
+CUDA tensors (or raw integer device pointers), host buffers numpy arrays or CPU
+tensors.  A non-zero status raises :class:`LblError` with the library's
+message.  There is no CPU fallback: if ``liblbl.so`` cannot be built or loaded
+the import of the first call fails.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LBL_OK = 0
+LBL_EINVAL = -1
+LBL_ENOMEM = -2
+LBL_ECUDA = -3
+LBL_ETIMEOUT = -4
+LBL_EUNSUPPORTED = -5
+
+LBL_ORDER_ROWMAJOR = 0
+LBL_ORDER_MORTON = 1
+
+LBL_ALGO_AUTO = 0
+LBL_ALGO_CSR = 1
+LBL_ALGO_BITTILE = 2
+
+LBL_UPLOAD_DEVICE_PTRS = 1
+LBL_UPLOAD_BITTILE = 2
+
+# every entry point declared in include/lbl.h
+EXPORTS = (
+    "lbl_last_error", "lbl_version",
+    "lbl_roadmap_upload", "lbl_roadmap_free", "lbl_roadmap_info",
+    "lbl_frame_transform",
+    "lbl_monitor_create", "lbl_monitor_free", "lbl_monitor_step",
+    "lbl_label",
+    "lbl_session_create", "lbl_session_run", "lbl_session_free",
+)
+
+
+class LblError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class lbl_grid(ctypes.Structure):
+    _fields_ = [("w", ctypes.c_int32), ("h", ctypes.c_int32), ("res", ctypes.c_double),
+                ("x0", ctypes.c_double), ("y0", ctypes.c_double), ("order", ctypes.c_int32)]
+
+
+class lbl_pose(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_double), ("y", ctypes.c_double), ("theta", ctypes.c_double)]
+
+
+class lbl_config(ctypes.Structure):
+    _fields_ = [("algo", ctypes.c_int32), ("lanes_per_edge", ctypes.c_int32),
+                ("early_exit", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_needed: bool = True):
+    """Load liblbl.so (building it first when sources are newer)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_needed:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise ImportError(f"liblbl.so is not built ({_build.LIB}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(_build.LIB)
+    p, i32, i64, u32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
+    G = ctypes.POINTER(lbl_grid)
+    sig = {
+        "lbl_last_error": (ctypes.c_char_p, []),
+        "lbl_version": (ctypes.c_int, []),
+        "lbl_roadmap_upload": (ctypes.c_int, [G, p, p, i64, i64, u32, p, ctypes.POINTER(p)]),
+        "lbl_roadmap_free": (ctypes.c_int, [p]),
+        "lbl_roadmap_info": (ctypes.c_int, [p, p, p, p, p]),
+        "lbl_frame_transform": (ctypes.c_int, [G, p, i32, lbl_pose, G, p, p]),
+        "lbl_monitor_create": (ctypes.c_int, [i32, i32, p, p, i32, ctypes.POINTER(p)]),
+        "lbl_monitor_free": (ctypes.c_int, [p]),
+        "lbl_monitor_step": (ctypes.c_int, [p, p, i64, p, p, p]),
+        "lbl_label": (ctypes.c_int, [p, p, i32, p, p, p, p, ctypes.POINTER(lbl_config), p]),
+        "lbl_session_create": (ctypes.c_int, [p, G, i32, p, ctypes.POINTER(lbl_config), ctypes.POINTER(p)]),
+        "lbl_session_run": (ctypes.c_int, [p, p, lbl_pose, p, p, p, p]),
+        "lbl_session_free": (ctypes.c_int, [p]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+# ------------------------------------------------------------- marshalling
+
+def _grid(g) -> lbl_grid:
+    if isinstance(g, lbl_grid):
+        return g
+    return lbl_grid(int(g.w), int(g.h), float(g.res), float(g.x0), float(g.y0), int(getattr(g, "order", 0)))
+
+
+def _pose(p) -> lbl_pose:
+    if isinstance(p, lbl_pose):
+        return p
+    return lbl_pose(float(p[0]), float(p[1]), float(p[2]))
+
+
+def _cfg(cfg):
+    if cfg is None:
+        return None
+    if isinstance(cfg, lbl_config):
+        return ctypes.byref(cfg)
+    c = lbl_config(int(cfg.get("algo", 0)), int(cfg.get("lanes_per_edge", 0)), int(cfg.get("early_exit", -1)),
+                   int(cfg.get("ctas_per_sm", 0)))
+    return ctypes.byref(c)
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _dev(x, dtype_name: str, what: str):
+    """Device pointer of a CUDA tensor (contiguous, given dtype) or an int."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if not _is_torch(x) or not x.is_cuda:
+        raise TypeError(f"{what}: expected a CUDA tensor")
+    if str(x.dtype) != "torch." + dtype_name:
+        raise TypeError(f"{what}: expected torch.{dtype_name}, got {x.dtype}")
+    if not x.is_contiguous():
+        raise ValueError(f"{what}: tensor must be contiguous")
+    return x.data_ptr()
+
+
+def _host(x, np_dtype, what: str):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if _is_torch(x):
+        if x.is_cuda:
+            raise TypeError(f"{what}: expected host memory")
+        if not x.is_contiguous():
+            raise ValueError(f"{what}: tensor must be contiguous")
+        return x.data_ptr()
+    a = x
+    if not isinstance(a, np.ndarray) or a.dtype != np_dtype or not a.flags["C_CONTIGUOUS"]:
+        raise TypeError(f"{what}: expected a contiguous numpy {np.dtype(np_dtype).name} array")
+    return a.ctypes.data
+
+
+def _stream(s):
+    if s is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _check(rc: int):
+    if rc != LBL_OK:
+        msg = load().lbl_last_error()
+        raise LblError(rc, msg.decode() if msg else "")
+
+
+# ---------------------------------------------------------------- entry points
+
+def lbl_version() -> int:
+    return load().lbl_version()
+
+
+def lbl_last_error() -> str:
+    return load().lbl_last_error().decode()
+
+
+def lbl_roadmap_upload(agent, rowptr, colidx, flags: int = 0, stream=None) -> int:
+    """Make a roadmap resident on the device; returns the handle.
+    rowptr int64[E+1] / colidx int32[nnz]: numpy/CPU tensors, or CUDA tensors
+    (then LBL_UPLOAD_DEVICE_PTRS is set)."""
+    lib = load()
+    E = int(rowptr.shape[0]) - 1
+    nnz = int(colidx.shape[0])
+    if _is_torch(rowptr) and rowptr.is_cuda:
+        flags |= LBL_UPLOAD_DEVICE_PTRS
+        rp, ci = _dev(rowptr, "int64", "rowptr"), _dev(colidx, "int32", "colidx")
+    else:
+        rp, ci = _host(rowptr, np.int64, "rowptr"), _host(colidx, np.int32, "colidx")
+    out = ctypes.c_void_p()
+    g = _grid(agent)
+    _check(lib.lbl_roadmap_upload(ctypes.byref(g), rp, ci, E, nnz, flags, _stream(stream), ctypes.byref(out)))
+    return out.value
+
+
+def lbl_roadmap_free(rm) -> None:
+    _check(load().lbl_roadmap_free(rm))
+
+
+def lbl_roadmap_info(rm):
+    """(n_edges, nnz, n_block_entries, device_bytes) of a roadmap."""
+    e, n, k, b = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(load().lbl_roadmap_info(rm, ctypes.byref(e), ctypes.byref(n), ctypes.byref(k), ctypes.byref(b)))
+    return e.value, n.value, k.value, b.value
+
+
+def lbl_frame_transform(world, d_planes, n_props: int, pose, agent, d_O, stream=None) -> None:
+    w, a = _grid(world), _grid(agent)
+    _check(load().lbl_frame_transform(ctypes.byref(w), _dev(d_planes, "uint8", "planes"), int(n_props),
+                                      _pose(pose), ctypes.byref(a), _dev(d_O, "uint64", "O"), _stream(stream)))
+
+
+def lbl_monitor_create(n_states: int, m: int, relbits, delta, reject: int) -> int:
+    rel = np.ascontiguousarray(relbits, np.uint8)
+    dl = np.ascontiguousarray(delta, np.uint8).ravel()
+    out = ctypes.c_void_p()
+    _check(load().lbl_monitor_create(int(n_states), int(m), rel.ctypes.data if rel.size else None,
+                                     dl.ctypes.data, int(reject), ctypes.byref(out)))
+    return out.value
+
+
+def lbl_monitor_free(mon) -> None:
+    _check(load().lbl_monitor_free(mon))
+
+
+def lbl_monitor_step(mon, d_L, n: int, d_next, d_viol, stream=None) -> None:
+    _check(load().lbl_monitor_step(mon, _dev(d_L, "uint64", "L"), int(n), _dev(d_next, "uint64", "next"),
+                                   _dev(d_viol, "uint16", "viol"), _stream(stream)))
+
+
+def lbl_label(rm, d_O, n_props: int, d_L, mon=None, d_next=None, d_viol=None, cfg=None, stream=None) -> None:
+    _check(load().lbl_label(rm, _dev(d_O, "uint64", "O"), int(n_props), _dev(d_L, "uint64", "L"), mon,
+                            _dev(d_next, "uint64", "next"), _dev(d_viol, "uint16", "viol"), _cfg(cfg),
+                            _stream(stream)))
+
+
+def lbl_session_create(rm, world, n_props: int, mon=None, cfg=None) -> int:
+    out = ctypes.c_void_p()
+    w = _grid(world)
+    _check(load().lbl_session_create(rm, ctypes.byref(w), int(n_props), mon, _cfg(cfg), ctypes.byref(out)))
+    return out.value
+
+
+def lbl_session_run(ss, h_planes, pose, h_L, h_next=None, h_viol=None, stream=None) -> None:
+    _check(load().lbl_session_run(ss, _host(h_planes, np.uint8, "planes"), _pose(pose),
+                                  _host(h_L, np.uint64, "L"), _host(h_next, np.uint64, "next"),
+                                  _host(h_viol, np.uint16, "viol"), _stream(stream)))
+
+
+def lbl_session_free(ss) -> None:
+    _check(load().lbl_session_free(ss))

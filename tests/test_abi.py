@@ -1,0 +1,96 @@
+"""The C-ABI library loads and exports every entry point that include/lbl.h
+declares; argument checks that run before any device work reject bad input.
+No kernel is launched here (CPU only)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from conftest import ROOT
+
+import paper_1810_02612_gb300 as L
+from paper_1810_02612_gb300 import lbl as B
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "lbl.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbl_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("lbl_roadmap_upload", "lbl_frame_transform", "lbl_label", "lbl_monitor_step"):
+        assert required in names
+    assert sorted(B.EXPORTS) == names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = ctypes.CDLL(B.library_path() if os.path.exists(B.library_path()) else B._build.build())
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_python_binding_has_the_same_names():
+    for name in declared_functions():
+        assert callable(getattr(L, name)), name
+
+
+def test_struct_layouts_match_the_header():
+    assert ctypes.sizeof(B.lbl_grid) == 40
+    assert B.lbl_grid.res.offset == 8 and B.lbl_grid.order.offset == 32
+    assert ctypes.sizeof(B.lbl_pose) == 24
+    assert ctypes.sizeof(B.lbl_config) == 16
+
+
+def test_version_and_empty_error():
+    assert L.lbl_version() == 10000
+    assert L.lbl_last_error() == ""
+
+
+@pytest.mark.parametrize("args", [
+    (0, 1, [0], [[0, 0]], -1),        # no states
+    (17, 0, [], [[0]] * 17, -1),       # too many states
+    (2, 9, list(range(9)), np.zeros((2, 512)), -1),  # too many letter bits
+    (2, 1, [64], [[0, 0], [0, 0]], -1),  # label bit out of range
+    (2, 1, [3], [[0, 2], [0, 0]], -1),   # delta names a missing state
+    (2, 1, [3], [[0, 1], [0, 0]], 2),    # reject is not a state
+])
+def test_monitor_create_rejects_bad_tables(args):
+    n, m, rel, delta, rej = args
+    with pytest.raises(L.LblError) as ei:
+        L.lbl_monitor_create(n, m, rel, delta, rej)
+    assert ei.value.code == L.LBL_EINVAL
+    assert L.lbl_last_error() != ""
+
+
+@pytest.mark.parametrize("grid", [
+    dict(w=0, h=4, res=1.0, x0=0.0, y0=0.0, order=0),
+    dict(w=4, h=4, res=0.0, x0=0.0, y0=0.0, order=0),
+    dict(w=6, h=6, res=1.0, x0=0.0, y0=0.0, order=1),   # z-order needs a power of two
+    dict(w=8, h=4, res=1.0, x0=0.0, y0=0.0, order=1),   # and a square
+    dict(w=8, h=8, res=1.0, x0=0.0, y0=0.0, order=7),
+])
+def test_roadmap_upload_rejects_bad_grids_before_device_work(grid):
+    g = B.lbl_grid(**grid)
+    with pytest.raises(L.LblError) as ei:
+        L.lbl_roadmap_upload(g, np.zeros(1, np.int64), np.zeros(0, np.int32), stream=0)
+    assert ei.value.code == L.LBL_EINVAL
+
+
+def test_null_handles_are_rejected_or_ignored():
+    L.lbl_roadmap_free(None)
+    L.lbl_monitor_free(None)
+    L.lbl_session_free(None)
+    with pytest.raises(L.LblError):
+        L.lbl_roadmap_info(None)
+    with pytest.raises(L.LblError):
+        L.lbl_label(None, 0, 1, 0, stream=0)
+
+
+def test_binding_refuses_host_arrays_for_device_arguments():
+    g = B.lbl_grid(8, 8, 1.0, 0.0, 0.0, 0)
+    with pytest.raises(TypeError):
+        L.lbl_frame_transform(g, np.zeros((1, 8, 8), np.uint8), 1, (0, 0, 0), g, np.zeros(64, np.uint64), stream=0)

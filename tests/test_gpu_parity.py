@@ -1,0 +1,313 @@
+"""GPU parity: every CUDA result equals the oracle bit for bit (integer and
+bitwise work, so the tolerance is zero).  Inputs are seeded synthetic
+workloads; every call goes through the C ABI."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1810_02612_gb300 as L  # noqa: E402
+from paper_1810_02612_gb300.lbl import lbl_grid  # noqa: E402
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def empty_u64(n):
+    return torch.empty(max(n, 1), dtype=torch.uint64, device="cuda")[:n]
+
+
+def empty_u16(n):
+    return torch.empty(max(n, 1), dtype=torch.uint16, device="cuda")[:n]
+
+
+class Roadmap:
+    def __init__(self, agent, rowptr, colidx, bittile=False):
+        self.E = rowptr.shape[0] - 1
+        self.h = L.lbl_roadmap_upload(agent, rowptr, colidx, flags=L.LBL_UPLOAD_BITTILE if bittile else 0)
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            L.lbl_roadmap_free(self.h)
+
+
+def gpu_O(wl, pose=None, planes=None):
+    planes = wl.planes if planes is None else planes
+    O = empty_u64(wl.agent.cells)
+    L.lbl_frame_transform(wl.world, cuda(planes), planes.shape[0], wl.pose if pose is None else pose, wl.agent, O)
+    return O
+
+
+def gpu_label(rm, O, P, cfg=None, mon=None):
+    out = empty_u64(rm.E)
+    nxt = empty_u64(rm.E) if mon else None
+    viol = empty_u16(rm.E) if mon else None
+    L.lbl_label(rm.h, O, P, out, mon, nxt, viol, cfg)
+    if mon:
+        return host(out), host(nxt), host(viol)
+    return host(out)
+
+
+CFGS = [
+    dict(algo=L.LBL_ALGO_CSR, lanes_per_edge=4, early_exit=0),
+    dict(algo=L.LBL_ALGO_CSR, lanes_per_edge=8, early_exit=0),
+    dict(algo=L.LBL_ALGO_CSR, lanes_per_edge=16, early_exit=1),
+    dict(algo=L.LBL_ALGO_CSR, lanes_per_edge=32, early_exit=0),
+    dict(algo=L.LBL_ALGO_CSR, lanes_per_edge=32, early_exit=1),
+    dict(algo=L.LBL_ALGO_BITTILE, early_exit=0),
+    dict(algo=L.LBL_ALGO_BITTILE, early_exit=1),
+    dict(algo=L.LBL_ALGO_AUTO),
+]
+
+
+@pytest.fixture(scope="module")
+def plain():
+    return synth.make("plain", seed=3)
+
+
+@pytest.fixture(scope="module")
+def driving_small():
+    return synth.make("driving", seed=4, edges=20_000)
+
+
+@pytest.fixture(scope="module")
+def large_small():
+    return synth.make("large", seed=5, edges=30_000)
+
+
+@pytest.fixture(scope="module")
+def paper_small():
+    return synth.make("paper", seed=6, edges=40_000)
+
+
+# ------------------------------------------------------------ frame transform
+
+@pytest.mark.parametrize("name", ["plain", "driving_small", "large_small", "paper_small"])
+def test_frame_transform_matches_oracle(name, request):
+    wl = request.getfixturevalue(name)
+    rng = np.random.default_rng(1)
+    poses = [wl.pose, synth.random_pose(rng, wl.world), (wl.pose[0], wl.pose[1], math.pi / 2),
+             (wl.pose[0] + 3.3, wl.pose[1] - 7.1, -2.5), (-50.0, 10.0, 0.7)]  # last: mostly off the world
+    for pose in poses:
+        got = host(gpu_O(wl, pose=pose))
+        want = oracle.frame_transform(wl.world, wl.planes, pose, wl.agent)
+        assert np.array_equal(got, want), pose
+
+
+@pytest.mark.parametrize("P", [0, 1, 7, 8, 9, 63, 64])
+def test_frame_transform_prop_counts_and_odd_grids(P):
+    rng = np.random.default_rng(P)
+    world = synth.world_grid(53, 41, 0.37)
+    planes = (rng.random((P, 41, 53)) < 0.3).astype(np.uint8) * rng.integers(1, 255, size=(P, 41, 53)).astype(np.uint8)
+    for agent in (synth.agent_grid(32, 0.25, synth.MORTON), synth.Grid(37, 29, 0.3, -5.0, -4.0, synth.ROWMAJOR)):
+        pose = (9.0 + rng.random(), 7.5 + rng.random(), rng.random() * 6.3)
+        O = empty_u64(agent.cells)
+        L.lbl_frame_transform(world, cuda(planes) if P else torch.empty(1, dtype=torch.uint8, device="cuda"), P,
+                              pose, agent, O)
+        assert np.array_equal(host(O), oracle.frame_transform(world, planes, pose, agent))
+
+
+def test_frame_transform_rejects_out_of_range_pose():
+    world = synth.world_grid(8, 8, 1.0)
+    agent = synth.agent_grid(8, 1.0, synth.MORTON)
+    O = empty_u64(64)
+    with pytest.raises(L.LblError) as ei:
+        L.lbl_frame_transform(world, cuda(np.zeros((1, 8, 8), np.uint8)), 1, (1e12, 0.0, 0.0), agent, O)
+    assert ei.value.code == L.LBL_EINVAL
+    with pytest.raises(L.LblError):
+        L.lbl_frame_transform(world, cuda(np.zeros((1, 8, 8), np.uint8)), 65, (0.0, 0.0, 0.0), agent, O)
+
+
+# ---------------------------------------------------------------- labeling
+
+@pytest.mark.parametrize("name", ["plain", "driving_small", "large_small", "paper_small"])
+def test_label_all_algorithms_match_oracle(name, request):
+    wl = request.getfixturevalue(name)
+    rm = Roadmap(wl.agent, wl.rowptr, wl.colidx, bittile=True)
+    O = gpu_O(wl)
+    O_h = host(O)
+    want = oracle.label(wl.rowptr, wl.colidx, O_h, wl.P, threads=8)
+    for cfg in CFGS:
+        assert np.array_equal(gpu_label(rm, O, wl.P, cfg), want), cfg
+    assert np.array_equal(gpu_label(rm, O, wl.P, None), want)
+
+
+def test_label_with_fused_monitor_matches_oracle(large_small):
+    wl = large_small
+    rm = Roadmap(wl.agent, wl.rowptr, wl.colidx, bittile=True)
+    mon = wl.monitor
+    h = L.lbl_monitor_create(mon.n_states, mon.m, mon.relbits, mon.delta, mon.reject)
+    try:
+        O = gpu_O(wl)
+        want_L = oracle.label(wl.rowptr, wl.colidx, host(O), wl.P, threads=8)
+        want_n, want_v = oracle.monitor(mon.n_states, mon.m, mon.relbits, mon.delta, mon.reject, want_L)
+        assert (want_v != 0).any() and (want_v == 0).any()
+        for cfg in CFGS:
+            got_L, got_n, got_v = gpu_label(rm, O, wl.P, cfg, mon=h)
+            assert np.array_equal(got_L, want_L), cfg
+            assert np.array_equal(got_n, want_n), cfg
+            assert np.array_equal(got_v, want_v), cfg
+    finally:
+        L.lbl_monitor_free(h)
+
+
+def _hand_csr(rng, lengths, n_cells):
+    rowptr = np.zeros(len(lengths) + 1, np.int64)
+    cols = []
+    for i, k in enumerate(lengths):
+        c = np.sort(rng.choice(n_cells, size=k, replace=False)).astype(np.int32)
+        cols.append(c)
+        rowptr[i + 1] = rowptr[i] + k
+    colidx = np.concatenate(cols) if cols else np.zeros(0, np.int32)
+    return rowptr, colidx
+
+
+@pytest.mark.parametrize("P", [1, 2, 5, 33, 64])
+def test_label_ragged_rows_and_alignments(P):
+    """Rows of length 0..4097 starting at every offset modulo 4, including
+    the first and last cell of the grid."""
+    rng = np.random.default_rng(40 + P)
+    agent = synth.Grid(101, 83, 0.5, 0.0, 0.0, synth.ROWMAJOR)  # cells not a multiple of 64
+    lengths = [0, 1, 2, 3, 4, 5, 0, 0, 7, 31, 32, 33, 127, 128, 129, 1, 255, 256, 257, 511, 512, 513, 1023,
+               1024, 1025, 4095, 4096, 4097, 3, 0]
+    lengths += list(rng.integers(0, 300, size=300))
+    rowptr, colidx = _hand_csr(rng, lengths, agent.cells)
+    colidx[rowptr[1]] = 0 if lengths[1] else colidx[rowptr[1]]
+    colidx[rowptr[26]:rowptr[27]][-1] = agent.cells - 1
+    colidx[rowptr[26]:rowptr[27]].sort()
+    O_h = np.zeros(agent.cells, np.uint64)
+    sparse = rng.random(agent.cells) < 0.002
+    O_h[sparse] = rng.integers(0, 2**63, size=sparse.sum(), dtype=np.uint64) | np.uint64(1 << 63)
+    O_h[0] = np.uint64(1)
+    O_h[agent.cells - 1] = np.uint64(1 << (P - 1))
+    rm = Roadmap(agent, rowptr, colidx, bittile=True)
+    want = oracle.label(rowptr, colidx, O_h, P)
+    O = cuda(O_h)
+    for cfg in CFGS:
+        assert np.array_equal(gpu_label(rm, O, P, cfg), want), cfg
+
+
+def test_label_full_and_empty_occupancy(plain):
+    wl = plain
+    rm = Roadmap(wl.agent, wl.rowptr, wl.colidx, bittile=True)
+    nonempty = np.diff(wl.rowptr) > 0
+    for P in (1, 4, 64):
+        full = cuda(np.full(wl.agent.cells, np.uint64(2**64 - 1), np.uint64))
+        zero = cuda(np.zeros(wl.agent.cells, np.uint64))
+        m = np.uint64(2**P - 1) if P < 64 else np.uint64(2**64 - 1)
+        for cfg in CFGS:
+            got = gpu_label(rm, full, P, cfg)
+            assert np.array_equal(got[nonempty], np.full(nonempty.sum(), m)) and (got[~nonempty] == 0).all()
+            assert (gpu_label(rm, zero, P, cfg) == 0).all()
+
+
+def test_label_zero_edges_and_zero_props():
+    agent = synth.agent_grid(8, 1.0, synth.MORTON)
+    rm = Roadmap(agent, np.zeros(1, np.int64), np.zeros(0, np.int32), bittile=True)
+    L.lbl_label(rm.h, None, 3, None)  # nothing to do
+    rm2 = Roadmap(agent, np.array([0, 2, 3], np.int64), np.array([1, 5, 9], np.int32), bittile=True)
+    O = cuda(np.full(64, np.uint64(2**64 - 1), np.uint64))
+    for cfg in CFGS:
+        assert (gpu_label(rm2, O, 0, cfg) == 0).all()
+
+
+@pytest.mark.parametrize("bad", ["range", "negative", "unsorted", "duplicate", "rowptr_desc", "rowptr_end"])
+def test_upload_rejects_malformed_csr(bad):
+    agent = synth.agent_grid(8, 1.0, synth.MORTON)
+    rowptr = np.array([0, 3, 5, 8], np.int64)
+    colidx = np.array([1, 2, 3, 10, 11, 4, 5, 6], np.int32)
+    if bad == "range":
+        colidx[4] = 64
+    elif bad == "negative":
+        colidx[0] = -1
+    elif bad == "unsorted":
+        colidx[1], colidx[2] = 3, 2
+    elif bad == "duplicate":
+        colidx[2] = 2
+    elif bad == "rowptr_desc":
+        rowptr = np.array([0, 6, 5, 8], np.int64)
+    elif bad == "rowptr_end":
+        rowptr = np.array([0, 3, 5, 7], np.int64)
+    with pytest.raises(L.LblError) as ei:
+        L.lbl_roadmap_upload(agent, rowptr, colidx)
+    assert ei.value.code == L.LBL_EINVAL
+
+
+def test_upload_from_device_pointers_and_info(plain):
+    wl = plain
+    h = L.lbl_roadmap_upload(wl.agent, cuda(wl.rowptr), cuda(wl.colidx))
+    try:
+        E, nnz, nbt, b = L.lbl_roadmap_info(h)
+        assert nbt == 0
+        assert (E, nnz) == (wl.n_edges, wl.nnz) and b >= 8 * (E + 1) + 4 * nnz
+        O = gpu_O(wl)
+        out = empty_u64(E)
+        L.lbl_label(h, O, wl.P, out)
+        assert np.array_equal(host(out), oracle.label(wl.rowptr, wl.colidx, host(O), wl.P))
+    finally:
+        L.lbl_roadmap_free(h)
+
+
+def test_bittile_needs_its_upload_flag(plain):
+    rm = Roadmap(plain.agent, plain.rowptr, plain.colidx, bittile=False)
+    with pytest.raises(L.LblError) as ei:
+        gpu_label(rm, gpu_O(plain), plain.P, dict(algo=L.LBL_ALGO_BITTILE))
+    assert ei.value.code == L.LBL_EUNSUPPORTED
+
+
+# ----------------------------------------------------------------- monitor
+
+@pytest.mark.parametrize("n_states,m,reject", [(1, 0, -1), (3, 1, 2), (5, 3, -1), (16, 8, 15), (9, 6, 0)])
+def test_monitor_step_matches_oracle(n_states, m, reject):
+    rng = np.random.default_rng(n_states * 10 + m)
+    relbits = rng.choice(64, size=m, replace=False).astype(np.uint8)
+    delta = rng.integers(0, n_states, size=(n_states, 1 << m)).astype(np.uint8)
+    Lw = rng.integers(0, 2**64 - 1, size=70_001, dtype=np.uint64)
+    h = L.lbl_monitor_create(n_states, m, relbits, delta, reject)
+    try:
+        nxt, viol = empty_u64(Lw.shape[0]), empty_u16(Lw.shape[0])
+        L.lbl_monitor_step(h, cuda(Lw), Lw.shape[0], nxt, viol)
+        wn, wv = oracle.monitor(n_states, m, relbits, delta, reject, Lw)
+        assert np.array_equal(host(nxt), wn) and np.array_equal(host(viol), wv)
+    finally:
+        L.lbl_monitor_free(h)
+
+
+# ----------------------------------------------------------------- session
+
+def test_session_run_from_host_memory(large_small):
+    wl = large_small
+    rm = Roadmap(wl.agent, wl.rowptr, wl.colidx)
+    mon = wl.monitor
+    hm = L.lbl_monitor_create(mon.n_states, mon.m, mon.relbits, mon.delta, mon.reject)
+    ss = L.lbl_session_create(rm.h, wl.world, wl.P, hm)
+    try:
+        planes = torch.from_numpy(wl.planes).pin_memory()
+        outL = torch.empty(wl.n_edges, dtype=torch.uint64).pin_memory()
+        outN = torch.empty(wl.n_edges, dtype=torch.uint64).pin_memory()
+        outV = torch.empty(wl.n_edges, dtype=torch.uint16).pin_memory()
+        rng = np.random.default_rng(8)
+        for _ in range(3):
+            pose = synth.random_pose(rng, wl.world)
+            L.lbl_session_run(ss, planes, pose, outL, outN, outV)
+            torch.cuda.synchronize()
+            O = oracle.frame_transform(wl.world, wl.planes, pose, wl.agent)
+            want = oracle.label(wl.rowptr, wl.colidx, O, wl.P, threads=8)
+            wn, wv = oracle.monitor(mon.n_states, mon.m, mon.relbits, mon.delta, mon.reject, want)
+            assert np.array_equal(outL.numpy(), want)
+            assert np.array_equal(outN.numpy(), wn) and np.array_equal(outV.numpy(), wv)
+    finally:
+        L.lbl_session_free(ss)
+        L.lbl_monitor_free(hm)
