@@ -153,7 +153,8 @@ def test_label_with_fused_monitor_matches_oracle(large_small):
         O = gpu_O(wl)
         want_L = oracle.label(wl.rowptr, wl.colidx, host(O), wl.P, threads=8)
         want_n, want_v = oracle.monitor(mon.n_states, mon.m, mon.relbits, mon.delta, mon.reject, want_L)
-        assert (want_v != 0).any() and (want_v == 0).any()
+        # the reject sink always rejects (bit 15); the other states must vary
+        assert len(np.unique(want_v)) > 4
         for cfg in CFGS:
             got_L, got_n, got_v = gpu_label(rm, O, wl.P, cfg, mon=h)
             assert np.array_equal(got_L, want_L), cfg
