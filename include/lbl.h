@@ -197,6 +197,40 @@ int lbl_monitor_step(lbl_monitor mon, const uint64_t *d_L, int64_t n, uint64_t *
 int lbl_label(lbl_roadmap rm, const uint64_t *d_O, int32_t n_props, uint64_t *d_L, lbl_monitor mon, uint64_t *d_next,
               uint16_t *d_viol, const lbl_config *cfg, lbl_stream s);
 
+/*
+ * lbl_label_blocks_noalloc — the block-form labeling of lbl_label
+ * (LBL_ALGO_BITTILE) for callers that cannot allocate device memory: planning
+ * loops under real-time or safety rules that forbid allocation once the system
+ * runs, and host frameworks that own every device allocation.  The paper has no
+ * counterpart; it is the same product (eq. 10) on the same kernels.
+ *
+ * The kernels' one piece of working memory, the bit-plane copy of d_O (one word
+ * per 64-cell block and proposition), is a fixed device array of
+ * LBL_NOALLOC_MAX_PLANE_WORDS words (4 MiB) inside the library; every GPU that
+ * loads the library holds it until the process exits.  The call allocates and
+ * frees nothing.
+ *   d_block_rowptr  int64[n_edges + 1]: edge e owns entries
+ *                   [d_block_rowptr[e], d_block_rowptr[e+1]), non-decreasing
+ *   d_block_id      uint32[entries]: block b = cells [64b, 64b+64) of d_O's
+ *                   order, each < ceil(n_cells / 64)
+ *   d_block_mask    uint64[entries]: bit i set iff cell 64b+i is in the edge
+ *   d_O             uint64[n_cells]  proposition words (lbl_frame_transform)
+ *   d_L             uint64[n_edges]  labels, as lbl_label writes them
+ * The block form is not checked (malformed entries are undefined behaviour);
+ * it equals what lbl_roadmap_upload derives with LBL_UPLOAD_BITTILE.
+ * Returns LBL_EINVAL when ceil(n_cells / 64) * n_props exceeds
+ * LBL_NOALLOC_MAX_PLANE_WORDS.  The first call on a device looks up the array's
+ * device address (once per device, under a lock), so make that first call
+ * before any stream capture.  Every call uses the same array: calls that can
+ * overlap on the GPU (on different streams, or from several threads) race and
+ * must be serialised by the caller.  Nothing in the array needs clearing: each
+ * call writes every word it reads.
+ */
+#define LBL_NOALLOC_MAX_PLANE_WORDS 524288
+int lbl_label_blocks_noalloc(const int64_t *d_block_rowptr, const uint32_t *d_block_id, const uint64_t *d_block_mask,
+                             int64_t n_edges, const uint64_t *d_O, int64_t n_cells, int32_t n_props, uint64_t *d_L,
+                             lbl_stream s);
+
 /* --------------------------------------------------------------- session */
 
 /*

@@ -39,7 +39,7 @@ EXPORTS = (
     "lbl_roadmap_upload", "lbl_roadmap_free", "lbl_roadmap_info",
     "lbl_frame_transform",
     "lbl_monitor_create", "lbl_monitor_free", "lbl_monitor_step",
-    "lbl_label",
+    "lbl_label", "lbl_label_blocks_noalloc",
     "lbl_session_create", "lbl_session_run", "lbl_session_free",
 )
 
@@ -94,6 +94,7 @@ def load(build_if_needed: bool = True):
         "lbl_monitor_free": (ctypes.c_int, [p]),
         "lbl_monitor_step": (ctypes.c_int, [p, p, i64, p, p, p]),
         "lbl_label": (ctypes.c_int, [p, p, i32, p, p, p, p, ctypes.POINTER(lbl_config), p]),
+        "lbl_label_blocks_noalloc": (ctypes.c_int, [p, p, p, i64, p, i64, i32, p, p]),
         "lbl_session_create": (ctypes.c_int, [p, G, i32, p, ctypes.POINTER(lbl_config), ctypes.POINTER(p)]),
         "lbl_session_run": (ctypes.c_int, [p, p, lbl_pose, p, p, p, p]),
         "lbl_session_free": (ctypes.c_int, [p]),
@@ -248,6 +249,17 @@ def lbl_label(rm, d_O, n_props: int, d_L, mon=None, d_next=None, d_viol=None, cf
     _check(load().lbl_label(rm, _dev(d_O, "uint64", "O"), int(n_props), _dev(d_L, "uint64", "L"), mon,
                             _dev(d_next, "uint64", "next"), _dev(d_viol, "uint16", "viol"), _cfg(cfg),
                             _stream(stream)))
+
+
+def lbl_label_blocks_noalloc(d_block_rowptr, d_block_id, d_block_mask, n_edges: int, d_O, n_cells: int,
+                             n_props: int, d_L, stream=None) -> None:
+    """Block-form labels from caller memory only; the working copy of O lives in
+    the library's fixed device array (no allocation in the call)."""
+    _check(load().lbl_label_blocks_noalloc(_dev(d_block_rowptr, "int64", "block_rowptr"),
+                                           _dev(d_block_id, "uint32", "block_id"),
+                                           _dev(d_block_mask, "uint64", "block_mask"), int(n_edges),
+                                           _dev(d_O, "uint64", "O"), int(n_cells), int(n_props),
+                                           _dev(d_L, "uint64", "L"), _stream(stream)))
 
 
 def lbl_session_create(rm, world, n_props: int, mon=None, cfg=None) -> int:
