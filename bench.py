@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--algo", default="auto", choices=["auto", "csr", "bittile"])
     ap.add_argument("--lanes", type=int, default=0)
     ap.add_argument("--early-exit", type=int, default=-1)
+    ap.add_argument("--pipeline", type=int, default=0, help="1 registers, 2 bulk copies, 3 cp.async")
+    ap.add_argument("--ctas", type=int, default=0)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--edges", type=int, default=None, help="shrink the workload (not for reported numbers)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle baseline")
@@ -253,7 +255,7 @@ def main():
         m = wl.monitor
         mon = L.lbl_monitor_create(m.n_states, m.m, m.relbits, m.delta, m.reject)
     E, P = wl.n_edges, wl.P
-    cfg = lbl_config(algo, args.lanes, args.early_exit, 0)
+    cfg = lbl_config(algo, args.lanes, args.early_exit, args.ctas, args.pipeline)
     with torch.cuda.stream(stream):
         d_planes = torch.from_numpy(wl.planes).to("cuda", non_blocking=False)
         d_O = torch.empty(wl.agent.cells, dtype=torch.uint64, device="cuda")

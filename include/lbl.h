@@ -81,11 +81,20 @@ typedef struct {
 
 typedef struct {
   int32_t algo;           /* LBL_ALGO_* */
-  int32_t lanes_per_edge; /* CSR: lanes that share one edge, 0 = auto, else 4/8/16/32 */
+  int32_t lanes_per_edge; /* CSR: 0 = streaming form (each warp streams a contiguous,
+                             nonzero-balanced range of edges); 4/8/16/32 = lane
+                             groups of that size, one edge each */
   int32_t early_exit;     /* 1 = stop a row once every proposition is set (Sec. 5,
-                             early termination); 0 = off; -1 = auto */
+                             early termination; lane-group CSR and block forms);
+                             0 or -1 = off */
   int32_t ctas_per_sm;    /* persistent grid size per SM, 0 = auto */
+  int32_t pipeline;       /* streaming CSR index stream (LBL_PIPE_*), 0 = default */
 } lbl_config;
+
+/* How the streaming CSR form moves each warp's column indices from HBM. */
+#define LBL_PIPE_REGISTERS 1 /* loads into registers, 8 groups of 32 ahead */
+#define LBL_PIPE_BULK 2      /* cp.async.bulk (TMA engine) into a shared-memory ring */
+#define LBL_PIPE_ASYNC 3     /* per-lane cp.async into a shared-memory ring */
 
 typedef struct lbl_roadmap_s *lbl_roadmap;
 typedef struct lbl_monitor_s *lbl_monitor;
@@ -123,6 +132,14 @@ int lbl_roadmap_upload(const lbl_grid *agent, const int64_t *rowptr, const int32
 
 /* Release a roadmap (synchronises the device first). NULL is accepted. */
 int lbl_roadmap_free(lbl_roadmap rm);
+
+/*
+ * lbl_roadmap_status — synchronise `s`, then report whether any labeling kernel
+ * on this roadmap gave up a bounded wait (its index stream did not arrive
+ * within 2 s): LBL_ETIMEOUT if so (the labels of that call are incomplete; the
+ * flag is cleared), LBL_OK otherwise.  Kernels never spin without a bound.
+ */
+int lbl_roadmap_status(lbl_roadmap rm, lbl_stream s);
 
 /* Shape of a roadmap: edges, nonzeros, (block, mask) entries of the block form
    (0 without LBL_UPLOAD_BITTILE) and device bytes held.  Any out pointer may be

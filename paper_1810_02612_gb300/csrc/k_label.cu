@@ -1,11 +1,12 @@
 // Labeling kernels: the Boolean product L = M.P of eq. 10 (Sec. 4.2-4.3).
 //
-// k_label_csr   gather-OR over CSR rows (the sparse form of Sec. 4.3): lanes of
-//               a group stream an edge's column indices with 16-byte loads that
-//               bypass L1, gather the proposition words of those cells (O is a
-//               few MiB and stays in L2/L1) and OR them; the group then ORs its
-//               lanes together.  Optional early exit once every proposition is
-//               set (the early termination of Sec. 5).
+// k_label_csr   gather-OR over CSR rows (the sparse form of Sec. 4.3): the lanes
+//               of a group read consecutive column indices of an edge (loads
+//               that bypass L1 and are evicted first from L2), gather the
+//               proposition words of those cells (O is a few MiB and stays in
+//               L2/L1) and OR them; the group then ORs its lanes together.
+//               Optional early exit once every proposition is set (the early
+//               termination of Sec. 5).
 // k_label_bt    the dense bit-packed form: each edge is a list of 64-cell
 //               blocks with a cell mask; proposition p is hit iff
 //               (mask AND plane[block][p]) != 0.  Lanes own propositions, so
@@ -20,14 +21,6 @@ namespace lbl {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-
-__device__ __forceinline__ int4 ld_stream_v4(const int32_t *p) {
-  int4 r;
-  asm("ld.global.nc.L1::no_allocate.v4.s32 {%0, %1, %2, %3}, [%4];"
-      : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
-      : "l"(p));
-  return r;
-}
 
 __device__ __forceinline__ uint64_t or_xor(uint64_t v, int off) { return v | __shfl_xor_sync(kFull, v, off); }
 
@@ -54,17 +47,34 @@ __device__ __forceinline__ void epilogue(const MonitorTables &mon, const EpiSmem
   mon.viol[e] = sm.V[letter];
 }
 
-// LPE lanes per edge (32/LPE edges per warp at a time); U steps of 4*LPE
-// indices per group in flight.
+// Index load that bypasses L1 and asks L2 to evict the line first: the column
+// indices are streamed exactly once, O should keep its L2 residency.
+__device__ __forceinline__ uint64_t evict_first_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+
+__device__ __forceinline__ int32_t ld_stream(const int32_t *p, uint64_t pol) {
+  int32_t r;
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(r) : "l"(p), "l"(pol));
+  return r;
+}
+
+// LPE lanes per edge (32/LPE edges per warp at a time).  Lane gl of a group
+// handles elements a + s*LPE + gl, so one gather instruction of the group reads
+// LPE consecutive entries of the (z-order sorted) row: neighbouring cells,
+// few distinct sectors.  U steps are in flight, and the indices of the next U
+// steps are requested before the current gathers are consumed.
 template <int LPE, int U, bool EPI, bool EARLY>
 __global__ void __launch_bounds__(kThreads) k_label_csr(const int64_t *__restrict__ rowptr,
                                                         const int32_t *__restrict__ colidx,
                                                         const uint64_t *__restrict__ O, int64_t E, uint64_t mask,
                                                         uint64_t *__restrict__ L, MonitorTables mon) {
   constexpr int G = 32 / LPE;
-  constexpr int SPAN = 4 * LPE;
   __shared__ EpiSmem sm;
   if (EPI) load_tables(mon, sm);
+  const uint64_t pol = evict_first_policy();
   const int lane = threadIdx.x & 31;
   const int g = lane / LPE;
   const int gl = lane % LPE;
@@ -77,28 +87,31 @@ __global__ void __launch_bounds__(kThreads) k_label_csr(const int64_t *__restric
       beg = __ldg(rowptr + e);
       end = __ldg(rowptr + e + 1);
     }
-    const int64_t a = beg & ~static_cast<int64_t>(3);  // 16-byte aligned start
-    int64_t lim = end;                                   // loads stop here
-    const uint32_t steps = static_cast<uint32_t>((end - a + SPAN - 1) / SPAN);
+    const int64_t a = beg & ~static_cast<int64_t>(LPE - 1);  // LPE*4-byte aligned start
+    int64_t lim = end;
+    const uint32_t steps = static_cast<uint32_t>((end - a + LPE - 1) / LPE);
     const uint32_t nsteps = __reduce_max_sync(kFull, steps);
     uint64_t acc = 0;
+    int32_t nxt[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t k = a + static_cast<int64_t>(u) * LPE + gl;
+      nxt[u] = (k >= beg && k < lim) ? ld_stream(colidx + k, pol) : -1;
+    }
     for (uint32_t s = 0; s < nsteps; s += U) {
-      int4 v[U];
-      int64_t idx[U];
+      int32_t cur[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) cur[u] = nxt[u];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        idx[u] = a + static_cast<int64_t>(s + u) * SPAN + 4 * gl;
-        v[u] = idx[u] < lim ? ld_stream_v4(colidx + idx[u]) : make_int4(0, 0, 0, 0);
+        const int64_t k = a + static_cast<int64_t>(s + U + u) * LPE + gl;
+        nxt[u] = (k >= beg && k < lim) ? ld_stream(colidx + k, pol) : -1;
       }
+      uint64_t w[U];
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int32_t c[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+      for (int u = 0; u < U; ++u) w[u] = cur[u] >= 0 ? __ldg(O + cur[u]) : 0ull;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int64_t k = idx[u] + j;
-          if (k >= beg && k < lim) acc |= __ldg(O + c[j]);
-        }
-      }
+      for (int u = 0; u < U; ++u) acc |= w[u];
       if (EARLY) {
         uint64_t r = acc;
 #pragma unroll
@@ -116,6 +129,436 @@ __global__ void __launch_bounds__(kThreads) k_label_csr(const int64_t *__restric
       if (EPI) epilogue(mon, sm, e, acc);
     }
   }
+}
+
+// Streaming form of the gather-OR.  Warp w owns the contiguous edge range
+// [part[w], part[w+1]) (balanced by nonzeros plus a per-edge cost at upload),
+// so its column indices are one contiguous stream: lane l reads entry g + l of
+// each 32-entry group, the loads of the next U groups are in flight while the
+// current gathers are consumed, and edge boundaries never stall the stream.
+// A boundary inside a group (some valid lane with k >= end of the current
+// edge) flushes the current edge: its lanes' words are ORed in, the warp
+// reduces, lane 0 writes the label, and the next edge starts.  Empty edges are
+// flushed the same way with nothing ORed in.
+template <int U, bool EPI>
+__global__ void __launch_bounds__(kThreads, 4) k_label_stream(const int64_t *__restrict__ rowptr,
+                                                           const int32_t *__restrict__ colidx,
+                                                           const uint64_t *__restrict__ O,
+                                                           const int64_t *__restrict__ part, uint64_t mask,
+                                                           uint64_t *__restrict__ L, MonitorTables mon) {
+  __shared__ EpiSmem sm;
+  if (EPI) load_tables(mon, sm);
+  const uint64_t pol = evict_first_policy();
+  const int lane = threadIdx.x & 31;
+  const int64_t w = (static_cast<int64_t>(blockIdx.x) * kThreads + threadIdx.x) >> 5;
+  const int64_t e_beg = __ldg(part + w), e_end = __ldg(part + w + 1);
+  if (e_beg >= e_end) return;  // warp-uniform
+  // window of edge ends: lane i holds rowptr[win + i + 1] (the end of edge win + i)
+  int64_t win = e_beg;
+  int64_t rp = win + lane < e_end ? __ldg(rowptr + win + lane + 1) : 0;
+  int64_t cur = e_beg;
+  int64_t stop = __shfl_sync(kFull, rp, 0);
+  const int64_t p0 = __ldg(rowptr + e_beg), p1 = __ldg(rowptr + e_end);
+  const int64_t a = p0 & ~static_cast<int64_t>(31);
+  uint64_t acc = 0;
+
+  auto flush = [&]() {
+    uint64_t r = acc;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) r = or_xor(r, off);
+    if (lane == 0) {
+      r &= mask;
+      L[cur] = r;
+      if (EPI) epilogue(mon, sm, cur, r);
+    }
+    acc = 0;
+    ++cur;
+    if (cur < e_end) {
+      if (cur - win == 32) {
+        win = cur;
+        rp = win + lane < e_end ? __ldg(rowptr + win + lane + 1) : 0;
+      }
+      stop = __shfl_sync(kFull, rp, static_cast<int>(cur - win));
+    }
+  };
+
+  // Lane l's entry of group g (relative to a) is base[g + l]; whether a
+  // group crosses the end of the current edge is a warp-uniform test on
+  // scalars, so the common case (no boundary) only ORs.
+  const int32_t *base = colidx + a + lane;
+  const int64_t n_rel = p1 - a;
+  const int head = static_cast<int>(p0 - a);
+  int32_t nxt[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int off = 32 * u + lane;
+    nxt[u] = (off >= head && off < n_rel) ? ld_stream(base + 32 * u, pol) : -1;
+  }
+  for (int64_t g = 0; g < n_rel; g += 32 * U) {
+    int32_t c[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) c[u] = nxt[u];
+    // prefetch the next group: unconditional when it lies wholly inside the range
+    if (g + 64 * U <= n_rel) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) nxt[u] = ld_stream(base + g + 32 * (U + u), pol);
+    } else {
+      const int64_t rem64 = n_rel - g - 32 * U;
+      const int rem = rem64 > 0x7fffffff ? 0x7fffffff : static_cast<int>(rem64);
+#pragma unroll
+      for (int u = 0; u < U; ++u) nxt[u] = (32 * u + lane < rem) ? ld_stream(base + g + 32 * (U + u), pol) : -1;
+    }
+    uint64_t wv[U];
+    if ((g > 0 || head == 0) && g + 32 * U <= n_rel) {  // every entry valid
+#pragma unroll
+      for (int u = 0; u < U; ++u) wv[u] = __ldg(O + c[u]);
+    } else {
+#pragma unroll
+      for (int u = 0; u < U; ++u) wv[u] = c[u] >= 0 ? __ldg(O + c[u]) : 0ull;
+    }
+    const int64_t grp_end = min(a + g + 32 * U, p1);
+    if (grp_end <= stop) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) acc |= wv[u];
+      continue;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t k = a + g + 32 * u + lane;
+      const int64_t sub_end = min(a + g + 32 * (u + 1), p1);
+      while (sub_end > stop) {  // some valid entry of this 32-group is past the current edge
+        if (k < stop) {
+          acc |= wv[u];
+          wv[u] = 0;
+        }
+        flush();
+      }
+      acc |= wv[u];
+    }
+  }
+  while (cur < e_end) flush();
+}
+
+// ---------------------------------------------------------------------------
+// Bulk-copy (TMA engine) form of the streaming gather-OR.  Same partition and
+// boundary logic as k_label_stream, but each warp's index stream is moved by
+// cp.async.bulk into a per-warp ring of kStages shared-memory chunks of
+// kChunk indices, one mbarrier per chunk.  Lane 0 issues the copies; every
+// lane reads its entries from shared memory (consecutive, conflict free) and
+// issues kChunk/32 independent gathers.  The index stream therefore never
+// waits on gathers and needs no registers for prefetching.
+constexpr int kStages = 6;
+constexpr int kChunk = 256;                   // indices per chunk (1 KiB)
+constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s bound on any wait
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(bar))),
+               "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  // potentially blocking: the thread is suspended until the phase completes or
+  // a system-dependent time limit passes
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(static_cast<uint32_t>(__cvta_generic_to_shared(bar))), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the phase with the given parity, by every lane of the warp
+// (each lane's own acquire makes the copied bytes visible to it).  The timer
+// is read only when a try_wait returns without the phase.  False after kWaitNs.
+__device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, int lane) {
+  bool ok = mbar_try_wait(bar, parity);
+  if (__all_sync(kFull, ok)) return true;
+  const uint64_t t0 = global_ns();
+  for (uint32_t it = 0; it < (1u << 30); ++it) {
+    if (!ok) ok = mbar_try_wait(bar, parity);
+    if (__all_sync(kFull, ok)) return true;
+    const uint64_t t = __shfl_sync(kFull, global_ns(), 0);
+    if (t - t0 > kWaitNs) return false;
+  }
+  return false;
+}
+
+// cp.async.bulk of `bytes` (multiple of 16, both addresses 16-byte aligned)
+// from global memory into this CTA's shared memory, completing on `bar`.
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar, uint64_t pol) {
+  const uint32_t b = static_cast<uint32_t>(__cvta_generic_to_shared(bar));
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes) : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+          static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+      "l"(src), "r"(bytes), "r"(b), "l"(pol)
+      : "memory");
+}
+
+template <bool EPI>
+__global__ void __launch_bounds__(kThreads, 4) k_label_tma(const int64_t *__restrict__ rowptr,
+                                                           const int32_t *__restrict__ colidx,
+                                                           const uint64_t *__restrict__ O,
+                                                           const int64_t *__restrict__ part, uint64_t mask,
+                                                           uint64_t *__restrict__ L, MonitorTables mon,
+                                                           int *__restrict__ err) {
+  constexpr int W = kThreads / 32;
+  constexpr int J = kChunk / 32;
+  __shared__ __align__(128) int32_t ring[W][kStages][kChunk];
+  __shared__ __align__(8) uint64_t bars[W][kStages];
+  __shared__ EpiSmem sm;
+  const int lane = threadIdx.x & 31;
+  const int wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    for (int st = 0; st < kStages; ++st) mbar_init(&bars[wid][st], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (EPI) load_tables(mon, sm);  // contains __syncthreads
+  __syncwarp();
+  const uint64_t pol = evict_first_policy();
+  const int64_t w = static_cast<int64_t>(blockIdx.x) * W + wid;
+  const int64_t e_beg = __ldg(part + w), e_end = __ldg(part + w + 1);
+  if (e_beg >= e_end) return;  // warp-uniform
+  int64_t win = e_beg;
+  int64_t rp = win + lane < e_end ? __ldg(rowptr + win + lane + 1) : 0;
+  int64_t cur = e_beg;
+  int64_t stop = __shfl_sync(kFull, rp, 0);
+  const int64_t p0 = __ldg(rowptr + e_beg), p1 = __ldg(rowptr + e_end);
+  const int64_t a4 = p0 & ~static_cast<int64_t>(3);        // 16-byte aligned start
+  const int64_t end4 = (p1 + 3) & ~static_cast<int64_t>(3);  // inside the padded allocation
+  const int64_t n_chunks = (end4 - a4 + kChunk - 1) / kChunk;
+  uint64_t acc = 0;
+
+  auto flush = [&]() {
+    uint64_t r = acc;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) r = or_xor(r, off);
+    if (lane == 0) {
+      r &= mask;
+      L[cur] = r;
+      if (EPI) epilogue(mon, sm, cur, r);
+    }
+    acc = 0;
+    ++cur;
+    if (cur < e_end) {
+      if (cur - win == 32) {
+        win = cur;
+        rp = win + lane < e_end ? __ldg(rowptr + win + lane + 1) : 0;
+      }
+      stop = __shfl_sync(kFull, rp, static_cast<int>(cur - win));
+    }
+  };
+  auto issue = [&](int64_t i) {  // lane 0 only
+    const int64_t start = a4 + i * kChunk;
+    const int64_t n = end4 - start < kChunk ? end4 - start : kChunk;
+    bulk_load(ring[wid][i % kStages], colidx + start, static_cast<uint32_t>(n * 4), &bars[wid][i % kStages], pol);
+  };
+
+  if (lane == 0)
+    for (int64_t i = 0; i < kStages && i < n_chunks; ++i) issue(i);
+  for (int64_t i = 0; i < n_chunks; ++i) {
+    const int st = static_cast<int>(i % kStages);
+    if (!warp_wait(&bars[wid][st], static_cast<uint32_t>((i / kStages) & 1), lane)) {
+      // give up: record it, let the copies still in flight land, leave
+      if (lane == 0) {
+        atomicExch(err, 1);
+        for (int64_t j = i + 1; j < n_chunks && j < i + kStages; ++j) {
+          const uint64_t t0 = global_ns();
+          while (!mbar_try_wait(&bars[wid][j % kStages], static_cast<uint32_t>((j / kStages) & 1)) &&
+                 global_ns() - t0 < kWaitNs) {
+          }
+        }
+      }
+      __syncwarp();
+      return;
+    }
+    const int64_t cb = a4 + i * kChunk;  // global index of ring entry 0
+    const int64_t lo64 = p0 - cb, hi64 = p1 - cb;
+    const int lo = lo64 < 0 ? 0 : static_cast<int>(lo64);
+    const int hi = hi64 > kChunk ? kChunk : static_cast<int>(hi64);
+    uint64_t wv[J];
+    if (lo == 0 && hi == kChunk) {  // every entry of the chunk is valid
+#pragma unroll
+      for (int j = 0; j < J; ++j) wv[j] = __ldg(O + ring[wid][st][32 * j + lane]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        const int off = 32 * j + lane;
+        const int32_t c = (off >= lo && off < hi) ? ring[wid][st][off] : -1;
+        wv[j] = c >= 0 ? __ldg(O + c) : 0ull;
+      }
+    }
+    if (min(cb + kChunk, p1) <= stop) {
+#pragma unroll
+      for (int j = 0; j < J; ++j) acc |= wv[j];
+    } else {
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        const int64_t k = cb + 32 * j + lane;
+        const int64_t sub_end = min(cb + 32 * (j + 1), p1);
+        while (sub_end > stop) {
+          if (k < stop) {
+            acc |= wv[j];
+            wv[j] = 0;
+          }
+          flush();
+        }
+        acc |= wv[j];
+      }
+    }
+    __syncwarp();  // every lane is done with this chunk's shared memory
+    if (lane == 0 && i + kStages < n_chunks) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(i + kStages);
+    }
+  }
+  while (cur < e_end) flush();
+}
+
+// ---------------------------------------------------------------------------
+// Asynchronous-copy form of the streaming gather-OR: every lane copies 2 x 16
+// bytes (8 indices) of the warp's index stream into a per-warp shared-memory
+// ring with cp.async, one commit group per 256-index stage, kAsyncStages - 1
+// stages ahead of the 8 gathers per lane of the stage being consumed.
+// Waiting is cp.async.wait_group (the warp is descheduled, nothing polls), and
+// indices in flight occupy shared memory instead of registers.
+constexpr int kAsyncStages = 4;
+constexpr int kAsyncStage = 256;  // indices per stage: 32 lanes x 2 x 16 bytes
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(
+                   static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+               "l"(src), "r"(src_bytes)
+               : "memory");
+}
+
+template <bool EPI>
+__global__ void __launch_bounds__(kThreads, 4) k_label_async(const int64_t *__restrict__ rowptr,
+                                                             const int32_t *__restrict__ colidx,
+                                                             const uint64_t *__restrict__ O,
+                                                             const int64_t *__restrict__ part, uint64_t mask,
+                                                             uint64_t *__restrict__ L, MonitorTables mon) {
+  constexpr int W = kThreads / 32;
+  constexpr int J = kAsyncStage / 32;
+  __shared__ __align__(128) int32_t ring[W][kAsyncStages][kAsyncStage];
+  __shared__ EpiSmem sm;
+  if (EPI) load_tables(mon, sm);
+  const int lane = threadIdx.x & 31;
+  const int wid = threadIdx.x >> 5;
+  const int64_t w = static_cast<int64_t>(blockIdx.x) * W + wid;
+  const int64_t e_beg = __ldg(part + w), e_end = __ldg(part + w + 1);
+  if (e_beg >= e_end) return;  // warp-uniform
+  int64_t win = e_beg;
+  int64_t rp = win + lane < e_end ? __ldg(rowptr + win + lane + 1) : 0;
+  int64_t cur = e_beg;
+  int64_t stop = __shfl_sync(kFull, rp, 0);
+  const int64_t p0 = __ldg(rowptr + e_beg), p1 = __ldg(rowptr + e_end);
+  const int64_t a4 = p0 & ~static_cast<int64_t>(3);        // 16-byte aligned start
+  const int64_t end4 = (p1 + 3) & ~static_cast<int64_t>(3);  // inside the padded allocation
+  const int64_t n_st = (end4 - a4 + kAsyncStage - 1) / kAsyncStage;
+  uint64_t acc = 0;
+
+  auto flush = [&]() {
+    uint64_t r = acc;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) r = or_xor(r, off);
+    if (lane == 0) {
+      r &= mask;
+      L[cur] = r;
+      if (EPI) epilogue(mon, sm, cur, r);
+    }
+    acc = 0;
+    ++cur;
+    if (cur < e_end) {
+      if (cur - win == 32) {
+        win = cur;
+        rp = win + lane < e_end ? __ldg(rowptr + win + lane + 1) : 0;
+      }
+      stop = __shfl_sync(kFull, rp, static_cast<int>(cur - win));
+    }
+  };
+  // stage i: lane copies indices [a4 + 256 i + 128 h + 4 lane, +4), h = 0, 1,
+  // when they start before end4 (zero-filled otherwise)
+  auto issue = [&](int64_t i) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t src = a4 + i * kAsyncStage + 128 * h + 4 * lane;
+      const bool in = i < n_st && src < end4;
+      cp_async16(&ring[wid][i % kAsyncStages][128 * h + 4 * lane], colidx + (in ? src : a4), in ? 16u : 0u);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+
+  for (int64_t i = 0; i < kAsyncStages - 1; ++i) issue(i);
+  for (int64_t i = 0; i < n_st; ++i) {
+    issue(i + kAsyncStages - 1);  // always one group per iteration, possibly empty
+    asm volatile("cp.async.wait_group %0;" ::"n"(kAsyncStages - 1) : "memory");
+    __syncwarp();  // every lane's part of stage i has landed
+    const int st = static_cast<int>(i % kAsyncStages);
+    const int64_t cb = a4 + i * kAsyncStage;
+    uint64_t wv[J];
+    if (cb >= p0 && cb + kAsyncStage <= p1) {
+#pragma unroll
+      for (int j = 0; j < J; ++j) wv[j] = __ldg(O + ring[wid][st][32 * j + lane]);
+    } else {
+      const int64_t lo64 = p0 - cb, hi64 = p1 - cb;
+      const int lo = lo64 < 0 ? 0 : static_cast<int>(lo64);
+      const int hi = hi64 > kAsyncStage ? kAsyncStage : static_cast<int>(hi64);
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        const int off = 32 * j + lane;
+        wv[j] = (off >= lo && off < hi) ? __ldg(O + ring[wid][st][off]) : 0ull;
+      }
+    }
+    if (min(cb + kAsyncStage, p1) <= stop) {
+#pragma unroll
+      for (int j = 0; j < J; ++j) acc |= wv[j];
+    } else {
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        const int64_t k = cb + 32 * j + lane;
+        const int64_t sub_end = min(cb + 32 * (j + 1), p1);
+        while (sub_end > stop) {
+          if (k < stop) {
+            acc |= wv[j];
+            wv[j] = 0;
+          }
+          flush();
+        }
+        acc |= wv[j];
+      }
+    }
+    __syncwarp();  // stage i is free before any lane refills it
+  }
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  while (cur < e_end) flush();
+}
+
+// Edge partition of the streaming kernel: part[w] = first edge e with
+// rowptr[e] + edge_cost * e >= w * total / W  (total = nnz + edge_cost * E).
+__global__ void k_partition(const int64_t *__restrict__ rowptr, int64_t E, int64_t W, int64_t edge_cost,
+                            int64_t *__restrict__ part) {
+  const int64_t w = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (w > W) return;
+  const int64_t total = rowptr[E] + edge_cost * E;
+  const int64_t target = w == W ? total : total / W * w + (total % W) * w / W;
+  int64_t lo = 0, hi = E;
+  while (lo < hi) {
+    const int64_t mid = lo + (hi - lo) / 2;
+    if (rowptr[mid] + edge_cost * mid < target)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  part[w] = lo;
 }
 
 // Bit-plane re-layout of O for the block form: one warp per 64-cell block.
@@ -143,7 +586,9 @@ __global__ void __launch_bounds__(kThreads) k_planes(const uint64_t *__restrict_
 }
 
 // LPB lanes per block entry (a power of two >= min(P, 32)); 32/LPB entries per
-// step; lane owns propositions q = lane % LPB + k * LPB.
+// step; lane owns propositions q = lane % LPB + t * LPB (t < 2 only when LPB is
+// 32 and P > 32).  Each lane keeps one hit flag per owned proposition; the
+// entry loop is unrolled so several entries' plane loads are in flight.
 template <int LPB, bool EPI, bool EARLY>
 __global__ void __launch_bounds__(kThreads) k_label_bt(const int64_t *__restrict__ brow,
                                                        const uint32_t *__restrict__ bblock,
@@ -151,16 +596,22 @@ __global__ void __launch_bounds__(kThreads) k_label_bt(const int64_t *__restrict
                                                        const uint64_t *__restrict__ planes, int32_t P, int64_t E,
                                                        uint64_t mask, uint64_t *__restrict__ L, MonitorTables mon) {
   constexpr int EPS = 32 / LPB;
+  constexpr int T = LPB == 32 ? 2 : 1;
   __shared__ EpiSmem sm;
   if (EPI) load_tables(mon, sm);
   const int lane = threadIdx.x & 31;
   const int sub = lane / LPB;
   const int pl = lane % LPB;
+  bool owns[T];
+#pragma unroll
+  for (int t = 0; t < T; ++t) owns[t] = pl + t * LPB < P;
   const int64_t warp = (static_cast<int64_t>(blockIdx.x) * kThreads + threadIdx.x) >> 5;
   const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * kThreads) >> 5;
   for (int64_t e = warp; e < E; e += nwarps) {
     const int64_t beg = __ldg(brow + e), end = __ldg(brow + e + 1);
-    uint64_t word = 0;
+    bool hit[T];
+#pragma unroll
+    for (int t = 0; t < T; ++t) hit[t] = false;
     for (int64_t k0 = beg; k0 < end; k0 += 32) {
       const int64_t k = k0 + lane;
       uint32_t b = 0;
@@ -170,23 +621,30 @@ __global__ void __launch_bounds__(kThreads) k_label_bt(const int64_t *__restrict
         m = __ldg(bmask + k);
       }
       const int n = static_cast<int>(end - k0 < 32 ? end - k0 : 32);
+#pragma unroll 4
       for (int j = 0; j < n; j += EPS) {
-        const int src = j + sub;
+        const int src = j + sub;  // < 32; lanes past the row's end carry m = 0
         const uint32_t bj = __shfl_sync(kFull, b, src);
         const uint64_t mj = __shfl_sync(kFull, m, src);
-        if (mj) {
-          const uint64_t *pp = planes + static_cast<int64_t>(bj) * P;
-          for (int q = pl; q < P; q += LPB)
-            if (__ldg(pp + q) & mj) word |= 1ull << q;
+        const uint64_t *pp = planes + static_cast<int64_t>(bj) * P + pl;
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+          const uint64_t v = owns[t] ? __ldg(pp + t * LPB) : 0ull;
+          hit[t] |= (v & mj) != 0;
         }
       }
       if (EARLY) {
-        uint64_t r = word;
+        uint64_t r = 0;
+#pragma unroll
+        for (int t = 0; t < T; ++t) r |= static_cast<uint64_t>(hit[t]) << (pl + t * LPB);
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) r = or_xor(r, off);
         if ((r & mask) == mask) break;  // warp-uniform: r is the same in every lane
       }
     }
+    uint64_t word = 0;
+#pragma unroll
+    for (int t = 0; t < T; ++t) word |= static_cast<uint64_t>(hit[t]) << (pl + t * LPB);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) word = or_xor(word, off);
     if (lane == 0) {
@@ -226,7 +684,7 @@ cudaError_t run_csr(const Roadmap &rm, const uint64_t *O, uint64_t mask, uint64_
 template <int LPE, bool EPI, bool EARLY>
 cudaError_t pick_u(const Roadmap &rm, const uint64_t *O, uint64_t mask, uint64_t *L, const MonitorTables &mon,
                    int ctas_per_sm, cudaStream_t s) {
-  return run_csr<LPE, 2, EPI, EARLY>(rm, O, mask, L, mon, ctas_per_sm, s);
+  return run_csr<LPE, 4, EPI, EARLY>(rm, O, mask, L, mon, ctas_per_sm, s);
 }
 
 template <bool EPI, bool EARLY>
@@ -265,6 +723,70 @@ cudaError_t pick_lpb(int32_t P, const Roadmap &rm, uint64_t mask, uint64_t *L, c
 uint64_t prop_mask(int32_t P) { return P >= 64 ? ~0ull : ((1ull << P) - 1ull); }
 
 }  // namespace
+
+int tma_ctas_per_sm() {
+  static const int occ = std::min(occupancy(k_label_tma<false>), occupancy(k_label_tma<true>));
+  return occ;
+}
+
+cudaError_t launch_label_tma(const Roadmap &rm, const uint64_t *O, int32_t P, uint64_t *L, const MonitorTables *mon,
+                             cudaStream_t s) {
+  if (rm.E == 0) return cudaSuccess;
+  const uint64_t mask = prop_mask(P);
+  const unsigned grid = static_cast<unsigned>(rm.num_sms * rm.part_ctas);
+  MonitorTables none{};
+  if (mon)
+    k_label_tma<true><<<grid, kThreads, 0, s>>>(rm.rowptr, rm.colidx, O, rm.part, mask, L, *mon, rm.err);
+  else
+    k_label_tma<false><<<grid, kThreads, 0, s>>>(rm.rowptr, rm.colidx, O, rm.part, mask, L, none, rm.err);
+  return cudaGetLastError();
+}
+
+int async_ctas_per_sm() {
+  static const int occ = std::min(occupancy(k_label_async<false>), occupancy(k_label_async<true>));
+  return occ;
+}
+
+cudaError_t launch_label_async(const Roadmap &rm, const uint64_t *O, int32_t P, uint64_t *L,
+                               const MonitorTables *mon, cudaStream_t s) {
+  if (rm.E == 0) return cudaSuccess;
+  const uint64_t mask = prop_mask(P);
+  const unsigned grid = static_cast<unsigned>(rm.num_sms * rm.part_ctas);
+  MonitorTables none{};
+  if (mon)
+    k_label_async<true><<<grid, kThreads, 0, s>>>(rm.rowptr, rm.colidx, O, rm.part, mask, L, *mon);
+  else
+    k_label_async<false><<<grid, kThreads, 0, s>>>(rm.rowptr, rm.colidx, O, rm.part, mask, L, none);
+  return cudaGetLastError();
+}
+
+int stream_ctas_per_sm(int unroll) {
+  (void)unroll;
+  static const int occ8 = std::min(occupancy(k_label_stream<8, false>), occupancy(k_label_stream<8, true>));
+  return occ8;
+}
+
+cudaError_t launch_partition(const Roadmap &rm, int ctas_per_sm, cudaStream_t s) {
+  const int64_t W = static_cast<int64_t>(rm.num_sms) * ctas_per_sm * (kThreads / 32);
+  if (rm.E == 0 || W + 1 > rm.part_cap) return cudaErrorInvalidValue;
+  k_partition<<<static_cast<unsigned>((W + 1 + 255) / 256), 256, 0, s>>>(rm.rowptr, rm.E, W, kEdgeCost, rm.part);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_label_stream(const Roadmap &rm, const uint64_t *O, int32_t P, uint64_t *L,
+                                const MonitorTables *mon, int unroll, cudaStream_t s) {
+  if (rm.E == 0) return cudaSuccess;
+  const uint64_t mask = prop_mask(P);
+  const unsigned grid = static_cast<unsigned>(rm.num_sms * rm.part_ctas);
+  MonitorTables none{};
+  const MonitorTables &mt = mon ? *mon : none;
+  (void)unroll;
+  if (mon)
+    k_label_stream<8, true><<<grid, kThreads, 0, s>>>(rm.rowptr, rm.colidx, O, rm.part, mask, L, mt);
+  else
+    k_label_stream<8, false><<<grid, kThreads, 0, s>>>(rm.rowptr, rm.colidx, O, rm.part, mask, L, mt);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_label_csr(const Roadmap &rm, const uint64_t *O, int32_t P, uint64_t *L, const MonitorTables *mon,
                              int lanes_per_edge, bool early_exit, int ctas_per_sm, cudaStream_t s) {

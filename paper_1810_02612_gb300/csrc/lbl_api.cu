@@ -4,6 +4,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -13,6 +14,7 @@ namespace lbl {
 
 namespace {
 thread_local std::string g_err;
+constexpr int kDefaultPipeline = LBL_PIPE_REGISTERS;  // measured fastest on GB300
 
 int device_sms(int dev) {
   static int cache[64] = {0};
@@ -116,6 +118,8 @@ void free_roadmap(Roadmap *rm) {
   cudaFree(rm->bt_block);
   cudaFree(rm->bt_mask);
   cudaFree(rm->planes);
+  cudaFree(rm->part);
+  cudaFree(rm->err);
   delete rm;
 }
 
@@ -242,6 +246,9 @@ int lbl_roadmap_upload(const lbl_grid *agent, const int64_t *rowptr, const int32
     return fail(LBL_EINVAL);
   }
   const bool want_bt = flags & LBL_UPLOAD_BITTILE;
+  if ((e = dev_alloc(&rm->err, 1, &rm->bytes)) != cudaSuccess ||
+      (e = cudaMemsetAsync(rm->err, 0, sizeof(int), st)) != cudaSuccess)
+    return fail(cuda_fail(e, "roadmap upload: error flag"));
   if ((e = dev_alloc(&d_bad, 1, nullptr)) != cudaSuccess) return fail(cuda_fail(e, "roadmap upload: scratch"));
   if (want_bt && (e = dev_alloc(&d_cnt, static_cast<size_t>(n_edges), nullptr)) != cudaSuccess)
     return fail(cuda_fail(e, "roadmap upload: block counts"));
@@ -257,6 +264,15 @@ int lbl_roadmap_upload(const lbl_grid *agent, const int64_t *rowptr, const int32
               "not strictly increasing inside [0, %lld))",
               bad, static_cast<long long>(rm->cells));
     return fail(LBL_EINVAL);
+  }
+  if (n_edges > 0) {
+    // edge partition of the streaming CSR kernel, for its default grid
+    rm->part_cap = static_cast<int64_t>(rm->num_sms) * kMaxCtasPerSm * (kThreads / 32) + 1;
+    if ((e = dev_alloc(&rm->part, static_cast<size_t>(rm->part_cap), &rm->bytes)) != cudaSuccess)
+      return fail(cuda_fail(e, "roadmap upload: partition"));
+    rm->part_ctas = stream_ctas_per_sm(8);
+    if ((e = launch_partition(*rm, rm->part_ctas, st)) != cudaSuccess)
+      return fail(cuda_fail(e, "roadmap upload: partition"));
   }
   if (want_bt) {
     std::vector<int32_t> cnt(static_cast<size_t>(n_edges));
@@ -283,6 +299,7 @@ int lbl_roadmap_upload(const lbl_grid *agent, const int64_t *rowptr, const int32
       return fail(cuda_fail(e, "roadmap upload: block form"));
     rm->has_bt = true;
   }
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(cuda_fail(e, "roadmap upload"));
   cudaFree(d_bad);
   cudaFree(d_cnt);
   *out = rm;
@@ -308,6 +325,26 @@ int lbl_roadmap_info(lbl_roadmap rm, int64_t *n_edges, int64_t *nnz, int64_t *n_
   if (nnz) *nnz = rm->nnz;
   if (n_block_entries) *n_block_entries = rm->n_bt;
   if (device_bytes) *device_bytes = rm->bytes;
+  return LBL_OK;
+}
+
+int lbl_roadmap_status(lbl_roadmap rm, lbl_stream s) {
+  g_err.clear();
+  if (!rm) {
+    set_error("roadmap status: NULL roadmap");
+    return LBL_EINVAL;
+  }
+  if (!same_device(rm->device)) return LBL_EINVAL;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(s);
+  int flag = 0;
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = cudaMemcpy(&flag, rm->err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && flag) e = cudaMemset(rm->err, 0, sizeof(int));
+  if (e != cudaSuccess) return cuda_fail(e, "roadmap status");
+  if (flag) {
+    set_error("a labeling kernel gave up waiting for its index stream; its labels are incomplete");
+    return LBL_ETIMEOUT;
+  }
   return LBL_OK;
 }
 
@@ -468,15 +505,40 @@ static int label_impl(lbl_roadmap rm, const uint64_t *d_O, int32_t n_props, uint
   }
   if (algo == LBL_ALGO_AUTO) algo = (rm->has_bt && n_props <= 16) ? LBL_ALGO_BITTILE : LBL_ALGO_CSR;
   int ee = cfg ? cfg->early_exit : -1;
-  const bool early = ee < 0 ? (n_props <= 4) : (ee != 0);
+  const bool early = ee > 0;  // measured: the per-step OR-reduce costs more than it saves
   const int ctas = cfg ? cfg->ctas_per_sm : 0;
+  const int lpe = cfg ? cfg->lanes_per_edge : 0;
   MonitorTables t{};
   if (mon) t = tables_of(*mon, d_next, d_viol);
   cudaError_t e;
-  if (algo == LBL_ALGO_BITTILE)
+  if (algo == LBL_ALGO_BITTILE) {
     e = launch_label_bittile(*rm, d_O, n_props, d_L, mon ? &t : nullptr, early, ctas, st);
-  else
+  } else if (early || lpe > 0) {
+    // lanes-per-edge form (one edge per lane group; supports early exit)
     e = launch_label_csr(*rm, d_O, n_props, d_L, mon ? &t : nullptr, resolve_lpe(*rm, cfg), early, ctas, st);
+  } else {
+    // streaming form over the edge partition; re-partition for a new grid
+    int pipe = cfg ? cfg->pipeline : 0;
+    if (pipe < 0 || pipe > LBL_PIPE_ASYNC) {
+      set_error("label: unknown pipeline %d", pipe);
+      return LBL_EINVAL;
+    }
+    if (pipe == 0) pipe = kDefaultPipeline;
+    if (rm->E > 0) {
+      const int occ = pipe == LBL_PIPE_BULK ? tma_ctas_per_sm()
+                      : pipe == LBL_PIPE_ASYNC ? async_ctas_per_sm()
+                                               : stream_ctas_per_sm(8);
+      const int want = ctas > 0 ? std::min(ctas, occ) : occ;
+      if (want != rm->part_ctas) {
+        if ((e = launch_partition(*rm, want, st)) != cudaSuccess) return cuda_fail(e, "label: partition");
+        rm->part_ctas = want;
+      }
+    }
+    const MonitorTables *mt = mon ? &t : nullptr;
+    e = pipe == LBL_PIPE_BULK    ? launch_label_tma(*rm, d_O, n_props, d_L, mt, st)
+        : pipe == LBL_PIPE_ASYNC ? launch_label_async(*rm, d_O, n_props, d_L, mt, st)
+                                 : launch_label_stream(*rm, d_O, n_props, d_L, mt, 8, st);
+  }
   if (e != cudaSuccess) return cuda_fail(e, "label: launch");
   return LBL_OK;
 }

@@ -23,6 +23,8 @@
 namespace lbl {
 
 constexpr int kThreads = 256;  // threads per CTA of every labeling kernel
+constexpr int kMaxCtasPerSm = 8;  // 2048 resident threads per SM / kThreads
+constexpr int64_t kEdgeCost = 32;  // partition weight of one edge, in nonzeros
 
 struct MonitorTables {
   const uint64_t *T;  // T[letter]: packed next states of all monitor states
@@ -48,6 +50,11 @@ struct Roadmap {
   uint32_t *bt_block = nullptr;
   uint64_t *bt_mask = nullptr;
   uint64_t *planes = nullptr;  // n_blocks * 64 words of working memory
+  // edge partition of the streaming CSR kernel: warp w owns [part[w], part[w+1])
+  int64_t *part = nullptr;
+  int64_t part_cap = 0;  // entries allocated
+  int part_ctas = 0;     // CTAs per SM the partition was made for
+  int *err = nullptr;    // device flag: a bounded wait in a kernel ran out
   int64_t bytes = 0;
 };
 
@@ -75,6 +82,18 @@ cudaError_t launch_frame_transform(const FrameMap &m, const uint8_t *planes, int
 
 cudaError_t launch_label_csr(const Roadmap &rm, const uint64_t *O, int32_t P, uint64_t *L, const MonitorTables *mon,
                              int lanes_per_edge, bool early_exit, int ctas_per_sm, cudaStream_t s);
+
+// streaming CSR form: CTAs per SM it runs with, its partition, its launch
+int stream_ctas_per_sm(int unroll);
+int tma_ctas_per_sm();
+int async_ctas_per_sm();
+cudaError_t launch_label_async(const Roadmap &rm, const uint64_t *O, int32_t P, uint64_t *L,
+                               const MonitorTables *mon, cudaStream_t s);
+cudaError_t launch_label_tma(const Roadmap &rm, const uint64_t *O, int32_t P, uint64_t *L, const MonitorTables *mon,
+                             cudaStream_t s);
+cudaError_t launch_partition(const Roadmap &rm, int ctas_per_sm, cudaStream_t s);
+cudaError_t launch_label_stream(const Roadmap &rm, const uint64_t *O, int32_t P, uint64_t *L,
+                                const MonitorTables *mon, int unroll, cudaStream_t s);
 
 cudaError_t launch_label_bittile(const Roadmap &rm, const uint64_t *O, int32_t P, uint64_t *L,
                                  const MonitorTables *mon, bool early_exit, int ctas_per_sm, cudaStream_t s);

@@ -30,13 +30,17 @@ LBL_ALGO_AUTO = 0
 LBL_ALGO_CSR = 1
 LBL_ALGO_BITTILE = 2
 
+LBL_PIPE_REGISTERS = 1
+LBL_PIPE_BULK = 2
+LBL_PIPE_ASYNC = 3
+
 LBL_UPLOAD_DEVICE_PTRS = 1
 LBL_UPLOAD_BITTILE = 2
 
 # every entry point declared in include/lbl.h
 EXPORTS = (
     "lbl_last_error", "lbl_version",
-    "lbl_roadmap_upload", "lbl_roadmap_free", "lbl_roadmap_info",
+    "lbl_roadmap_upload", "lbl_roadmap_free", "lbl_roadmap_info", "lbl_roadmap_status",
     "lbl_frame_transform",
     "lbl_monitor_create", "lbl_monitor_free", "lbl_monitor_step",
     "lbl_label", "lbl_label_blocks_noalloc",
@@ -61,7 +65,7 @@ class lbl_pose(ctypes.Structure):
 
 class lbl_config(ctypes.Structure):
     _fields_ = [("algo", ctypes.c_int32), ("lanes_per_edge", ctypes.c_int32),
-                ("early_exit", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32)]
+                ("early_exit", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("pipeline", ctypes.c_int32)]
 
 
 _lib = None
@@ -89,6 +93,7 @@ def load(build_if_needed: bool = True):
         "lbl_roadmap_upload": (ctypes.c_int, [G, p, p, i64, i64, u32, p, ctypes.POINTER(p)]),
         "lbl_roadmap_free": (ctypes.c_int, [p]),
         "lbl_roadmap_info": (ctypes.c_int, [p, p, p, p, p]),
+        "lbl_roadmap_status": (ctypes.c_int, [p, p]),
         "lbl_frame_transform": (ctypes.c_int, [G, p, i32, lbl_pose, G, p, p]),
         "lbl_monitor_create": (ctypes.c_int, [i32, i32, p, p, i32, ctypes.POINTER(p)]),
         "lbl_monitor_free": (ctypes.c_int, [p]),
@@ -127,7 +132,7 @@ def _cfg(cfg):
     if isinstance(cfg, lbl_config):
         return ctypes.byref(cfg)
     c = lbl_config(int(cfg.get("algo", 0)), int(cfg.get("lanes_per_edge", 0)), int(cfg.get("early_exit", -1)),
-                   int(cfg.get("ctas_per_sm", 0)))
+                   int(cfg.get("ctas_per_sm", 0)), int(cfg.get("pipeline", 0)))
     return ctypes.byref(c)
 
 
@@ -219,6 +224,12 @@ def lbl_roadmap_info(rm):
     e, n, k, b = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
     _check(load().lbl_roadmap_info(rm, ctypes.byref(e), ctypes.byref(n), ctypes.byref(k), ctypes.byref(b)))
     return e.value, n.value, k.value, b.value
+
+
+def lbl_roadmap_status(rm, stream=None) -> None:
+    """Synchronise the stream; raise LblError(LBL_ETIMEOUT) if a labeling kernel
+    on this roadmap gave up a bounded wait since the last check."""
+    _check(load().lbl_roadmap_status(rm, _stream(stream)))
 
 
 def lbl_frame_transform(world, d_planes, n_props: int, pose, agent, d_O, stream=None) -> None:

@@ -61,6 +61,12 @@ def gpu_label(rm, O, P, cfg=None, mon=None):
 
 
 CFGS = [
+    dict(algo=L.LBL_ALGO_CSR),                   # streaming form, default partition
+    dict(algo=L.LBL_ALGO_CSR, ctas_per_sm=1),    # streaming form, re-partitioned
+    dict(algo=L.LBL_ALGO_CSR, ctas_per_sm=2, pipeline=L.LBL_PIPE_BULK),
+    dict(algo=L.LBL_ALGO_CSR, pipeline=L.LBL_PIPE_BULK),
+    dict(algo=L.LBL_ALGO_CSR, pipeline=L.LBL_PIPE_ASYNC),
+    dict(algo=L.LBL_ALGO_CSR, ctas_per_sm=3, pipeline=L.LBL_PIPE_ASYNC),
     dict(algo=L.LBL_ALGO_CSR, lanes_per_edge=4, early_exit=0),
     dict(algo=L.LBL_ALGO_CSR, lanes_per_edge=8, early_exit=0),
     dict(algo=L.LBL_ALGO_CSR, lanes_per_edge=16, early_exit=1),
@@ -142,6 +148,7 @@ def test_label_all_algorithms_match_oracle(name, request):
     for cfg in CFGS:
         assert np.array_equal(gpu_label(rm, O, wl.P, cfg), want), cfg
     assert np.array_equal(gpu_label(rm, O, wl.P, None), want)
+    L.lbl_roadmap_status(rm.h)  # no kernel gave up a bounded wait
 
 
 def test_label_with_fused_monitor_matches_oracle(large_small):
@@ -198,6 +205,24 @@ def test_label_ragged_rows_and_alignments(P):
     O = cuda(O_h)
     for cfg in CFGS:
         assert np.array_equal(gpu_label(rm, O, P, cfg), want), cfg
+
+
+def test_label_mostly_empty_rows():
+    """Long runs of empty rows between short ones, and a roadmap whose rows
+    are all empty: every edge still gets its (possibly zero) label."""
+    rng = np.random.default_rng(77)
+    agent = synth.agent_grid(64, 0.5, synth.MORTON)
+    lengths = np.where(rng.random(20_000) < 0.03, rng.integers(1, 200, size=20_000), 0)
+    lengths[-500:] = 0
+    rowptr, colidx = _hand_csr(rng, list(lengths), agent.cells)
+    O_h = rng.integers(0, 2**63, size=agent.cells, dtype=np.uint64)
+    rm = Roadmap(agent, rowptr, colidx, bittile=True)
+    want = oracle.label(rowptr, colidx, O_h, 64)
+    for cfg in CFGS:
+        assert np.array_equal(gpu_label(rm, cuda(O_h), 64, cfg), want), cfg
+    rm0 = Roadmap(agent, np.zeros(1001, np.int64), np.zeros(0, np.int32), bittile=True)
+    for cfg in CFGS:
+        assert (gpu_label(rm0, cuda(O_h), 64, cfg) == 0).all(), cfg
 
 
 def test_label_full_and_empty_occupancy(plain):
