@@ -70,6 +70,27 @@ def parse():
     return ap.parse_args()
 
 
+def rank_seed(seed: int, rank: int) -> int:
+    """Every rank labels its own independent roadmap and frame."""
+    return seed + 1000 * rank
+
+
+def max_over_ranks(x: float, dist, device) -> float:
+    """The job's time is the slowest rank's."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, edges: int, props: int, steps: int, total_ms: float) -> float:
+    """Edge x proposition labels per second over all ranks (weak scaling:
+    every rank labels edges x props per step)."""
+    return world * edges * props * steps / (total_ms / 1e3)
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -243,7 +264,7 @@ def main():
 
     # ---- inputs: every rank its own independent roadmap and frame
     t_gen = time.perf_counter()
-    wl = synth.make(args.workload, seed=args.seed + 1000 * rank, edges=args.edges, threads=cpu_cores())
+    wl = synth.make(args.workload, seed=rank_seed(args.seed, rank), edges=args.edges, threads=cpu_cores())
     t_gen = time.perf_counter() - t_gen
     algo = {"auto": L.LBL_ALGO_AUTO, "csr": L.LBL_ALGO_CSR, "bittile": L.LBL_ALGO_BITTILE}[args.algo]
     want_bt = args.algo in ("auto", "bittile")
@@ -269,10 +290,15 @@ def main():
         L.lbl_frame_transform(wl.world, d_planes, P, wl.pose, wl.agent, d_O, stream=stream)
         L.lbl_label(rm, d_O, P, d_L, mon, d_next, d_viol, cfg, stream=stream)
 
-    # resolve what AUTO picked (for the roofline accounting)
-    used = args.algo
-    if used == "auto":
-        used = "bittile" if (want_bt and P <= 16) else "csr"
+    # AUTO: measure every labeling variant on this frame once (untimed) and
+    # let the roadmap keep the fastest
+    tuned = None
+    if args.algo == "auto":
+        L.lbl_frame_transform(wl.world, d_planes, P, wl.pose, wl.agent, d_O, stream=stream)
+        tuned = L.lbl_roadmap_autotune(rm, d_O, P, d_L, mon, d_next, d_viol, reps=5, stream=stream)
+        used = "bittile" if tuned["algo"] == L.LBL_ALGO_BITTILE else "csr"
+    else:
+        used = args.algo
     launches_per_step = 2 + (1 if used == "bittile" else 0)
 
     # ---- warm-up
@@ -304,12 +330,8 @@ def main():
     frame_ms = np.array([a.elapsed_time(b) for a, b, c in ev])
     label_ms = np.array([b.elapsed_time(c) for a, b, c in ev])
     clk = clocks.stop(t0, t1)
-    total_ms = float(step_ms.sum())
-    if dist:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * E * P * args.steps / (total_ms / 1e3)
+    total_ms = max_over_ranks(float(step_ms.sum()), dist, "cuda")
+    value = job_throughput(world, E, P, args.steps, total_ms)
 
     # ---- end to end through the session API with pinned host buffers
     ss = L.lbl_session_create(rm, wl.world, P, mon, cfg)
@@ -331,12 +353,8 @@ def main():
         e_ev[i][1].record(stream)
     torch.cuda.synchronize()
     e2e_ms_steps = np.array([a.elapsed_time(b) for a, b in e_ev])
-    e2e_ms = float(e2e_ms_steps.sum())
-    if dist:
-        t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = world * E * P * args.steps / (e2e_ms / 1e3)
+    e2e_ms = max_over_ranks(float(e2e_ms_steps.sum()), dist, "cuda")
+    e2e_value = job_throughput(world, E, P, args.steps, e2e_ms)
     h2d = int(wl.planes.nbytes)
     d2h = 8 * E + ((8 + 2) * E if mon else 0)
     L.lbl_session_free(ss)
@@ -366,7 +384,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": WORKLOADS[args.workload], "name": args.workload, "edges": E, "nnz": wl.nnz,
-                       "props": P, "grid": f"{wl.agent.w}x{wl.agent.h}", "algo": used,
+                       "props": P, "grid": f"{wl.agent.w}x{wl.agent.h}", "algo": used, "tuned": tuned,
                        "monitor": bool(mon), "l2": "flushed before every step (256 MiB write); CSR "
                        f"{(4 * wl.nnz) / 1e9:.2f} GB > L2", "parallelism": f"replicas x{world}"},
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),

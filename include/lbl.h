@@ -248,6 +248,20 @@ int lbl_label_blocks_noalloc(const int64_t *d_block_rowptr, const uint32_t *d_bl
                              int64_t n_edges, const uint64_t *d_O, int64_t n_cells, int32_t n_props, uint64_t *d_L,
                              lbl_stream s);
 
+/*
+ * lbl_roadmap_autotune — pick the labeling form of this roadmap by measurement
+ * (the two forms of Sec. 4.3 and their variants compute the same eq. 10; which
+ * is fastest depends on the roadmap, the grid order and n_props).  Every
+ * applicable variant (streaming CSR with each LBL_PIPE_*, lane groups of 8, 16
+ * and 32, and the block form if the roadmap has it) labels d_O once untimed and
+ * `reps` times timed with CUDA events on `s`; the fastest becomes what
+ * LBL_ALGO_AUTO runs for this n_props on this roadmap.  d_L (and d_next/d_viol
+ * with a monitor) receive labels as lbl_label writes them.  *chosen (may be
+ * NULL) gets the winner.  Synchronises `s`.  1 <= reps <= 1000.
+ */
+int lbl_roadmap_autotune(lbl_roadmap rm, const uint64_t *d_O, int32_t n_props, lbl_monitor mon, uint64_t *d_L,
+                         uint64_t *d_next, uint16_t *d_viol, int32_t reps, lbl_config *chosen, lbl_stream s);
+
 /* --------------------------------------------------------------- session */
 
 /*

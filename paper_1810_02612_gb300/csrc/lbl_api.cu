@@ -503,7 +503,13 @@ static int label_impl(lbl_roadmap rm, const uint64_t *d_O, int32_t n_props, uint
     set_error("label: LBL_ALGO_BITTILE needs a roadmap uploaded with LBL_UPLOAD_BITTILE");
     return LBL_EUNSUPPORTED;
   }
-  if (algo == LBL_ALGO_AUTO) algo = (rm->has_bt && n_props <= 16) ? LBL_ALGO_BITTILE : LBL_ALGO_CSR;
+  lbl_config tuned_cfg;
+  if (algo == LBL_ALGO_AUTO && rm->tuned_valid[n_props]) {
+    tuned_cfg = rm->tuned[n_props];  // measured by lbl_roadmap_autotune
+    cfg = &tuned_cfg;
+    algo = tuned_cfg.algo;
+  }
+  if (algo == LBL_ALGO_AUTO) algo = (rm->has_bt && n_props <= 8) ? LBL_ALGO_BITTILE : LBL_ALGO_CSR;
   int ee = cfg ? cfg->early_exit : -1;
   const bool early = ee > 0;  // measured: the per-step OR-reduce costs more than it saves
   const int ctas = cfg ? cfg->ctas_per_sm : 0;
@@ -547,6 +553,51 @@ int lbl_label(lbl_roadmap rm, const uint64_t *d_O, int32_t n_props, uint64_t *d_
               uint16_t *d_viol, const lbl_config *cfg, lbl_stream s) {
   g_err.clear();
   return label_impl(rm, d_O, n_props, d_L, mon, d_next, d_viol, cfg, reinterpret_cast<cudaStream_t>(s));
+}
+
+int lbl_roadmap_autotune(lbl_roadmap rm, const uint64_t *d_O, int32_t n_props, lbl_monitor mon, uint64_t *d_L,
+                         uint64_t *d_next, uint16_t *d_viol, int32_t reps, lbl_config *chosen, lbl_stream s) {
+  g_err.clear();
+  if (!rm || n_props < 0 || n_props > 64 || reps < 1 || reps > 1000) {
+    set_error("autotune: need a roadmap, 0 <= n_props <= 64 and 1 <= reps <= 1000");
+    return LBL_EINVAL;
+  }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(s);
+  std::vector<lbl_config> cand;
+  for (int pipe : {LBL_PIPE_REGISTERS, LBL_PIPE_BULK, LBL_PIPE_ASYNC})
+    cand.push_back(lbl_config{LBL_ALGO_CSR, 0, 0, 0, pipe});
+  for (int lpe : {8, 16, 32}) cand.push_back(lbl_config{LBL_ALGO_CSR, lpe, 0, 0, 0});
+  if (rm->has_bt) cand.push_back(lbl_config{LBL_ALGO_BITTILE, 0, 0, 0, 0});
+  cudaEvent_t t0, t1;
+  cudaError_t e = cudaEventCreate(&t0);
+  if (e == cudaSuccess) e = cudaEventCreate(&t1);
+  if (e != cudaSuccess) return cuda_fail(e, "autotune: events");
+  float best = 0.f;
+  int best_i = -1, rc = LBL_OK;
+  for (size_t i = 0; i < cand.size() && rc == LBL_OK; ++i) {
+    rc = label_impl(rm, d_O, n_props, d_L, mon, d_next, d_viol, &cand[i], st);  // warm-up, re-partition
+    if (rc != LBL_OK) break;
+    e = cudaEventRecord(t0, st);
+    for (int r = 0; r < reps && rc == LBL_OK && e == cudaSuccess; ++r)
+      rc = label_impl(rm, d_O, n_props, d_L, mon, d_next, d_viol, &cand[i], st);
+    if (e == cudaSuccess) e = cudaEventRecord(t1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+    if (e != cudaSuccess) break;
+    if (best_i < 0 || ms < best) {
+      best = ms;
+      best_i = static_cast<int>(i);
+    }
+  }
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  if (rc != LBL_OK) return rc;
+  if (e != cudaSuccess) return cuda_fail(e, "autotune: timing");
+  rm->tuned[n_props] = cand[best_i];
+  rm->tuned_valid[n_props] = true;
+  if (chosen) *chosen = cand[best_i];
+  return LBL_OK;
 }
 
 int lbl_session_create(lbl_roadmap rm, const lbl_grid *world, int32_t n_props, lbl_monitor mon,

@@ -55,6 +55,9 @@ struct Roadmap {
   int64_t part_cap = 0;  // entries allocated
   int part_ctas = 0;     // CTAs per SM the partition was made for
   int *err = nullptr;    // device flag: a bounded wait in a kernel ran out
+  // AUTO choice per proposition count, set by lbl_roadmap_autotune
+  bool tuned_valid[65] = {false};
+  lbl_config tuned[65] = {};
   int64_t bytes = 0;
 };
 

@@ -43,7 +43,7 @@ EXPORTS = (
     "lbl_roadmap_upload", "lbl_roadmap_free", "lbl_roadmap_info", "lbl_roadmap_status",
     "lbl_frame_transform",
     "lbl_monitor_create", "lbl_monitor_free", "lbl_monitor_step",
-    "lbl_label", "lbl_label_blocks_noalloc",
+    "lbl_label", "lbl_label_blocks_noalloc", "lbl_roadmap_autotune",
     "lbl_session_create", "lbl_session_run", "lbl_session_free",
 )
 
@@ -100,6 +100,7 @@ def load(build_if_needed: bool = True):
         "lbl_monitor_step": (ctypes.c_int, [p, p, i64, p, p, p]),
         "lbl_label": (ctypes.c_int, [p, p, i32, p, p, p, p, ctypes.POINTER(lbl_config), p]),
         "lbl_label_blocks_noalloc": (ctypes.c_int, [p, p, p, i64, p, i64, i32, p, p]),
+        "lbl_roadmap_autotune": (ctypes.c_int, [p, p, i32, p, p, p, p, i32, ctypes.POINTER(lbl_config), p]),
         "lbl_session_create": (ctypes.c_int, [p, G, i32, p, ctypes.POINTER(lbl_config), ctypes.POINTER(p)]),
         "lbl_session_run": (ctypes.c_int, [p, p, lbl_pose, p, p, p, p]),
         "lbl_session_free": (ctypes.c_int, [p]),
@@ -271,6 +272,17 @@ def lbl_label_blocks_noalloc(d_block_rowptr, d_block_id, d_block_mask, n_edges: 
                                            _dev(d_block_mask, "uint64", "block_mask"), int(n_edges),
                                            _dev(d_O, "uint64", "O"), int(n_cells), int(n_props),
                                            _dev(d_L, "uint64", "L"), _stream(stream)))
+
+
+def lbl_roadmap_autotune(rm, d_O, n_props: int, d_L, mon=None, d_next=None, d_viol=None, reps: int = 5,
+                         stream=None) -> dict:
+    """Time every labeling variant on this frame; the fastest becomes the
+    roadmap's AUTO choice for n_props.  Returns the chosen configuration."""
+    c = lbl_config()
+    _check(load().lbl_roadmap_autotune(rm, _dev(d_O, "uint64", "O"), int(n_props), mon, _dev(d_L, "uint64", "L"),
+                                       _dev(d_next, "uint64", "next"), _dev(d_viol, "uint16", "viol"), int(reps),
+                                       ctypes.byref(c), _stream(stream)))
+    return {f: getattr(c, f) for f, _ in lbl_config._fields_}
 
 
 def lbl_session_create(rm, world, n_props: int, mon=None, cfg=None) -> int:

@@ -337,3 +337,17 @@ def test_session_run_from_host_memory(large_small):
     finally:
         L.lbl_session_free(ss)
         L.lbl_monitor_free(hm)
+
+
+def test_autotune_choice_is_exact_and_sticks(driving_small):
+    wl = driving_small
+    rm = Roadmap(wl.agent, wl.rowptr, wl.colidx, bittile=True)
+    O = gpu_O(wl)
+    want = oracle.label(wl.rowptr, wl.colidx, host(O), wl.P, threads=8)
+    out = empty_u64(rm.E)
+    chosen = L.lbl_roadmap_autotune(rm.h, O, wl.P, out, reps=2)
+    assert chosen["algo"] in (L.LBL_ALGO_CSR, L.LBL_ALGO_BITTILE)
+    assert np.array_equal(host(out), want)
+    assert np.array_equal(gpu_label(rm, O, wl.P, dict(algo=L.LBL_ALGO_AUTO)), want)
+    assert np.array_equal(gpu_label(rm, O, wl.P, None), want)
+    L.lbl_roadmap_status(rm.h)
