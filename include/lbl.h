@@ -99,6 +99,7 @@ typedef struct {
 typedef struct lbl_roadmap_s *lbl_roadmap;
 typedef struct lbl_monitor_s *lbl_monitor;
 typedef struct lbl_session_s *lbl_session;
+typedef struct lbl_batch_s *lbl_batch;
 
 /* Message describing the last failure on the calling thread ("" if none).
    The pointer stays valid until the thread's next lbl_* call. */
@@ -261,6 +262,52 @@ int lbl_label_blocks_noalloc(const int64_t *d_block_rowptr, const uint32_t *d_bl
  */
 int lbl_roadmap_autotune(lbl_roadmap rm, const uint64_t *d_O, int32_t n_props, lbl_monitor mon, uint64_t *d_L,
                          uint64_t *d_next, uint16_t *d_viol, int32_t reps, lbl_config *chosen, lbl_stream s);
+
+/* ----------------------------------------------------------------- batch */
+
+/*
+ * Batched frames: many roadmaps (agents, or uneven abstractions), one frame each,
+ * transformed and labeled by two kernel launches in total instead of two per
+ * frame.  Sec. 5 runs one labeling query at a time; the batch runs many.  Every
+ * item's labels equal what lbl_frame_transform + lbl_label produce for it.
+ *
+ * lbl_batch_create    plan for n (1..128) roadmaps with their proposition counts
+ *                     and optional monitors (mons may be NULL): every roadmap is
+ *                     cut into edge ranges ("work units") of about equal cost
+ *                     (nonzeros + 32 per edge), about 8 per warp of one
+ *                     persistent grid; warps take units in roadmap order from a
+ *                     counter, so the load balances and few frames are live in
+ *                     L2 at once.  ctas_per_sm 0 = as many as fit.
+ *                     Synchronises the legacy default stream.
+ * lbl_batch_set_frames  host-side only: frames[i] is item i's world planes,
+ *                     pose and output buffers (see lbl_frame).  Checked here.
+ * lbl_batch_launch    enqueues on `s`, for the frames last set, the stages asked
+ *                     for: LBL_STAGE_TRANSFORM (all frame transforms, one
+ *                     launch) and/or LBL_STAGE_LABEL (all labels with the fused
+ *                     monitors, one launch after a 8-byte memset of the unit
+ *                     counter; reads each frame's d_O).  It only enqueues
+ *                     kernels and that memset, so it can be captured in a CUDA
+ *                     graph and replayed; replays use the buffers and poses of
+ *                     the frames set before capture.  Launches of one batch
+ *                     must not overlap on the device (they share the counter).
+ */
+typedef struct {
+  lbl_grid world;          /* world grid of d_planes (its order is ignored) */
+  const uint8_t *d_planes; /* uint8[n_props][world.h][world.w] */
+  lbl_pose pose;           /* agent pose in the world */
+  uint64_t *d_O;           /* uint64[agent cells]: transformed words (written) */
+  uint64_t *d_L;           /* uint64[E]: labels */
+  uint64_t *d_next;        /* uint64[E], uint16[E]: monitor outputs when the item */
+  uint16_t *d_viol;        /*   has a monitor, else ignored */
+} lbl_frame;
+
+int lbl_batch_create(int32_t n, const lbl_roadmap *rms, const int32_t *n_props, const lbl_monitor *mons,
+                     int32_t ctas_per_sm, lbl_batch *out);
+int lbl_batch_set_frames(lbl_batch b, const lbl_frame *frames);
+#define LBL_STAGE_TRANSFORM 1u
+#define LBL_STAGE_LABEL 2u
+int lbl_batch_launch(lbl_batch b, uint32_t stages, lbl_stream s);
+int lbl_batch_free(lbl_batch b);
 
 /* --------------------------------------------------------------- session */
 

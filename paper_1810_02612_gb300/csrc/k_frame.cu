@@ -61,6 +61,43 @@ __global__ void __launch_bounds__(256) k_frame_transform(FrameArgs a) {
   }
 }
 
+// Batched frame transform: thread per (frame, agent cell) over all frames'
+// cells; the frame is found by binary search over the items' first cells.
+__global__ void __launch_bounds__(256) k_frame_batch(const __grid_constant__ FrameTable tab) {
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t gidx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; gidx < tab.total;
+       gidx += stride) {
+    int lo = 0, hi = tab.n - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) / 2;
+      if (tab.items[mid].cell0 <= gidx)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    const FrameItem &f = tab.items[lo];
+    const int64_t idx = gidx - f.cell0;
+    int64_t ix, iy;
+    if (f.order == LBL_ORDER_MORTON) {
+      ix = gather_even_bits(static_cast<uint64_t>(idx) >> 1);
+      iy = gather_even_bits(static_cast<uint64_t>(idx));
+    } else {
+      iy = idx / f.aw;
+      ix = idx - iy * f.aw;
+    }
+    const int64_t u = f.A00 * ix + f.A01 * iy + f.B0;
+    const int64_t v = f.A10 * ix + f.A11 * iy + f.B1;
+    const int64_t wx = u >> 32;
+    const int64_t wy = v >> 32;
+    uint64_t word = 0;
+    if (wx >= 0 && wx < f.ww && wy >= 0 && wy < f.wh) {
+      const uint8_t *p = f.planes + wy * f.ww + wx;
+      for (int q = 0; q < f.P; ++q) word |= static_cast<uint64_t>(__ldg(p + q * f.plane_cells) != 0) << q;
+    }
+    f.O[idx] = word;
+  }
+}
+
 // letter = sum_j bit(L, rel[j]) << j ; next/viol from the per-letter tables.
 __global__ void __launch_bounds__(256) k_monitor_step(MonitorTables mon, const uint64_t *__restrict__ L, int64_t n) {
   __shared__ uint64_t sT[256];
@@ -92,6 +129,15 @@ cudaError_t launch_frame_transform(const FrameMap &m, const uint8_t *planes, int
   const int64_t cap = static_cast<int64_t>(num_sms) * 8;
   if (blocks > cap) blocks = cap;
   k_frame_transform<<<static_cast<unsigned>(blocks), 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_frame_batch(const FrameTable &tab, int num_sms, cudaStream_t s) {
+  if (tab.total == 0) return cudaSuccess;
+  int64_t blocks = (tab.total + 255) / 256;
+  const int64_t cap = static_cast<int64_t>(num_sms) * 8;
+  if (blocks > cap) blocks = cap;
+  k_frame_batch<<<static_cast<unsigned>(blocks), 256, 0, s>>>(tab);
   return cudaGetLastError();
 }
 

@@ -131,28 +131,19 @@ __global__ void __launch_bounds__(kThreads) k_label_csr(const int64_t *__restric
   }
 }
 
-// Streaming form of the gather-OR.  Warp w owns the contiguous edge range
-// [part[w], part[w+1]) (balanced by nonzeros plus a per-edge cost at upload),
-// so its column indices are one contiguous stream: lane l reads entry g + l of
-// each 32-entry group, the loads of the next U groups are in flight while the
-// current gathers are consumed, and edge boundaries never stall the stream.
-// A boundary inside a group (some valid lane with k >= end of the current
-// edge) flushes the current edge: its lanes' words are ORed in, the warp
-// reduces, lane 0 writes the label, and the next edge starts.  Empty edges are
-// flushed the same way with nothing ORed in.
-template <int U, bool EPI>
-__global__ void __launch_bounds__(kThreads, 4) k_label_stream(const int64_t *__restrict__ rowptr,
-                                                           const int32_t *__restrict__ colidx,
-                                                           const uint64_t *__restrict__ O,
-                                                           const int64_t *__restrict__ part, uint64_t mask,
-                                                           uint64_t *__restrict__ L, MonitorTables mon) {
-  __shared__ EpiSmem sm;
-  if (EPI) load_tables(mon, sm);
-  const uint64_t pol = evict_first_policy();
-  const int lane = threadIdx.x & 31;
-  const int64_t w = (static_cast<int64_t>(blockIdx.x) * kThreads + threadIdx.x) >> 5;
-  const int64_t e_beg = __ldg(part + w), e_end = __ldg(part + w + 1);
-  if (e_beg >= e_end) return;  // warp-uniform
+// Streaming form of the gather-OR.  A warp owns the contiguous edge range
+// [e_beg, e_end) (balanced by nonzeros plus a per-edge cost when the roadmap
+// is uploaded), so its column indices are one contiguous stream: lane l reads
+// entry g + l of each 32-entry group, the loads of the next U groups are in
+// flight while the current gathers are consumed, and edge boundaries never
+// stall the stream.  A boundary inside a group (some valid lane with k >= end
+// of the current edge) flushes the current edge: its lanes' words are ORed in,
+// the warp reduces, lane 0 hands the label to `emit`, and the next edge starts.
+// Empty edges are flushed the same way with nothing ORed in.
+template <int U, typename Emit>
+__device__ __forceinline__ void stream_range(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
+                                             const uint64_t *__restrict__ O, int64_t e_beg, int64_t e_end,
+                                             uint64_t pol, int lane, Emit emit) {
   // window of edge ends: lane i holds rowptr[win + i + 1] (the end of edge win + i)
   int64_t win = e_beg;
   int64_t rp = win + lane < e_end ? __ldg(rowptr + win + lane + 1) : 0;
@@ -166,11 +157,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_label_stream(const int64_t *__r
     uint64_t r = acc;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) r = or_xor(r, off);
-    if (lane == 0) {
-      r &= mask;
-      L[cur] = r;
-      if (EPI) epilogue(mon, sm, cur, r);
-    }
+    if (lane == 0) emit(cur, r);
     acc = 0;
     ++cur;
     if (cur < e_end) {
@@ -237,6 +224,71 @@ __global__ void __launch_bounds__(kThreads, 4) k_label_stream(const int64_t *__r
     }
   }
   while (cur < e_end) flush();
+}
+
+template <int U, bool EPI>
+__global__ void __launch_bounds__(kThreads, 4) k_label_stream(const int64_t *__restrict__ rowptr,
+                                                           const int32_t *__restrict__ colidx,
+                                                           const uint64_t *__restrict__ O,
+                                                           const int64_t *__restrict__ part, uint64_t mask,
+                                                           uint64_t *__restrict__ L, MonitorTables mon) {
+  __shared__ EpiSmem sm;
+  if (EPI) load_tables(mon, sm);
+  const uint64_t pol = evict_first_policy();
+  const int lane = threadIdx.x & 31;
+  const int64_t w = (static_cast<int64_t>(blockIdx.x) * kThreads + threadIdx.x) >> 5;
+  const int64_t e_beg = __ldg(part + w), e_end = __ldg(part + w + 1);
+  if (e_beg >= e_end) return;  // warp-uniform
+  stream_range<U>(rowptr, colidx, O, e_beg, e_end, pol, lane, [&](int64_t e, uint64_t r) {
+    r &= mask;
+    L[e] = r;
+    if (EPI) epilogue(mon, sm, e, r);
+  });
+}
+
+// Batched streaming labels: many roadmaps (one frame each) in one launch.  The
+// batch plan cut item i into `units` nonzero-balanced edge ranges (unit ids
+// [unit0_i, unit0_i + units_i), in item order).  Warps take units from a
+// global counter (zeroed before the launch), so the load stays balanced and
+// only the few items being worked on keep their O words hot in L2.  Monitor
+// tables, if any, are read through L1.
+__global__ void __launch_bounds__(kThreads, 4) k_label_batch(const __grid_constant__ BatchTable tab,
+                                                          unsigned long long *__restrict__ next_unit) {
+  const uint64_t pol = evict_first_policy();
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    unsigned long long u = 0;
+    if (lane == 0) u = atomicAdd(next_unit, 1ull);
+    u = __shfl_sync(kFull, u, 0);
+    if (u >= static_cast<unsigned long long>(tab.total)) return;
+    const int64_t unit = static_cast<int64_t>(u);
+    int lo = 0, hi = tab.n - 1;  // last item with unit0 <= unit
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) / 2;
+      if (tab.items[mid].warp0 <= unit)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    const BatchItem *it = tab.items + lo;  // in the constant bank
+    const int64_t lu = unit - it->warp0;
+    if (lu >= it->warps) continue;
+    const int64_t *part = it->part;
+    const int64_t e_beg = __ldg(part + lu), e_end = __ldg(part + lu + 1);
+    if (e_beg >= e_end) continue;
+    stream_range<8>(it->rowptr, it->colidx, it->O, e_beg, e_end, pol, lane, [&](int64_t e, uint64_t r) {
+      r &= it->mask;
+      it->L[e] = r;
+      const uint64_t *T = it->T;
+      if (T) {
+        uint32_t letter = 0;
+        const int m = it->m;
+        for (int j = 0; j < m; ++j) letter |= static_cast<uint32_t>((r >> it->rel[j]) & 1u) << j;
+        it->next[e] = __ldg(T + letter);
+        it->viol[e] = __ldg(it->V + letter);
+      }
+    });
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -723,6 +775,26 @@ cudaError_t pick_lpb(int32_t P, const Roadmap &rm, uint64_t mask, uint64_t *L, c
 uint64_t prop_mask(int32_t P) { return P >= 64 ? ~0ull : ((1ull << P) - 1ull); }
 
 }  // namespace
+
+int batch_ctas_per_sm() {
+  static const int occ = occupancy(k_label_batch);
+  return occ;
+}
+
+cudaError_t launch_label_batch(const BatchTable &tab, unsigned long long *counter, int num_sms, int ctas_per_sm,
+                               cudaStream_t s) {
+  if (tab.total == 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  k_label_batch<<<static_cast<unsigned>(num_sms * ctas_per_sm), kThreads, 0, s>>>(tab, counter);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_partition_into(const int64_t *rowptr, int64_t E, int64_t W, int64_t *part, cudaStream_t s) {
+  if (E == 0 || W == 0) return cudaSuccess;
+  k_partition<<<static_cast<unsigned>((W + 1 + 255) / 256), 256, 0, s>>>(rowptr, E, W, kEdgeCost, part);
+  return cudaGetLastError();
+}
 
 int tma_ctas_per_sm() {
   static const int occ = std::min(occupancy(k_label_tma<false>), occupancy(k_label_tma<true>));

@@ -154,6 +154,21 @@ using namespace lbl;
 
 struct lbl_roadmap_s : Roadmap {};
 struct lbl_monitor_s : Monitor {};
+struct lbl_batch_s {
+  int device = 0;
+  int num_sms = 1;
+  int32_t n = 0;
+  std::vector<lbl_roadmap> rms;
+  std::vector<int32_t> P;
+  std::vector<lbl_monitor> mons;
+  int64_t *part = nullptr;  // every item's partition, concatenated
+  unsigned long long *counter = nullptr;  // next work unit of the label launch
+  int ctas = 1;
+  BatchTable tab{};
+  FrameTable ftab{};
+  bool frames_set = false;
+};
+
 struct lbl_session_s {
   int device = 0;
   lbl_roadmap rm = nullptr;
@@ -597,6 +612,159 @@ int lbl_roadmap_autotune(lbl_roadmap rm, const uint64_t *d_O, int32_t n_props, l
   rm->tuned[n_props] = cand[best_i];
   rm->tuned_valid[n_props] = true;
   if (chosen) *chosen = cand[best_i];
+  return LBL_OK;
+}
+
+int lbl_batch_create(int32_t n, const lbl_roadmap *rms, const int32_t *n_props, const lbl_monitor *mons,
+                     int32_t ctas_per_sm, lbl_batch *out) {
+  g_err.clear();
+  if (!out) {
+    set_error("batch create: out is NULL");
+    return LBL_EINVAL;
+  }
+  *out = nullptr;
+  if (n < 1 || n > kMaxBatch || !rms || !n_props) {
+    set_error("batch create: need 1 <= n <= %d roadmaps and their proposition counts", kMaxBatch);
+    return LBL_EINVAL;
+  }
+  for (int i = 0; i < n; ++i) {
+    if (!rms[i] || n_props[i] < 0 || n_props[i] > 64) {
+      set_error("batch create: item %d has no roadmap or n_props outside 0..64", i);
+      return LBL_EINVAL;
+    }
+    if (rms[i]->device != rms[0]->device || (mons && mons[i] && mons[i]->device != rms[0]->device)) {
+      set_error("batch create: items live on different devices");
+      return LBL_EINVAL;
+    }
+  }
+  if (!same_device(rms[0]->device)) return LBL_EINVAL;
+  lbl_batch_s *b = new (std::nothrow) lbl_batch_s();
+  if (!b) {
+    set_error("batch create: out of host memory");
+    return LBL_ENOMEM;
+  }
+  b->device = rms[0]->device;
+  b->num_sms = rms[0]->num_sms;
+  b->n = n;
+  b->rms.assign(rms, rms + n);
+  b->P.assign(n_props, n_props + n);
+  b->mons.assign(n, nullptr);
+  if (mons) b->mons.assign(mons, mons + n);
+  // The persistent grid's warps take work units from a counter; items are
+  // cut into units of about equal cost (nonzeros + kEdgeCost per edge),
+  // kUnitsPerWarp per warp overall, at least one per item with edges.
+  const int occ = batch_ctas_per_sm();
+  const int ctas = ctas_per_sm > 0 ? std::min<int>(ctas_per_sm, occ) : occ;
+  b->ctas = ctas;
+  constexpr int64_t kUnitsPerWarp = 8;
+  const int64_t units_target = static_cast<int64_t>(b->num_sms) * ctas * (kThreads / 32) * kUnitsPerWarp;
+  double total = 0;
+  for (int i = 0; i < n; ++i) total += static_cast<double>(rms[i]->nnz + kEdgeCost * rms[i]->E);
+  const double unit_cost = total > 0 ? total / static_cast<double>(units_target) : 1.0;
+  std::vector<int64_t> W(n), off(n + 1, 0);
+  for (int i = 0; i < n; ++i) {
+    const Roadmap &r = *rms[i];
+    W[i] = 0;
+    if (r.E > 0) {
+      const double c = static_cast<double>(r.nnz + kEdgeCost * r.E);
+      W[i] = std::max<int64_t>(1, static_cast<int64_t>(std::ceil(c / unit_cost)));
+      W[i] = std::min<int64_t>(W[i], r.E);  // never more units than edges
+    }
+    off[i + 1] = off[i] + W[i] + 1;
+  }
+  cudaError_t e = dev_alloc(&b->part, static_cast<size_t>(off[n]), nullptr);
+  if (e == cudaSuccess) e = dev_alloc(&b->counter, 1, nullptr);
+  int64_t warp0 = 0;
+  for (int i = 0; i < n && e == cudaSuccess; ++i) {
+    const Roadmap &r = *rms[i];
+    e = launch_partition_into(r.rowptr, r.E, W[i], b->part + off[i], nullptr);
+    BatchItem &it = b->tab.items[i];
+    it = BatchItem{};
+    it.rowptr = r.rowptr;
+    it.colidx = r.colidx;
+    it.part = b->part + off[i];
+    it.mask = n_props[i] >= 64 ? ~0ull : ((1ull << n_props[i]) - 1ull);
+    it.warp0 = warp0;
+    it.warps = W[i];
+    if (b->mons[i]) {
+      const Monitor &m = *b->mons[i];
+      it.T = m.T;
+      it.V = m.V;
+      it.m = m.m;
+      for (int j = 0; j < 8; ++j) it.rel[j] = m.rel[j];
+    }
+    warp0 += W[i];
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
+  if (e != cudaSuccess) {
+    cudaFree(b->part);
+    cudaFree(b->counter);
+    delete b;
+    return cuda_fail(e, "batch create: partitions");
+  }
+  b->tab.n = n;
+  b->tab.total = warp0;
+  b->ftab.n = n;
+  *out = b;
+  return LBL_OK;
+}
+
+int lbl_batch_set_frames(lbl_batch b, const lbl_frame *frames) {
+  g_err.clear();
+  if (!b || !frames) {
+    set_error("batch frames: NULL batch or frames");
+    return LBL_EINVAL;
+  }
+  int64_t cell0 = 0;
+  for (int i = 0; i < b->n; ++i) {
+    const lbl_frame &f = frames[i];
+    const Roadmap &r = *b->rms[i];
+    const int32_t P = b->P[i];
+    if (!valid_grid(&f.world, "batch frames (world)", false)) return LBL_EINVAL;
+    if ((P > 0 && !f.d_planes) || !f.d_O || (r.E > 0 && !f.d_L) ||
+        (b->mons[i] && r.E > 0 && (!f.d_next || !f.d_viol))) {
+      set_error("batch frames: frame %d is missing a buffer", i);
+      return LBL_EINVAL;
+    }
+    FrameMap m;
+    if (!frame_map(f.world, r.agent, f.pose, &m)) return LBL_EINVAL;
+    FrameItem &fi = b->ftab.items[i];
+    fi = FrameItem{m.A00, m.A01, m.B0, m.A10, m.A11, m.B1, f.d_planes, f.d_O,
+                   static_cast<int64_t>(f.world.w) * f.world.h, cell0, f.world.w, f.world.h, r.agent.w,
+                   r.agent.h, P, r.agent.order};
+    cell0 += r.cells;
+    BatchItem &it = b->tab.items[i];
+    it.O = f.d_O;
+    it.L = f.d_L;
+    it.next = f.d_next;
+    it.viol = f.d_viol;
+  }
+  b->ftab.total = cell0;
+  b->frames_set = true;
+  return LBL_OK;
+}
+
+int lbl_batch_launch(lbl_batch b, uint32_t stages, lbl_stream s) {
+  g_err.clear();
+  if (!b || !b->frames_set || (stages & ~(LBL_STAGE_TRANSFORM | LBL_STAGE_LABEL))) {
+    set_error("batch launch: NULL batch, no frames set, or unknown stages");
+    return LBL_EINVAL;
+  }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(s);
+  cudaError_t e = cudaSuccess;
+  if (stages & LBL_STAGE_TRANSFORM) e = launch_frame_batch(b->ftab, b->num_sms, st);
+  if (e == cudaSuccess && (stages & LBL_STAGE_LABEL)) e = launch_label_batch(b->tab, b->counter, b->num_sms, b->ctas, st);
+  if (e != cudaSuccess) return cuda_fail(e, "batch launch");
+  return LBL_OK;
+}
+
+int lbl_batch_free(lbl_batch b) {
+  g_err.clear();
+  if (!b) return LBL_OK;
+  cudaDeviceSynchronize();
+  cudaFree(b->part);
+  cudaFree(b->counter);
+  delete b;
   return LBL_OK;
 }
 

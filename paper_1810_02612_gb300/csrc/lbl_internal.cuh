@@ -35,6 +35,45 @@ struct MonitorTables {
   uint8_t rel[8];
 };
 
+// One roadmap's share of a batched labeling launch (device table entry).
+struct BatchItem {
+  const int64_t *rowptr;
+  const int32_t *colidx;
+  const int64_t *part;  // warps + 1 entries
+  const uint64_t *O;
+  uint64_t *L, *next;
+  uint16_t *viol;
+  const uint64_t *T;  // monitor tables, NULL without a monitor
+  const uint16_t *V;
+  uint64_t mask;
+  int64_t warp0, warps;  // work units [warp0, warp0 + warps) of the batch
+  int32_t m;
+  uint8_t rel[8];
+};
+
+// One frame's share of a batched frame-transform launch (device table entry).
+struct FrameItem {
+  int64_t A00, A01, B0, A10, A11, B1;  // Q32.32 map
+  const uint8_t *planes;
+  uint64_t *O;
+  int64_t plane_cells;  // ww * wh
+  int64_t cell0;        // first global cell of this frame
+  int32_t ww, wh, aw, ah, P, order;
+};
+
+// Batched launches take their whole item table as one kernel parameter.
+constexpr int kMaxBatch = 128;
+struct BatchTable {
+  BatchItem items[kMaxBatch];
+  int32_t n;
+  int64_t total;  // work units
+};
+struct FrameTable {
+  FrameItem items[kMaxBatch];
+  int32_t n;
+  int64_t total;  // cells
+};
+
 struct Roadmap {
   int device = 0;
   int num_sms = 0;
@@ -102,6 +141,13 @@ cudaError_t launch_label_bittile(const Roadmap &rm, const uint64_t *O, int32_t P
                                  const MonitorTables *mon, bool early_exit, int ctas_per_sm, cudaStream_t s);
 
 cudaError_t launch_monitor_step(const MonitorTables &mon, const uint64_t *L, int64_t n, int num_sms, cudaStream_t s);
+
+// batched launches over device tables of items
+int batch_ctas_per_sm();
+cudaError_t launch_label_batch(const BatchTable &tab, unsigned long long *counter, int num_sms, int ctas_per_sm,
+                               cudaStream_t s);
+cudaError_t launch_partition_into(const int64_t *rowptr, int64_t E, int64_t W, int64_t *part, cudaStream_t s);
+cudaError_t launch_frame_batch(const FrameTable &tab, int num_sms, cudaStream_t s);
 
 // roadmap preparation: row checks, block counts, block fill
 cudaError_t launch_scan_rows(const int64_t *rowptr, const int32_t *colidx, int64_t E, int64_t nnz, int64_t cells,

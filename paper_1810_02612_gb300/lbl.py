@@ -34,6 +34,9 @@ LBL_PIPE_REGISTERS = 1
 LBL_PIPE_BULK = 2
 LBL_PIPE_ASYNC = 3
 
+LBL_STAGE_TRANSFORM = 1
+LBL_STAGE_LABEL = 2
+
 LBL_UPLOAD_DEVICE_PTRS = 1
 LBL_UPLOAD_BITTILE = 2
 
@@ -45,6 +48,7 @@ EXPORTS = (
     "lbl_monitor_create", "lbl_monitor_free", "lbl_monitor_step",
     "lbl_label", "lbl_label_blocks_noalloc", "lbl_roadmap_autotune",
     "lbl_session_create", "lbl_session_run", "lbl_session_free",
+    "lbl_batch_create", "lbl_batch_set_frames", "lbl_batch_launch", "lbl_batch_free",
 )
 
 
@@ -61,6 +65,11 @@ class lbl_grid(ctypes.Structure):
 
 class lbl_pose(ctypes.Structure):
     _fields_ = [("x", ctypes.c_double), ("y", ctypes.c_double), ("theta", ctypes.c_double)]
+
+
+class lbl_frame(ctypes.Structure):
+    _fields_ = [("world", lbl_grid), ("d_planes", ctypes.c_void_p), ("pose", lbl_pose), ("d_O", ctypes.c_void_p),
+                ("d_L", ctypes.c_void_p), ("d_next", ctypes.c_void_p), ("d_viol", ctypes.c_void_p)]
 
 
 class lbl_config(ctypes.Structure):
@@ -104,6 +113,10 @@ def load(build_if_needed: bool = True):
         "lbl_session_create": (ctypes.c_int, [p, G, i32, p, ctypes.POINTER(lbl_config), ctypes.POINTER(p)]),
         "lbl_session_run": (ctypes.c_int, [p, p, lbl_pose, p, p, p, p]),
         "lbl_session_free": (ctypes.c_int, [p]),
+        "lbl_batch_create": (ctypes.c_int, [i32, p, p, p, i32, ctypes.POINTER(p)]),
+        "lbl_batch_set_frames": (ctypes.c_int, [p, ctypes.POINTER(lbl_frame)]),
+        "lbl_batch_launch": (ctypes.c_int, [p, u32, p]),
+        "lbl_batch_free": (ctypes.c_int, [p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -300,3 +313,37 @@ def lbl_session_run(ss, h_planes, pose, h_L, h_next=None, h_viol=None, stream=No
 
 def lbl_session_free(ss) -> None:
     _check(load().lbl_session_free(ss))
+
+
+def lbl_batch_create(rms, n_props, mons=None, ctas_per_sm: int = 0) -> int:
+    """Plan one batched launch over these roadmaps (one frame each)."""
+    n = len(rms)
+    R = (ctypes.c_void_p * n)(*rms)
+    Pn = (ctypes.c_int32 * n)(*[int(p) for p in n_props])
+    M = (ctypes.c_void_p * n)(*(mons if mons is not None else [None] * n))
+    out = ctypes.c_void_p()
+    _check(load().lbl_batch_create(n, R, Pn, M, int(ctas_per_sm), ctypes.byref(out)))
+    return out.value
+
+
+def lbl_batch_set_frames(b, frames) -> None:
+    """frames: list of dicts with world, d_planes, pose, d_O, d_L[, d_next, d_viol]."""
+    arr = (lbl_frame * len(frames))()
+    for i, f in enumerate(frames):
+        arr[i].world = _grid(f["world"])
+        arr[i].d_planes = _dev(f["d_planes"], "uint8", "planes")
+        arr[i].pose = _pose(f["pose"])
+        arr[i].d_O = _dev(f["d_O"], "uint64", "O")
+        arr[i].d_L = _dev(f["d_L"], "uint64", "L")
+        arr[i].d_next = _dev(f.get("d_next"), "uint64", "next")
+        arr[i].d_viol = _dev(f.get("d_viol"), "uint16", "viol")
+    _check(load().lbl_batch_set_frames(b, arr))
+
+
+def lbl_batch_launch(b, stages: int = 3, stream=None) -> None:
+    """stages: LBL_STAGE_TRANSFORM | LBL_STAGE_LABEL (default both)."""
+    _check(load().lbl_batch_launch(b, int(stages), _stream(stream)))
+
+
+def lbl_batch_free(b) -> None:
+    _check(load().lbl_batch_free(b))

@@ -322,3 +322,57 @@ def make(name: str, seed: int = 0, edges: int | None = None, threads: int = 0, *
         mon = random_monitor(rng, r["monitor"][0], r["monitor"][1], P)
     return Workload(name, agent, world, P, arcs, r["radius"], rowptr, colidx, planes, pose, mon,
                     meta=dict(seed=seed, recipe=r))
+
+
+# ------------------------------------------------------------- batched frames
+
+@dataclass
+class BatchFrame:
+    """One frame of a batch: a roadmap (rows of a master pool), its world planes
+    (the first P planes of the pool's), P and a pose."""
+    agent: Grid
+    world: Grid
+    P: int
+    rowptr: np.ndarray
+    colidx: np.ndarray
+    planes: np.ndarray
+    pose: tuple
+    grid_key: int
+
+    @property
+    def n_edges(self) -> int:
+        return self.rowptr.shape[0] - 1
+
+    @property
+    def nnz(self) -> int:
+        return int(self.rowptr[-1])
+
+
+def make_batch(seed: int = 0, frames: int = 64, edges=(10_000, 500_000), grids=(128, 256, 512), res: float = 0.25,
+               props=(8, 64), threads: int = 0):
+    """`frames` agents/frames with roadmaps of log-uniform size in `edges`, grids
+    from `grids` at `res` (z-order), propositions U{props}; driving arc law.
+    Roadmaps are the first rows of one master pool per grid size, planes the
+    first P of one 64-proposition set per grid size."""
+    rng = np.random.default_rng(seed)
+    sizes = np.exp(rng.uniform(np.log(edges[0]), np.log(edges[1]), size=frames)).astype(np.int64)
+    keys = rng.integers(0, len(grids), size=frames)
+    Ps = rng.integers(props[0], props[1] + 1, size=frames)
+    pools = {}
+    for k in sorted(set(int(x) for x in keys)):
+        n = grids[k]
+        agent = agent_grid(n, res, MORTON)
+        world = world_grid(n, n, res)
+        n_max = int(sizes[keys == k].max())
+        arcs = sample_arcs(rng, n_max, agent, (-0.3, 0.3), (5.0, 40.0))
+        rowptr, colidx = sweep_csr(arcs, 1.2, agent, threads)
+        planes = planes_mixed(rng, props[1], world)
+        pools[k] = (agent, world, rowptr, colidx, planes)
+    out = []
+    for i in range(frames):
+        agent, world, rowptr, colidx, planes = pools[int(keys[i])]
+        E = int(sizes[i])
+        rp = rowptr[: E + 1]
+        out.append(BatchFrame(agent, world, int(Ps[i]), rp, colidx[: int(rp[-1])], planes[: int(Ps[i])],
+                              random_pose(rng, world), int(keys[i])))
+    return out
