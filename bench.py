@@ -47,6 +47,9 @@ WORKLOADS = {
     "plain": "2,000 arcs on a 64x64 grid at 0.5 m (z-order), 4 disc propositions",
     "paper": "1,097,702 short arcs on a 2048x1024 row-major grid at 0.1 m (2^21 cells), 2 propositions at ~1 % and "
              "~90 % fill",
+    "serving": "request loop: Poisson arrivals at 2,000 req/s, each a random pose + 32 world planes (256x256 at "
+               "0.25 m) against one of 8 resident roadmaps of 20k-1M edges; continuous batching over 2 lanes vs one "
+               "request per launch; latency = scheduled arrival to labels in host memory",
     "batched": "64 frames/agents with roadmaps of log-uniform 10k-500k edges on 128^2-512^2 z-order grids at 0.25 m, "
                "8-64 propositions each, one CUDA-graph replay of the batched launch per step vs 64 frame-by-frame "
                "transform+label call pairs",
@@ -265,6 +268,11 @@ def main():
     import paper_1810_02612_gb300 as L
     from paper_1810_02612_gb300.lbl import lbl_config
 
+    if args.workload == "serving":
+        run_serving(args, rank, world, local, dist, torch, L)
+        if dist:
+            dist.destroy_process_group()
+        return
     if args.workload == "batched":
         run_batched(args, rank, world, local, dist, torch, L)
         if dist:
@@ -527,6 +535,96 @@ def run_batched(args, rank, world, local, dist, torch, L):
         }
         print(json.dumps(line), flush=True)
     L.lbl_batch_free(b)
+    for r in rms:
+        L.lbl_roadmap_free(r)
+
+
+def run_serving(args, rank, world, local, dist, torch, L):
+    """Poisson request stream against 8 resident roadmaps; the same stream is
+    served with continuous batching and with one request per launch."""
+    import threading
+    rate = 2000.0
+    sizes = [20_000, 35_000, 61_000, 107_000, 187_000, 327_000, 572_000, 1_000_000]
+    t_gen = time.perf_counter()
+    rng = np.random.default_rng(rank_seed(args.seed, rank))
+    agent = synth.agent_grid(256, 0.25, synth.MORTON)
+    wgrid = synth.world_grid(256, 256, 0.25)
+    arcs = synth.sample_arcs(rng, sizes[-1], agent, (-0.3, 0.3), (5.0, 40.0))
+    rowptr, colidx = synth.sweep_csr(arcs, 1.2, agent, cpu_cores())
+    P = 32
+    plane_sets = [torch.from_numpy(synth.planes_mixed(rng, P, wgrid)).pin_memory() for _ in range(8)]
+    t_gen = time.perf_counter() - t_gen
+    rms = [L.lbl_roadmap_upload(agent, rowptr[: n + 1], colidx[: int(rowptr[n])]) for n in sizes]
+    n_req = args.steps if args.steps >= 1000 else 20_000
+    warm = min(args.warmup * 100, n_req // 10)
+    gaps = rng.exponential(1.0 / rate, size=n_req)
+    which = rng.integers(0, len(sizes), size=n_req)
+    sets = rng.integers(0, len(plane_sets), size=n_req)
+    poses = [synth.random_pose(rng, wgrid) for _ in range(n_req)]
+    ring = 256
+    outs = [torch.empty(sizes[-1], dtype=torch.uint64).pin_memory() for _ in range(ring)]
+
+    def serve(max_batch):
+        srv = L.lbl_server_create(rms, [P] * len(sizes), None, lanes=2, mem_budget=4 << 30, max_batch=max_batch)
+        tickets = [None] * n_req
+        lat = np.zeros(n_req)
+        done_t = np.zeros(n_req)
+        submitted = threading.Semaphore(0)
+
+        def waiter():
+            for i in range(n_req):
+                submitted.acquire()
+                lat[i] = L.lbl_server_wait(srv, tickets[i], 60000) / 1e6
+                done_t[i] = time.monotonic_ns()
+
+        th = threading.Thread(target=waiter)
+        th.start()
+        t0 = time.monotonic_ns() + 20_000_000
+        arrival = t0 + np.cumsum(gaps * 1e9).astype(np.int64)
+        for i in range(n_req):
+            while time.monotonic_ns() < arrival[i]:
+                pass
+            if i >= ring:  # the output buffer of request i - ring is free again
+                while done_t[i - ring] == 0:
+                    time.sleep(0)
+            k = int(which[i])
+            tickets[i] = L.lbl_server_submit(srv, k, wgrid, plane_sets[int(sets[i])], poses[i],
+                                             outs[i % ring][: sizes[k]], arrival_ns=int(arrival[i]))
+            submitted.release()
+        th.join()
+        st = L.lbl_server_stats(srv)
+        L.lbl_server_free(srv)
+        sel = slice(warm, n_req)
+        span_s = (done_t[n_req - 1] - arrival[warm]) / 1e9
+        labels = float(sum(sizes[int(k)] for k in which[sel])) * P
+        return {"labels_per_s": labels / span_s, "p50_ms": float(np.percentile(lat[sel], 50)),
+                "p99_ms": float(np.percentile(lat[sel], 99)), "p999_ms": float(np.percentile(lat[sel], 99.9)),
+                "mean_ms": float(lat[sel].mean()), "achieved_req_per_s": (n_req - warm) / span_s,
+                "batches": st["batches"], "mean_batch": n_req / max(st["batches"], 1), "max_batch": st["max_batch"]}
+
+    clocks = ClockSampler(local, enabled=not args.no_clocks and rank == 0)
+    t0 = time.time()
+    cont = serve(128)
+    t1 = time.time()
+    clk = clocks.stop(t0, t1)
+    plain = serve(1)
+    value = cont["labels_per_s"]
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": n_req, "warmup": warm,
+            "ms_per_step": cont["mean_ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u64", "data": "synthetic",
+            "config": {"workload": WORKLOADS["serving"], "name": "serving", "requests": n_req, "rate_req_s": rate,
+                       "roadmap_edges": sizes, "nnz_largest": int(rowptr[-1]), "props": P,
+                       "parallelism": f"replicas x{world}"},
+            "serving": {"continuous_batching": cont, "one_request_per_launch": plain,
+                        "p99_speedup": plain["p99_ms"] / cont["p99_ms"]},
+            "latency_ms": {"p50": cont["p50_ms"], "p99": cont["p99_ms"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": P * wgrid.cells,
+                    "d2h_bytes_per_step": int(8 * np.mean([sizes[int(k)] for k in which]))},
+            "clocks": clk, "setup_s": {"generate": t_gen},
+        }
+        print(json.dumps(line), flush=True)
     for r in rms:
         L.lbl_roadmap_free(r)
 

@@ -100,6 +100,7 @@ typedef struct lbl_roadmap_s *lbl_roadmap;
 typedef struct lbl_monitor_s *lbl_monitor;
 typedef struct lbl_session_s *lbl_session;
 typedef struct lbl_batch_s *lbl_batch;
+typedef struct lbl_server_s *lbl_server;
 
 /* Message describing the last failure on the calling thread ("" if none).
    The pointer stays valid until the thread's next lbl_* call. */
@@ -308,6 +309,52 @@ int lbl_batch_set_frames(lbl_batch b, const lbl_frame *frames);
 #define LBL_STAGE_LABEL 2u
 int lbl_batch_launch(lbl_batch b, uint32_t stages, lbl_stream s);
 int lbl_batch_free(lbl_batch b);
+
+/* ---------------------------------------------------------------- server */
+
+/*
+ * A serving loop with continuous batching.  The roadmaps stay resident; each
+ * request is one planning query (Sec. 5): a pose and world proposition planes
+ * in host memory, answered with the labels (and monitor outputs) of one
+ * roadmap, copied back to host memory.  A scheduler thread inside the library
+ *   - admits requests first come first served into a device arena of
+ *     `mem_budget` bytes (planes, agent words and outputs of each request), so
+ *     a request waits until memory frees up;
+ *   - whenever one of `lanes` execution lanes (CUDA streams) is free, launches
+ *     everything admitted so far (up to 128 requests) as one batch: copies in,
+ *     one batched frame-transform launch, one batched labeling launch over
+ *     work units precomputed per roadmap, copies out.  Requests that arrive
+ *     while batches run join the next batch, and batches on different lanes
+ *     overlap on the device.  max_batch = 1 gives the plain form: one request
+ *     per launch pair.
+ * Every request's outputs equal what lbl_session_run returns for it alone.
+ *
+ * lbl_server_create  n resident roadmaps (1..), their proposition counts and
+ *                    optional monitors (mons may be NULL), 1..16 lanes, the
+ *                    largest batch (1..128), arena bytes.  Allocates everything
+ *                    the loop needs up front.
+ * lbl_server_submit  queue a request against roadmap `roadmap`: h_planes
+ *                    uint8[n_props][world.h][world.w]; outputs h_L uint64[E],
+ *                    h_next/h_viol (monitor only, may be NULL).  All host
+ *                    buffers must stay valid until the request completes; use
+ *                    pinned memory for asynchronous copies.  arrival_ns: the
+ *                    request's arrival on CLOCK_MONOTONIC (0 = now), the start
+ *                    of its latency.  LBL_ENOMEM if it can never fit the arena.
+ * lbl_server_wait    block up to timeout_ms for a ticket (LBL_ETIMEOUT
+ *                    otherwise); on return the outputs are in host memory and
+ *                    *latency_ns = completion - arrival.  Each ticket is waited
+ *                    for once.
+ * lbl_server_stats   batches launched, requests completed, largest batch,
+ *                    arena bytes in use (any pointer may be NULL).
+ * lbl_server_free    stop the loop after the batches in flight, release all.
+ */
+int lbl_server_create(int32_t n, const lbl_roadmap *rms, const int32_t *n_props, const lbl_monitor *mons,
+                      int32_t lanes, int32_t max_batch, int64_t mem_budget, lbl_server *out);
+int lbl_server_submit(lbl_server srv, int32_t roadmap, const lbl_grid *world, const uint8_t *h_planes, lbl_pose pose,
+                      uint64_t *h_L, uint64_t *h_next, uint16_t *h_viol, int64_t arrival_ns, int64_t *ticket);
+int lbl_server_wait(lbl_server srv, int64_t ticket, int64_t timeout_ms, int64_t *latency_ns);
+int lbl_server_stats(lbl_server srv, int64_t *batches, int64_t *completed, int64_t *max_batch, int64_t *arena_used);
+int lbl_server_free(lbl_server srv);
 
 /* --------------------------------------------------------------- session */
 

@@ -65,6 +65,38 @@ bool same_device(int dev) {
   return true;
 }
 
+template <typename T>
+cudaError_t dev_alloc(T **p, size_t count, int64_t *bytes) {
+  const size_t b = count * sizeof(T);
+  cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), b ? b : 16);
+  if (e == cudaSuccess && bytes) *bytes += static_cast<int64_t>(b);
+  return e;
+}
+
+void free_roadmap(Roadmap *rm) {
+  if (!rm) return;
+  cudaFree(rm->rowptr);
+  cudaFree(rm->colidx);
+  cudaFree(rm->bt_rowptr);
+  cudaFree(rm->bt_block);
+  cudaFree(rm->bt_mask);
+  cudaFree(rm->planes);
+  cudaFree(rm->part);
+  cudaFree(rm->err);
+  delete rm;
+}
+
+int resolve_lpe(const Roadmap &rm, const lbl_config *cfg) {
+  int lpe = cfg ? cfg->lanes_per_edge : 0;
+  if (lpe == 4 || lpe == 8 || lpe == 16 || lpe == 32) return lpe;
+  const double avg = rm.E ? static_cast<double>(rm.nnz) / static_cast<double>(rm.E) : 0.0;
+  lpe = 4;
+  while (lpe < 32 && lpe * 16 < avg) lpe *= 2;
+  return lpe;
+}
+
+}  // namespace
+
 // Q32.32 coefficients of (ix, iy) -> continuous world-cell coordinates:
 //   u = a00*ix + a01*iy + b0,  v = a10*ix + a11*iy + b1,
 // from world point q = (X, Y) + R(theta) * centre(ix, iy) (Sec. 5, eq. 13).
@@ -102,38 +134,6 @@ bool frame_map(const lbl_grid &W, const lbl_grid &A, const lbl_pose &p, FrameMap
   return true;
 }
 
-template <typename T>
-cudaError_t dev_alloc(T **p, size_t count, int64_t *bytes) {
-  const size_t b = count * sizeof(T);
-  cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), b ? b : 16);
-  if (e == cudaSuccess && bytes) *bytes += static_cast<int64_t>(b);
-  return e;
-}
-
-void free_roadmap(Roadmap *rm) {
-  if (!rm) return;
-  cudaFree(rm->rowptr);
-  cudaFree(rm->colidx);
-  cudaFree(rm->bt_rowptr);
-  cudaFree(rm->bt_block);
-  cudaFree(rm->bt_mask);
-  cudaFree(rm->planes);
-  cudaFree(rm->part);
-  cudaFree(rm->err);
-  delete rm;
-}
-
-int resolve_lpe(const Roadmap &rm, const lbl_config *cfg) {
-  int lpe = cfg ? cfg->lanes_per_edge : 0;
-  if (lpe == 4 || lpe == 8 || lpe == 16 || lpe == 32) return lpe;
-  const double avg = rm.E ? static_cast<double>(rm.nnz) / static_cast<double>(rm.E) : 0.0;
-  lpe = 4;
-  while (lpe < 32 && lpe * 16 < avg) lpe *= 2;
-  return lpe;
-}
-
-}  // namespace
-
 void set_error(const char *fmt, ...) {
   char buf[512];
   va_list ap;
@@ -151,9 +151,6 @@ int cuda_fail(cudaError_t e, const char *what) {
 }  // namespace lbl
 
 using namespace lbl;
-
-struct lbl_roadmap_s : Roadmap {};
-struct lbl_monitor_s : Monitor {};
 struct lbl_batch_s {
   int device = 0;
   int num_sms = 1;

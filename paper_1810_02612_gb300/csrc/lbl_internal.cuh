@@ -119,6 +119,10 @@ struct FrameMap {
   int64_t A00, A01, B0, A10, A11, B1;  // Q32.32
 };
 
+// Fixed-point map of the equivariant frame transform (world grid W, agent
+// grid A, pose p); false (with the error set) if it could overflow.
+bool frame_map(const lbl_grid &W, const lbl_grid &A, const lbl_pose &p, FrameMap *out);
+
 cudaError_t launch_frame_transform(const FrameMap &m, const uint8_t *planes, int32_t ww, int32_t wh, int32_t P,
                                    int32_t aw, int32_t ah, int32_t order, uint64_t *O, int num_sms, cudaStream_t s);
 
@@ -156,3 +160,7 @@ cudaError_t launch_bt_fill(const int64_t *rowptr, const int32_t *colidx, int64_t
                            uint32_t *bt_block, uint64_t *bt_mask, cudaStream_t s);
 
 }  // namespace lbl
+
+// The opaque handles of the C ABI are the internal objects.
+struct lbl_roadmap_s : lbl::Roadmap {};
+struct lbl_monitor_s : lbl::Monitor {};

@@ -49,6 +49,7 @@ EXPORTS = (
     "lbl_label", "lbl_label_blocks_noalloc", "lbl_roadmap_autotune",
     "lbl_session_create", "lbl_session_run", "lbl_session_free",
     "lbl_batch_create", "lbl_batch_set_frames", "lbl_batch_launch", "lbl_batch_free",
+    "lbl_server_create", "lbl_server_submit", "lbl_server_wait", "lbl_server_stats", "lbl_server_free",
 )
 
 
@@ -117,6 +118,11 @@ def load(build_if_needed: bool = True):
         "lbl_batch_set_frames": (ctypes.c_int, [p, ctypes.POINTER(lbl_frame)]),
         "lbl_batch_launch": (ctypes.c_int, [p, u32, p]),
         "lbl_batch_free": (ctypes.c_int, [p]),
+        "lbl_server_create": (ctypes.c_int, [i32, p, p, p, i32, i32, i64, ctypes.POINTER(p)]),
+        "lbl_server_submit": (ctypes.c_int, [p, i32, G, p, lbl_pose, p, p, p, i64, ctypes.POINTER(i64)]),
+        "lbl_server_wait": (ctypes.c_int, [p, i64, i64, ctypes.POINTER(i64)]),
+        "lbl_server_stats": (ctypes.c_int, [p, p, p, p, p]),
+        "lbl_server_free": (ctypes.c_int, [p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -347,3 +353,42 @@ def lbl_batch_launch(b, stages: int = 3, stream=None) -> None:
 
 def lbl_batch_free(b) -> None:
     _check(load().lbl_batch_free(b))
+
+
+def lbl_server_create(rms, n_props, mons=None, lanes: int = 2, mem_budget: int = 1 << 30, max_batch: int = 128) -> int:
+    """Start a serving loop over these resident roadmaps."""
+    n = len(rms)
+    R = (ctypes.c_void_p * n)(*rms)
+    Pn = (ctypes.c_int32 * n)(*[int(p) for p in n_props])
+    M = (ctypes.c_void_p * n)(*(mons if mons is not None else [None] * n))
+    out = ctypes.c_void_p()
+    _check(load().lbl_server_create(n, R, Pn, M, int(lanes), int(max_batch), int(mem_budget), ctypes.byref(out)))
+    return out.value
+
+
+def lbl_server_submit(srv, roadmap: int, world, h_planes, pose, h_L, h_next=None, h_viol=None,
+                      arrival_ns: int = 0) -> int:
+    """Queue one request; returns its ticket.  Host buffers must outlive it."""
+    t = ctypes.c_int64()
+    w = _grid(world)
+    _check(load().lbl_server_submit(srv, int(roadmap), ctypes.byref(w), _host(h_planes, np.uint8, "planes"),
+                                    _pose(pose), _host(h_L, np.uint64, "L"), _host(h_next, np.uint64, "next"),
+                                    _host(h_viol, np.uint16, "viol"), int(arrival_ns), ctypes.byref(t)))
+    return t.value
+
+
+def lbl_server_wait(srv, ticket: int, timeout_ms: int = 10000) -> int:
+    """Wait for a ticket; returns its latency in ns (arrival to host-visible)."""
+    lat = ctypes.c_int64()
+    _check(load().lbl_server_wait(srv, int(ticket), int(timeout_ms), ctypes.byref(lat)))
+    return lat.value
+
+
+def lbl_server_stats(srv) -> dict:
+    v = [ctypes.c_int64() for _ in range(4)]
+    _check(load().lbl_server_stats(srv, *[ctypes.byref(x) for x in v]))
+    return dict(zip(("batches", "completed", "max_batch", "arena_used"), [x.value for x in v]))
+
+
+def lbl_server_free(srv) -> None:
+    _check(load().lbl_server_free(srv))
