@@ -73,6 +73,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--rates", default="2000,3500,5000", help="serving: request rates (req/s); the first is the "
+                    "configured rate of the headline line, the others a saturation sweep")
     return ap.parse_args()
 
 
@@ -543,7 +545,8 @@ def run_serving(args, rank, world, local, dist, torch, L):
     """Poisson request stream against 8 resident roadmaps; the same stream is
     served with continuous batching and with one request per launch."""
     import threading
-    rate = 2000.0
+    rates = [float(x) for x in args.rates.split(",")]
+    rate = rates[0]
     sizes = [20_000, 35_000, 61_000, 107_000, 187_000, 327_000, 572_000, 1_000_000]
     t_gen = time.perf_counter()
     rng = np.random.default_rng(rank_seed(args.seed, rank))
@@ -555,16 +558,17 @@ def run_serving(args, rank, world, local, dist, torch, L):
     plane_sets = [torch.from_numpy(synth.planes_mixed(rng, P, wgrid)).pin_memory() for _ in range(8)]
     t_gen = time.perf_counter() - t_gen
     rms = [L.lbl_roadmap_upload(agent, rowptr[: n + 1], colidx[: int(rowptr[n])]) for n in sizes]
-    n_req = args.steps if args.steps >= 1000 else 20_000
-    warm = min(args.warmup * 100, n_req // 10)
-    gaps = rng.exponential(1.0 / rate, size=n_req)
-    which = rng.integers(0, len(sizes), size=n_req)
-    sets = rng.integers(0, len(plane_sets), size=n_req)
-    poses = [synth.random_pose(rng, wgrid) for _ in range(n_req)]
+    n_max = args.steps if args.steps >= 1000 else 20_000
+    unit_gaps = rng.exponential(1.0, size=n_max)  # scaled by 1/rate per run
+    which = rng.integers(0, len(sizes), size=n_max)
+    sets = rng.integers(0, len(plane_sets), size=n_max)
+    poses = [synth.random_pose(rng, wgrid) for _ in range(n_max)]
     ring = 256
     outs = [torch.empty(sizes[-1], dtype=torch.uint64).pin_memory() for _ in range(ring)]
 
-    def serve(max_batch):
+    def serve(max_batch, rate, n_req):
+        warm = min(args.warmup * 100, n_req // 10)
+        gaps = unit_gaps[:n_req] / rate
         srv = L.lbl_server_create(rms, [P] * len(sizes), None, lanes=2, mem_budget=4 << 30, max_batch=max_batch)
         tickets = [None] * n_req
         lat = np.zeros(n_req)
@@ -597,31 +601,38 @@ def run_serving(args, rank, world, local, dist, torch, L):
         sel = slice(warm, n_req)
         span_s = (done_t[n_req - 1] - arrival[warm]) / 1e9
         labels = float(sum(sizes[int(k)] for k in which[sel])) * P
-        return {"labels_per_s": labels / span_s, "p50_ms": float(np.percentile(lat[sel], 50)),
+        return {"rate_req_s": rate, "requests": n_req, "warmup": warm,
+                "labels_per_s": labels / span_s, "p50_ms": float(np.percentile(lat[sel], 50)),
                 "p99_ms": float(np.percentile(lat[sel], 99)), "p999_ms": float(np.percentile(lat[sel], 99.9)),
                 "mean_ms": float(lat[sel].mean()), "achieved_req_per_s": (n_req - warm) / span_s,
                 "batches": st["batches"], "mean_batch": n_req / max(st["batches"], 1), "max_batch": st["max_batch"]}
 
     clocks = ClockSampler(local, enabled=not args.no_clocks and rank == 0)
     t0 = time.time()
-    cont = serve(128)
+    cont = serve(128, rate, n_max)
     t1 = time.time()
     clk = clocks.stop(t0, t1)
-    plain = serve(1)
+    plain = serve(1, rate, n_max)
+    sweep = []
+    for r in rates[1:]:
+        n = min(n_max, 10_000)
+        c, p = serve(128, r, n), serve(1, r, n)
+        sweep.append({"rate_req_s": r, "continuous_batching": c, "one_request_per_launch": p,
+                      "throughput_gain": c["labels_per_s"] / p["labels_per_s"], "p99_gain": p["p99_ms"] / c["p99_ms"]})
     value = cont["labels_per_s"]
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": n_req, "warmup": warm,
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": n_max, "warmup": cont["warmup"],
             "ms_per_step": cont["mean_ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "u64", "data": "synthetic",
-            "config": {"workload": WORKLOADS["serving"], "name": "serving", "requests": n_req, "rate_req_s": rate,
+            "config": {"workload": WORKLOADS["serving"], "name": "serving", "requests": n_max, "rate_req_s": rate,
                        "roadmap_edges": sizes, "nnz_largest": int(rowptr[-1]), "props": P,
                        "parallelism": f"replicas x{world}"},
             "serving": {"continuous_batching": cont, "one_request_per_launch": plain,
-                        "p99_speedup": plain["p99_ms"] / cont["p99_ms"]},
+                        "p99_gain": plain["p99_ms"] / cont["p99_ms"], "saturation_sweep": sweep},
             "latency_ms": {"p50": cont["p50_ms"], "p99": cont["p99_ms"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": P * wgrid.cells,
-                    "d2h_bytes_per_step": int(8 * np.mean([sizes[int(k)] for k in which]))},
+                    "d2h_bytes_per_step": int(8 * np.mean([sizes[int(k)] for k in which[:n_max]]))},
             "clocks": clk, "setup_s": {"generate": t_gen},
         }
         print(json.dumps(line), flush=True)
