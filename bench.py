@@ -63,11 +63,13 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--algo", default="auto", choices=["auto", "csr", "bittile"])
+    ap.add_argument("--algo", default="csr", choices=["auto", "csr", "bittile", "sector"],
+                    help="labeling form; auto = measure every form on the first frame and keep the fastest")
     ap.add_argument("--lanes", type=int, default=0)
     ap.add_argument("--early-exit", type=int, default=-1)
     ap.add_argument("--pipeline", type=int, default=0, help="1 registers, 2 bulk copies, 3 cp.async")
     ap.add_argument("--ctas", type=int, default=0)
+    ap.add_argument("--depth", type=int, default=0)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--edges", type=int, default=None, help="shrink the workload (not for reported numbers)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle baseline")
@@ -167,11 +169,13 @@ def measured_peaks():
         return None
 
 
-def label_bytes(wl, algo: str, n_bt: int | None, with_monitor: bool) -> int:
+def label_bytes(wl, algo: str, n_bt: int | None, with_monitor: bool, n_sec: int | None = None) -> int:
     """Algorithmic HBM bytes of one labeling launch (each array read or written
     once; O and the bit planes counted once although they are re-read from L2)."""
     E = wl.n_edges
     out = 8 * E + (10 * E if with_monitor else 0)
+    if algo == "sector":
+        return 4 * n_sec + 8 * (E + 1) + 8 * wl.agent.cells + out
     if algo == "bittile":
         blocks = (wl.agent.cells + 63) // 64
         return 12 * n_bt + 8 * (E + 1) + 8 * wl.agent.cells + 8 * wl.P * blocks + out
@@ -285,17 +289,18 @@ def main():
     t_gen = time.perf_counter()
     wl = synth.make(args.workload, seed=rank_seed(args.seed, rank), edges=args.edges, threads=cpu_cores())
     t_gen = time.perf_counter() - t_gen
-    algo = {"auto": L.LBL_ALGO_AUTO, "csr": L.LBL_ALGO_CSR, "bittile": L.LBL_ALGO_BITTILE}[args.algo]
-    want_bt = args.algo in ("auto", "bittile")
+    algo = {"auto": L.LBL_ALGO_AUTO, "csr": L.LBL_ALGO_CSR, "bittile": L.LBL_ALGO_BITTILE,
+            "sector": L.LBL_ALGO_SECTOR}[args.algo]
+    flags = ((L.LBL_UPLOAD_BITTILE if args.algo in ("auto", "bittile") else 0)
+             | (L.LBL_UPLOAD_SECTOR if args.algo in ("auto", "sector") else 0))
     stream = torch.cuda.Stream()
-    rm = L.lbl_roadmap_upload(wl.agent, wl.rowptr, wl.colidx, flags=L.LBL_UPLOAD_BITTILE if want_bt else 0,
-                              stream=stream)
+    rm = L.lbl_roadmap_upload(wl.agent, wl.rowptr, wl.colidx, flags=flags, stream=stream)
     mon = None
     if wl.monitor is not None:
         m = wl.monitor
         mon = L.lbl_monitor_create(m.n_states, m.m, m.relbits, m.delta, m.reject)
     E, P = wl.n_edges, wl.P
-    cfg = lbl_config(algo, args.lanes, args.early_exit, args.ctas, args.pipeline)
+    cfg = lbl_config(algo, args.lanes, args.early_exit, args.ctas, args.pipeline, args.depth)
     with torch.cuda.stream(stream):
         d_planes = torch.from_numpy(wl.planes).to("cuda", non_blocking=False)
         d_O = torch.empty(wl.agent.cells, dtype=torch.uint64, device="cuda")
@@ -315,7 +320,7 @@ def main():
     if args.algo == "auto":
         L.lbl_frame_transform(wl.world, d_planes, P, wl.pose, wl.agent, d_O, stream=stream)
         tuned = L.lbl_roadmap_autotune(rm, d_O, P, d_L, mon, d_next, d_viol, reps=5, stream=stream)
-        used = "bittile" if tuned["algo"] == L.LBL_ALGO_BITTILE else "csr"
+        used = {L.LBL_ALGO_BITTILE: "bittile", L.LBL_ALGO_SECTOR: "sector"}.get(tuned["algo"], "csr")
     else:
         used = args.algo
     launches_per_step = 2 + (1 if used == "bittile" else 0)
@@ -379,8 +384,8 @@ def main():
     L.lbl_session_free(ss)
 
     # ---- roofline of the dominant kernel (labeling)
-    n_bt = L.lbl_roadmap_info(rm)[2]
-    lb = label_bytes(wl, used, n_bt, mon is not None)
+    info = L.lbl_roadmap_info(rm)
+    lb = label_bytes(wl, used, info[2], mon is not None, info[3])
     label_avg_s = float(label_ms.mean()) / 1e3
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0

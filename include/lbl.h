@@ -78,6 +78,9 @@ typedef struct {
 #define LBL_ALGO_AUTO 0    /* pick from the roadmap's shape and n_props */
 #define LBL_ALGO_CSR 1     /* gather-OR over the CSR cell lists */
 #define LBL_ALGO_BITTILE 2 /* AND over per-edge 64-cell block masks */
+#define LBL_ALGO_SECTOR 3  /* gather-OR over per-edge 4-cell sectors (compressed A):
+                              one u32 (sector << 4 | cell mask) per touched 32-byte
+                              sector of O; needs O 32-byte aligned */
 
 typedef struct {
   int32_t algo;           /* LBL_ALGO_* */
@@ -89,6 +92,9 @@ typedef struct {
                              0 or -1 = off */
   int32_t ctas_per_sm;    /* persistent grid size per SM, 0 = auto */
   int32_t pipeline;       /* streaming CSR index stream (LBL_PIPE_*), 0 = default */
+  int32_t depth;          /* register pipelines: groups of 32 entries in flight per
+                             warp; CSR 8 (default), 12 or 16; sector form 4 (default)
+                             or 8.  Deeper variants run fewer CTAs per SM */
 } lbl_config;
 
 /* How the streaming CSR form moves each warp's column indices from HBM. */
@@ -114,6 +120,9 @@ int lbl_version(void);
 #define LBL_UPLOAD_DEVICE_PTRS 1u /* rowptr/colidx are device pointers (default: host) */
 #define LBL_UPLOAD_BITTILE 2u     /* also derive the 64-cell block form used by
                                      LBL_ALGO_BITTILE (costs ~12 B per touched block) */
+#define LBL_UPLOAD_SECTOR 4u      /* also derive the 4-cell sector form used by
+                                     LBL_ALGO_SECTOR (4 B per touched sector; grids of
+                                     at most 2^30 cells) */
 
 /*
  * lbl_roadmap_upload — make a roadmap resident on the device.
@@ -144,10 +153,10 @@ int lbl_roadmap_free(lbl_roadmap rm);
 int lbl_roadmap_status(lbl_roadmap rm, lbl_stream s);
 
 /* Shape of a roadmap: edges, nonzeros, (block, mask) entries of the block form
-   (0 without LBL_UPLOAD_BITTILE) and device bytes held.  Any out pointer may be
-   NULL. */
+   (0 without LBL_UPLOAD_BITTILE), entries of the sector form (0 without
+   LBL_UPLOAD_SECTOR) and device bytes held.  Any out pointer may be NULL. */
 int lbl_roadmap_info(lbl_roadmap rm, int64_t *n_edges, int64_t *nnz, int64_t *n_block_entries,
-                     int64_t *device_bytes);
+                     int64_t *n_sector_entries, int64_t *device_bytes);
 
 /* ------------------------------------------------------- frame transform */
 
@@ -209,8 +218,8 @@ int lbl_monitor_step(lbl_monitor mon, const uint64_t *d_L, int64_t n, uint64_t *
  *   n_props  0..64
  *   d_L      uint64[n_edges]
  *   cfg      NULL = defaults (LBL_ALGO_AUTO)
- * LBL_ALGO_BITTILE needs a roadmap uploaded with LBL_UPLOAD_BITTILE
- * (LBL_EUNSUPPORTED otherwise).  The roadmap holds per-launch working memory,
+ * LBL_ALGO_BITTILE / LBL_ALGO_SECTOR need a roadmap uploaded with
+ * LBL_UPLOAD_BITTILE / LBL_UPLOAD_SECTOR (LBL_EUNSUPPORTED otherwise).  The roadmap holds per-launch working memory,
  * so two lbl_label calls on the same roadmap must not overlap on the device.
  */
 int lbl_label(lbl_roadmap rm, const uint64_t *d_O, int32_t n_props, uint64_t *d_L, lbl_monitor mon, uint64_t *d_next,
@@ -255,7 +264,8 @@ int lbl_label_blocks_noalloc(const int64_t *d_block_rowptr, const uint32_t *d_bl
  * (the two forms of Sec. 4.3 and their variants compute the same eq. 10; which
  * is fastest depends on the roadmap, the grid order and n_props).  Every
  * applicable variant (streaming CSR with each LBL_PIPE_*, lane groups of 8, 16
- * and 32, and the block form if the roadmap has it) labels d_O once untimed and
+ * and 32, and the block and sector forms if the roadmap has them) labels d_O
+ * once untimed and
  * `reps` times timed with CUDA events on `s`; the fastest becomes what
  * LBL_ALGO_AUTO runs for this n_props on this roadmap.  d_L (and d_next/d_viol
  * with a monitor) receive labels as lbl_label writes them.  *chosen (may be

@@ -140,10 +140,18 @@ __global__ void __launch_bounds__(kThreads) k_label_csr(const int64_t *__restric
 // of the current edge) flushes the current edge: its lanes' words are ORed in,
 // the warp reduces, lane 0 hands the label to `emit`, and the next edge starts.
 // Empty edges are flushed the same way with nothing ORed in.
-template <int U, typename Emit>
+// Gather for the CSR stream: entry = cell index, -1 = no entry.
+struct CsrGather {
+  const uint64_t *__restrict__ O;
+  static constexpr int32_t kNone = -1;
+  __device__ __forceinline__ uint64_t full(int32_t c) const { return __ldg(O + c); }
+  __device__ __forceinline__ uint64_t masked(int32_t c) const { return c >= 0 ? __ldg(O + c) : 0ull; }
+};
+
+template <int U, typename Gather, typename Emit>
 __device__ __forceinline__ void stream_range(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
-                                             const uint64_t *__restrict__ O, int64_t e_beg, int64_t e_end,
-                                             uint64_t pol, int lane, Emit emit) {
+                                             const Gather gather, int64_t e_beg, int64_t e_end, uint64_t pol,
+                                             int lane, Emit emit) {
   // window of edge ends: lane i holds rowptr[win + i + 1] (the end of edge win + i)
   int64_t win = e_beg;
   int64_t rp = win + lane < e_end ? __ldg(rowptr + win + lane + 1) : 0;
@@ -179,7 +187,7 @@ __device__ __forceinline__ void stream_range(const int64_t *__restrict__ rowptr,
 #pragma unroll
   for (int u = 0; u < U; ++u) {
     const int off = 32 * u + lane;
-    nxt[u] = (off >= head && off < n_rel) ? ld_stream(base + 32 * u, pol) : -1;
+    nxt[u] = (off >= head && off < n_rel) ? ld_stream(base + 32 * u, pol) : Gather::kNone;
   }
   for (int64_t g = 0; g < n_rel; g += 32 * U) {
     int32_t c[U];
@@ -193,15 +201,16 @@ __device__ __forceinline__ void stream_range(const int64_t *__restrict__ rowptr,
       const int64_t rem64 = n_rel - g - 32 * U;
       const int rem = rem64 > 0x7fffffff ? 0x7fffffff : static_cast<int>(rem64);
 #pragma unroll
-      for (int u = 0; u < U; ++u) nxt[u] = (32 * u + lane < rem) ? ld_stream(base + g + 32 * (U + u), pol) : -1;
+      for (int u = 0; u < U; ++u)
+        nxt[u] = (32 * u + lane < rem) ? ld_stream(base + g + 32 * (U + u), pol) : Gather::kNone;
     }
     uint64_t wv[U];
     if ((g > 0 || head == 0) && g + 32 * U <= n_rel) {  // every entry valid
 #pragma unroll
-      for (int u = 0; u < U; ++u) wv[u] = __ldg(O + c[u]);
+      for (int u = 0; u < U; ++u) wv[u] = gather.full(c[u]);
     } else {
 #pragma unroll
-      for (int u = 0; u < U; ++u) wv[u] = c[u] >= 0 ? __ldg(O + c[u]) : 0ull;
+      for (int u = 0; u < U; ++u) wv[u] = gather.masked(c[u]);
     }
     const int64_t grp_end = min(a + g + 32 * U, p1);
     if (grp_end <= stop) {
@@ -226,8 +235,15 @@ __device__ __forceinline__ void stream_range(const int64_t *__restrict__ rowptr,
   while (cur < e_end) flush();
 }
 
+// Resident CTAs per SM each streaming variant is compiled for: deeper
+// pipelines hold more entries in flight per warp and get more registers.
+template <int U>
+constexpr int stream_min_blocks() {
+  return U <= 8 ? 4 : (U <= 12 ? 3 : 2);
+}
+
 template <int U, bool EPI>
-__global__ void __launch_bounds__(kThreads, 4) k_label_stream(const int64_t *__restrict__ rowptr,
+__global__ void __launch_bounds__(kThreads, stream_min_blocks<U>()) k_label_stream(const int64_t *__restrict__ rowptr,
                                                            const int32_t *__restrict__ colidx,
                                                            const uint64_t *__restrict__ O,
                                                            const int64_t *__restrict__ part, uint64_t mask,
@@ -239,7 +255,55 @@ __global__ void __launch_bounds__(kThreads, 4) k_label_stream(const int64_t *__r
   const int64_t w = (static_cast<int64_t>(blockIdx.x) * kThreads + threadIdx.x) >> 5;
   const int64_t e_beg = __ldg(part + w), e_end = __ldg(part + w + 1);
   if (e_beg >= e_end) return;  // warp-uniform
-  stream_range<U>(rowptr, colidx, O, e_beg, e_end, pol, lane, [&](int64_t e, uint64_t r) {
+  stream_range<U>(rowptr, colidx, CsrGather{O}, e_beg, e_end, pol, lane, [&](int64_t e, uint64_t r) {
+    r &= mask;
+    L[e] = r;
+    if (EPI) epilogue(mon, sm, e, r);
+  });
+}
+
+// Sector form (compressed A at L2-sector granularity): an entry is
+// (sector << 4) | mask, sector = 4 consecutive cells of O (32 bytes), mask
+// bit i = cell 4*sector + i is in the row; 0 = no entry (a real entry has a
+// non-empty mask).  A lane fetches its whole sector with one 256-bit load and
+// ORs the words its mask selects; the stream, partition and boundary logic
+// are the CSR stream's, over entries instead of cells.
+struct SectorGather {
+  const uint64_t *__restrict__ O;  // 32-byte aligned
+  int64_t cells;
+  static constexpr int32_t kNone = 0;
+  __device__ __forceinline__ uint64_t pick(uint32_t v) const {
+    const int64_t c0 = static_cast<int64_t>(v >> 4) * 4;
+    const uint32_t m = v & 15u;
+    uint64_t a, b, c, d;
+    if (c0 + 4 <= cells) {
+      asm("ld.global.nc.v4.u64 {%0, %1, %2, %3}, [%4];" : "=l"(a), "=l"(b), "=l"(c), "=l"(d) : "l"(O + c0));
+    } else {  // the grid's last, partial sector: only the cells that exist
+      a = __ldg(O + c0);
+      b = c0 + 1 < cells ? __ldg(O + c0 + 1) : 0ull;
+      c = c0 + 2 < cells ? __ldg(O + c0 + 2) : 0ull;
+      d = 0ull;
+    }
+    return ((m & 1u) ? a : 0ull) | ((m & 2u) ? b : 0ull) | ((m & 4u) ? c : 0ull) | ((m & 8u) ? d : 0ull);
+  }
+  __device__ __forceinline__ uint64_t full(int32_t v) const { return pick(static_cast<uint32_t>(v)); }
+  __device__ __forceinline__ uint64_t masked(int32_t v) const { return v ? pick(static_cast<uint32_t>(v)) : 0ull; }
+};
+
+template <int U, bool EPI>
+__global__ void __launch_bounds__(kThreads, stream_min_blocks<2 * U>()) k_label_sector(const int64_t *__restrict__ srow,
+                                                           const int32_t *__restrict__ sec,
+                                                           const uint64_t *__restrict__ O, int64_t cells,
+                                                           const int64_t *__restrict__ part, uint64_t mask,
+                                                           uint64_t *__restrict__ L, MonitorTables mon) {
+  __shared__ EpiSmem sm;
+  if (EPI) load_tables(mon, sm);
+  const uint64_t pol = evict_first_policy();
+  const int lane = threadIdx.x & 31;
+  const int64_t w = (static_cast<int64_t>(blockIdx.x) * kThreads + threadIdx.x) >> 5;
+  const int64_t e_beg = __ldg(part + w), e_end = __ldg(part + w + 1);
+  if (e_beg >= e_end) return;  // warp-uniform
+  stream_range<U>(srow, sec, SectorGather{O, cells}, e_beg, e_end, pol, lane, [&](int64_t e, uint64_t r) {
     r &= mask;
     L[e] = r;
     if (EPI) epilogue(mon, sm, e, r);
@@ -276,7 +340,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_label_batch(const __grid_consta
     const int64_t *part = it->part;
     const int64_t e_beg = __ldg(part + lu), e_end = __ldg(part + lu + 1);
     if (e_beg >= e_end) continue;
-    stream_range<8>(it->rowptr, it->colidx, it->O, e_beg, e_end, pol, lane, [&](int64_t e, uint64_t r) {
+    stream_range<8>(it->rowptr, it->colidx, CsrGather{it->O}, e_beg, e_end, pol, lane, [&](int64_t e, uint64_t r) {
       r &= it->mask;
       it->L[e] = r;
       const uint64_t *T = it->T;
@@ -776,6 +840,36 @@ uint64_t prop_mask(int32_t P) { return P >= 64 ? ~0ull : ((1ull << P) - 1ull); }
 
 }  // namespace
 
+int sector_ctas_per_sm(int depth) {
+  static const int o4 = std::min(occupancy(k_label_sector<4, false>), occupancy(k_label_sector<4, true>));
+  static const int o8 = std::min(occupancy(k_label_sector<8, false>), occupancy(k_label_sector<8, true>));
+  return depth == 8 ? o8 : o4;
+}
+
+template <int U>
+void sector_launch(const Roadmap &rm, const uint64_t *O, uint64_t mask, uint64_t *L, const MonitorTables *mon,
+                   cudaStream_t s) {
+  const unsigned grid = static_cast<unsigned>(rm.num_sms * rm.sec_part_ctas);
+  MonitorTables none{};
+  if (mon)
+    k_label_sector<U, true><<<grid, kThreads, 0, s>>>(rm.sec_rowptr, rm.sec, O, rm.cells, rm.sec_part, mask, L,
+                                                      *mon);
+  else
+    k_label_sector<U, false><<<grid, kThreads, 0, s>>>(rm.sec_rowptr, rm.sec, O, rm.cells, rm.sec_part, mask, L,
+                                                       none);
+}
+
+cudaError_t launch_label_sector(const Roadmap &rm, const uint64_t *O, int32_t P, uint64_t *L,
+                                const MonitorTables *mon, int depth, cudaStream_t s) {
+  if (rm.E == 0) return cudaSuccess;
+  const uint64_t mask = prop_mask(P);
+  if (depth == 8)
+    sector_launch<8>(rm, O, mask, L, mon, s);
+  else
+    sector_launch<4>(rm, O, mask, L, mon, s);
+  return cudaGetLastError();
+}
+
 int batch_ctas_per_sm() {
   static const int occ = occupancy(k_label_batch);
   return occ;
@@ -832,10 +926,11 @@ cudaError_t launch_label_async(const Roadmap &rm, const uint64_t *O, int32_t P, 
   return cudaGetLastError();
 }
 
-int stream_ctas_per_sm(int unroll) {
-  (void)unroll;
-  static const int occ8 = std::min(occupancy(k_label_stream<8, false>), occupancy(k_label_stream<8, true>));
-  return occ8;
+int stream_ctas_per_sm(int depth) {
+  static const int o8 = std::min(occupancy(k_label_stream<8, false>), occupancy(k_label_stream<8, true>));
+  static const int o12 = std::min(occupancy(k_label_stream<12, false>), occupancy(k_label_stream<12, true>));
+  static const int o16 = std::min(occupancy(k_label_stream<16, false>), occupancy(k_label_stream<16, true>));
+  return depth == 16 ? o16 : depth == 12 ? o12 : o8;
 }
 
 cudaError_t launch_partition(const Roadmap &rm, int ctas_per_sm, cudaStream_t s) {
@@ -845,18 +940,27 @@ cudaError_t launch_partition(const Roadmap &rm, int ctas_per_sm, cudaStream_t s)
   return cudaGetLastError();
 }
 
-cudaError_t launch_label_stream(const Roadmap &rm, const uint64_t *O, int32_t P, uint64_t *L,
-                                const MonitorTables *mon, int unroll, cudaStream_t s) {
-  if (rm.E == 0) return cudaSuccess;
-  const uint64_t mask = prop_mask(P);
+template <int U>
+void stream_launch(const Roadmap &rm, const uint64_t *O, uint64_t mask, uint64_t *L, const MonitorTables *mon,
+                   cudaStream_t s) {
   const unsigned grid = static_cast<unsigned>(rm.num_sms * rm.part_ctas);
   MonitorTables none{};
-  const MonitorTables &mt = mon ? *mon : none;
-  (void)unroll;
   if (mon)
-    k_label_stream<8, true><<<grid, kThreads, 0, s>>>(rm.rowptr, rm.colidx, O, rm.part, mask, L, mt);
+    k_label_stream<U, true><<<grid, kThreads, 0, s>>>(rm.rowptr, rm.colidx, O, rm.part, mask, L, *mon);
   else
-    k_label_stream<8, false><<<grid, kThreads, 0, s>>>(rm.rowptr, rm.colidx, O, rm.part, mask, L, mt);
+    k_label_stream<U, false><<<grid, kThreads, 0, s>>>(rm.rowptr, rm.colidx, O, rm.part, mask, L, none);
+}
+
+cudaError_t launch_label_stream(const Roadmap &rm, const uint64_t *O, int32_t P, uint64_t *L,
+                                const MonitorTables *mon, int depth, cudaStream_t s) {
+  if (rm.E == 0) return cudaSuccess;
+  const uint64_t mask = prop_mask(P);
+  if (depth == 16)
+    stream_launch<16>(rm, O, mask, L, mon, s);
+  else if (depth == 12)
+    stream_launch<12>(rm, O, mask, L, mon, s);
+  else
+    stream_launch<8>(rm, O, mask, L, mon, s);
   return cudaGetLastError();
 }
 

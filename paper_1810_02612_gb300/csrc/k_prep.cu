@@ -68,6 +68,45 @@ __global__ void __launch_bounds__(256) k_bt_fill(const int64_t *__restrict__ row
   }
 }
 
+// Sector form: per row, the number of distinct 4-cell sectors (count) and the
+// entries (sector << 4) | cell mask (fill), rows already checked.
+__global__ void __launch_bounds__(256) k_sector_count(const int64_t *__restrict__ rowptr,
+                                                      const int32_t *__restrict__ colidx, int64_t E,
+                                                      int32_t *__restrict__ count) {
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < E; e += stride) {
+    int32_t n = 0;
+    int64_t prev = -1;
+    for (int64_t k = rowptr[e]; k < rowptr[e + 1]; ++k) {
+      const int64_t sct = colidx[k] >> 2;
+      n += sct != prev;
+      prev = sct;
+    }
+    count[e] = n;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_sector_fill(const int64_t *__restrict__ rowptr,
+                                                     const int32_t *__restrict__ colidx, int64_t E,
+                                                     const int64_t *__restrict__ srow, int32_t *__restrict__ sec) {
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < E; e += stride) {
+    int64_t out = srow[e];
+    int64_t cur = -1;
+    uint32_t m = 0;
+    for (int64_t k = rowptr[e]; k < rowptr[e + 1]; ++k) {
+      const int64_t c = colidx[k];
+      if ((c >> 2) != cur) {
+        if (cur >= 0) sec[out++] = static_cast<int32_t>((static_cast<uint32_t>(cur) << 4) | m);
+        cur = c >> 2;
+        m = 0;
+      }
+      m |= 1u << (c & 3);
+    }
+    if (cur >= 0) sec[out] = static_cast<int32_t>((static_cast<uint32_t>(cur) << 4) | m);
+  }
+}
+
 unsigned blocks_for(int64_t n) {
   int64_t b = (n + 255) / 256;
   if (b > 65535LL * 8) b = 65535LL * 8;
@@ -75,6 +114,20 @@ unsigned blocks_for(int64_t n) {
 }
 
 }  // namespace
+
+cudaError_t launch_sector_count(const int64_t *rowptr, const int32_t *colidx, int64_t E, int32_t *count,
+                                cudaStream_t s) {
+  if (E == 0) return cudaSuccess;
+  k_sector_count<<<blocks_for(E), 256, 0, s>>>(rowptr, colidx, E, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sector_fill(const int64_t *rowptr, const int32_t *colidx, int64_t E, const int64_t *srow,
+                               int32_t *sec, cudaStream_t s) {
+  if (E == 0) return cudaSuccess;
+  k_sector_fill<<<blocks_for(E), 256, 0, s>>>(rowptr, colidx, E, srow, sec);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_scan_rows(const int64_t *rowptr, const int32_t *colidx, int64_t E, int64_t nnz, int64_t cells,
                              unsigned long long *n_bad, int32_t *bt_count, cudaStream_t s) {

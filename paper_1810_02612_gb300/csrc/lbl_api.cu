@@ -83,6 +83,9 @@ void free_roadmap(Roadmap *rm) {
   cudaFree(rm->planes);
   cudaFree(rm->part);
   cudaFree(rm->err);
+  cudaFree(rm->sec_rowptr);
+  cudaFree(rm->sec);
+  cudaFree(rm->sec_part);
   delete rm;
 }
 
@@ -202,7 +205,7 @@ int lbl_roadmap_upload(const lbl_grid *agent, const int64_t *rowptr, const int32
     set_error("roadmap upload: rowptr/colidx is NULL");
     return LBL_EINVAL;
   }
-  if (flags & ~(LBL_UPLOAD_DEVICE_PTRS | LBL_UPLOAD_BITTILE)) {
+  if (flags & ~(LBL_UPLOAD_DEVICE_PTRS | LBL_UPLOAD_BITTILE | LBL_UPLOAD_SECTOR)) {
     set_error("roadmap upload: unknown flags 0x%x", flags);
     return LBL_EINVAL;
   }
@@ -311,6 +314,39 @@ int lbl_roadmap_upload(const lbl_grid *agent, const int64_t *rowptr, const int32
       return fail(cuda_fail(e, "roadmap upload: block form"));
     rm->has_bt = true;
   }
+  if ((flags & LBL_UPLOAD_SECTOR) && n_edges > 0) {
+    if (rm->cells > (1LL << 30)) {
+      set_error("roadmap upload: the sector form needs at most 2^30 cells");
+      return fail(LBL_EINVAL);
+    }
+    std::vector<int32_t> cnt(static_cast<size_t>(n_edges));
+    std::vector<int64_t> srow(static_cast<size_t>(n_edges + 1));
+    int32_t *d_sc = nullptr;
+    if ((e = dev_alloc(&d_sc, static_cast<size_t>(n_edges), nullptr)) != cudaSuccess ||
+        (e = launch_sector_count(rm->rowptr, rm->colidx, n_edges, d_sc, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(cnt.data(), d_sc, sizeof(int32_t) * n_edges, cudaMemcpyDeviceToHost, st)) !=
+            cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess) {
+      cudaFree(d_sc);
+      return fail(cuda_fail(e, "roadmap upload: sector form"));
+    }
+    cudaFree(d_sc);
+    srow[0] = 0;
+    for (int64_t i = 0; i < n_edges; ++i) srow[i + 1] = srow[i] + cnt[i];
+    rm->n_sec = srow[n_edges];
+    if ((e = dev_alloc(&rm->sec_rowptr, static_cast<size_t>(n_edges + 1), &rm->bytes)) != cudaSuccess ||
+        (e = dev_alloc(&rm->sec, static_cast<size_t>(rm->n_sec), &rm->bytes)) != cudaSuccess ||
+        (e = dev_alloc(&rm->sec_part, static_cast<size_t>(rm->part_cap), &rm->bytes)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(rm->sec_rowptr, srow.data(), sizeof(int64_t) * (n_edges + 1), cudaMemcpyHostToDevice,
+                             st)) != cudaSuccess ||
+        (e = launch_sector_fill(rm->rowptr, rm->colidx, n_edges, rm->sec_rowptr, rm->sec, st)) != cudaSuccess)
+      return fail(cuda_fail(e, "roadmap upload: sector form"));
+    rm->sec_part_ctas = sector_ctas_per_sm(4);
+    const int64_t W = static_cast<int64_t>(rm->num_sms) * rm->sec_part_ctas * (kThreads / 32);
+    if ((e = launch_partition_into(rm->sec_rowptr, n_edges, W, rm->sec_part, st)) != cudaSuccess)
+      return fail(cuda_fail(e, "roadmap upload: sector partition"));
+    rm->has_sec = true;
+  }
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(cuda_fail(e, "roadmap upload"));
   cudaFree(d_bad);
   cudaFree(d_cnt);
@@ -327,7 +363,7 @@ int lbl_roadmap_free(lbl_roadmap rm) {
 }
 
 int lbl_roadmap_info(lbl_roadmap rm, int64_t *n_edges, int64_t *nnz, int64_t *n_block_entries,
-                     int64_t *device_bytes) {
+                     int64_t *n_sector_entries, int64_t *device_bytes) {
   g_err.clear();
   if (!rm) {
     set_error("roadmap info: NULL roadmap");
@@ -336,6 +372,7 @@ int lbl_roadmap_info(lbl_roadmap rm, int64_t *n_edges, int64_t *nnz, int64_t *n_
   if (n_edges) *n_edges = rm->E;
   if (nnz) *nnz = rm->nnz;
   if (n_block_entries) *n_block_entries = rm->n_bt;
+  if (n_sector_entries) *n_sector_entries = rm->n_sec;
   if (device_bytes) *device_bytes = rm->bytes;
   return LBL_OK;
 }
@@ -507,13 +544,21 @@ static int label_impl(lbl_roadmap rm, const uint64_t *d_O, int32_t n_props, uint
     return LBL_EINVAL;
   }
   int algo = cfg ? cfg->algo : LBL_ALGO_AUTO;
-  if (algo < LBL_ALGO_AUTO || algo > LBL_ALGO_BITTILE) {
+  if (algo < LBL_ALGO_AUTO || algo > LBL_ALGO_SECTOR) {
     set_error("label: unknown algo %d", algo);
     return LBL_EINVAL;
   }
   if (algo == LBL_ALGO_BITTILE && !rm->has_bt) {
     set_error("label: LBL_ALGO_BITTILE needs a roadmap uploaded with LBL_UPLOAD_BITTILE");
     return LBL_EUNSUPPORTED;
+  }
+  if (algo == LBL_ALGO_SECTOR && !rm->has_sec) {
+    set_error("label: LBL_ALGO_SECTOR needs a roadmap uploaded with LBL_UPLOAD_SECTOR");
+    return LBL_EUNSUPPORTED;
+  }
+  if (algo == LBL_ALGO_SECTOR && rm->E > 0 && (reinterpret_cast<uintptr_t>(d_O) & 31u)) {
+    set_error("label: LBL_ALGO_SECTOR needs O 32-byte aligned");
+    return LBL_EINVAL;
   }
   lbl_config tuned_cfg;
   if (algo == LBL_ALGO_AUTO && rm->tuned_valid[n_props]) {
@@ -531,6 +576,19 @@ static int label_impl(lbl_roadmap rm, const uint64_t *d_O, int32_t n_props, uint
   cudaError_t e;
   if (algo == LBL_ALGO_BITTILE) {
     e = launch_label_bittile(*rm, d_O, n_props, d_L, mon ? &t : nullptr, early, ctas, st);
+  } else if (algo == LBL_ALGO_SECTOR) {
+    const int depth = (cfg && cfg->depth == 8) ? 8 : 4;
+    if (rm->E > 0) {
+      const int occ = sector_ctas_per_sm(depth);
+      const int want = ctas > 0 ? std::min(ctas, occ) : occ;
+      if (want != rm->sec_part_ctas) {
+        const int64_t W = static_cast<int64_t>(rm->num_sms) * want * (kThreads / 32);
+        if ((e = launch_partition_into(rm->sec_rowptr, rm->E, W, rm->sec_part, st)) != cudaSuccess)
+          return cuda_fail(e, "label: sector partition");
+        rm->sec_part_ctas = want;
+      }
+    }
+    e = launch_label_sector(*rm, d_O, n_props, d_L, mon ? &t : nullptr, depth, st);
   } else if (early || lpe > 0) {
     // lanes-per-edge form (one edge per lane group; supports early exit)
     e = launch_label_csr(*rm, d_O, n_props, d_L, mon ? &t : nullptr, resolve_lpe(*rm, cfg), early, ctas, st);
@@ -542,10 +600,11 @@ static int label_impl(lbl_roadmap rm, const uint64_t *d_O, int32_t n_props, uint
       return LBL_EINVAL;
     }
     if (pipe == 0) pipe = kDefaultPipeline;
+    const int depth = cfg ? cfg->depth : 0;
     if (rm->E > 0) {
       const int occ = pipe == LBL_PIPE_BULK ? tma_ctas_per_sm()
                       : pipe == LBL_PIPE_ASYNC ? async_ctas_per_sm()
-                                               : stream_ctas_per_sm(8);
+                                               : stream_ctas_per_sm(depth);
       const int want = ctas > 0 ? std::min(ctas, occ) : occ;
       if (want != rm->part_ctas) {
         if ((e = launch_partition(*rm, want, st)) != cudaSuccess) return cuda_fail(e, "label: partition");
@@ -555,7 +614,7 @@ static int label_impl(lbl_roadmap rm, const uint64_t *d_O, int32_t n_props, uint
     const MonitorTables *mt = mon ? &t : nullptr;
     e = pipe == LBL_PIPE_BULK    ? launch_label_tma(*rm, d_O, n_props, d_L, mt, st)
         : pipe == LBL_PIPE_ASYNC ? launch_label_async(*rm, d_O, n_props, d_L, mt, st)
-                                 : launch_label_stream(*rm, d_O, n_props, d_L, mt, 8, st);
+                                 : launch_label_stream(*rm, d_O, n_props, d_L, mt, depth, st);
   }
   if (e != cudaSuccess) return cuda_fail(e, "label: launch");
   return LBL_OK;
@@ -576,10 +635,12 @@ int lbl_roadmap_autotune(lbl_roadmap rm, const uint64_t *d_O, int32_t n_props, l
   }
   cudaStream_t st = reinterpret_cast<cudaStream_t>(s);
   std::vector<lbl_config> cand;
-  for (int pipe : {LBL_PIPE_REGISTERS, LBL_PIPE_BULK, LBL_PIPE_ASYNC})
-    cand.push_back(lbl_config{LBL_ALGO_CSR, 0, 0, 0, pipe});
-  for (int lpe : {8, 16, 32}) cand.push_back(lbl_config{LBL_ALGO_CSR, lpe, 0, 0, 0});
-  if (rm->has_bt) cand.push_back(lbl_config{LBL_ALGO_BITTILE, 0, 0, 0, 0});
+  for (int depth : {8, 12, 16}) cand.push_back(lbl_config{LBL_ALGO_CSR, 0, 0, 0, LBL_PIPE_REGISTERS, depth});
+  for (int pipe : {LBL_PIPE_BULK, LBL_PIPE_ASYNC}) cand.push_back(lbl_config{LBL_ALGO_CSR, 0, 0, 0, pipe, 0});
+  for (int lpe : {8, 16, 32}) cand.push_back(lbl_config{LBL_ALGO_CSR, lpe, 0, 0, 0, 0});
+  if (rm->has_bt) cand.push_back(lbl_config{LBL_ALGO_BITTILE, 0, 0, 0, 0, 0});
+  if (rm->has_sec && !(reinterpret_cast<uintptr_t>(d_O) & 31u))
+    for (int depth : {4, 8}) cand.push_back(lbl_config{LBL_ALGO_SECTOR, 0, 0, 0, 0, depth});
   cudaEvent_t t0, t1;
   cudaError_t e = cudaEventCreate(&t0);
   if (e == cudaSuccess) e = cudaEventCreate(&t1);

@@ -89,6 +89,13 @@ struct Roadmap {
   uint32_t *bt_block = nullptr;
   uint64_t *bt_mask = nullptr;
   uint64_t *planes = nullptr;  // n_blocks * 64 words of working memory
+  // sector form (optional): per edge the entries (sector << 4) | 4-cell mask
+  bool has_sec = false;
+  int64_t n_sec = 0;
+  int64_t *sec_rowptr = nullptr;
+  int32_t *sec = nullptr;      // n_sec entries, padded like colidx
+  int64_t *sec_part = nullptr;  // partition of the sector kernel's grid
+  int sec_part_ctas = 0;
   // edge partition of the streaming CSR kernel: warp w owns [part[w], part[w+1])
   int64_t *part = nullptr;
   int64_t part_cap = 0;  // entries allocated
@@ -130,7 +137,7 @@ cudaError_t launch_label_csr(const Roadmap &rm, const uint64_t *O, int32_t P, ui
                              int lanes_per_edge, bool early_exit, int ctas_per_sm, cudaStream_t s);
 
 // streaming CSR form: CTAs per SM it runs with, its partition, its launch
-int stream_ctas_per_sm(int unroll);
+int stream_ctas_per_sm(int depth);
 int tma_ctas_per_sm();
 int async_ctas_per_sm();
 cudaError_t launch_label_async(const Roadmap &rm, const uint64_t *O, int32_t P, uint64_t *L,
@@ -139,7 +146,7 @@ cudaError_t launch_label_tma(const Roadmap &rm, const uint64_t *O, int32_t P, ui
                              cudaStream_t s);
 cudaError_t launch_partition(const Roadmap &rm, int ctas_per_sm, cudaStream_t s);
 cudaError_t launch_label_stream(const Roadmap &rm, const uint64_t *O, int32_t P, uint64_t *L,
-                                const MonitorTables *mon, int unroll, cudaStream_t s);
+                                const MonitorTables *mon, int depth, cudaStream_t s);
 
 cudaError_t launch_label_bittile(const Roadmap &rm, const uint64_t *O, int32_t P, uint64_t *L,
                                  const MonitorTables *mon, bool early_exit, int ctas_per_sm, cudaStream_t s);
@@ -147,6 +154,13 @@ cudaError_t launch_label_bittile(const Roadmap &rm, const uint64_t *O, int32_t P
 cudaError_t launch_monitor_step(const MonitorTables &mon, const uint64_t *L, int64_t n, int num_sms, cudaStream_t s);
 
 // batched launches over device tables of items
+int sector_ctas_per_sm(int depth);
+cudaError_t launch_label_sector(const Roadmap &rm, const uint64_t *O, int32_t P, uint64_t *L,
+                                const MonitorTables *mon, int depth, cudaStream_t s);
+cudaError_t launch_sector_count(const int64_t *rowptr, const int32_t *colidx, int64_t E, int32_t *count,
+                                cudaStream_t s);
+cudaError_t launch_sector_fill(const int64_t *rowptr, const int32_t *colidx, int64_t E, const int64_t *srow,
+                               int32_t *sec, cudaStream_t s);
 int batch_ctas_per_sm();
 cudaError_t launch_label_batch(const BatchTable &tab, unsigned long long *counter, int num_sms, int ctas_per_sm,
                                cudaStream_t s);

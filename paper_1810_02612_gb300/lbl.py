@@ -29,6 +29,7 @@ LBL_ORDER_MORTON = 1
 LBL_ALGO_AUTO = 0
 LBL_ALGO_CSR = 1
 LBL_ALGO_BITTILE = 2
+LBL_ALGO_SECTOR = 3
 
 LBL_PIPE_REGISTERS = 1
 LBL_PIPE_BULK = 2
@@ -39,6 +40,7 @@ LBL_STAGE_LABEL = 2
 
 LBL_UPLOAD_DEVICE_PTRS = 1
 LBL_UPLOAD_BITTILE = 2
+LBL_UPLOAD_SECTOR = 4
 
 # every entry point declared in include/lbl.h
 EXPORTS = (
@@ -75,7 +77,8 @@ class lbl_frame(ctypes.Structure):
 
 class lbl_config(ctypes.Structure):
     _fields_ = [("algo", ctypes.c_int32), ("lanes_per_edge", ctypes.c_int32),
-                ("early_exit", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("pipeline", ctypes.c_int32)]
+                ("early_exit", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("pipeline", ctypes.c_int32),
+                ("depth", ctypes.c_int32)]
 
 
 _lib = None
@@ -102,7 +105,7 @@ def load(build_if_needed: bool = True):
         "lbl_version": (ctypes.c_int, []),
         "lbl_roadmap_upload": (ctypes.c_int, [G, p, p, i64, i64, u32, p, ctypes.POINTER(p)]),
         "lbl_roadmap_free": (ctypes.c_int, [p]),
-        "lbl_roadmap_info": (ctypes.c_int, [p, p, p, p, p]),
+        "lbl_roadmap_info": (ctypes.c_int, [p, p, p, p, p, p]),
         "lbl_roadmap_status": (ctypes.c_int, [p, p]),
         "lbl_frame_transform": (ctypes.c_int, [G, p, i32, lbl_pose, G, p, p]),
         "lbl_monitor_create": (ctypes.c_int, [i32, i32, p, p, i32, ctypes.POINTER(p)]),
@@ -152,7 +155,7 @@ def _cfg(cfg):
     if isinstance(cfg, lbl_config):
         return ctypes.byref(cfg)
     c = lbl_config(int(cfg.get("algo", 0)), int(cfg.get("lanes_per_edge", 0)), int(cfg.get("early_exit", -1)),
-                   int(cfg.get("ctas_per_sm", 0)), int(cfg.get("pipeline", 0)))
+                   int(cfg.get("ctas_per_sm", 0)), int(cfg.get("pipeline", 0)), int(cfg.get("depth", 0)))
     return ctypes.byref(c)
 
 
@@ -240,10 +243,10 @@ def lbl_roadmap_free(rm) -> None:
 
 
 def lbl_roadmap_info(rm):
-    """(n_edges, nnz, n_block_entries, device_bytes) of a roadmap."""
-    e, n, k, b = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
-    _check(load().lbl_roadmap_info(rm, ctypes.byref(e), ctypes.byref(n), ctypes.byref(k), ctypes.byref(b)))
-    return e.value, n.value, k.value, b.value
+    """(n_edges, nnz, n_block_entries, n_sector_entries, device_bytes) of a roadmap."""
+    v = [ctypes.c_int64() for _ in range(5)]
+    _check(load().lbl_roadmap_info(rm, *[ctypes.byref(x) for x in v]))
+    return tuple(x.value for x in v)
 
 
 def lbl_roadmap_status(rm, stream=None) -> None:

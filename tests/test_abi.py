@@ -42,7 +42,7 @@ def test_struct_layouts_match_the_header():
     assert ctypes.sizeof(B.lbl_grid) == 40
     assert B.lbl_grid.res.offset == 8 and B.lbl_grid.order.offset == 32
     assert ctypes.sizeof(B.lbl_pose) == 24
-    assert ctypes.sizeof(B.lbl_config) == 20
+    assert ctypes.sizeof(B.lbl_config) == 24
 
 
 def test_version_and_empty_error():

@@ -36,7 +36,8 @@ def empty_u16(n):
 class Roadmap:
     def __init__(self, agent, rowptr, colidx, bittile=False):
         self.E = rowptr.shape[0] - 1
-        self.h = L.lbl_roadmap_upload(agent, rowptr, colidx, flags=L.LBL_UPLOAD_BITTILE if bittile else 0)
+        self.h = L.lbl_roadmap_upload(agent, rowptr, colidx,
+                                      flags=(L.LBL_UPLOAD_BITTILE | L.LBL_UPLOAD_SECTOR) if bittile else 0)
 
     def __del__(self):
         if getattr(self, "h", None):
@@ -73,6 +74,10 @@ CFGS = [
     dict(algo=L.LBL_ALGO_CSR, lanes_per_edge=32, early_exit=0),
     dict(algo=L.LBL_ALGO_CSR, lanes_per_edge=32, early_exit=1),
     dict(algo=L.LBL_ALGO_BITTILE, early_exit=0),
+    dict(algo=L.LBL_ALGO_SECTOR),
+    dict(algo=L.LBL_ALGO_SECTOR, depth=8),
+    dict(algo=L.LBL_ALGO_CSR, depth=12),
+    dict(algo=L.LBL_ALGO_CSR, depth=16),
     dict(algo=L.LBL_ALGO_BITTILE, early_exit=1),
     dict(algo=L.LBL_ALGO_AUTO),
 ]
@@ -275,8 +280,8 @@ def test_upload_from_device_pointers_and_info(plain):
     wl = plain
     h = L.lbl_roadmap_upload(wl.agent, cuda(wl.rowptr), cuda(wl.colidx))
     try:
-        E, nnz, nbt, b = L.lbl_roadmap_info(h)
-        assert nbt == 0
+        E, nnz, nbt, nsec, b = L.lbl_roadmap_info(h)
+        assert nbt == 0 and nsec == 0
         assert (E, nnz) == (wl.n_edges, wl.nnz) and b >= 8 * (E + 1) + 4 * nnz
         O = gpu_O(wl)
         out = empty_u64(E)
@@ -346,7 +351,7 @@ def test_autotune_choice_is_exact_and_sticks(driving_small):
     want = oracle.label(wl.rowptr, wl.colidx, host(O), wl.P, threads=8)
     out = empty_u64(rm.E)
     chosen = L.lbl_roadmap_autotune(rm.h, O, wl.P, out, reps=2)
-    assert chosen["algo"] in (L.LBL_ALGO_CSR, L.LBL_ALGO_BITTILE)
+    assert chosen["algo"] in (L.LBL_ALGO_CSR, L.LBL_ALGO_BITTILE, L.LBL_ALGO_SECTOR)
     assert np.array_equal(host(out), want)
     assert np.array_equal(gpu_label(rm, O, wl.P, dict(algo=L.LBL_ALGO_AUTO)), want)
     assert np.array_equal(gpu_label(rm, O, wl.P, None), want)
