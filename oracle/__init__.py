@@ -63,6 +63,15 @@ def _load():
         lib.orc_label_rows.argtypes = [i64, p, p, p, p, i32, p]
         lib.orc_monitor.restype = ctypes.c_int
         lib.orc_monitor.argtypes = [i32, i32, p, p, i32, p, i64, p, p]
+        lib.orc_morton3.restype = ctypes.c_uint64
+        lib.orc_morton3.argtypes = [ctypes.c_uint32] * 3
+        lib.orc_cell_index3.restype = i64
+        lib.orc_cell_index3.argtypes = [i32] * 6
+        lib.orc_time_coeffs.restype = None
+        lib.orc_time_coeffs.argtypes = [f64] * 5 + [p]
+        lib.orc_frame_transform3.restype = ctypes.c_int
+        lib.orc_frame_transform3.argtypes = ([i32, i32, i32] + [f64] * 5 + [p, i32] + [f64] * 4 + [i32, i32, i32]
+                                             + [f64] * 5 + [i32, p])
         _lib = lib
     return _lib
 
@@ -138,3 +147,28 @@ def monitor(n_states: int, m: int, relbits, delta, reject: int, L: np.ndarray):
     if rc != 0:
         raise ValueError("oracle monitor rejected its arguments")
     return nxt, viol
+
+
+def morton3(ix: int, iy: int, it: int) -> int:
+    """3-D z-order index of cell (ix, iy, it) of the (x, y, tau) workspace."""
+    return int(_load().orc_morton3(ix, iy, it))
+
+
+def cell_index3(order: int, w: int, h: int, ix: int, iy: int, it: int) -> int:
+    return int(_load().orc_cell_index3(order, w, h, ix, iy, it))
+
+
+def frame_transform3(world, vols: np.ndarray, pose, agent) -> np.ndarray:
+    """Agent-frame words of a time-augmented workspace: vols uint8[P][d][h][w],
+    pose (X, Y, theta, T); grids carry d, tres, t0 (Sec. 5, eq. 13)."""
+    vols = np.ascontiguousarray(vols, dtype=np.uint8)
+    P = vols.shape[0]
+    assert vols.shape[1:] == (world.d, world.h, world.w)
+    O = np.zeros(agent.w * agent.h * agent.d, np.uint64)
+    rc = _load().orc_frame_transform3(world.w, world.h, world.d, world.res, world.x0, world.y0, world.tres,
+                                      world.t0, _ptr(vols), P, float(pose[0]), float(pose[1]), float(pose[2]),
+                                      float(pose[3]), agent.w, agent.h, agent.d, agent.res, agent.x0, agent.y0,
+                                      agent.tres, agent.t0, agent.order, _ptr(O))
+    if rc != 0:
+        raise ValueError("oracle 3-D frame transform rejected its arguments")
+    return O

@@ -19,6 +19,10 @@
  *                                (proposition, row, nonzero)
  *   orc_monitor                  safety-monitor transition delta(q, L(e)) for every
  *                                monitor state, Sec. 3.2
+ *   orc_morton3 / orc_cell_index3 / orc_time_coeffs / orc_frame_transform3
+ *                                the time-augmented (x, y, tau) workspace of Sec. 5:
+ *                                3-D z-order and the frame transform with the
+ *                                time shift of eq. 13
  *
  * Readings of the paper used here (the paper is silent or garbled at these
  * points):
@@ -33,6 +37,9 @@
  *   - Label bits at positions >= P are zero.
  *   - Monitor: deterministic table delta[q][letter] with an explicit reject
  *     state; the letter is formed from m <= 8 selected proposition bits.
+ *   - Time axis: agent time cell it has its centre at t0 + (it+.5)tres relative
+ *     to the query time T; the world time cell is the floor of
+ *     ((T + centre) - t0_w)/tres_w, again a Q32.32 affine map rounded once.
  *
  * Build: gcc -O2 -fPIC -shared -fopenmp -ffp-contract=off (no contraction, so the
  * double arithmetic of orc_frame_coeffs is evaluated exactly as written).
@@ -195,6 +202,73 @@ int orc_monitor(int32_t n_states, int32_t m, const uint8_t *relbits, const uint8
     }
     next[e] = word;
     viol[e] = v;
+  }
+  return 0;
+}
+
+/* ------------------------------------------------ time-augmented workspace */
+
+/*
+ * Sec. 5: the workspace is (x, y, tau); dynamic objects become static volumes.
+ * 3-D z-order (Algorithm 1 with k = 3, axis 0 = x split first): bit i of ix
+ * goes to index bit 3i+2, of iy to 3i+1, of it (time) to 3i.
+ */
+uint64_t orc_morton3(uint32_t ix, uint32_t iy, uint32_t it) {
+  uint64_t n = 0;
+  for (int i = 0; i < 21; i++) {
+    n |= (uint64_t)((ix >> i) & 1u) << (3 * i + 2);
+    n |= (uint64_t)((iy >> i) & 1u) << (3 * i + 1);
+    n |= (uint64_t)((it >> i) & 1u) << (3 * i);
+  }
+  return n;
+}
+
+int64_t orc_cell_index3(int32_t order, int32_t w, int32_t h, int32_t ix, int32_t iy, int32_t it) {
+  if (order == ORC_MORTON) return (int64_t)orc_morton3((uint32_t)ix, (uint32_t)iy, (uint32_t)it);
+  return ((int64_t)it * h + iy) * w + ix;
+}
+
+/* Q32.32 time map it -> continuous world time-cell coordinate:
+   v_t = at * it + bt, the agent time-cell centre shifted by the query time T
+   (the equivariance of eq. 13 in t).  out = {At, Bt}. */
+void orc_time_coeffs(double wtres, double wt0, double atres, double at0, double T, int64_t *out) {
+  double a = atres / wtres;
+  double ta = at0 + 0.5 * atres; /* centre of agent time cell 0 */
+  double b = ((T + ta) - wt0) / wtres;
+  out[0] = to_q32(a);
+  out[1] = to_q32(b);
+}
+
+/*
+ * 3-D frame transform: agent cell (ix, iy, it) reads the world volume cell
+ * (wx, wy, wt) with (wx, wy) as in orc_frame_transform and wt the floor of the
+ * time map; volumes: uint8[P][wd][wh][ww]; outside the world volume reads 0.
+ * O: uint64[aw * ah * ad] in the agent order.
+ */
+int orc_frame_transform3(int32_t ww, int32_t wh, int32_t wd, double wres, double wx0, double wy0, double wtres,
+                         double wt0, const uint8_t *vols, int32_t P, double X, double Y, double theta, double T,
+                         int32_t aw, int32_t ah, int32_t ad, double ares, double ax0, double ay0, double atres,
+                         double at0, int32_t aorder, uint64_t *O) {
+  if (P < 0 || P > 64) return -1;
+  int64_t q[6], qt[2];
+  orc_frame_coeffs(wres, wx0, wy0, ares, ax0, ay0, X, Y, theta, q);
+  orc_time_coeffs(wtres, wt0, atres, at0, T, qt);
+  for (int32_t it = 0; it < ad; it++) {
+    int64_t wtc = floor_q32(qt[0] * it + qt[1]);
+    for (int32_t iy = 0; iy < ah; iy++) {
+      for (int32_t ix = 0; ix < aw; ix++) {
+        int64_t wxc = floor_q32(q[0] * ix + q[1] * iy + q[2]);
+        int64_t wyc = floor_q32(q[3] * ix + q[4] * iy + q[5]);
+        uint64_t word = 0;
+        if (wxc >= 0 && wxc < ww && wyc >= 0 && wyc < wh && wtc >= 0 && wtc < wd) {
+          for (int32_t p = 0; p < P; p++) {
+            size_t off = (((size_t)p * wd + (size_t)wtc) * wh + (size_t)wyc) * ww + (size_t)wxc;
+            if (vols[off] != 0) word |= (uint64_t)1 << p;
+          }
+        }
+        O[orc_cell_index3(aorder, aw, ah, ix, iy, it)] = word;
+      }
+    }
   }
   return 0;
 }

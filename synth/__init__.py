@@ -73,6 +73,10 @@ def _load():
         lib.synth_plane_band.argtypes = [p, i32, i32, f64, f64, f64, p, f64]
         lib.synth_plane_polygon.restype = i64
         lib.synth_plane_polygon.argtypes = [p, i32, i32, f64, f64, f64, p, p, i32]
+        lib.synth_sweep3_build.restype = p
+        lib.synth_sweep3_build.argtypes = [i64, p, f64, i32, i32, i32, f64, f64, f64, f64, f64, i32, i32, p]
+        lib.synth_volume_moving_disc.restype = i64
+        lib.synth_volume_moving_disc.argtypes = [p, i32, i32, i32] + [f64] * 10
         _lib = lib
     return _lib
 
@@ -85,17 +89,21 @@ def _ptr(a: np.ndarray):
 class Grid:
     """Occupancy-grid descriptor: ``w`` x ``h`` cells of side ``res`` metres whose
     cell (0,0) has its lower-left corner at (x0, y0) in the grid's own frame;
-    ``order`` is the cell numbering (ROWMAJOR or MORTON)."""
+    ``order`` is the cell numbering (ROWMAJOR or MORTON).  A time-augmented grid
+    (Sec. 5) has ``d`` > 1 time slabs of ``tres`` seconds starting at ``t0``."""
     w: int
     h: int
     res: float
     x0: float
     y0: float
     order: int = ROWMAJOR
+    d: int = 1
+    tres: float = 1.0
+    t0: float = 0.0
 
     @property
     def cells(self) -> int:
-        return self.w * self.h
+        return self.w * self.h * self.d
 
 
 def agent_grid(w: int, res: float, order: int = MORTON, h: int | None = None) -> Grid:
@@ -134,6 +142,25 @@ def sweep_csr(arcs: np.ndarray, radius: float, grid: Grid, threads: int = 0):
                                   grid.order, int(threads), ctypes.byref(nnz))
     if not h:
         raise MemoryError("sweep rasterisation failed")
+    rowptr = np.empty(E + 1, np.int64)
+    colidx = np.empty(nnz.value, np.int32)
+    if _load().synth_sweep_take(h, _ptr(rowptr), _ptr(colidx)) != 0:
+        raise MemoryError("sweep copy failed")
+    return rowptr, colidx
+
+
+def sweep3_csr(arcs6: np.ndarray, radius: float, grid: Grid, threads: int = 0):
+    """CSR rows of the time-augmented cells swept by arcs travelled at constant
+    speed: arcs6[n] = (x, y, heading, curvature, length, speed); cell
+    (ix, iy, it) is in the row iff a point reached during time slab it (closed)
+    lies within ``radius`` of the cell's (x, y) centre."""
+    arcs6 = np.ascontiguousarray(arcs6, np.float64)
+    E = arcs6.shape[0]
+    nnz = ctypes.c_int64(0)
+    h = _load().synth_sweep3_build(E, _ptr(arcs6), float(radius), grid.w, grid.h, grid.d, grid.res, grid.x0,
+                                   grid.y0, grid.tres, grid.t0, grid.order, int(threads), ctypes.byref(nnz))
+    if not h:
+        raise MemoryError("3-D sweep rasterisation failed")
     rowptr = np.empty(E + 1, np.int64)
     colidx = np.empty(nnz.value, np.int32)
     if _load().synth_sweep_take(h, _ptr(rowptr), _ptr(colidx)) != 0:
@@ -376,3 +403,63 @@ def make_batch(seed: int = 0, frames: int = 64, edges=(10_000, 500_000), grids=(
         out.append(BatchFrame(agent, world, int(Ps[i]), rp, colidx[: int(rp[-1])], planes[: int(Ps[i])],
                               random_pose(rng, world), int(keys[i])))
     return out
+
+
+# ------------------------------------------------ time-augmented workspace
+
+def agent_grid3(n: int, res: float, d: int, tres: float, order: int = MORTON) -> Grid:
+    """Agent-frame (x, y, tau) grid: n x n cells centred on the agent, d time
+    slabs of tres seconds from the query time 0."""
+    return Grid(n, n, float(res), -n * res / 2.0, -n * res / 2.0, order, d, float(tres), 0.0)
+
+
+def world_grid3(w: int, h: int, res: float, d: int, tres: float) -> Grid:
+    return Grid(w, h, float(res), 0.0, 0.0, ROWMAJOR, d, float(tres), 0.0)
+
+
+def volumes_paper3d(rng, g: Grid) -> np.ndarray:
+    """Two time-augmented propositions shaped like Sec. 5's: moving vehicles
+    (discs of 1-2.5 m moving at 5-15 m/s, ~1 % of the volume) and the outside of
+    a circular lane loop (static, ~90 %)."""
+    vols = np.zeros((2, g.d, g.h, g.w), np.uint8)
+    goal = 0.01 * g.cells
+    filled, shapes = 0, 0
+    while filled < goal and shapes < 10000:
+        cx = g.x0 + rng.random() * g.w * g.res
+        cy = g.y0 + rng.random() * g.h * g.res
+        sp = 5.0 + 10.0 * rng.random()
+        hd = 2 * math.pi * rng.random()
+        filled += _load().synth_volume_moving_disc(_ptr(vols[0]), g.w, g.h, g.d, g.res, g.x0, g.y0, g.tres, g.t0,
+                                                   cx, cy, sp * math.cos(hd), sp * math.sin(hd),
+                                                   1.0 + 1.5 * rng.random())
+        shapes += 1
+    cx, cy = g.x0 + g.w * g.res / 2, g.y0 + g.h * g.res / 2
+    R = 0.39 * min(g.w, g.h) * g.res
+    half = 0.05 * g.w * g.h * g.res * g.res / (2 * math.pi * R)
+    lane = np.zeros((g.h, g.w), np.uint8)
+    _add_band(lane, g, (cx + R, cy, math.pi / 2, 1.0 / R, 2 * math.pi * R * 1.01), half)
+    vols[1] = (1 - lane)[None, :, :]
+    return vols
+
+
+def sample_arcs3(rng, n: int, grid: Grid, kappa=(-0.3, 0.3), length=(5.0, 30.0), speed=(8.0, 15.0)) -> np.ndarray:
+    a = np.empty((n, 6), np.float64)
+    a[:, :5] = sample_arcs(rng, n, grid, kappa, length)
+    a[:, 5] = speed[0] + rng.random(n) * (speed[1] - speed[0])
+    return a
+
+
+def make_paper3d(seed: int = 0, edges: int = 1_097_702, n: int = 128, d: int = 128, threads: int = 0,
+                 res: float = 0.4, tres: float = 0.05, radius: float = 0.8, order: int = MORTON) -> Workload:
+    """The paper's time-augmented workspace (Sec. 5): 128 x 128 x 128 = 2^21
+    cells of 0.4 m x 0.4 m x 0.05 s, two propositions, arcs travelled at
+    8-15 m/s with a 0.8 m disc footprint."""
+    rng = np.random.default_rng(seed)
+    agent = agent_grid3(n, res, d, tres, order)
+    world = world_grid3(n, n, res, d, tres)
+    vols = volumes_paper3d(rng, world)
+    pose = random_pose(rng, world) + (0.0,)
+    arcs = sample_arcs3(rng, edges, agent)
+    rowptr, colidx = sweep3_csr(arcs, radius, agent, threads)
+    return Workload("paper3d", agent, world, 2, arcs, radius, rowptr, colidx, vols, pose, None,
+                    meta=dict(seed=seed))

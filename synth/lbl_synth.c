@@ -463,3 +463,130 @@ int64_t synth_plane_polygon(uint8_t *plane, int32_t w, int32_t h, double res, do
     }
   return added;
 }
+
+/* ------------------------------------------- time-augmented (x, y, tau) grids */
+
+static uint64_t spread3_bits(uint64_t v) {
+  uint64_t r = 0;
+  for (int i = 0; i < 21; i++) r |= ((v >> i) & 1ull) << (3 * i);
+  return r;
+}
+
+static inline uint32_t cell_key3(int order, int w, int h, int ix, int iy, int it) {
+  if (order == SYN_ORDER_MORTON)
+    return (uint32_t)((spread3_bits((uint64_t)ix) << 2) | (spread3_bits((uint64_t)iy) << 1) |
+                      spread3_bits((uint64_t)it));
+  return ((uint32_t)it * (uint32_t)h + (uint32_t)iy) * (uint32_t)w + (uint32_t)ix;
+}
+
+/*
+ * Swept cells of arcs travelled at constant speed from time 0: arcs =
+ * float64[n][6] (x, y, heading, curvature, length, speed).  Cell (ix, iy, it)
+ * belongs to the row iff some point of the arc reached during time slab it
+ * (closed interval [t0 + it*tres, t0 + (it+1)*tres]) lies within `radius` of
+ * the cell's (x, y) centre.  Same build/take protocol as synth_sweep_build.
+ */
+void *synth_sweep3_build(int64_t n_edges, const double *arcs, double radius, int32_t w, int32_t h, int32_t d,
+                         double res, double x0, double y0, double tres, double t0, int32_t order, int32_t n_threads,
+                         int64_t *nnz_out) {
+  build_t *b = (build_t *)calloc(1, sizeof(build_t));
+  if (!b) return NULL;
+  b->n_edges = n_edges;
+  b->chunk = 256;
+  b->n_chunks = (n_edges + b->chunk - 1) / b->chunk;
+  b->counts = (int64_t *)calloc((size_t)(n_edges > 0 ? n_edges : 1), sizeof(int64_t));
+  b->bufs = (uint32_t **)calloc((size_t)(b->n_chunks > 0 ? b->n_chunks : 1), sizeof(uint32_t *));
+  b->chunk_nnz = (int64_t *)calloc((size_t)(b->n_chunks > 0 ? b->n_chunks : 1), sizeof(int64_t));
+  if (!b->counts || !b->bufs || !b->chunk_nnz) {
+    synth_free_build(b);
+    return NULL;
+  }
+  int failed = 0;
+#ifdef _OPENMP
+  if (n_threads > 0) omp_set_num_threads(n_threads);
+#endif
+#pragma omp parallel reduction(| : failed)
+  {
+    scratch_t s;
+    memset(&s, 0, sizeof(s));
+    uint32_t *row = NULL, *tmp = NULL;
+    size_t row_cap = 0, tmp_cap = 0;
+#pragma omp for schedule(dynamic, 1)
+    for (int64_t c = 0; c < b->n_chunks; c++) {
+      int64_t e0 = c * b->chunk, e1 = e0 + b->chunk < n_edges ? e0 + b->chunk : n_edges;
+      size_t cap = 0, used = 0;
+      uint32_t *buf = NULL;
+      for (int64_t e = e0; e < e1 && !failed; e++) {
+        const double *a = arcs + 6 * e;
+        const double len = a[4], v = a[5];
+        size_t n_row = 0;
+        for (int32_t it = 0; it < d && !failed; it++) {
+          double sa = v * (t0 + it * tres), sb = v * (t0 + (it + 1) * tres);
+          if (sa < 0) sa = 0;
+          if (sb > len) sb = len;
+          if (sa > sb) continue;
+          /* the sub-arc travelled during the slab, as an arc of its own */
+          const double k = a[3], th = a[2];
+          double px, py;
+          if (fabs(k) < 1e-9) {
+            px = a[0] + sa * cos(th);
+            py = a[1] + sa * sin(th);
+          } else {
+            px = a[0] + (sin(th + k * sa) - sin(th)) / k;
+            py = a[1] - (cos(th + k * sa) - cos(th)) / k;
+          }
+          arcgeom_t g;
+          arc_setup(&g, px, py, th + k * sa, k, sb - sa);
+          long n = sweep_one(&s, &g, radius, w, h, res, x0, y0, SYN_ORDER_ROWMAJOR);
+          if (n < 0 || grow((void **)&row, &row_cap, n_row + (size_t)n + 1, sizeof(uint32_t))) {
+            failed = 1;
+            break;
+          }
+          for (long i = 0; i < n; i++) {
+            const int ix = (int)(s.keys[i] % (uint32_t)w), iy = (int)(s.keys[i] / (uint32_t)w);
+            row[n_row++] = cell_key3(order, w, h, ix, iy, it);
+          }
+        }
+        if (failed || grow((void **)&tmp, &tmp_cap, n_row + 1, sizeof(uint32_t)) ||
+            grow((void **)&buf, &cap, used + n_row + 1, sizeof(uint32_t))) {
+          failed = 1;
+          break;
+        }
+        radix_sort_u32(row, tmp, n_row);
+        memcpy(buf + used, row, n_row * sizeof(uint32_t));
+        used += n_row;
+        b->counts[e] = (int64_t)n_row;
+      }
+      b->bufs[c] = buf;
+      b->chunk_nnz[c] = (int64_t)used;
+    }
+    free(s.stamp);
+    free(s.queue);
+    free(s.keys);
+    free(s.tmp);
+    free(row);
+    free(tmp);
+  }
+  if (failed) {
+    synth_free_build(b);
+    return NULL;
+  }
+  int64_t nnz = 0;
+  for (int64_t c = 0; c < b->n_chunks; c++) nnz += b->chunk_nnz[c];
+  b->nnz = nnz;
+  *nnz_out = nnz;
+  return b;
+}
+
+/* A disc of radius rad whose centre moves as (cx + vx t, cy + vy t): in every
+   time slab of the volume (uint8[d][h][w]) the cells whose centre lies in the
+   disc at the slab's mid time.  Returns the cells that changed from 0 to 1. */
+int64_t synth_volume_moving_disc(uint8_t *vol, int32_t w, int32_t h, int32_t d, double res, double x0, double y0,
+                                 double tres, double t0, double cx, double cy, double vx, double vy, double rad) {
+  int64_t added = 0;
+  for (int32_t it = 0; it < d; it++) {
+    const double t = t0 + (it + 0.5) * tres;
+    added += synth_plane_disc(vol + (size_t)it * w * h, w, h, res, x0, y0, cx + vx * t, cy + vy * t, rad);
+  }
+  return added;
+}
