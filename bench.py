@@ -50,6 +50,9 @@ WORKLOADS = {
     "serving": "request loop: Poisson arrivals at 2,000 req/s, each a random pose + 32 world planes (256x256 at "
                "0.25 m) against one of 8 resident roadmaps of 20k-1M edges; continuous batching over 2 lanes vs one "
                "request per launch; latency = scheduled arrival to labels in host memory",
+    "paper3d": "1,097,702 arcs travelled at 8-15 m/s in a time-augmented (x, y, tau) workspace of 128x128x128 = 2^21 "
+               "cells (0.4 m, 0.05 s; 3-D z-order), 2 propositions: moving vehicles (~1 %) and outside a lane loop "
+               "(~90 %); 472 swept cells per edge",
     "batched": "64 frames/agents with roadmaps of log-uniform 10k-500k edges on 128^2-512^2 z-order grids at 0.25 m, "
                "8-64 propositions each, one CUDA-graph replay of the batched launch per step vs 64 frame-by-frame "
                "transform+label call pairs",
@@ -212,7 +215,10 @@ def oracle_step_rate(wl, n_sample: int, threads: int):
     rp = wl.rowptr[: n_sample + 1]
     ci = wl.colidx[: int(rp[-1])]
     t = time.perf_counter()
-    O = oracle.frame_transform(wl.world, wl.planes, wl.pose, wl.agent)
+    if wl.agent.d > 1:
+        O = oracle.frame_transform3(wl.world, wl.planes, wl.pose, wl.agent)
+    else:
+        O = oracle.frame_transform(wl.world, wl.planes, wl.pose, wl.agent)
     Lw = oracle.label(rp, ci, O, wl.P, threads=threads)
     if wl.monitor is not None:
         m = wl.monitor
@@ -230,7 +236,10 @@ def calibrate_sample(wl, seconds: float, threads: int) -> int:
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    wl = synth.make(args.workload, seed=args.seed, edges=args.edges, threads=cpu_cores())
+    if args.workload == "paper3d":
+        wl = synth.make_paper3d(seed=args.seed, threads=cpu_cores(), **({"edges": args.edges} if args.edges else {}))
+    else:
+        wl = synth.make(args.workload, seed=args.seed, edges=args.edges, threads=cpu_cores())
     threads = cpu_cores()
     per_step = max(0.5, min(6.0, 120.0 / max(args.steps + args.warmup, 1)))
     n = calibrate_sample(wl, per_step, threads)
@@ -287,7 +296,11 @@ def main():
 
     # ---- inputs: every rank its own independent roadmap and frame
     t_gen = time.perf_counter()
-    wl = synth.make(args.workload, seed=rank_seed(args.seed, rank), edges=args.edges, threads=cpu_cores())
+    if args.workload == "paper3d":
+        wl = synth.make_paper3d(seed=rank_seed(args.seed, rank), threads=cpu_cores(),
+                                **({"edges": args.edges} if args.edges else {}))
+    else:
+        wl = synth.make(args.workload, seed=rank_seed(args.seed, rank), edges=args.edges, threads=cpu_cores())
     t_gen = time.perf_counter() - t_gen
     algo = {"auto": L.LBL_ALGO_AUTO, "csr": L.LBL_ALGO_CSR, "bittile": L.LBL_ALGO_BITTILE,
             "sector": L.LBL_ALGO_SECTOR}[args.algo]
@@ -408,7 +421,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": WORKLOADS[args.workload], "name": args.workload, "edges": E, "nnz": wl.nnz,
-                       "props": P, "grid": f"{wl.agent.w}x{wl.agent.h}", "algo": used, "tuned": tuned,
+                       "props": P, "grid": "x".join(str(v) for v in (wl.agent.w, wl.agent.h, wl.agent.d) if v > 1), "algo": used, "tuned": tuned,
                        "monitor": bool(mon), "l2": "flushed before every step (256 MiB write); CSR "
                        f"{(4 * wl.nnz) / 1e9:.2f} GB > L2", "parallelism": f"replicas x{world}"},
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),

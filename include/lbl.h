@@ -60,18 +60,27 @@ typedef struct CUstream_st *lbl_stream;
  * (ix, iy) covers [x0 + ix*res, x0 + (ix+1)*res) x [y0 + iy*res, y0 + (iy+1)*res)
  * in the grid's own frame (world frame for perception grids, agent frame for
  * the roadmap grid).  `order` numbers the cells (LBL_ORDER_*).
- * Limits: 1 <= w, h <= 32768; w*h <= 2^31 - 1; res > 0.
+ * Time-augmented workspace (Sec. 5, (x, y, tau) with dynamic objects as static
+ * volumes): d > 1 time slabs, slab it covering [t0 + it*tres, t0 + (it+1)*tres)
+ * seconds (relative to the query time in the agent frame).  d <= 1 is a plain
+ * 2-D grid (tres and t0 ignored); cell index = (it*h + iy)*w + ix row-major, or
+ * the 3-D z-order (bit i of ix -> 3i+2, of iy -> 3i+1, of it -> 3i; needs
+ * w == h == d, a power of two).
+ * Limits: 1 <= w, h, d <= 32768; w*h*d <= 2^31 - 1; res > 0; tres > 0 if d > 1.
  */
 typedef struct {
   int32_t w, h;
   double res, x0, y0;
   int32_t order;
+  int32_t d;        /* time slabs, <= 1 = 2-D */
+  double tres, t0;  /* slab length and start, seconds */
 } lbl_grid;
 
 /* Agent pose in the world frame: position (x, y) in metres, heading theta in
-   radians (the agent frame's +x axis points along theta). */
+   radians (the agent frame's +x axis points along theta), and the query time t
+   in seconds (used by time-augmented grids, eq. 13's shift in t). */
 typedef struct {
-  double x, y, theta;
+  double x, y, theta, t;
 } lbl_pose;
 
 /* Labeling algorithm (Sec. 4.3: both compute eq. 10 exactly). */
@@ -165,16 +174,20 @@ int lbl_roadmap_info(lbl_roadmap rm, int64_t *n_edges, int64_t *nnz, int64_t *n_
  * For every cell (ix, iy) of `agent`, take its centre c in the agent frame,
  * move it to the world point q = (pose.x, pose.y) + R(pose.theta) c, and set
  * bit p of d_O[index(ix, iy)] iff d_planes[p] is non-zero at the world cell
- * containing q; world points outside `world` read as 0.
+ * containing q; world points outside `world` read as 0.  Time-augmented
+ * grids: agent slab it (centre t0 + (it+.5)tres) reads the world slab holding
+ * pose.t + that centre; a 2-D world under a time-augmented agent grid is a
+ * static world (every slab reads its single plane); a time-augmented world
+ * needs a time-augmented agent grid.
  * Exactness: the map (ix, iy) -> world cell coordinates is affine; its six
  * coefficients are computed once in double on the host and rounded (half to
  * even) to Q32.32 fixed point; the map is then evaluated exactly in 64-bit
  * integers and floored, so every device and every run give the same cells.
  *   world     grid of the planes (row-major planes, its `order` is ignored)
- *   d_planes  uint8[n_props][world.h][world.w], non-zero = occupied
+ *   d_planes  uint8[n_props][world.d][world.h][world.w], non-zero = occupied
  *   n_props   0..64
  *   agent     roadmap grid; d_O is written in agent.order
- *   d_O       uint64[agent.w * agent.h]
+ *   d_O       uint64[agent.w * agent.h * agent.d]
  * Errors: LBL_EINVAL for bad grids, n_props > 64, or a pose whose fixed-point
  * map could overflow 64 bits.
  */
@@ -304,7 +317,7 @@ int lbl_roadmap_autotune(lbl_roadmap rm, const uint64_t *d_O, int32_t n_props, l
  */
 typedef struct {
   lbl_grid world;          /* world grid of d_planes (its order is ignored) */
-  const uint8_t *d_planes; /* uint8[n_props][world.h][world.w] */
+  const uint8_t *d_planes; /* uint8[n_props][world.d][world.h][world.w] */
   lbl_pose pose;           /* agent pose in the world */
   uint64_t *d_O;           /* uint64[agent cells]: transformed words (written) */
   uint64_t *d_L;           /* uint64[E]: labels */
@@ -347,7 +360,8 @@ int lbl_batch_free(lbl_batch b);
  *                    uint8[n_props][world.h][world.w]; outputs h_L uint64[E],
  *                    h_next/h_viol (monitor only, may be NULL).  All host
  *                    buffers must stay valid until the request completes; use
- *                    pinned memory for asynchronous copies.  arrival_ns: the
+ *                    pinned memory for asynchronous copies (planes are
+ *                    uint8[n_props][world.d][world.h][world.w]).  arrival_ns: the
  *                    request's arrival on CLOCK_MONOTONIC (0 = now), the start
  *                    of its latency.  LBL_ENOMEM if it can never fit the arena.
  * lbl_server_wait    block up to timeout_ms for a ticket (LBL_ETIMEOUT
@@ -376,7 +390,7 @@ int lbl_server_free(lbl_server srv);
  *   lbl_session_create  allocates the device buffers (planes, O, labels,
  *                       monitor outputs) for `world` and n_props.
  *   lbl_session_run     enqueues H2D(h_planes) -> transform -> label -> D2H on
- *                       `s`.  h_planes: uint8[n_props][world.h][world.w];
+ *                       `s`.  h_planes: uint8[n_props][world.d][world.h][world.w];
  *                       h_L: uint64[E]; h_next/h_viol: uint64[E]/uint16[E] or
  *                       NULL.  Host buffers should be pinned for asynchronous
  *                       copies.  Results are valid after `s` completes; a

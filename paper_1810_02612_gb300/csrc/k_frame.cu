@@ -17,48 +17,67 @@ __device__ __forceinline__ uint32_t gather_even_bits(uint64_t v) {
   return static_cast<uint32_t>(v);
 }
 
-struct FrameArgs {
-  FrameMap map;
-  const uint8_t *planes;
-  uint64_t *O;
-  int64_t plane_cells;  // ww * wh
-  int32_t ww, wh, aw, ah, P, order;
-};
+// Every third bit of v (positions 0, 3, ..., 60) packed into the low 21 bits:
+// the inverse of the 3-D z-order interleave for one coordinate.
+__device__ __forceinline__ uint32_t gather_third_bits(uint64_t v) {
+  v &= 0x1249249249249249ull;
+  v = (v | (v >> 2)) & 0x10C30C30C30C30C3ull;
+  v = (v | (v >> 4)) & 0x100F00F00F00F00Full;
+  v = (v | (v >> 8)) & 0x001F0000FF0000FFull;
+  v = (v | (v >> 16)) & 0x001F00000000FFFFull;
+  v = (v | (v >> 32)) & 0x00000000001FFFFFull;
+  return static_cast<uint32_t>(v);
+}
+
+// World word of agent cell idx of frame f (2-D or time-augmented).  The world
+// cell is the floor of exact Q32.32 affine maps of (ix, iy) and of the slab it.
+__device__ __forceinline__ uint64_t frame_word(const FrameItem &f, int64_t idx) {
+  int64_t ix, iy, it = 0;
+  if (f.ad > 1) {
+    if (f.order == LBL_ORDER_MORTON) {
+      ix = gather_third_bits(static_cast<uint64_t>(idx) >> 2);
+      iy = gather_third_bits(static_cast<uint64_t>(idx) >> 1);
+      it = gather_third_bits(static_cast<uint64_t>(idx));
+    } else {
+      const int64_t plane = static_cast<int64_t>(f.aw) * f.ah;
+      it = idx / plane;
+      const int64_t r = idx - it * plane;
+      iy = r / f.aw;
+      ix = r - iy * f.aw;
+    }
+  } else if (f.order == LBL_ORDER_MORTON) {
+    ix = gather_even_bits(static_cast<uint64_t>(idx) >> 1);
+    iy = gather_even_bits(static_cast<uint64_t>(idx));
+  } else {
+    iy = idx / f.aw;
+    ix = idx - iy * f.aw;
+  }
+  const int64_t wx = (f.A00 * ix + f.A01 * iy + f.B0) >> 32;  // arithmetic shift: floor
+  const int64_t wy = (f.A10 * ix + f.A11 * iy + f.B1) >> 32;
+  const int64_t wt = f.wd > 1 ? ((f.At * it + f.Bt) >> 32) : 0;  // a 2-D world is static in time
+  uint64_t word = 0;
+  if (wx >= 0 && wx < f.ww && wy >= 0 && wy < f.wh && wt >= 0 && wt < f.wd) {
+    const uint8_t *p = f.planes + (wt * f.wh + wy) * f.ww + wx;
+    int q = 0;
+    for (; q + 8 <= f.P; q += 8) {
+      uint8_t b[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) b[j] = __ldg(p + (q + j) * f.plane_cells);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) word |= static_cast<uint64_t>(b[j] != 0) << (q + j);
+    }
+    for (; q < f.P; ++q) word |= static_cast<uint64_t>(__ldg(p + q * f.plane_cells) != 0) << q;
+  }
+  return word;
+}
 
 // One thread per agent cell, in output (cell-order) index so the O stores are
-// coalesced.  The world cell is the floor of an exact Q32.32 affine map of
-// (ix, iy); P byte gathers build the proposition word.
-__global__ void __launch_bounds__(256) k_frame_transform(FrameArgs a) {
-  const int64_t n = static_cast<int64_t>(a.aw) * a.ah;
+// coalesced.
+__global__ void __launch_bounds__(256) k_frame_transform(const __grid_constant__ FrameItem f) {
+  const int64_t n = static_cast<int64_t>(f.aw) * f.ah * f.ad;
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-  for (int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; idx < n; idx += stride) {
-    int64_t ix, iy;
-    if (a.order == LBL_ORDER_MORTON) {
-      ix = gather_even_bits(static_cast<uint64_t>(idx) >> 1);
-      iy = gather_even_bits(static_cast<uint64_t>(idx));
-    } else {
-      iy = idx / a.aw;
-      ix = idx - iy * a.aw;
-    }
-    const int64_t u = a.map.A00 * ix + a.map.A01 * iy + a.map.B0;
-    const int64_t v = a.map.A10 * ix + a.map.A11 * iy + a.map.B1;
-    const int64_t wx = u >> 32;  // arithmetic shift: floor for negative values too
-    const int64_t wy = v >> 32;
-    uint64_t word = 0;
-    if (wx >= 0 && wx < a.ww && wy >= 0 && wy < a.wh) {
-      const uint8_t *p = a.planes + wy * a.ww + wx;
-      int q = 0;
-      for (; q + 8 <= a.P; q += 8) {
-        uint8_t b[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) b[j] = __ldg(p + (q + j) * a.plane_cells);
-#pragma unroll
-        for (int j = 0; j < 8; ++j) word |= static_cast<uint64_t>(b[j] != 0) << (q + j);
-      }
-      for (; q < a.P; ++q) word |= static_cast<uint64_t>(__ldg(p + q * a.plane_cells) != 0) << q;
-    }
-    a.O[idx] = word;
-  }
+  for (int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; idx < n; idx += stride)
+    f.O[idx] = frame_word(f, idx);
 }
 
 // Batched frame transform: thread per (frame, agent cell) over all frames'
@@ -77,24 +96,7 @@ __global__ void __launch_bounds__(256) k_frame_batch(const __grid_constant__ Fra
     }
     const FrameItem &f = tab.items[lo];
     const int64_t idx = gidx - f.cell0;
-    int64_t ix, iy;
-    if (f.order == LBL_ORDER_MORTON) {
-      ix = gather_even_bits(static_cast<uint64_t>(idx) >> 1);
-      iy = gather_even_bits(static_cast<uint64_t>(idx));
-    } else {
-      iy = idx / f.aw;
-      ix = idx - iy * f.aw;
-    }
-    const int64_t u = f.A00 * ix + f.A01 * iy + f.B0;
-    const int64_t v = f.A10 * ix + f.A11 * iy + f.B1;
-    const int64_t wx = u >> 32;
-    const int64_t wy = v >> 32;
-    uint64_t word = 0;
-    if (wx >= 0 && wx < f.ww && wy >= 0 && wy < f.wh) {
-      const uint8_t *p = f.planes + wy * f.ww + wx;
-      for (int q = 0; q < f.P; ++q) word |= static_cast<uint64_t>(__ldg(p + q * f.plane_cells) != 0) << q;
-    }
-    f.O[idx] = word;
+    f.O[idx] = frame_word(f, idx);
   }
 }
 
@@ -120,15 +122,13 @@ __global__ void __launch_bounds__(256) k_monitor_step(MonitorTables mon, const u
 
 }  // namespace
 
-cudaError_t launch_frame_transform(const FrameMap &m, const uint8_t *planes, int32_t ww, int32_t wh, int32_t P,
-                                   int32_t aw, int32_t ah, int32_t order, uint64_t *O, int num_sms, cudaStream_t s) {
-  const int64_t n = static_cast<int64_t>(aw) * ah;
+cudaError_t launch_frame_transform(const FrameItem &f, int num_sms, cudaStream_t s) {
+  const int64_t n = static_cast<int64_t>(f.aw) * f.ah * f.ad;
   if (n == 0) return cudaSuccess;
-  FrameArgs a{m, planes, O, static_cast<int64_t>(ww) * wh, ww, wh, aw, ah, P, order};
   int64_t blocks = (n + 255) / 256;
   const int64_t cap = static_cast<int64_t>(num_sms) * 8;
   if (blocks > cap) blocks = cap;
-  k_frame_transform<<<static_cast<unsigned>(blocks), 256, 0, s>>>(a);
+  k_frame_transform<<<static_cast<unsigned>(blocks), 256, 0, s>>>(f);
   return cudaGetLastError();
 }
 

@@ -30,13 +30,19 @@ bool valid_grid(const lbl_grid *g, const char *name, bool need_order) {
     set_error("%s: grid pointer is NULL", name);
     return false;
   }
-  if (g->w < 1 || g->h < 1 || g->w > 32768 || g->h > 32768 ||
-      static_cast<int64_t>(g->w) * g->h > 2147483647LL) {
-    set_error("%s: grid size %d x %d outside 1..32768 per side / 2^31-1 cells", name, g->w, g->h);
+  const int64_t d = grid_depth(*g);
+  if (g->w < 1 || g->h < 1 || g->w > 32768 || g->h > 32768 || d > 32768 ||
+      static_cast<int64_t>(g->w) * g->h * d > 2147483647LL) {
+    set_error("%s: grid size %d x %d x %lld outside 1..32768 per side / 2^31-1 cells", name, g->w, g->h,
+              static_cast<long long>(d));
     return false;
   }
   if (!(g->res > 0.0) || !std::isfinite(g->res) || !std::isfinite(g->x0) || !std::isfinite(g->y0)) {
     set_error("%s: resolution must be positive and the corner finite", name);
+    return false;
+  }
+  if (d > 1 && (!(g->tres > 0.0) || !std::isfinite(g->tres) || !std::isfinite(g->t0))) {
+    set_error("%s: a time-augmented grid needs a positive slab length and a finite start", name);
     return false;
   }
   if (need_order) {
@@ -44,8 +50,9 @@ bool valid_grid(const lbl_grid *g, const char *name, bool need_order) {
       set_error("%s: unknown cell order %d", name, g->order);
       return false;
     }
-    if (g->order == LBL_ORDER_MORTON && (g->w != g->h || (g->w & (g->w - 1)) != 0)) {
-      set_error("%s: z-order needs a square power-of-two grid (got %d x %d)", name, g->w, g->h);
+    if (g->order == LBL_ORDER_MORTON && (g->w != g->h || (d > 1 && d != g->w) || (g->w & (g->w - 1)) != 0)) {
+      set_error("%s: z-order needs a cube (or square) power-of-two grid (got %d x %d x %lld)", name, g->w, g->h,
+                static_cast<long long>(d));
       return false;
     }
   }
@@ -106,8 +113,12 @@ int resolve_lpe(const Roadmap &rm, const lbl_config *cfg) {
 // The double expressions are evaluated exactly as written (the library is built
 // without floating-point contraction) and each is rounded half to even.
 bool frame_map(const lbl_grid &W, const lbl_grid &A, const lbl_pose &p, FrameMap *out) {
-  if (!std::isfinite(p.x) || !std::isfinite(p.y) || !std::isfinite(p.theta)) {
+  if (!std::isfinite(p.x) || !std::isfinite(p.y) || !std::isfinite(p.theta) || !std::isfinite(p.t)) {
     set_error("frame transform: pose must be finite");
+    return false;
+  }
+  if (grid_depth(W) > 1 && grid_depth(A) <= 1) {
+    set_error("frame transform: a time-augmented world needs a time-augmented agent grid");
     return false;
   }
   const double c = std::cos(p.theta);
@@ -134,7 +145,27 @@ bool frame_map(const lbl_grid &W, const lbl_grid &A, const lbl_pose &p, FrameMap
   out->A10 = q(a10);
   out->A11 = q(a11);
   out->B1 = q(b1);
+  out->At = out->Bt = 0;
+  if (grid_depth(W) > 1) {
+    // slab it of the agent (centre t0 + (it + 1/2) tres after the query time)
+    // -> continuous world slab coordinate, the time shift of eq. 13
+    const double at = A.tres / W.tres;
+    const double ta = A.t0 + 0.5 * A.tres;
+    const double bt = ((p.t + ta) - W.t0) / W.tres;
+    if (!(std::fabs(at) <= lim_a && std::fabs(bt) <= lim_b)) {
+      set_error("frame transform: query time or slab ratio out of the fixed-point range");
+      return false;
+    }
+    out->At = q(at);
+    out->Bt = q(bt);
+  }
   return true;
+}
+
+FrameItem frame_item(const FrameMap &m, const lbl_grid &W, const lbl_grid &A, const uint8_t *planes, int32_t P,
+                     uint64_t *O, int64_t cell0) {
+  return FrameItem{m.A00, m.A01, m.B0, m.A10, m.A11, m.B1, m.At, m.Bt, planes, O, grid_cells(W), cell0,
+                   W.w, W.h, grid_depth(W), A.w, A.h, grid_depth(A), P, A.order};
 }
 
 void set_error(const char *fmt, ...) {
@@ -225,7 +256,7 @@ int lbl_roadmap_upload(const lbl_grid *agent, const int64_t *rowptr, const int32
   rm->agent = *agent;
   rm->E = n_edges;
   rm->nnz = nnz;
-  rm->cells = static_cast<int64_t>(agent->w) * agent->h;
+  rm->cells = grid_cells(*agent);
   const int64_t padded = ((nnz + 3) / 4) * 4 + 4;  // whole 16-byte vectors, plus one
   unsigned long long *d_bad = nullptr;
   int32_t *d_cnt = nullptr;
@@ -415,8 +446,8 @@ int lbl_frame_transform(const lbl_grid *world, const uint8_t *d_planes, int32_t 
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "frame transform: cudaGetDevice");
-  e = launch_frame_transform(m, d_planes, world->w, world->h, n_props, agent->w, agent->h, agent->order, d_O,
-                             device_sms(dev), reinterpret_cast<cudaStream_t>(s));
+  e = launch_frame_transform(frame_item(m, *world, *agent, d_planes, n_props, d_O, 0), device_sms(dev),
+                             reinterpret_cast<cudaStream_t>(s));
   if (e != cudaSuccess) return cuda_fail(e, "frame transform: launch");
   return LBL_OK;
 }
@@ -786,10 +817,7 @@ int lbl_batch_set_frames(lbl_batch b, const lbl_frame *frames) {
     }
     FrameMap m;
     if (!frame_map(f.world, r.agent, f.pose, &m)) return LBL_EINVAL;
-    FrameItem &fi = b->ftab.items[i];
-    fi = FrameItem{m.A00, m.A01, m.B0, m.A10, m.A11, m.B1, f.d_planes, f.d_O,
-                   static_cast<int64_t>(f.world.w) * f.world.h, cell0, f.world.w, f.world.h, r.agent.w,
-                   r.agent.h, P, r.agent.order};
+    b->ftab.items[i] = frame_item(m, f.world, r.agent, f.d_planes, P, f.d_O, cell0);
     cell0 += r.cells;
     BatchItem &it = b->tab.items[i];
     it.O = f.d_O;
@@ -858,7 +886,7 @@ int lbl_session_create(lbl_roadmap rm, const lbl_grid *world, int32_t n_props, l
     ss->cfg = *cfg;
     ss->has_cfg = true;
   }
-  const size_t plane_bytes = static_cast<size_t>(n_props) * world->w * world->h;
+  const size_t plane_bytes = static_cast<size_t>(n_props) * grid_cells(*world);
   cudaError_t e = dev_alloc(&ss->planes, plane_bytes, nullptr);
   if (e == cudaSuccess) e = dev_alloc(&ss->O, static_cast<size_t>(rm->cells), nullptr);
   if (e == cudaSuccess) e = dev_alloc(&ss->L, static_cast<size_t>(rm->E), nullptr);
@@ -891,7 +919,7 @@ int lbl_session_run(lbl_session ss, const uint8_t *h_planes, lbl_pose pose, uint
   }
   if (!same_device(ss->device)) return LBL_EINVAL;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(s);
-  const size_t plane_bytes = static_cast<size_t>(ss->P) * ss->world.w * ss->world.h;
+  const size_t plane_bytes = static_cast<size_t>(ss->P) * grid_cells(ss->world);
   cudaError_t e = cudaSuccess;
   if (plane_bytes) e = cudaMemcpyAsync(ss->planes, h_planes, plane_bytes, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_fail(e, "session run: copy planes");

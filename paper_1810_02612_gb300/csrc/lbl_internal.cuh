@@ -54,11 +54,12 @@ struct BatchItem {
 // One frame's share of a batched frame-transform launch (device table entry).
 struct FrameItem {
   int64_t A00, A01, B0, A10, A11, B1;  // Q32.32 map
+  int64_t At, Bt;                      // Q32.32 time map
   const uint8_t *planes;
   uint64_t *O;
-  int64_t plane_cells;  // ww * wh
+  int64_t plane_cells;  // ww * wh * wd
   int64_t cell0;        // first global cell of this frame
-  int32_t ww, wh, aw, ah, P, order;
+  int32_t ww, wh, wd, aw, ah, ad, P, order;
 };
 
 // Batched launches take their whole item table as one kernel parameter.
@@ -123,15 +124,24 @@ int cuda_fail(cudaError_t e, const char *what);
 
 // --------------------------------------------------------------- kernels
 struct FrameMap {
-  int64_t A00, A01, B0, A10, A11, B1;  // Q32.32
+  int64_t A00, A01, B0, A10, A11, B1;  // Q32.32 (x, y)
+  int64_t At, Bt;                      // Q32.32 time slab map (time-augmented worlds)
 };
+
+// Cells of a grid (d <= 1 counts as one slab).
+inline int64_t grid_cells(const lbl_grid &g) {
+  return static_cast<int64_t>(g.w) * g.h * (g.d > 1 ? g.d : 1);
+}
+inline int32_t grid_depth(const lbl_grid &g) { return g.d > 1 ? g.d : 1; }
 
 // Fixed-point map of the equivariant frame transform (world grid W, agent
 // grid A, pose p); false (with the error set) if it could overflow.
 bool frame_map(const lbl_grid &W, const lbl_grid &A, const lbl_pose &p, FrameMap *out);
+struct FrameItem;
+FrameItem frame_item(const FrameMap &m, const lbl_grid &W, const lbl_grid &A, const uint8_t *planes, int32_t P,
+                     uint64_t *O, int64_t cell0);
 
-cudaError_t launch_frame_transform(const FrameMap &m, const uint8_t *planes, int32_t ww, int32_t wh, int32_t P,
-                                   int32_t aw, int32_t ah, int32_t order, uint64_t *O, int num_sms, cudaStream_t s);
+cudaError_t launch_frame_transform(const FrameItem &f, int num_sms, cudaStream_t s);
 
 cudaError_t launch_label_csr(const Roadmap &rm, const uint64_t *O, int32_t P, uint64_t *L, const MonitorTables *mon,
                              int lanes_per_edge, bool early_exit, int ctas_per_sm, cudaStream_t s);

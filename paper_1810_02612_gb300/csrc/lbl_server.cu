@@ -143,7 +143,7 @@ namespace {
 size_t request_bytes(const lbl_server_s &S, const Request &r) {
   const Resident &R = S.res[r.res];
   const lbl::Roadmap &rm = *R.rm;
-  size_t b = align_up(static_cast<size_t>(R.P) * r.world.w * r.world.h);
+  size_t b = align_up(static_cast<size_t>(R.P) * lbl::grid_cells(r.world));
   b += align_up(static_cast<size_t>(rm.cells) * 8);
   b += align_up(static_cast<size_t>(rm.E) * 8);
   if (R.mon) b += align_up(static_cast<size_t>(rm.E) * 8) + align_up(static_cast<size_t>(rm.E) * 2);
@@ -155,7 +155,7 @@ void carve(lbl_server_s &S, Request &r) {
   const lbl::Roadmap &rm = *R.rm;
   uint8_t *p = S.arena_base + r.off;
   r.d_planes = p;
-  p += align_up(static_cast<size_t>(R.P) * r.world.w * r.world.h);
+  p += align_up(static_cast<size_t>(R.P) * lbl::grid_cells(r.world));
   r.d_O = reinterpret_cast<uint64_t *>(p);
   p += align_up(static_cast<size_t>(rm.cells) * 8);
   r.d_L = reinterpret_cast<uint64_t *>(p);
@@ -178,13 +178,11 @@ cudaError_t launch_group(lbl_server_s &S, Lane &lane, std::vector<Request *> &gr
     Request &r = *group[i];
     const Resident &R = S.res[r.res];
     const lbl::Roadmap &rm = *R.rm;
-    const size_t plane_bytes = static_cast<size_t>(R.P) * r.world.w * r.world.h;
+    const size_t plane_bytes = static_cast<size_t>(R.P) * lbl::grid_cells(r.world);
     if (plane_bytes) e = cudaMemcpyAsync(r.d_planes, r.h_planes, plane_bytes, cudaMemcpyHostToDevice, lane.s);
     lbl::FrameMap m{};
     lbl::frame_map(r.world, rm.agent, r.pose, &m);  // checked at submit
-    ftab.items[i] = FrameItem{m.A00, m.A01, m.B0, m.A10, m.A11, m.B1, r.d_planes, r.d_O,
-                              static_cast<int64_t>(r.world.w) * r.world.h, cell0, r.world.w, r.world.h, rm.agent.w,
-                              rm.agent.h, R.P, rm.agent.order};
+    ftab.items[i] = lbl::frame_item(m, r.world, rm.agent, r.d_planes, R.P, r.d_O, cell0);
     cell0 += rm.cells;
     BatchItem &it = tab.items[i];
     it = BatchItem{};
@@ -396,8 +394,8 @@ int lbl_server_submit(lbl_server S, int32_t roadmap, const lbl_grid *world, cons
     return LBL_EINVAL;
   }
   const Resident &R = S->res[roadmap];
-  if (world->w < 1 || world->h < 1 || world->w > 32768 || world->h > 32768 || !(world->res > 0) ||
-      (R.P > 0 && !h_planes) || (R.rm->E > 0 && !h_L)) {
+  if (world->w < 1 || world->h < 1 || world->w > 32768 || world->h > 32768 || world->d > 32768 ||
+      !(world->res > 0) || (world->d > 1 && !(world->tres > 0)) || (R.P > 0 && !h_planes) || (R.rm->E > 0 && !h_L)) {
     lbl::set_error("server submit: bad world grid or missing host buffer");
     return LBL_EINVAL;
   }

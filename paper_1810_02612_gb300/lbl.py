@@ -63,11 +63,13 @@ class LblError(RuntimeError):
 
 class lbl_grid(ctypes.Structure):
     _fields_ = [("w", ctypes.c_int32), ("h", ctypes.c_int32), ("res", ctypes.c_double),
-                ("x0", ctypes.c_double), ("y0", ctypes.c_double), ("order", ctypes.c_int32)]
+                ("x0", ctypes.c_double), ("y0", ctypes.c_double), ("order", ctypes.c_int32),
+                ("d", ctypes.c_int32), ("tres", ctypes.c_double), ("t0", ctypes.c_double)]
 
 
 class lbl_pose(ctypes.Structure):
-    _fields_ = [("x", ctypes.c_double), ("y", ctypes.c_double), ("theta", ctypes.c_double)]
+    _fields_ = [("x", ctypes.c_double), ("y", ctypes.c_double), ("theta", ctypes.c_double),
+                ("t", ctypes.c_double)]
 
 
 class lbl_frame(ctypes.Structure):
@@ -140,13 +142,15 @@ def load(build_if_needed: bool = True):
 def _grid(g) -> lbl_grid:
     if isinstance(g, lbl_grid):
         return g
-    return lbl_grid(int(g.w), int(g.h), float(g.res), float(g.x0), float(g.y0), int(getattr(g, "order", 0)))
+    return lbl_grid(int(g.w), int(g.h), float(g.res), float(g.x0), float(g.y0), int(getattr(g, "order", 0)),
+                    int(getattr(g, "d", 1)), float(getattr(g, "tres", 1.0)), float(getattr(g, "t0", 0.0)))
 
 
 def _pose(p) -> lbl_pose:
+    """(x, y, theta) or (x, y, theta, t)."""
     if isinstance(p, lbl_pose):
         return p
-    return lbl_pose(float(p[0]), float(p[1]), float(p[2]))
+    return lbl_pose(float(p[0]), float(p[1]), float(p[2]), float(p[3]) if len(p) > 3 else 0.0)
 
 
 def _cfg(cfg):

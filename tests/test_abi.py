@@ -39,9 +39,10 @@ def test_python_binding_has_the_same_names():
 
 
 def test_struct_layouts_match_the_header():
-    assert ctypes.sizeof(B.lbl_grid) == 40
+    assert ctypes.sizeof(B.lbl_grid) == 56
     assert B.lbl_grid.res.offset == 8 and B.lbl_grid.order.offset == 32
-    assert ctypes.sizeof(B.lbl_pose) == 24
+    assert B.lbl_grid.d.offset == 36 and B.lbl_grid.tres.offset == 40 and B.lbl_grid.t0.offset == 48
+    assert ctypes.sizeof(B.lbl_pose) == 32
     assert ctypes.sizeof(B.lbl_config) == 24
 
 
@@ -72,6 +73,9 @@ def test_monitor_create_rejects_bad_tables(args):
     dict(w=6, h=6, res=1.0, x0=0.0, y0=0.0, order=1),   # z-order needs a power of two
     dict(w=8, h=4, res=1.0, x0=0.0, y0=0.0, order=1),   # and a square
     dict(w=8, h=8, res=1.0, x0=0.0, y0=0.0, order=7),
+    dict(w=8, h=8, res=1.0, x0=0.0, y0=0.0, order=1, d=4, tres=0.1, t0=0.0),  # z-order cube needs d == w
+    dict(w=8, h=8, res=1.0, x0=0.0, y0=0.0, order=0, d=4, tres=0.0, t0=0.0),  # slabs need a length
+    dict(w=32768, h=32768, res=1.0, x0=0.0, y0=0.0, order=0, d=4, tres=1.0, t0=0.0),  # too many cells
 ])
 def test_roadmap_upload_rejects_bad_grids_before_device_work(grid):
     g = B.lbl_grid(**grid)
