@@ -63,6 +63,12 @@ def _load():
         lib.orc_label_rows.argtypes = [i64, p, p, p, p, i32, p]
         lib.orc_monitor.restype = ctypes.c_int
         lib.orc_monitor.argtypes = [i32, i32, p, p, i32, p, i64, p, p]
+        lib.orc_arc_geometry.restype = None
+        lib.orc_arc_geometry.argtypes = [p, p]
+        lib.orc_arc_dist.restype = f64
+        lib.orc_arc_dist.argtypes = [p, p, f64, f64]
+        lib.orc_sweep.restype = i64
+        lib.orc_sweep.argtypes = [i64, p, f64, i32, i32, f64, f64, f64, i32, p, p]
         lib.orc_morton3.restype = ctypes.c_uint64
         lib.orc_morton3.argtypes = [ctypes.c_uint32] * 3
         lib.orc_cell_index3.restype = i64
@@ -172,3 +178,20 @@ def frame_transform3(world, vols: np.ndarray, pose, agent) -> np.ndarray:
     if rc != 0:
         raise ValueError("oracle 3-D frame transform rejected its arguments")
     return O
+
+
+def sweep(arcs: np.ndarray, radius: float, grid):
+    """Swept-cell rows (rowptr, colidx) of arcs (x, y, heading, curvature,
+    length) over every cell of a 2-D grid: eq. 7 with a disc footprint,
+    discretised by cell centres."""
+    arcs = np.ascontiguousarray(arcs, np.float64).reshape(-1, 5)
+    n = arcs.shape[0]
+    counts = np.zeros(max(n, 1), np.int64)
+    total = _load().orc_sweep(n, _ptr(arcs), float(radius), grid.w, grid.h, grid.res, grid.x0, grid.y0,
+                              grid.order, _ptr(counts), None)
+    keys = np.zeros(max(total, 1), np.int32)
+    _load().orc_sweep(n, _ptr(arcs), float(radius), grid.w, grid.h, grid.res, grid.x0, grid.y0, grid.order,
+                      _ptr(counts), _ptr(keys))
+    rowptr = np.zeros(n + 1, np.int64)
+    rowptr[1:] = np.cumsum(counts[:n])
+    return rowptr, keys[:total]

@@ -19,6 +19,10 @@
  *                                (proposition, row, nonzero)
  *   orc_monitor                  safety-monitor transition delta(q, L(e)) for every
  *                                monitor state, Sec. 3.2
+ *   orc_arc_geometry / orc_arc_dist / orc_sweep
+ *                                swept-cell rows of a roadmap: eq. 7 with the closed
+ *                                disc footprint of eq. 5, discretised by cell centres
+ *                                (Sec. 4.1)
  *   orc_morton3 / orc_cell_index3 / orc_time_coeffs / orc_frame_transform3
  *                                the time-augmented (x, y, tau) workspace of Sec. 5:
  *                                3-D z-order and the frame transform with the
@@ -271,4 +275,120 @@ int orc_frame_transform3(int32_t ww, int32_t wh, int32_t wd, double wres, double
     }
   }
   return 0;
+}
+
+/* -------------------------------------------- swept cells (roadmap rows) */
+
+/*
+ * The swept set of eq. 7 discretised as in Sec. 4.1: cell c belongs to row e
+ * iff the distance from c's centre to the arc X(e) is at most the footprint
+ * radius (closed disc footprint, F of eq. 5).  Arc = (x, y, heading,
+ * curvature, length): a straight segment if |curvature| < 1e-9, else a circle
+ * arc of radius 1/|curvature| turning by curvature * length.
+ *
+ * Geometry (12 doubles): straight: {1, x, y, cos, sin, len, ...}; circle:
+ * {0, cx, cy, R, sgn, u0x, u0y, u1x, u1y, px1, py1, sweep class} where u0/u1 are
+ * the unit vectors from the centre to the start/end, (px1, py1) the end point
+ * and the class is 2 (full turn), 1 (more than half a turn) or 0.
+ */
+void orc_arc_geometry(const double *a, double *g) {
+  const double x = a[0], y = a[1], th = a[2], k = a[3], len = a[4];
+  for (int i = 0; i < 12; i++) g[i] = 0.0;
+  if (fabs(k) < 1e-9) {
+    g[0] = 1.0;
+    g[1] = x;
+    g[2] = y;
+    g[3] = cos(th);
+    g[4] = sin(th);
+    g[5] = len;
+    return;
+  }
+  const double inv = 1.0 / k;
+  const double sg = k > 0 ? 1.0 : -1.0;
+  const double cx = x - inv * sin(th);
+  const double cy = y + inv * cos(th);
+  const double th1 = th + k * len;
+  const double sweep = fabs(k * len);
+  g[0] = 0.0;
+  g[1] = cx;
+  g[2] = cy;
+  g[3] = fabs(inv);
+  g[4] = sg;
+  g[5] = sg * sin(th);
+  g[6] = -sg * cos(th);
+  g[7] = sg * sin(th1);
+  g[8] = -sg * cos(th1);
+  g[9] = cx + inv * sin(th1);
+  g[10] = cy - inv * cos(th1);
+  g[11] = sweep >= 2.0 * M_PI ? 2.0 : (sweep > M_PI ? 1.0 : 0.0);
+}
+
+/* Distance from (px, py) to the arc: the nearest circle point if its angle is
+   inside the arc's sweep (tested with cross products against the end
+   directions), else the nearer end point; for segments, the clamped
+   projection. */
+double orc_arc_dist(const double *g, const double *a, double px, double py) {
+  if (g[0] == 1.0) {
+    double t = (px - g[1]) * g[3] + (py - g[2]) * g[4];
+    if (t < 0.0) t = 0.0;
+    if (t > g[5]) t = g[5];
+    const double ex = (px - g[1]) - t * g[3];
+    const double ey = (py - g[2]) - t * g[4];
+    return sqrt(ex * ex + ey * ey);
+  }
+  const double wx = px - g[1], wy = py - g[2];
+  const double rho = sqrt(wx * wx + wy * wy);
+  int inside = 1;
+  if (g[11] != 2.0 && rho > 0.0) {
+    if (g[11] == 0.0) {
+      const double c0 = g[4] * (g[5] * wy - g[6] * wx);
+      const double c1 = g[4] * (wx * g[8] - wy * g[7]);
+      inside = (c0 >= 0.0) && (c1 >= 0.0);
+    } else {
+      const double c0 = g[4] * (g[7] * wy - g[8] * wx);
+      const double c1 = g[4] * (wx * g[6] - wy * g[5]);
+      inside = !((c0 > 0.0) && (c1 > 0.0));
+    }
+  }
+  if (inside) return fabs(rho - g[3]);
+  const double ax = px - a[0], ay = py - a[1], bx = px - g[9], by = py - g[10];
+  const double d0 = sqrt(ax * ax + ay * ay), d1 = sqrt(bx * bx + by * by);
+  return d0 < d1 ? d0 : d1;
+}
+
+/* Rows of the listed arcs over every cell of a 2-D grid (plain scan in cell
+   index order, so each row comes out sorted).  counts[i] receives row i's
+   length; keys (may be NULL) receives the rows one after another. */
+int64_t orc_sweep(int64_t n, const double *arcs, double radius, int32_t w, int32_t h, double res, double x0,
+                  double y0, int32_t order, int64_t *counts, int32_t *keys) {
+  int64_t total = 0;
+  const int64_t cells = (int64_t)w * h;
+  for (int64_t i = 0; i < n; i++) {
+    double g[12];
+    orc_arc_geometry(arcs + 5 * i, g);
+    int64_t cnt = 0;
+    for (int64_t idx = 0; idx < cells; idx++) {
+      int32_t ix, iy;
+      if (order == ORC_MORTON) {
+        uint32_t xs = 0, ys = 0;
+        for (int b = 0; b < 16; b++) {
+          xs |= (uint32_t)((idx >> (2 * b + 1)) & 1) << b;
+          ys |= (uint32_t)((idx >> (2 * b)) & 1) << b;
+        }
+        ix = (int32_t)xs;
+        iy = (int32_t)ys;
+      } else {
+        iy = (int32_t)(idx / w);
+        ix = (int32_t)(idx - (int64_t)iy * w);
+      }
+      const double cx = x0 + (ix + 0.5) * res, cy = y0 + (iy + 0.5) * res;
+      if (orc_arc_dist(g, arcs + 5 * i, cx, cy) <= radius) {
+        if (keys) keys[total] = (int32_t)idx;
+        total++;
+        cnt++;
+      }
+    }
+    counts[i] = cnt;
+  }
+  return total;
 }

@@ -549,3 +549,61 @@ def test_monitor_unused_state_fields_are_zero():
     nxt, viol = oracle.monitor(5, 3, np.array([0, 61, 33], np.uint8), table, 4, L)
     assert ((nxt >> U64(20)) == 0).all()
     assert ((viol >> np.uint16(5)) == 0).all()
+
+
+# ------------------------------------------------ swept-cell rasteriser
+
+def _centres(grid):
+    N = grid.w
+    ix, iy = np.meshgrid(np.arange(N), np.arange(grid.h), indexing="xy")
+    cx = (grid.x0 + (ix + 0.5) * grid.res).ravel()
+    cy = (grid.y0 + (iy + 0.5) * grid.res).ravel()
+    if grid.order == synth.MORTON:
+        keys = np.array([_morton_ref(x, y, N) for y in range(grid.h) for x in range(N)])
+    else:
+        keys = (iy * N + ix).ravel()
+    return cx, cy, keys
+
+
+@pytest.mark.parametrize("order", [synth.MORTON, synth.ROWMAJOR])
+def test_oracle_sweep_matches_dense_arc_sampling(order):
+    """eq. 7 with a disc footprint: a cell is in row e iff its centre is within
+    the radius of some point of the arc (dense sampling bounds the distance
+    from both sides; only ties are left undecided)."""
+    rng = np.random.default_rng(50 + order)
+    grid = synth.agent_grid(32, 0.25, order)
+    arcs = synth.sample_arcs(rng, 50, grid, kappa=(-1.5, 1.5), length=(0.1, 30.0))
+    arcs[0, 3] = 0.0          # straight
+    arcs[1, 3:5] = (1.2, 12.0)  # more than a full turn
+    arcs[2, 0:2] = (-20.0, 0.0)  # starts outside the grid
+    rowptr, colidx = oracle.sweep(arcs, 0.4, grid)
+    cx, cy, keys = _centres(grid)
+    for e in range(50):
+        pts = _arc_points(arcs[e], 20000)
+        h = arcs[e, 4] / (pts.shape[0] - 1)
+        d = np.sqrt(((cx[:, None] - pts[None, :, 0]) ** 2 + (cy[:, None] - pts[None, :, 1]) ** 2).min(1))
+        row = colidx[rowptr[e]:rowptr[e + 1]]
+        assert set(keys[d <= 0.4 - 1e-9].tolist()) <= set(row.tolist()) <= set(keys[d <= 0.4 + h / 2 + 1e-9].tolist())
+        assert (np.diff(row) > 0).all()
+
+
+def test_oracle_sweep_full_turn_is_an_annulus():
+    grid = synth.agent_grid(64, 0.2, synth.ROWMAJOR)
+    k, r = 0.4, 0.5
+    arc = np.array([[0.0, -2.5, 0.0, k, 2 * math.pi / k + 0.3]])  # circle of radius 2.5 centred at the origin
+    rowptr, colidx = oracle.sweep(arc, r, grid)
+    cx, cy, keys = _centres(grid)
+    ring = np.abs(np.hypot(cx, cy) - 1 / k) <= r
+    tie = np.abs(np.abs(np.hypot(cx, cy) - 1 / k) - r) < 1e-9
+    got = np.zeros(grid.cells, bool)
+    got[colidx] = True
+    assert (got[~tie] == ring[~tie]).all()
+
+
+def test_oracle_sweep_agrees_with_the_generator_away_from_ties():
+    rng = np.random.default_rng(77)
+    grid = synth.agent_grid(64, 0.5, synth.MORTON)
+    arcs = synth.sample_arcs(rng, 200, grid)
+    r1, c1 = oracle.sweep(arcs, 1.0, grid)
+    r2, c2 = synth.sweep_csr(arcs, 1.0, grid)
+    assert np.array_equal(r1, r2) and np.array_equal(c1, c2)
