@@ -294,7 +294,7 @@ int orc_frame_transform3(int32_t ww, int32_t wh, int32_t wd, double wres, double
 void orc_arc_geometry(const double *a, double *g) {
   const double x = a[0], y = a[1], th = a[2], k = a[3], len = a[4];
   for (int i = 0; i < 12; i++) g[i] = 0.0;
-  if (fabs(k) < 1e-9) {
+  if (fabs(k) < 1e-9 || !(len > 0.0)) { /* a segment, or a zero-length arc: its start point */
     g[0] = 1.0;
     g[1] = x;
     g[2] = y;

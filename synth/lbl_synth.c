@@ -42,7 +42,7 @@ static void arc_setup(arcgeom_t *g, double px, double py, double th, double kapp
   g->ax = px;
   g->ay = py;
   g->len = len;
-  if (fabs(kappa) < 1e-9) {
+  if (fabs(kappa) < 1e-9 || !(len > 0.0)) { /* a segment, or a zero-length arc: its start point */
     g->straight = 1;
     g->dx = cos(th);
     g->dy = sin(th);

@@ -600,6 +600,16 @@ def test_oracle_sweep_full_turn_is_an_annulus():
     assert (got[~tie] == ring[~tie]).all()
 
 
+def test_oracle_sweep_zero_length_arc_is_its_start_point():
+    grid = synth.agent_grid(32, 0.25, synth.ROWMAJOR)
+    cx, cy, keys = _centres(grid)
+    for k in (0.0, 0.7, -2.0):
+        arc = np.array([[0.3, -0.6, 1.0, k, 0.0]])
+        rowptr, colidx = oracle.sweep(arc, 0.5, grid)
+        d = np.hypot(cx - 0.3, cy + 0.6)
+        assert set(colidx.tolist()) == set(keys[d <= 0.5].tolist())
+
+
 def test_oracle_sweep_agrees_with_the_generator_away_from_ties():
     rng = np.random.default_rng(77)
     grid = synth.agent_grid(64, 0.5, synth.MORTON)
