@@ -150,6 +150,26 @@ int lbl_version(void);
 int lbl_roadmap_upload(const lbl_grid *agent, const int64_t *rowptr, const int32_t *colidx, int64_t n_edges,
                        int64_t nnz, uint32_t flags, lbl_stream s, lbl_roadmap *out);
 
+/*
+ * lbl_roadmap_rasterize — build a roadmap's rows on the device: row e holds the
+ * cells of `agent` whose centre lies within `radius` of arc e (eq. 7 with the
+ * closed disc footprint of eq. 5, discretised by cell centres as in Sec. 4.1),
+ * sorted in agent.order.  h_arcs = double[n_edges][5] on the host: start x, y
+ * (agent frame, metres), heading (rad), curvature (1/m; |c| < 1e-9 is a
+ * straight segment), length (m, >= 0).  Each membership decision equals the
+ * fp64 evaluation of that distance test: the arc geometry is computed on the
+ * host, cells within 1 mm of the radius are decided in fp64 with correctly
+ * rounded operations, the rest by an fp32 screen.  2-D grids only
+ * (LBL_EUNSUPPORTED for time-augmented ones); flags: LBL_UPLOAD_BITTILE /
+ * LBL_UPLOAD_SECTOR as for lbl_roadmap_upload.  Synchronises `s`.
+ */
+int lbl_roadmap_rasterize(const lbl_grid *agent, const double *h_arcs, int64_t n_edges, double radius,
+                          uint32_t flags, lbl_stream s, lbl_roadmap *out);
+
+/* Copy a roadmap's rows (CSR of eq. 11, in the caller's edge order) into
+   caller device buffers d_rowptr int64[E+1], d_colidx int32[nnz], on `s`. */
+int lbl_roadmap_rows(lbl_roadmap rm, int64_t *d_rowptr, int32_t *d_colidx, lbl_stream s);
+
 /* Release a roadmap (synchronises the device first). NULL is accepted. */
 int lbl_roadmap_free(lbl_roadmap rm);
 

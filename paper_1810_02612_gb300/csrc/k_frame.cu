@@ -5,18 +5,6 @@
 namespace lbl {
 namespace {
 
-// Even-position bits of v packed into the low half: the inverse of the
-// z-order interleave for one coordinate (Sec. 4.1).
-__device__ __forceinline__ uint32_t gather_even_bits(uint64_t v) {
-  v &= 0x5555555555555555ull;
-  v = (v | (v >> 1)) & 0x3333333333333333ull;
-  v = (v | (v >> 2)) & 0x0F0F0F0F0F0F0F0Full;
-  v = (v | (v >> 4)) & 0x00FF00FF00FF00FFull;
-  v = (v | (v >> 8)) & 0x0000FFFF0000FFFFull;
-  v = (v | (v >> 16)) & 0x00000000FFFFFFFFull;
-  return static_cast<uint32_t>(v);
-}
-
 // Every third bit of v (positions 0, 3, ..., 60) packed into the low 21 bits:
 // the inverse of the 3-D z-order interleave for one coordinate.
 __device__ __forceinline__ uint32_t gather_third_bits(uint64_t v) {

@@ -213,6 +213,166 @@ struct lbl_session_s {
   uint16_t *viol = nullptr;
 };
 
+namespace lbl {
+
+bool valid_grid_public(const lbl_grid *g, const char *name, bool need_order) {
+  return valid_grid(g, name, need_order);
+}
+int device_sms_public(int dev) { return device_sms(dev); }
+void free_roadmap_public(lbl_roadmap_s *rm) { free_roadmap(rm); }
+
+// A roadmap with device arrays for its CSR (rowptr int64[E+1], colidx padded
+// to whole 16-byte vectors plus one, the padding zeroed); contents to be
+// filled by the caller before roadmap_finish.
+int roadmap_new(const lbl_grid &agent, int64_t n_edges, int64_t nnz, lbl_roadmap_s **out) {
+  lbl_roadmap_s *rm = new (std::nothrow) lbl_roadmap_s();
+  if (!rm) {
+    set_error("roadmap: out of host memory");
+    return LBL_ENOMEM;
+  }
+  cudaError_t e = cudaGetDevice(&rm->device);
+  if (e != cudaSuccess) {
+    delete rm;
+    return cuda_fail(e, "roadmap: cudaGetDevice");
+  }
+  rm->num_sms = device_sms(rm->device);
+  rm->agent = agent;
+  rm->E = n_edges;
+  rm->nnz = nnz;
+  rm->cells = grid_cells(agent);
+  const int64_t padded = ((nnz + 3) / 4) * 4 + 4;
+  if ((e = dev_alloc(&rm->rowptr, static_cast<size_t>(n_edges + 1), &rm->bytes)) != cudaSuccess ||
+      (e = dev_alloc(&rm->colidx, static_cast<size_t>(padded), &rm->bytes)) != cudaSuccess ||
+      (e = cudaMemset(rm->colidx + nnz, 0, sizeof(int32_t) * (padded - nnz))) != cudaSuccess) {
+    free_roadmap(rm);
+    return cuda_fail(e, "roadmap: CSR arrays");
+  }
+  *out = rm;
+  return LBL_OK;
+}
+
+// Check the CSR on the device and derive what the kernels need (edge
+// partition, optional block and sector forms); synchronises `st`.  Frees the
+// roadmap on failure.
+int roadmap_finish(lbl_roadmap_s *rm, uint32_t flags, cudaStream_t st) {
+  const int64_t n_edges = rm->E, nnz = rm->nnz;
+  unsigned long long *d_bad = nullptr;
+  int32_t *d_cnt = nullptr;
+  cudaError_t e = cudaSuccess;
+  auto fail = [&](int code) {
+    cudaStreamSynchronize(st);
+    cudaFree(d_bad);
+    cudaFree(d_cnt);
+    free_roadmap(rm);
+    return code;
+  };
+  // row pointer end points
+  int64_t ends[2] = {0, 0};
+  if ((e = cudaMemcpyAsync(&ends[0], rm->rowptr, sizeof(int64_t), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(&ends[1], rm->rowptr + n_edges, sizeof(int64_t), cudaMemcpyDeviceToHost, st)) !=
+          cudaSuccess ||
+      (e = cudaStreamSynchronize(st)) != cudaSuccess)
+    return fail(cuda_fail(e, "roadmap: read row pointer"));
+  if (ends[0] != 0 || ends[1] != nnz) {
+    set_error("roadmap: rowptr[0] = %lld and rowptr[E] = %lld, expected 0 and nnz = %lld",
+              static_cast<long long>(ends[0]), static_cast<long long>(ends[1]), static_cast<long long>(nnz));
+    return fail(LBL_EINVAL);
+  }
+  const bool want_bt = flags & LBL_UPLOAD_BITTILE;
+  if ((e = dev_alloc(&rm->err, 1, &rm->bytes)) != cudaSuccess ||
+      (e = cudaMemsetAsync(rm->err, 0, sizeof(int), st)) != cudaSuccess)
+    return fail(cuda_fail(e, "roadmap: error flag"));
+  if ((e = dev_alloc(&d_bad, 1, nullptr)) != cudaSuccess) return fail(cuda_fail(e, "roadmap: scratch"));
+  if (want_bt && (e = dev_alloc(&d_cnt, static_cast<size_t>(n_edges), nullptr)) != cudaSuccess)
+    return fail(cuda_fail(e, "roadmap: block counts"));
+  if ((e = cudaMemsetAsync(d_bad, 0, sizeof(unsigned long long), st)) != cudaSuccess ||
+      (e = launch_scan_rows(rm->rowptr, rm->colidx, n_edges, nnz, rm->cells, d_bad, d_cnt, st)) != cudaSuccess)
+    return fail(cuda_fail(e, "roadmap: row check"));
+  unsigned long long bad = 0;
+  if ((e = cudaMemcpyAsync(&bad, d_bad, sizeof(bad), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(st)) != cudaSuccess)
+    return fail(cuda_fail(e, "roadmap: row check"));
+  if (bad) {
+    set_error("roadmap: %llu malformed rows (row pointer decreasing or out of range, or column indices "
+              "not strictly increasing inside [0, %lld))",
+              bad, static_cast<long long>(rm->cells));
+    return fail(LBL_EINVAL);
+  }
+  if (n_edges > 0) {
+    // edge partition of the streaming CSR kernel, for its default grid
+    rm->part_cap = static_cast<int64_t>(rm->num_sms) * kMaxCtasPerSm * (kThreads / 32) + 1;
+    if ((e = dev_alloc(&rm->part, static_cast<size_t>(rm->part_cap), &rm->bytes)) != cudaSuccess)
+      return fail(cuda_fail(e, "roadmap: partition"));
+    rm->part_ctas = stream_ctas_per_sm(8);
+    if ((e = launch_partition(*rm, rm->part_ctas, st)) != cudaSuccess)
+      return fail(cuda_fail(e, "roadmap: partition"));
+  }
+  if (want_bt) {
+    std::vector<int32_t> cnt(static_cast<size_t>(n_edges));
+    std::vector<int64_t> brow(static_cast<size_t>(n_edges + 1));
+    if (n_edges &&
+        ((e = cudaMemcpyAsync(cnt.data(), d_cnt, sizeof(int32_t) * n_edges, cudaMemcpyDeviceToHost, st)) !=
+             cudaSuccess ||
+         (e = cudaStreamSynchronize(st)) != cudaSuccess))
+      return fail(cuda_fail(e, "roadmap: block counts"));
+    brow[0] = 0;
+    for (int64_t i = 0; i < n_edges; ++i) brow[i + 1] = brow[i] + cnt[i];
+    rm->n_bt = brow[n_edges];
+    rm->n_blocks = (rm->cells + 63) / 64;
+    if ((e = dev_alloc(&rm->bt_rowptr, static_cast<size_t>(n_edges + 1), &rm->bytes)) != cudaSuccess ||
+        (e = dev_alloc(&rm->bt_block, static_cast<size_t>(rm->n_bt), &rm->bytes)) != cudaSuccess ||
+        (e = dev_alloc(&rm->bt_mask, static_cast<size_t>(rm->n_bt), &rm->bytes)) != cudaSuccess ||
+        (e = dev_alloc(&rm->planes, static_cast<size_t>(rm->n_blocks * 64), &rm->bytes)) != cudaSuccess)
+      return fail(cuda_fail(e, "roadmap: block form"));
+    if ((e = cudaMemcpyAsync(rm->bt_rowptr, brow.data(), sizeof(int64_t) * (n_edges + 1), cudaMemcpyHostToDevice,
+                             st)) != cudaSuccess ||
+        (e = launch_bt_fill(rm->rowptr, rm->colidx, n_edges, rm->bt_rowptr, rm->bt_block, rm->bt_mask, st)) !=
+            cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+      return fail(cuda_fail(e, "roadmap: block form"));
+    rm->has_bt = true;
+  }
+  if ((flags & LBL_UPLOAD_SECTOR) && n_edges > 0) {
+    if (rm->cells > (1LL << 30)) {
+      set_error("roadmap: the sector form needs at most 2^30 cells");
+      return fail(LBL_EINVAL);
+    }
+    std::vector<int32_t> cnt(static_cast<size_t>(n_edges));
+    std::vector<int64_t> srow(static_cast<size_t>(n_edges + 1));
+    int32_t *d_sc = nullptr;
+    if ((e = dev_alloc(&d_sc, static_cast<size_t>(n_edges), nullptr)) != cudaSuccess ||
+        (e = launch_sector_count(rm->rowptr, rm->colidx, n_edges, d_sc, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(cnt.data(), d_sc, sizeof(int32_t) * n_edges, cudaMemcpyDeviceToHost, st)) !=
+            cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess) {
+      cudaFree(d_sc);
+      return fail(cuda_fail(e, "roadmap: sector form"));
+    }
+    cudaFree(d_sc);
+    srow[0] = 0;
+    for (int64_t i = 0; i < n_edges; ++i) srow[i + 1] = srow[i] + cnt[i];
+    rm->n_sec = srow[n_edges];
+    if ((e = dev_alloc(&rm->sec_rowptr, static_cast<size_t>(n_edges + 1), &rm->bytes)) != cudaSuccess ||
+        (e = dev_alloc(&rm->sec, static_cast<size_t>(rm->n_sec), &rm->bytes)) != cudaSuccess ||
+        (e = dev_alloc(&rm->sec_part, static_cast<size_t>(rm->part_cap), &rm->bytes)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(rm->sec_rowptr, srow.data(), sizeof(int64_t) * (n_edges + 1), cudaMemcpyHostToDevice,
+                             st)) != cudaSuccess ||
+        (e = launch_sector_fill(rm->rowptr, rm->colidx, n_edges, rm->sec_rowptr, rm->sec, st)) != cudaSuccess)
+      return fail(cuda_fail(e, "roadmap: sector form"));
+    rm->sec_part_ctas = sector_ctas_per_sm(4);
+    const int64_t W = static_cast<int64_t>(rm->num_sms) * rm->sec_part_ctas * (kThreads / 32);
+    if ((e = launch_partition_into(rm->sec_rowptr, n_edges, W, rm->sec_part, st)) != cudaSuccess)
+      return fail(cuda_fail(e, "roadmap: sector partition"));
+    rm->has_sec = true;
+  }
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(cuda_fail(e, "roadmap"));
+  cudaFree(d_bad);
+  cudaFree(d_cnt);
+  return LBL_OK;
+}
+
+}  // namespace lbl
+
 extern "C" {
 
 const char *lbl_last_error(void) { return g_err.c_str(); }
@@ -240,148 +400,20 @@ int lbl_roadmap_upload(const lbl_grid *agent, const int64_t *rowptr, const int32
     set_error("roadmap upload: unknown flags 0x%x", flags);
     return LBL_EINVAL;
   }
-  const bool dev_in = flags & LBL_UPLOAD_DEVICE_PTRS;
-  lbl_roadmap_s *rm = new (std::nothrow) lbl_roadmap_s();
-  if (!rm) {
-    set_error("roadmap upload: out of host memory");
-    return LBL_ENOMEM;
-  }
   cudaStream_t st = reinterpret_cast<cudaStream_t>(s);
-  cudaError_t e = cudaGetDevice(&rm->device);
+  lbl_roadmap_s *rm = nullptr;
+  int rc = roadmap_new(*agent, n_edges, nnz, &rm);
+  if (rc != LBL_OK) return rc;
+  const cudaMemcpyKind kind = (flags & LBL_UPLOAD_DEVICE_PTRS) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  cudaError_t e = cudaMemcpyAsync(rm->rowptr, rowptr, sizeof(int64_t) * (n_edges + 1), kind, st);
+  if (e == cudaSuccess && nnz > 0) e = cudaMemcpyAsync(rm->colidx, colidx, sizeof(int32_t) * nnz, kind, st);
   if (e != cudaSuccess) {
-    delete rm;
-    return cuda_fail(e, "roadmap upload: cudaGetDevice");
-  }
-  rm->num_sms = device_sms(rm->device);
-  rm->agent = *agent;
-  rm->E = n_edges;
-  rm->nnz = nnz;
-  rm->cells = grid_cells(*agent);
-  const int64_t padded = ((nnz + 3) / 4) * 4 + 4;  // whole 16-byte vectors, plus one
-  unsigned long long *d_bad = nullptr;
-  int32_t *d_cnt = nullptr;
-  int rc = LBL_OK;
-  auto fail = [&](int code) {
     cudaStreamSynchronize(st);
-    cudaFree(d_bad);
-    cudaFree(d_cnt);
     free_roadmap(rm);
-    return code;
-  };
-  if ((e = dev_alloc(&rm->rowptr, static_cast<size_t>(n_edges + 1), &rm->bytes)) != cudaSuccess)
-    return fail(cuda_fail(e, "roadmap upload: rowptr"));
-  if ((e = dev_alloc(&rm->colidx, static_cast<size_t>(padded), &rm->bytes)) != cudaSuccess)
-    return fail(cuda_fail(e, "roadmap upload: colidx"));
-  const cudaMemcpyKind kind = dev_in ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  if ((e = cudaMemcpyAsync(rm->rowptr, rowptr, sizeof(int64_t) * (n_edges + 1), kind, st)) != cudaSuccess)
-    return fail(cuda_fail(e, "roadmap upload: copy rowptr"));
-  if (nnz > 0 && (e = cudaMemcpyAsync(rm->colidx, colidx, sizeof(int32_t) * nnz, kind, st)) != cudaSuccess)
-    return fail(cuda_fail(e, "roadmap upload: copy colidx"));
-  if ((e = cudaMemsetAsync(rm->colidx + nnz, 0, sizeof(int32_t) * (padded - nnz), st)) != cudaSuccess)
-    return fail(cuda_fail(e, "roadmap upload: pad colidx"));
-  // row pointer end points
-  int64_t ends[2] = {0, 0};
-  if ((e = cudaMemcpyAsync(&ends[0], rm->rowptr, sizeof(int64_t), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-      (e = cudaMemcpyAsync(&ends[1], rm->rowptr + n_edges, sizeof(int64_t), cudaMemcpyDeviceToHost, st)) !=
-          cudaSuccess ||
-      (e = cudaStreamSynchronize(st)) != cudaSuccess)
-    return fail(cuda_fail(e, "roadmap upload: read row pointer"));
-  if (ends[0] != 0 || ends[1] != nnz) {
-    set_error("roadmap upload: rowptr[0] = %lld and rowptr[E] = %lld, expected 0 and nnz = %lld",
-              static_cast<long long>(ends[0]), static_cast<long long>(ends[1]), static_cast<long long>(nnz));
-    return fail(LBL_EINVAL);
+    return cuda_fail(e, "roadmap upload: copy");
   }
-  const bool want_bt = flags & LBL_UPLOAD_BITTILE;
-  if ((e = dev_alloc(&rm->err, 1, &rm->bytes)) != cudaSuccess ||
-      (e = cudaMemsetAsync(rm->err, 0, sizeof(int), st)) != cudaSuccess)
-    return fail(cuda_fail(e, "roadmap upload: error flag"));
-  if ((e = dev_alloc(&d_bad, 1, nullptr)) != cudaSuccess) return fail(cuda_fail(e, "roadmap upload: scratch"));
-  if (want_bt && (e = dev_alloc(&d_cnt, static_cast<size_t>(n_edges), nullptr)) != cudaSuccess)
-    return fail(cuda_fail(e, "roadmap upload: block counts"));
-  if ((e = cudaMemsetAsync(d_bad, 0, sizeof(unsigned long long), st)) != cudaSuccess ||
-      (e = launch_scan_rows(rm->rowptr, rm->colidx, n_edges, nnz, rm->cells, d_bad, d_cnt, st)) != cudaSuccess)
-    return fail(cuda_fail(e, "roadmap upload: row check"));
-  unsigned long long bad = 0;
-  if ((e = cudaMemcpyAsync(&bad, d_bad, sizeof(bad), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-      (e = cudaStreamSynchronize(st)) != cudaSuccess)
-    return fail(cuda_fail(e, "roadmap upload: row check"));
-  if (bad) {
-    set_error("roadmap upload: %llu malformed rows (row pointer decreasing or out of range, or column indices "
-              "not strictly increasing inside [0, %lld))",
-              bad, static_cast<long long>(rm->cells));
-    return fail(LBL_EINVAL);
-  }
-  if (n_edges > 0) {
-    // edge partition of the streaming CSR kernel, for its default grid
-    rm->part_cap = static_cast<int64_t>(rm->num_sms) * kMaxCtasPerSm * (kThreads / 32) + 1;
-    if ((e = dev_alloc(&rm->part, static_cast<size_t>(rm->part_cap), &rm->bytes)) != cudaSuccess)
-      return fail(cuda_fail(e, "roadmap upload: partition"));
-    rm->part_ctas = stream_ctas_per_sm(8);
-    if ((e = launch_partition(*rm, rm->part_ctas, st)) != cudaSuccess)
-      return fail(cuda_fail(e, "roadmap upload: partition"));
-  }
-  if (want_bt) {
-    std::vector<int32_t> cnt(static_cast<size_t>(n_edges));
-    std::vector<int64_t> brow(static_cast<size_t>(n_edges + 1));
-    if (n_edges &&
-        ((e = cudaMemcpyAsync(cnt.data(), d_cnt, sizeof(int32_t) * n_edges, cudaMemcpyDeviceToHost, st)) !=
-             cudaSuccess ||
-         (e = cudaStreamSynchronize(st)) != cudaSuccess))
-      return fail(cuda_fail(e, "roadmap upload: block counts"));
-    brow[0] = 0;
-    for (int64_t i = 0; i < n_edges; ++i) brow[i + 1] = brow[i] + cnt[i];
-    rm->n_bt = brow[n_edges];
-    rm->n_blocks = (rm->cells + 63) / 64;
-    if ((e = dev_alloc(&rm->bt_rowptr, static_cast<size_t>(n_edges + 1), &rm->bytes)) != cudaSuccess ||
-        (e = dev_alloc(&rm->bt_block, static_cast<size_t>(rm->n_bt), &rm->bytes)) != cudaSuccess ||
-        (e = dev_alloc(&rm->bt_mask, static_cast<size_t>(rm->n_bt), &rm->bytes)) != cudaSuccess ||
-        (e = dev_alloc(&rm->planes, static_cast<size_t>(rm->n_blocks * 64), &rm->bytes)) != cudaSuccess)
-      return fail(cuda_fail(e, "roadmap upload: block form"));
-    if ((e = cudaMemcpyAsync(rm->bt_rowptr, brow.data(), sizeof(int64_t) * (n_edges + 1), cudaMemcpyHostToDevice,
-                             st)) != cudaSuccess ||
-        (e = launch_bt_fill(rm->rowptr, rm->colidx, n_edges, rm->bt_rowptr, rm->bt_block, rm->bt_mask, st)) !=
-            cudaSuccess ||
-        (e = cudaStreamSynchronize(st)) != cudaSuccess)
-      return fail(cuda_fail(e, "roadmap upload: block form"));
-    rm->has_bt = true;
-  }
-  if ((flags & LBL_UPLOAD_SECTOR) && n_edges > 0) {
-    if (rm->cells > (1LL << 30)) {
-      set_error("roadmap upload: the sector form needs at most 2^30 cells");
-      return fail(LBL_EINVAL);
-    }
-    std::vector<int32_t> cnt(static_cast<size_t>(n_edges));
-    std::vector<int64_t> srow(static_cast<size_t>(n_edges + 1));
-    int32_t *d_sc = nullptr;
-    if ((e = dev_alloc(&d_sc, static_cast<size_t>(n_edges), nullptr)) != cudaSuccess ||
-        (e = launch_sector_count(rm->rowptr, rm->colidx, n_edges, d_sc, st)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(cnt.data(), d_sc, sizeof(int32_t) * n_edges, cudaMemcpyDeviceToHost, st)) !=
-            cudaSuccess ||
-        (e = cudaStreamSynchronize(st)) != cudaSuccess) {
-      cudaFree(d_sc);
-      return fail(cuda_fail(e, "roadmap upload: sector form"));
-    }
-    cudaFree(d_sc);
-    srow[0] = 0;
-    for (int64_t i = 0; i < n_edges; ++i) srow[i + 1] = srow[i] + cnt[i];
-    rm->n_sec = srow[n_edges];
-    if ((e = dev_alloc(&rm->sec_rowptr, static_cast<size_t>(n_edges + 1), &rm->bytes)) != cudaSuccess ||
-        (e = dev_alloc(&rm->sec, static_cast<size_t>(rm->n_sec), &rm->bytes)) != cudaSuccess ||
-        (e = dev_alloc(&rm->sec_part, static_cast<size_t>(rm->part_cap), &rm->bytes)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(rm->sec_rowptr, srow.data(), sizeof(int64_t) * (n_edges + 1), cudaMemcpyHostToDevice,
-                             st)) != cudaSuccess ||
-        (e = launch_sector_fill(rm->rowptr, rm->colidx, n_edges, rm->sec_rowptr, rm->sec, st)) != cudaSuccess)
-      return fail(cuda_fail(e, "roadmap upload: sector form"));
-    rm->sec_part_ctas = sector_ctas_per_sm(4);
-    const int64_t W = static_cast<int64_t>(rm->num_sms) * rm->sec_part_ctas * (kThreads / 32);
-    if ((e = launch_partition_into(rm->sec_rowptr, n_edges, W, rm->sec_part, st)) != cudaSuccess)
-      return fail(cuda_fail(e, "roadmap upload: sector partition"));
-    rm->has_sec = true;
-  }
-  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(cuda_fail(e, "roadmap upload"));
-  cudaFree(d_bad);
-  cudaFree(d_cnt);
-  *out = rm;
+  rc = roadmap_finish(rm, flags, st);
+  if (rc == LBL_OK) *out = rm;
   return rc;
 }
 
@@ -405,6 +437,21 @@ int lbl_roadmap_info(lbl_roadmap rm, int64_t *n_edges, int64_t *nnz, int64_t *n_
   if (n_block_entries) *n_block_entries = rm->n_bt;
   if (n_sector_entries) *n_sector_entries = rm->n_sec;
   if (device_bytes) *device_bytes = rm->bytes;
+  return LBL_OK;
+}
+
+int lbl_roadmap_rows(lbl_roadmap rm, int64_t *d_rowptr, int32_t *d_colidx, lbl_stream s) {
+  g_err.clear();
+  if (!rm || !d_rowptr || (rm->nnz > 0 && !d_colidx)) {
+    set_error("roadmap rows: NULL roadmap or buffer");
+    return LBL_EINVAL;
+  }
+  if (!same_device(rm->device)) return LBL_EINVAL;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(s);
+  cudaError_t e = cudaMemcpyAsync(d_rowptr, rm->rowptr, sizeof(int64_t) * (rm->E + 1), cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess && rm->nnz > 0)
+    e = cudaMemcpyAsync(d_colidx, rm->colidx, sizeof(int32_t) * rm->nnz, cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "roadmap rows");
   return LBL_OK;
 }
 

@@ -118,6 +118,18 @@ struct Monitor {
   uint16_t *V = nullptr;
 };
 
+// Even-position bits of v packed into the low half: the inverse of the 2-D
+// z-order interleave for one coordinate (Sec. 4.1).
+__device__ __forceinline__ uint32_t gather_even_bits(uint64_t v) {
+  v &= 0x5555555555555555ull;
+  v = (v | (v >> 1)) & 0x3333333333333333ull;
+  v = (v | (v >> 2)) & 0x0F0F0F0F0F0F0F0Full;
+  v = (v | (v >> 4)) & 0x00FF00FF00FF00FFull;
+  v = (v | (v >> 8)) & 0x0000FFFF0000FFFFull;
+  v = (v | (v >> 16)) & 0x00000000FFFFFFFFull;
+  return static_cast<uint32_t>(v);
+}
+
 // ---------------------------------------------------------------- errors
 void set_error(const char *fmt, ...);
 int cuda_fail(cudaError_t e, const char *what);
@@ -188,3 +200,11 @@ cudaError_t launch_bt_fill(const int64_t *rowptr, const int32_t *colidx, int64_t
 // The opaque handles of the C ABI are the internal objects.
 struct lbl_roadmap_s : lbl::Roadmap {};
 struct lbl_monitor_s : lbl::Monitor {};
+
+namespace lbl {
+int roadmap_new(const lbl_grid &agent, int64_t n_edges, int64_t nnz, lbl_roadmap_s **out);
+int roadmap_finish(lbl_roadmap_s *rm, uint32_t flags, cudaStream_t st);
+bool valid_grid_public(const lbl_grid *g, const char *name, bool need_order);
+int device_sms_public(int dev);
+void free_roadmap_public(lbl_roadmap_s *rm);
+}  // namespace lbl

@@ -45,7 +45,8 @@ LBL_UPLOAD_SECTOR = 4
 # every entry point declared in include/lbl.h
 EXPORTS = (
     "lbl_last_error", "lbl_version",
-    "lbl_roadmap_upload", "lbl_roadmap_free", "lbl_roadmap_info", "lbl_roadmap_status",
+    "lbl_roadmap_upload", "lbl_roadmap_rasterize", "lbl_roadmap_rows", "lbl_roadmap_free", "lbl_roadmap_info",
+    "lbl_roadmap_status",
     "lbl_frame_transform",
     "lbl_monitor_create", "lbl_monitor_free", "lbl_monitor_step",
     "lbl_label", "lbl_label_blocks_noalloc", "lbl_roadmap_autotune",
@@ -106,6 +107,8 @@ def load(build_if_needed: bool = True):
         "lbl_last_error": (ctypes.c_char_p, []),
         "lbl_version": (ctypes.c_int, []),
         "lbl_roadmap_upload": (ctypes.c_int, [G, p, p, i64, i64, u32, p, ctypes.POINTER(p)]),
+        "lbl_roadmap_rasterize": (ctypes.c_int, [G, p, i64, ctypes.c_double, u32, p, ctypes.POINTER(p)]),
+        "lbl_roadmap_rows": (ctypes.c_int, [p, p, p, p]),
         "lbl_roadmap_free": (ctypes.c_int, [p]),
         "lbl_roadmap_info": (ctypes.c_int, [p, p, p, p, p, p]),
         "lbl_roadmap_status": (ctypes.c_int, [p, p]),
@@ -240,6 +243,23 @@ def lbl_roadmap_upload(agent, rowptr, colidx, flags: int = 0, stream=None) -> in
     g = _grid(agent)
     _check(lib.lbl_roadmap_upload(ctypes.byref(g), rp, ci, E, nnz, flags, _stream(stream), ctypes.byref(out)))
     return out.value
+
+
+def lbl_roadmap_rasterize(agent, arcs, radius: float, flags: int = 0, stream=None) -> int:
+    """Build a roadmap on the device from arcs float64[E][5] (x, y, heading,
+    curvature, length) with a disc footprint of `radius`; returns the handle."""
+    a = np.ascontiguousarray(arcs, np.float64).reshape(-1, 5)
+    out = ctypes.c_void_p()
+    g = _grid(agent)
+    _check(load().lbl_roadmap_rasterize(ctypes.byref(g), a.ctypes.data if a.size else None, a.shape[0],
+                                        float(radius), int(flags), _stream(stream), ctypes.byref(out)))
+    return out.value
+
+
+def lbl_roadmap_rows(rm, d_rowptr, d_colidx, stream=None) -> None:
+    """Copy a roadmap's rows into device tensors int64[E+1] / int32[nnz]."""
+    _check(load().lbl_roadmap_rows(rm, _dev(d_rowptr, "int64", "rowptr"), _dev(d_colidx, "int32", "colidx"),
+                                   _stream(stream)))
 
 
 def lbl_roadmap_free(rm) -> None:
