@@ -227,10 +227,18 @@ def oracle_step_rate(wl, n_sample: int, threads: int):
 
 
 def calibrate_sample(wl, seconds: float, threads: int) -> int:
-    n = min(wl.n_edges, 2000)
-    dt = oracle_step_rate(wl, n, threads)
-    n = int(min(wl.n_edges, max(1000, n * seconds / max(dt, 1e-3))))
-    return n
+    """Edges per oracle frame so that one frame takes about `seconds`: two
+    probe sizes separate the fixed cost (whole-grid transform) from the
+    per-edge cost."""
+    n1 = min(wl.n_edges, 2000)
+    n2 = min(wl.n_edges, 20000)
+    t1 = oracle_step_rate(wl, n1, threads)
+    if n2 == n1:
+        return n1
+    t2 = oracle_step_rate(wl, n2, threads)
+    per_edge = max((t2 - t1) / (n2 - n1), 1e-9)
+    fixed = max(t1 - per_edge * n1, 0.0)
+    return int(min(wl.n_edges, max(1000, (seconds - fixed) / per_edge)))
 
 
 def run_reference(args, rank, world):
