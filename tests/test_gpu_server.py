@@ -99,3 +99,29 @@ def test_admission_waits_for_memory_and_refuses_oversize(resident):
             L.lbl_server_wait(srv, 10**9, 10)
     finally:
         L.lbl_server_free(srv)
+
+
+def test_wait_is_bounded_and_reports_timeout(resident):
+    """A wait that runs out returns LBL_ETIMEOUT and leaves the ticket valid: a
+    later wait on it succeeds.  The arena holds one request at a time, so the
+    last of eight requests is still queued behind seven when it is first waited
+    on with a zero limit."""
+    wls, mons, rms, mhs = resident
+    wl = wls[1]
+    srv = L.lbl_server_create([rms[1]], [wl.P], None, lanes=1, mem_budget=3 << 20)
+    try:
+        rng = np.random.default_rng(4)
+        planes = torch.from_numpy(wl.planes).pin_memory()
+        outs, ts = [], []
+        for i in range(8):
+            out = torch.zeros(wl.n_edges, dtype=torch.uint64).pin_memory()
+            ts.append(L.lbl_server_submit(srv, 0, wl.world, planes, synth.random_pose(rng, wl.world), out))
+            outs.append(out)
+        with pytest.raises(L.LblError) as ei:
+            L.lbl_server_wait(srv, ts[-1], 0)
+        assert ei.value.code == L.LBL_ETIMEOUT
+        for t in ts:
+            assert L.lbl_server_wait(srv, t, 20000) > 0
+        assert L.lbl_server_stats(srv)["completed"] == 8
+    finally:
+        L.lbl_server_free(srv)
