@@ -62,11 +62,11 @@ WORKLOADS = {
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--algo", default="csr", choices=["auto", "csr", "bittile", "sector"],
+    ap.add_argument("--algo", default="quad", choices=["auto", "csr", "bittile", "sector", "quad"],
                     help="labeling form; auto = measure every form on the first frame and keep the fastest")
     ap.add_argument("--lanes", type=int, default=0)
     ap.add_argument("--early-exit", type=int, default=-1)
@@ -172,11 +172,19 @@ def measured_peaks():
         return None
 
 
-def label_bytes(wl, algo: str, n_bt: int | None, with_monitor: bool, n_sec: int | None = None) -> int:
-    """Algorithmic HBM bytes of one labeling launch (each array read or written
-    once; O and the bit planes counted once although they are re-read from L2)."""
+def pyramid_words(cells: int, levels: int = 4) -> int:
+    return sum(cells >> (2 * k) for k in range(levels + 1))
+
+
+def label_bytes(wl, algo: str, n_bt: int | None, with_monitor: bool, n_sec: int | None = None,
+                n_qd: int | None = None) -> int:
+    """Algorithmic HBM bytes of one labeling call (each array read or written
+    once; O, the bit planes and the pyramid counted once although they are
+    re-read from L2)."""
     E = wl.n_edges
     out = 8 * E + (10 * E if with_monitor else 0)
+    if algo == "quad":  # pyramid: O read, pyramid written; stream: entries, rows, pyramid once
+        return 4 * n_qd + 8 * (E + 1) + 8 * wl.agent.cells + 16 * pyramid_words(wl.agent.cells) + out
     if algo == "sector":
         return 4 * n_sec + 8 * (E + 1) + 8 * wl.agent.cells + out
     if algo == "bittile":
@@ -311,9 +319,10 @@ def main():
         wl = synth.make(args.workload, seed=rank_seed(args.seed, rank), edges=args.edges, threads=cpu_cores())
     t_gen = time.perf_counter() - t_gen
     algo = {"auto": L.LBL_ALGO_AUTO, "csr": L.LBL_ALGO_CSR, "bittile": L.LBL_ALGO_BITTILE,
-            "sector": L.LBL_ALGO_SECTOR}[args.algo]
+            "sector": L.LBL_ALGO_SECTOR, "quad": L.LBL_ALGO_QUAD}[args.algo]
     flags = ((L.LBL_UPLOAD_BITTILE if args.algo in ("auto", "bittile") else 0)
-             | (L.LBL_UPLOAD_SECTOR if args.algo in ("auto", "sector") else 0))
+             | (L.LBL_UPLOAD_SECTOR if args.algo in ("auto", "sector") else 0)
+             | (L.LBL_UPLOAD_QUAD if args.algo in ("auto", "quad") else 0))
     stream = torch.cuda.Stream()
     rm = L.lbl_roadmap_upload(wl.agent, wl.rowptr, wl.colidx, flags=flags, stream=stream)
     mon = None
@@ -341,10 +350,11 @@ def main():
     if args.algo == "auto":
         L.lbl_frame_transform(wl.world, d_planes, P, wl.pose, wl.agent, d_O, stream=stream)
         tuned = L.lbl_roadmap_autotune(rm, d_O, P, d_L, mon, d_next, d_viol, reps=5, stream=stream)
-        used = {L.LBL_ALGO_BITTILE: "bittile", L.LBL_ALGO_SECTOR: "sector"}.get(tuned["algo"], "csr")
+        used = {L.LBL_ALGO_BITTILE: "bittile", L.LBL_ALGO_SECTOR: "sector",
+                L.LBL_ALGO_QUAD: "quad"}.get(tuned["algo"], "csr")
     else:
         used = args.algo
-    launches_per_step = 2 + (1 if used == "bittile" else 0)
+    launches_per_step = 2 + (1 if used in ("bittile", "quad") else 0)  # + planes / pyramid kernel
 
     # ---- warm-up
     for _ in range(args.warmup):
@@ -406,7 +416,7 @@ def main():
 
     # ---- roofline of the dominant kernel (labeling)
     info = L.lbl_roadmap_info(rm)
-    lb = label_bytes(wl, used, info[2], mon is not None, info[3])
+    lb = label_bytes(wl, used, info[2], mon is not None, info[3], info[4])
     label_avg_s = float(label_ms.mean()) / 1e3
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
@@ -441,6 +451,7 @@ def main():
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": f"label_{used}", "algorithmic_bytes_per_launch": lb,
+                         "csr_equivalent_gbs": label_bytes(wl, "csr", None, mon is not None) / label_avg_s / 1e9,
                          "peak_source": "measured" if peaks else "fallback"},
             "cpu_baseline": cpu,
             "clocks": clk,

@@ -90,6 +90,15 @@ typedef struct {
 #define LBL_ALGO_SECTOR 3  /* gather-OR over per-edge 4-cell sectors (compressed A):
                               one u32 (sector << 4 | cell mask) per touched 32-byte
                               sector of O; needs O 32-byte aligned */
+#define LBL_ALGO_QUAD 4    /* gather-OR over each row's maximal quadtree blocks
+                              (compressed A): a row is the union of blocks of 4^k
+                              consecutive cells of the cell order (k <= 4) that
+                              start at a multiple of 4^k (in z-order: the
+                              2^k x 2^k squares of the quadtree; in row-major
+                              order: aligned runs).  Per frame the library ORs O
+                              over every such block (a pyramid of ~4/3 words per
+                              cell) and each edge ORs one word per block.  Exact:
+                              OR is associative and idempotent */
 
 typedef struct {
   int32_t algo;           /* LBL_ALGO_* */
@@ -102,8 +111,8 @@ typedef struct {
   int32_t ctas_per_sm;    /* persistent grid size per SM, 0 = auto */
   int32_t pipeline;       /* streaming CSR index stream (LBL_PIPE_*), 0 = default */
   int32_t depth;          /* register pipelines: groups of 32 entries in flight per
-                             warp; CSR 8 (default), 12 or 16; sector form 4 (default)
-                             or 8.  Deeper variants run fewer CTAs per SM */
+                             warp; CSR and quadtree 8 (default), 12 or 16; sector form
+                             4 (default) or 8.  Deeper variants run fewer CTAs per SM */
 } lbl_config;
 
 /* How the streaming CSR form moves each warp's column indices from HBM. */
@@ -132,6 +141,9 @@ int lbl_version(void);
 #define LBL_UPLOAD_SECTOR 4u      /* also derive the 4-cell sector form used by
                                      LBL_ALGO_SECTOR (4 B per touched sector; grids of
                                      at most 2^30 cells) */
+#define LBL_UPLOAD_QUAD 8u        /* also derive the quadtree form used by LBL_ALGO_QUAD
+                                     (4 B per maximal block of a row, plus a pyramid of
+                                     ~11 B per cell; grids of fewer than 2^30 cells) */
 
 /*
  * lbl_roadmap_upload — make a roadmap resident on the device.
@@ -183,9 +195,10 @@ int lbl_roadmap_status(lbl_roadmap rm, lbl_stream s);
 
 /* Shape of a roadmap: edges, nonzeros, (block, mask) entries of the block form
    (0 without LBL_UPLOAD_BITTILE), entries of the sector form (0 without
-   LBL_UPLOAD_SECTOR) and device bytes held.  Any out pointer may be NULL. */
+   LBL_UPLOAD_SECTOR), entries of the quadtree form (0 without LBL_UPLOAD_QUAD)
+   and device bytes held.  Any out pointer may be NULL. */
 int lbl_roadmap_info(lbl_roadmap rm, int64_t *n_edges, int64_t *nnz, int64_t *n_block_entries,
-                     int64_t *n_sector_entries, int64_t *device_bytes);
+                     int64_t *n_sector_entries, int64_t *n_qdadic_entries, int64_t *device_bytes);
 
 /* ------------------------------------------------------- frame transform */
 
@@ -251,9 +264,13 @@ int lbl_monitor_step(lbl_monitor mon, const uint64_t *d_L, int64_t n, uint64_t *
  *   n_props  0..64
  *   d_L      uint64[n_edges]
  *   cfg      NULL = defaults (LBL_ALGO_AUTO)
- * LBL_ALGO_BITTILE / LBL_ALGO_SECTOR need a roadmap uploaded with
- * LBL_UPLOAD_BITTILE / LBL_UPLOAD_SECTOR (LBL_EUNSUPPORTED otherwise).  The roadmap holds per-launch working memory,
- * so two lbl_label calls on the same roadmap must not overlap on the device.
+ * LBL_ALGO_BITTILE / LBL_ALGO_SECTOR / LBL_ALGO_QUAD need a roadmap uploaded
+ * with LBL_UPLOAD_BITTILE / LBL_UPLOAD_SECTOR / LBL_UPLOAD_QUAD
+ * (LBL_EUNSUPPORTED otherwise).  LBL_ALGO_AUTO takes the form
+ * lbl_roadmap_autotune chose for n_props, else the quadtree form when the roadmap
+ * has it, else the block form for n_props <= 8 when present, else CSR.  The
+ * roadmap holds per-launch working memory (block planes, quadtree pyramid), so
+ * two lbl_label calls on the same roadmap must not overlap on the device.
  */
 int lbl_label(lbl_roadmap rm, const uint64_t *d_O, int32_t n_props, uint64_t *d_L, lbl_monitor mon, uint64_t *d_next,
               uint16_t *d_viol, const lbl_config *cfg, lbl_stream s);

@@ -148,71 +148,76 @@ struct CsrGather {
   __device__ __forceinline__ uint64_t masked(int32_t c) const { return c >= 0 ? __ldg(O + c) : 0ull; }
 };
 
-template <int U, typename Gather, typename Emit>
-__device__ __forceinline__ void stream_range(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
-                                             const Gather gather, int64_t e_beg, int64_t e_end, uint64_t pol,
-                                             int lane, Emit emit) {
-  // window of edge ends: lane i holds rowptr[win + i + 1] (the end of edge win + i)
-  int64_t win = e_beg;
-  int64_t rp = win + lane < e_end ? __ldg(rowptr + win + lane + 1) : 0;
-  int64_t cur = e_beg;
-  int64_t stop = __shfl_sync(kFull, rp, 0);
-  const int64_t p0 = __ldg(rowptr + e_beg), p1 = __ldg(rowptr + e_end);
+// Positions inside a warp's range are kept relative to its first entry `a`
+// and first edge in `Off` (int32_t whenever the range allows it: fewer
+// registers and cheaper boundary tests, so more warps fit per SM).  The U
+// gathers of a group are issued before the indices of the next group are
+// requested, so one register per lane and group holds both.
+template <int U, typename Off, typename Gather, typename Emit>
+__device__ __forceinline__ void stream_body(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
+                                            const Gather gather, int64_t e_beg, int64_t e_end, int64_t p0, int64_t p1,
+                                            uint64_t pol, int lane, Emit emit) {
+  constexpr int GS = 32 * U;
   const int64_t a = p0 & ~static_cast<int64_t>(31);
+  const Off n_e = static_cast<Off>(e_end - e_beg);
+  const Off n_rel = static_cast<Off>(p1 - a);
+  const int head = static_cast<int>(p0 - a);
+  const int64_t *rpb = rowptr + e_beg + 1;  // rpb[i] = end of edge e_beg + i
+  // window of edge ends: lane i holds the end of edge (win + i), relative to a
+  Off win = 0;
+  Off rp = lane < n_e ? static_cast<Off>(__ldg(rpb + lane) - a) : Off(0);
+  Off cur = 0;
+  Off stop = __shfl_sync(kFull, rp, 0);
   uint64_t acc = 0;
+  uint64_t mine = 0;  // lane i keeps the label of edge (win + i) until its window is complete
 
+  // Close the current edge: every lane gets the OR of the warp, the edge's
+  // lane keeps it; a complete window of 32 labels leaves in one coalesced
+  // store, each lane running the epilogue for its own edge.
   auto flush = [&]() {
     uint64_t r = acc;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) r = or_xor(r, off);
-    if (lane == 0) emit(cur, r);
+    if (lane == static_cast<int>(cur - win)) mine = r;
     acc = 0;
     ++cur;
-    if (cur < e_end) {
-      if (cur - win == 32) {
-        win = cur;
-        rp = win + lane < e_end ? __ldg(rowptr + win + lane + 1) : 0;
-      }
-      stop = __shfl_sync(kFull, rp, static_cast<int>(cur - win));
+    if (cur - win == 32) {
+      emit(e_beg + win + lane, mine);
+      win = cur;
+      if (cur < n_e) rp = win + lane < n_e ? static_cast<Off>(__ldg(rpb + win + lane) - a) : Off(0);
     }
+    if (cur < n_e) stop = __shfl_sync(kFull, rp, static_cast<int>(cur - win));
   };
 
-  // Lane l's entry of group g (relative to a) is base[g + l]; whether a
-  // group crosses the end of the current edge is a warp-uniform test on
-  // scalars, so the common case (no boundary) only ORs.
+  // Lane l's entry of group g is base[g + l]; whether a group crosses the end
+  // of the current edge is a warp-uniform test on scalars, so the common case
+  // (no boundary) only ORs.
   const int32_t *base = colidx + a + lane;
-  const int64_t n_rel = p1 - a;
-  const int head = static_cast<int>(p0 - a);
-  int32_t nxt[U];
+  int32_t idx[U];
 #pragma unroll
   for (int u = 0; u < U; ++u) {
-    const int off = 32 * u + lane;
-    nxt[u] = (off >= head && off < n_rel) ? ld_stream(base + 32 * u, pol) : Gather::kNone;
+    const Off off = 32 * u + lane;
+    idx[u] = (off >= head && off < n_rel) ? ld_stream(base + 32 * u, pol) : Gather::kNone;
   }
-  for (int64_t g = 0; g < n_rel; g += 32 * U) {
-    int32_t c[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) c[u] = nxt[u];
-    // prefetch the next group: unconditional when it lies wholly inside the range
-    if (g + 64 * U <= n_rel) {
-#pragma unroll
-      for (int u = 0; u < U; ++u) nxt[u] = ld_stream(base + g + 32 * (U + u), pol);
-    } else {
-      const int64_t rem64 = n_rel - g - 32 * U;
-      const int rem = rem64 > 0x7fffffff ? 0x7fffffff : static_cast<int>(rem64);
-#pragma unroll
-      for (int u = 0; u < U; ++u)
-        nxt[u] = (32 * u + lane < rem) ? ld_stream(base + g + 32 * (U + u), pol) : Gather::kNone;
-    }
+  for (Off g = 0; g < n_rel; g += GS) {
     uint64_t wv[U];
-    if ((g > 0 || head == 0) && g + 32 * U <= n_rel) {  // every entry valid
+    if ((g > 0 || head == 0) && g + GS <= n_rel) {  // every entry valid
 #pragma unroll
-      for (int u = 0; u < U; ++u) wv[u] = gather.full(c[u]);
+      for (int u = 0; u < U; ++u) wv[u] = gather.full(idx[u]);
     } else {
 #pragma unroll
-      for (int u = 0; u < U; ++u) wv[u] = gather.masked(c[u]);
+      for (int u = 0; u < U; ++u) wv[u] = gather.masked(idx[u]);
     }
-    const int64_t grp_end = min(a + g + 32 * U, p1);
+    const Off ns = g + GS;  // next group
+    const Off rem = n_rel - ns;
+    if (rem >= GS) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) idx[u] = ld_stream(base + ns + 32 * u, pol);
+    } else {
+#pragma unroll
+      for (int u = 0; u < U; ++u) idx[u] = (32 * u + lane < rem) ? ld_stream(base + ns + 32 * u, pol) : Gather::kNone;
+    }
+    const Off grp_end = min(ns, n_rel);
     if (grp_end <= stop) {
 #pragma unroll
       for (int u = 0; u < U; ++u) acc |= wv[u];
@@ -220,8 +225,8 @@ __device__ __forceinline__ void stream_range(const int64_t *__restrict__ rowptr,
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const int64_t k = a + g + 32 * u + lane;
-      const int64_t sub_end = min(a + g + 32 * (u + 1), p1);
+      const Off k = g + 32 * u + lane;
+      const Off sub_end = min(static_cast<Off>(g + 32 * (u + 1)), n_rel);
       while (sub_end > stop) {  // some valid entry of this 32-group is past the current edge
         if (k < stop) {
           acc |= wv[u];
@@ -232,7 +237,19 @@ __device__ __forceinline__ void stream_range(const int64_t *__restrict__ rowptr,
       acc |= wv[u];
     }
   }
-  while (cur < e_end) flush();
+  while (cur < n_e) flush();
+  if (lane < static_cast<int>(cur - win)) emit(e_beg + win + lane, mine);  // the last, partial window
+}
+
+// A warp's range: `Off` is int32_t when the whole roadmap has fewer than
+// kNarrowLimit nonzeros and edges (so every range fits), int64_t otherwise.
+
+template <int U, typename Off, typename Gather, typename Emit>
+__device__ __forceinline__ void stream_range(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
+                                             const Gather gather, int64_t e_beg, int64_t e_end, uint64_t pol,
+                                             int lane, Emit emit) {
+  const int64_t p0 = __ldg(rowptr + e_beg), p1 = __ldg(rowptr + e_end);
+  stream_body<U, Off>(rowptr, colidx, gather, e_beg, e_end, p0, p1, pol, lane, emit);
 }
 
 // Resident CTAs per SM each streaming variant is compiled for: deeper
@@ -242,7 +259,7 @@ constexpr int stream_min_blocks() {
   return U <= 8 ? 4 : (U <= 12 ? 3 : 2);
 }
 
-template <int U, bool EPI>
+template <int U, bool EPI, typename Off>
 __global__ void __launch_bounds__(kThreads, stream_min_blocks<U>()) k_label_stream(const int64_t *__restrict__ rowptr,
                                                            const int32_t *__restrict__ colidx,
                                                            const uint64_t *__restrict__ O,
@@ -255,7 +272,7 @@ __global__ void __launch_bounds__(kThreads, stream_min_blocks<U>()) k_label_stre
   const int64_t w = (static_cast<int64_t>(blockIdx.x) * kThreads + threadIdx.x) >> 5;
   const int64_t e_beg = __ldg(part + w), e_end = __ldg(part + w + 1);
   if (e_beg >= e_end) return;  // warp-uniform
-  stream_range<U>(rowptr, colidx, CsrGather{O}, e_beg, e_end, pol, lane, [&](int64_t e, uint64_t r) {
+  stream_range<U, Off>(rowptr, colidx, CsrGather{O}, e_beg, e_end, pol, lane, [&](int64_t e, uint64_t r) {
     r &= mask;
     L[e] = r;
     if (EPI) epilogue(mon, sm, e, r);
@@ -290,7 +307,7 @@ struct SectorGather {
   __device__ __forceinline__ uint64_t masked(int32_t v) const { return v ? pick(static_cast<uint32_t>(v)) : 0ull; }
 };
 
-template <int U, bool EPI>
+template <int U, bool EPI, typename Off>
 __global__ void __launch_bounds__(kThreads, stream_min_blocks<2 * U>()) k_label_sector(const int64_t *__restrict__ srow,
                                                            const int32_t *__restrict__ sec,
                                                            const uint64_t *__restrict__ O, int64_t cells,
@@ -303,7 +320,7 @@ __global__ void __launch_bounds__(kThreads, stream_min_blocks<2 * U>()) k_label_
   const int64_t w = (static_cast<int64_t>(blockIdx.x) * kThreads + threadIdx.x) >> 5;
   const int64_t e_beg = __ldg(part + w), e_end = __ldg(part + w + 1);
   if (e_beg >= e_end) return;  // warp-uniform
-  stream_range<U>(srow, sec, SectorGather{O, cells}, e_beg, e_end, pol, lane, [&](int64_t e, uint64_t r) {
+  stream_range<U, Off>(srow, sec, SectorGather{O, cells}, e_beg, e_end, pol, lane, [&](int64_t e, uint64_t r) {
     r &= mask;
     L[e] = r;
     if (EPI) epilogue(mon, sm, e, r);
@@ -316,6 +333,7 @@ __global__ void __launch_bounds__(kThreads, stream_min_blocks<2 * U>()) k_label_
 // global counter (zeroed before the launch), so the load stays balanced and
 // only the few items being worked on keep their O words hot in L2.  Monitor
 // tables, if any, are read through L1.
+template <typename Off>
 __global__ void __launch_bounds__(kThreads, 4) k_label_batch(const __grid_constant__ BatchTable tab,
                                                           unsigned long long *__restrict__ next_unit) {
   const uint64_t pol = evict_first_policy();
@@ -340,7 +358,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_label_batch(const __grid_consta
     const int64_t *part = it->part;
     const int64_t e_beg = __ldg(part + lu), e_end = __ldg(part + lu + 1);
     if (e_beg >= e_end) continue;
-    stream_range<8>(it->rowptr, it->colidx, CsrGather{it->O}, e_beg, e_end, pol, lane, [&](int64_t e, uint64_t r) {
+    stream_range<8, Off>(it->rowptr, it->colidx, CsrGather{it->O}, e_beg, e_end, pol, lane,
+                         [&](int64_t e, uint64_t r) {
       r &= it->mask;
       it->L[e] = r;
       const uint64_t *T = it->T;
@@ -352,6 +371,39 @@ __global__ void __launch_bounds__(kThreads, 4) k_label_batch(const __grid_consta
         it->viol[e] = __ldg(it->V + letter);
       }
     });
+  }
+}
+
+// Quadtree pyramid of O for the quadtree form (compressed A): level k holds,
+// for every block of 4^k consecutive cells in the grid's cell order that lies
+// wholly inside the grid, the OR of their words; level 0 is O itself.  Word of
+// block b at level k: pyr[off.at[k] + b].  One CTA covers 256 consecutive
+// cells: levels 1-2 (4 and 16 cells) by butterfly shuffles inside each warp,
+// levels 3-4 (64 and 256 cells) from the eight 32-cell warp words.
+__global__ void __launch_bounds__(kThreads) k_quad_pyramid(const uint64_t *__restrict__ O, int64_t cells,
+                                                           QuadOffsets off, uint64_t *__restrict__ pyr) {
+  static_assert(kThreads == 256 && kQuadLevels == 4, "one CTA = one block of the top level");
+  __shared__ uint64_t wsum[kThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * kThreads + threadIdx.x;
+  uint64_t v = i < cells ? __ldg(O + i) : 0ull;
+  if (i < cells) pyr[i] = v;
+  v = or_xor(or_xor(v, 1), 2);  // every lane: OR of its aligned 4-cell block
+  if ((lane & 3) == 0 && (i >> 2) < (cells >> 2)) pyr[off.at[1] + (i >> 2)] = v;
+  v = or_xor(or_xor(v, 4), 8);  // 16-cell block
+  if ((lane & 15) == 0 && (i >> 4) < (cells >> 4)) pyr[off.at[2] + (i >> 4)] = v;
+  v = or_xor(v, 16);  // the warp's 32 cells
+  if (lane == 0) wsum[wid] = v;
+  __syncthreads();
+  if (threadIdx.x < 4) {  // 64-cell blocks: warps (2t, 2t+1)
+    const int t = threadIdx.x;
+    const int64_t b = static_cast<int64_t>(blockIdx.x) * 4 + t;
+    if (b < (cells >> 6)) pyr[off.at[3] + b] = wsum[2 * t] | wsum[2 * t + 1];
+  } else if (threadIdx.x == 4) {  // the 256-cell block
+    uint64_t a = 0;
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; ++w) a |= wsum[w];
+    if (static_cast<int64_t>(blockIdx.x) < (cells >> 8)) pyr[off.at[4] + blockIdx.x] = a;
   }
 }
 
@@ -841,37 +893,39 @@ uint64_t prop_mask(int32_t P) { return P >= 64 ? ~0ull : ((1ull << P) - 1ull); }
 }  // namespace
 
 int sector_ctas_per_sm(int depth) {
-  static const int o4 = std::min(occupancy(k_label_sector<4, false>), occupancy(k_label_sector<4, true>));
-  static const int o8 = std::min(occupancy(k_label_sector<8, false>), occupancy(k_label_sector<8, true>));
+  static const int o4 = std::min(occupancy(k_label_sector<4, false, int32_t>), occupancy(k_label_sector<4, true, int32_t>));
+  static const int o8 = std::min(occupancy(k_label_sector<8, false, int32_t>), occupancy(k_label_sector<8, true, int32_t>));
   return depth == 8 ? o8 : o4;
 }
 
-template <int U>
+template <int U, typename Off>
 void sector_launch(const Roadmap &rm, const uint64_t *O, uint64_t mask, uint64_t *L, const MonitorTables *mon,
                    cudaStream_t s) {
   const unsigned grid = static_cast<unsigned>(rm.num_sms * rm.sec_part_ctas);
   MonitorTables none{};
   if (mon)
-    k_label_sector<U, true><<<grid, kThreads, 0, s>>>(rm.sec_rowptr, rm.sec, O, rm.cells, rm.sec_part, mask, L,
-                                                      *mon);
+    k_label_sector<U, true, Off><<<grid, kThreads, 0, s>>>(rm.sec_rowptr, rm.sec, O, rm.cells, rm.sec_part, mask, L,
+                                                           *mon);
   else
-    k_label_sector<U, false><<<grid, kThreads, 0, s>>>(rm.sec_rowptr, rm.sec, O, rm.cells, rm.sec_part, mask, L,
-                                                       none);
+    k_label_sector<U, false, Off><<<grid, kThreads, 0, s>>>(rm.sec_rowptr, rm.sec, O, rm.cells, rm.sec_part, mask,
+                                                            L, none);
 }
 
 cudaError_t launch_label_sector(const Roadmap &rm, const uint64_t *O, int32_t P, uint64_t *L,
                                 const MonitorTables *mon, int depth, cudaStream_t s) {
   if (rm.E == 0) return cudaSuccess;
   const uint64_t mask = prop_mask(P);
-  if (depth == 8)
-    sector_launch<8>(rm, O, mask, L, mon, s);
+  if (rm.n_sec >= kNarrowLimit || rm.E >= kNarrowLimit)
+    sector_launch<4, int64_t>(rm, O, mask, L, mon, s);
+  else if (depth == 8)
+    sector_launch<8, int32_t>(rm, O, mask, L, mon, s);
   else
-    sector_launch<4>(rm, O, mask, L, mon, s);
+    sector_launch<4, int32_t>(rm, O, mask, L, mon, s);
   return cudaGetLastError();
 }
 
 int batch_ctas_per_sm() {
-  static const int occ = occupancy(k_label_batch);
+  static const int occ = std::min(occupancy(k_label_batch<int32_t>), occupancy(k_label_batch<int64_t>));
   return occ;
 }
 
@@ -880,7 +934,10 @@ cudaError_t launch_label_batch(const BatchTable &tab, unsigned long long *counte
   if (tab.total == 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
-  k_label_batch<<<static_cast<unsigned>(num_sms * ctas_per_sm), kThreads, 0, s>>>(tab, counter);
+  if (tab.wide)
+    k_label_batch<int64_t><<<static_cast<unsigned>(num_sms * ctas_per_sm), kThreads, 0, s>>>(tab, counter);
+  else
+    k_label_batch<int32_t><<<static_cast<unsigned>(num_sms * ctas_per_sm), kThreads, 0, s>>>(tab, counter);
   return cudaGetLastError();
 }
 
@@ -927,9 +984,11 @@ cudaError_t launch_label_async(const Roadmap &rm, const uint64_t *O, int32_t P, 
 }
 
 int stream_ctas_per_sm(int depth) {
-  static const int o8 = std::min(occupancy(k_label_stream<8, false>), occupancy(k_label_stream<8, true>));
-  static const int o12 = std::min(occupancy(k_label_stream<12, false>), occupancy(k_label_stream<12, true>));
-  static const int o16 = std::min(occupancy(k_label_stream<16, false>), occupancy(k_label_stream<16, true>));
+  static const int o8 = std::min(occupancy(k_label_stream<8, false, int32_t>), occupancy(k_label_stream<8, true, int32_t>));
+  static const int o12 =
+      std::min(occupancy(k_label_stream<12, false, int32_t>), occupancy(k_label_stream<12, true, int32_t>));
+  static const int o16 =
+      std::min(occupancy(k_label_stream<16, false, int32_t>), occupancy(k_label_stream<16, true, int32_t>));
   return depth == 16 ? o16 : depth == 12 ? o12 : o8;
 }
 
@@ -940,28 +999,52 @@ cudaError_t launch_partition(const Roadmap &rm, int ctas_per_sm, cudaStream_t s)
   return cudaGetLastError();
 }
 
-template <int U>
-void stream_launch(const Roadmap &rm, const uint64_t *O, uint64_t mask, uint64_t *L, const MonitorTables *mon,
-                   cudaStream_t s) {
-  const unsigned grid = static_cast<unsigned>(rm.num_sms * rm.part_ctas);
+template <int U, typename Off>
+void rows_launch(const StreamRows &r, const uint64_t *base, uint64_t mask, uint64_t *L, const MonitorTables *mon,
+                 int num_sms, cudaStream_t s) {
+  const unsigned grid = static_cast<unsigned>(num_sms * r.part_ctas);
   MonitorTables none{};
   if (mon)
-    k_label_stream<U, true><<<grid, kThreads, 0, s>>>(rm.rowptr, rm.colidx, O, rm.part, mask, L, *mon);
+    k_label_stream<U, true, Off><<<grid, kThreads, 0, s>>>(r.rowptr, r.idx, base, r.part, mask, L, *mon);
   else
-    k_label_stream<U, false><<<grid, kThreads, 0, s>>>(rm.rowptr, rm.colidx, O, rm.part, mask, L, none);
+    k_label_stream<U, false, Off><<<grid, kThreads, 0, s>>>(r.rowptr, r.idx, base, r.part, mask, L, none);
+}
+
+cudaError_t launch_label_rows(const StreamRows &r, const uint64_t *base, int32_t P, uint64_t *L,
+                              const MonitorTables *mon, int depth, int num_sms, cudaStream_t s) {
+  if (r.E == 0) return cudaSuccess;
+  const uint64_t mask = prop_mask(P);
+  if (r.entries >= kNarrowLimit || r.E >= kNarrowLimit)
+    rows_launch<8, int64_t>(r, base, mask, L, mon, num_sms, s);
+  else if (depth == 16)
+    rows_launch<16, int32_t>(r, base, mask, L, mon, num_sms, s);
+  else if (depth == 12)
+    rows_launch<12, int32_t>(r, base, mask, L, mon, num_sms, s);
+  else
+    rows_launch<8, int32_t>(r, base, mask, L, mon, num_sms, s);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_label_stream(const Roadmap &rm, const uint64_t *O, int32_t P, uint64_t *L,
                                 const MonitorTables *mon, int depth, cudaStream_t s) {
-  if (rm.E == 0) return cudaSuccess;
-  const uint64_t mask = prop_mask(P);
-  if (depth == 16)
-    stream_launch<16>(rm, O, mask, L, mon, s);
-  else if (depth == 12)
-    stream_launch<12>(rm, O, mask, L, mon, s);
-  else
-    stream_launch<8>(rm, O, mask, L, mon, s);
+  const StreamRows r{rm.rowptr, rm.colidx, rm.part, rm.part_ctas, rm.E, rm.nnz};
+  return launch_label_rows(r, O, P, L, mon, depth, rm.num_sms, s);
+}
+
+cudaError_t launch_quad_pyramid(const Roadmap &rm, const uint64_t *O, cudaStream_t s) {
+  if (rm.cells == 0) return cudaSuccess;
+  const unsigned grid = static_cast<unsigned>((rm.cells + kThreads - 1) / kThreads);
+  k_quad_pyramid<<<grid, kThreads, 0, s>>>(O, rm.cells, rm.qd_off, rm.pyr);
   return cudaGetLastError();
+}
+
+cudaError_t launch_label_quad(const Roadmap &rm, const uint64_t *O, int32_t P, uint64_t *L,
+                                const MonitorTables *mon, int depth, cudaStream_t s) {
+  if (rm.E == 0) return cudaSuccess;
+  cudaError_t e = launch_quad_pyramid(rm, O, s);
+  if (e != cudaSuccess) return e;
+  const StreamRows r{rm.qd_rowptr, rm.qd_idx, rm.qd_part, rm.qd_part_ctas, rm.E, rm.n_qd};
+  return launch_label_rows(r, rm.pyr, P, L, mon, depth, rm.num_sms, s);
 }
 
 cudaError_t launch_label_csr(const Roadmap &rm, const uint64_t *O, int32_t P, uint64_t *L, const MonitorTables *mon,

@@ -107,6 +107,55 @@ __global__ void __launch_bounds__(256) k_sector_fill(const int64_t *__restrict__
   }
 }
 
+// Quadtree form: a row (strictly increasing cells) is cut greedily from its
+// first cell into blocks of 4^j consecutive cells starting at a multiple of
+// 4^j, each as large as the row allows (j <= kQuadLevels).  In z-order such a
+// block is a 2^j x 2^j square of the quadtree; in row-major order an aligned
+// run.  Level of the block that starts at entry k (cell c) of a row ending at
+// `end`.
+__device__ __forceinline__ int quad_level(const int32_t *__restrict__ colidx, int64_t k, int64_t end, int64_t c) {
+  int j = 0;
+  while (j < kQuadLevels) {
+    const int64_t n = 4LL << (2 * j);  // the next larger block
+    if ((c & (n - 1)) != 0 || k + n > end || colidx[k + n - 1] != c + n - 1) break;
+    ++j;
+  }
+  return j;
+}
+
+__global__ void __launch_bounds__(256) k_quad_count(const int64_t *__restrict__ rowptr,
+                                                    const int32_t *__restrict__ colidx, int64_t E,
+                                                    int32_t *__restrict__ count) {
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < E; e += stride) {
+    const int64_t end = rowptr[e + 1];
+    int32_t n = 0;
+    for (int64_t k = rowptr[e]; k < end; ++n) k += 1LL << (2 * quad_level(colidx, k, end, colidx[k]));
+    count[e] = n;
+  }
+}
+
+// Entries of a row are written level by level (level 0 first), ascending
+// inside a level, i.e. ascending pyramid index: neighbouring lanes then
+// gather neighbouring words of one level.
+__global__ void __launch_bounds__(256) k_quad_fill(const int64_t *__restrict__ rowptr,
+                                                   const int32_t *__restrict__ colidx, int64_t E, QuadOffsets off,
+                                                   const int64_t *__restrict__ qrow, int32_t *__restrict__ idx) {
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < E; e += stride) {
+    const int64_t beg = rowptr[e], end = rowptr[e + 1];
+    int64_t out = qrow[e];
+    for (int lev = 0; lev <= kQuadLevels; ++lev) {
+      for (int64_t k = beg; k < end;) {
+        const int64_t c = colidx[k];
+        const int j = quad_level(colidx, k, end, c);
+        if (j == lev) idx[out++] = static_cast<int32_t>(off.at[j] + (c >> (2 * j)));
+        k += 1LL << (2 * j);
+      }
+    }
+  }
+}
+
 unsigned blocks_for(int64_t n) {
   int64_t b = (n + 255) / 256;
   if (b > 65535LL * 8) b = 65535LL * 8;
@@ -140,6 +189,24 @@ cudaError_t launch_bt_fill(const int64_t *rowptr, const int32_t *colidx, int64_t
                            uint32_t *bt_block, uint64_t *bt_mask, cudaStream_t s) {
   if (E == 0) return cudaSuccess;
   k_bt_fill<<<blocks_for(E), 256, 0, s>>>(rowptr, colidx, E, bt_rowptr, bt_block, bt_mask);
+  return cudaGetLastError();
+}
+
+}  // namespace lbl
+
+namespace lbl {
+
+cudaError_t launch_quad_count(const int64_t *rowptr, const int32_t *colidx, int64_t E, int32_t *count,
+                              cudaStream_t s) {
+  if (E == 0) return cudaSuccess;
+  k_quad_count<<<blocks_for(E), 256, 0, s>>>(rowptr, colidx, E, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_quad_fill(const int64_t *rowptr, const int32_t *colidx, int64_t E, QuadOffsets off,
+                             const int64_t *qrow, int32_t *idx, cudaStream_t s) {
+  if (E == 0) return cudaSuccess;
+  k_quad_fill<<<blocks_for(E), 256, 0, s>>>(rowptr, colidx, E, off, qrow, idx);
   return cudaGetLastError();
 }
 

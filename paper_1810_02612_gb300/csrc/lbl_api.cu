@@ -93,6 +93,10 @@ void free_roadmap(Roadmap *rm) {
   cudaFree(rm->sec_rowptr);
   cudaFree(rm->sec);
   cudaFree(rm->sec_part);
+  cudaFree(rm->qd_rowptr);
+  cudaFree(rm->qd_idx);
+  cudaFree(rm->qd_part);
+  cudaFree(rm->pyr);
   delete rm;
 }
 
@@ -365,6 +369,48 @@ int roadmap_finish(lbl_roadmap_s *rm, uint32_t flags, cudaStream_t st) {
       return fail(cuda_fail(e, "roadmap: sector partition"));
     rm->has_sec = true;
   }
+  if ((flags & LBL_UPLOAD_QUAD) && n_edges > 0) {
+    if (rm->cells >= (1LL << 30)) {
+      set_error("roadmap: the quadtree form needs fewer than 2^30 cells");
+      return fail(LBL_EINVAL);
+    }
+    // pyramid layout: level k has floor(cells / 4^k) words
+    int64_t words = 0;
+    for (int k = 0; k <= kQuadLevels; ++k) {
+      rm->qd_off.at[k] = words;
+      words += rm->cells >> (2 * k);
+    }
+    rm->pyr_words = words;
+    std::vector<int32_t> cnt(static_cast<size_t>(n_edges));
+    std::vector<int64_t> drow(static_cast<size_t>(n_edges + 1));
+    int32_t *d_dc = nullptr;
+    if ((e = dev_alloc(&d_dc, static_cast<size_t>(n_edges), nullptr)) != cudaSuccess ||
+        (e = launch_quad_count(rm->rowptr, rm->colidx, n_edges, d_dc, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(cnt.data(), d_dc, sizeof(int32_t) * n_edges, cudaMemcpyDeviceToHost, st)) !=
+            cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess) {
+      cudaFree(d_dc);
+      return fail(cuda_fail(e, "roadmap: quadtree form"));
+    }
+    cudaFree(d_dc);
+    drow[0] = 0;
+    for (int64_t i = 0; i < n_edges; ++i) drow[i + 1] = drow[i] + cnt[i];
+    rm->n_qd = drow[n_edges];
+    if ((e = dev_alloc(&rm->qd_rowptr, static_cast<size_t>(n_edges + 1), &rm->bytes)) != cudaSuccess ||
+        (e = dev_alloc(&rm->qd_idx, static_cast<size_t>(rm->n_qd + 4), &rm->bytes)) != cudaSuccess ||
+        (e = dev_alloc(&rm->qd_part, static_cast<size_t>(rm->part_cap), &rm->bytes)) != cudaSuccess ||
+        (e = dev_alloc(&rm->pyr, static_cast<size_t>(words), &rm->bytes)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(rm->qd_rowptr, drow.data(), sizeof(int64_t) * (n_edges + 1), cudaMemcpyHostToDevice,
+                             st)) != cudaSuccess ||
+        (e = launch_quad_fill(rm->rowptr, rm->colidx, n_edges, rm->qd_off, rm->qd_rowptr, rm->qd_idx, st)) !=
+            cudaSuccess)
+      return fail(cuda_fail(e, "roadmap: quadtree form"));
+    rm->qd_part_ctas = stream_ctas_per_sm(8);
+    const int64_t W = static_cast<int64_t>(rm->num_sms) * rm->qd_part_ctas * (kThreads / 32);
+    if ((e = launch_partition_into(rm->qd_rowptr, n_edges, W, rm->qd_part, st)) != cudaSuccess)
+      return fail(cuda_fail(e, "roadmap: quadtree partition"));
+    rm->has_qd = true;
+  }
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(cuda_fail(e, "roadmap"));
   cudaFree(d_bad);
   cudaFree(d_cnt);
@@ -396,7 +442,7 @@ int lbl_roadmap_upload(const lbl_grid *agent, const int64_t *rowptr, const int32
     set_error("roadmap upload: rowptr/colidx is NULL");
     return LBL_EINVAL;
   }
-  if (flags & ~(LBL_UPLOAD_DEVICE_PTRS | LBL_UPLOAD_BITTILE | LBL_UPLOAD_SECTOR)) {
+  if (flags & ~(LBL_UPLOAD_DEVICE_PTRS | LBL_UPLOAD_BITTILE | LBL_UPLOAD_SECTOR | LBL_UPLOAD_QUAD)) {
     set_error("roadmap upload: unknown flags 0x%x", flags);
     return LBL_EINVAL;
   }
@@ -426,7 +472,7 @@ int lbl_roadmap_free(lbl_roadmap rm) {
 }
 
 int lbl_roadmap_info(lbl_roadmap rm, int64_t *n_edges, int64_t *nnz, int64_t *n_block_entries,
-                     int64_t *n_sector_entries, int64_t *device_bytes) {
+                     int64_t *n_sector_entries, int64_t *n_qdadic_entries, int64_t *device_bytes) {
   g_err.clear();
   if (!rm) {
     set_error("roadmap info: NULL roadmap");
@@ -436,6 +482,7 @@ int lbl_roadmap_info(lbl_roadmap rm, int64_t *n_edges, int64_t *nnz, int64_t *n_
   if (nnz) *nnz = rm->nnz;
   if (n_block_entries) *n_block_entries = rm->n_bt;
   if (n_sector_entries) *n_sector_entries = rm->n_sec;
+  if (n_qdadic_entries) *n_qdadic_entries = rm->n_qd;
   if (device_bytes) *device_bytes = rm->bytes;
   return LBL_OK;
 }
@@ -622,7 +669,7 @@ static int label_impl(lbl_roadmap rm, const uint64_t *d_O, int32_t n_props, uint
     return LBL_EINVAL;
   }
   int algo = cfg ? cfg->algo : LBL_ALGO_AUTO;
-  if (algo < LBL_ALGO_AUTO || algo > LBL_ALGO_SECTOR) {
+  if (algo < LBL_ALGO_AUTO || algo > LBL_ALGO_QUAD) {
     set_error("label: unknown algo %d", algo);
     return LBL_EINVAL;
   }
@@ -632,6 +679,10 @@ static int label_impl(lbl_roadmap rm, const uint64_t *d_O, int32_t n_props, uint
   }
   if (algo == LBL_ALGO_SECTOR && !rm->has_sec) {
     set_error("label: LBL_ALGO_SECTOR needs a roadmap uploaded with LBL_UPLOAD_SECTOR");
+    return LBL_EUNSUPPORTED;
+  }
+  if (algo == LBL_ALGO_QUAD && !rm->has_qd) {
+    set_error("label: LBL_ALGO_QUAD needs a roadmap uploaded with LBL_UPLOAD_QUAD");
     return LBL_EUNSUPPORTED;
   }
   if (algo == LBL_ALGO_SECTOR && rm->E > 0 && (reinterpret_cast<uintptr_t>(d_O) & 31u)) {
@@ -644,7 +695,8 @@ static int label_impl(lbl_roadmap rm, const uint64_t *d_O, int32_t n_props, uint
     cfg = &tuned_cfg;
     algo = tuned_cfg.algo;
   }
-  if (algo == LBL_ALGO_AUTO) algo = (rm->has_bt && n_props <= 8) ? LBL_ALGO_BITTILE : LBL_ALGO_CSR;
+  if (algo == LBL_ALGO_AUTO)
+    algo = rm->has_qd ? LBL_ALGO_QUAD : (rm->has_bt && n_props <= 8) ? LBL_ALGO_BITTILE : LBL_ALGO_CSR;
   int ee = cfg ? cfg->early_exit : -1;
   const bool early = ee > 0;  // measured: the per-step OR-reduce costs more than it saves
   const int ctas = cfg ? cfg->ctas_per_sm : 0;
@@ -667,6 +719,19 @@ static int label_impl(lbl_roadmap rm, const uint64_t *d_O, int32_t n_props, uint
       }
     }
     e = launch_label_sector(*rm, d_O, n_props, d_L, mon ? &t : nullptr, depth, st);
+  } else if (algo == LBL_ALGO_QUAD) {
+    const int depth = cfg ? cfg->depth : 0;
+    if (rm->E > 0) {
+      const int occ = stream_ctas_per_sm(depth);
+      const int want = ctas > 0 ? std::min(ctas, occ) : occ;
+      if (want != rm->qd_part_ctas) {
+        const int64_t W = static_cast<int64_t>(rm->num_sms) * want * (kThreads / 32);
+        if ((e = launch_partition_into(rm->qd_rowptr, rm->E, W, rm->qd_part, st)) != cudaSuccess)
+          return cuda_fail(e, "label: quadtree partition");
+        rm->qd_part_ctas = want;
+      }
+    }
+    e = launch_label_quad(*rm, d_O, n_props, d_L, mon ? &t : nullptr, depth, st);
   } else if (early || lpe > 0) {
     // lanes-per-edge form (one edge per lane group; supports early exit)
     e = launch_label_csr(*rm, d_O, n_props, d_L, mon ? &t : nullptr, resolve_lpe(*rm, cfg), early, ctas, st);
@@ -719,6 +784,8 @@ int lbl_roadmap_autotune(lbl_roadmap rm, const uint64_t *d_O, int32_t n_props, l
   if (rm->has_bt) cand.push_back(lbl_config{LBL_ALGO_BITTILE, 0, 0, 0, 0, 0});
   if (rm->has_sec && !(reinterpret_cast<uintptr_t>(d_O) & 31u))
     for (int depth : {4, 8}) cand.push_back(lbl_config{LBL_ALGO_SECTOR, 0, 0, 0, 0, depth});
+  if (rm->has_qd)
+    for (int depth : {8, 12}) cand.push_back(lbl_config{LBL_ALGO_QUAD, 0, 0, 0, 0, depth});
   cudaEvent_t t0, t1;
   cudaError_t e = cudaEventCreate(&t0);
   if (e == cudaSuccess) e = cudaEventCreate(&t1);
@@ -840,6 +907,9 @@ int lbl_batch_create(int32_t n, const lbl_roadmap *rms, const int32_t *n_props, 
   }
   b->tab.n = n;
   b->tab.total = warp0;
+  b->tab.wide = 0;
+  for (int i = 0; i < n; ++i)
+    if (rms[i]->nnz >= kNarrowLimit || rms[i]->E >= kNarrowLimit) b->tab.wide = 1;
   b->ftab.n = n;
   *out = b;
   return LBL_OK;

@@ -11,6 +11,12 @@
 //                                 cells [64b, 64b+64) in the grid's cell order
 //   planes  uint64[blocks][P]     bit-plane re-layout of O for the block form:
 //                                 bit i of planes[b][p] = bit p of O[64b + i]
+//   qd_*                          quadtree form of M: each row as the union of its
+//                                 maximal blocks of 4^k consecutive cells (k <= 4)
+//                                 starting at a multiple of 4^k; an entry is the
+//                                 index of the block's word in the pyramid
+//   pyr     uint64[~4/3 cells]    per-frame pyramid: level k, block b holds the OR
+//                                 of O over cells [b 4^k, (b+1) 4^k)
 #pragma once
 
 #include <cuda_runtime.h>
@@ -25,6 +31,9 @@ namespace lbl {
 constexpr int kThreads = 256;  // threads per CTA of every labeling kernel
 constexpr int kMaxCtasPerSm = 8;  // 2048 resident threads per SM / kThreads
 constexpr int64_t kEdgeCost = 32;  // partition weight of one edge, in nonzeros
+// Streamed row sets with fewer entries and edges than this keep positions in
+// 32-bit registers (headroom for the group arithmetic).
+constexpr int64_t kNarrowLimit = (1LL << 31) - 4096;
 
 struct MonitorTables {
   const uint64_t *T;  // T[letter]: packed next states of all monitor states
@@ -67,12 +76,29 @@ constexpr int kMaxBatch = 128;
 struct BatchTable {
   BatchItem items[kMaxBatch];
   int32_t n;
+  int32_t wide;   // some item has 2^31 - 4096 or more nonzeros or edges
   int64_t total;  // work units
 };
 struct FrameTable {
   FrameItem items[kMaxBatch];
   int32_t n;
   int64_t total;  // cells
+};
+
+// Levels of the quadtree form: blocks of up to 4^4 = 256 cells.
+constexpr int kQuadLevels = 4;
+struct QuadOffsets {
+  int64_t at[kQuadLevels + 1];  // first pyramid word of each level
+};
+
+// One streamed row set: CSR rows over some gather base (cells, sectors or
+// pyramid words) with its warp partition.
+struct StreamRows {
+  const int64_t *rowptr;
+  const int32_t *idx;
+  const int64_t *part;
+  int part_ctas;
+  int64_t E, entries;
 };
 
 struct Roadmap {
@@ -97,6 +123,16 @@ struct Roadmap {
   int32_t *sec = nullptr;      // n_sec entries, padded like colidx
   int64_t *sec_part = nullptr;  // partition of the sector kernel's grid
   int sec_part_ctas = 0;
+  // quadtree form (optional): per edge the pyramid indices of its maximal blocks
+  bool has_qd = false;
+  int64_t n_qd = 0;
+  int64_t *qd_rowptr = nullptr;
+  int32_t *qd_idx = nullptr;    // n_qd entries, padded like colidx
+  int64_t *qd_part = nullptr;   // partition of the quadtree stream's grid
+  int qd_part_ctas = 0;
+  QuadOffsets qd_off{};
+  int64_t pyr_words = 0;
+  uint64_t *pyr = nullptr;      // per-frame pyramid (working memory)
   // edge partition of the streaming CSR kernel: warp w owns [part[w], part[w+1])
   int64_t *part = nullptr;
   int64_t part_cap = 0;  // entries allocated
@@ -169,6 +205,17 @@ cudaError_t launch_label_tma(const Roadmap &rm, const uint64_t *O, int32_t P, ui
 cudaError_t launch_partition(const Roadmap &rm, int ctas_per_sm, cudaStream_t s);
 cudaError_t launch_label_stream(const Roadmap &rm, const uint64_t *O, int32_t P, uint64_t *L,
                                 const MonitorTables *mon, int depth, cudaStream_t s);
+cudaError_t launch_label_rows(const StreamRows &r, const uint64_t *base, int32_t P, uint64_t *L,
+                              const MonitorTables *mon, int depth, int num_sms, cudaStream_t s);
+
+// quadtree form: pyramid of O, then the stream over the quadtree rows
+cudaError_t launch_quad_pyramid(const Roadmap &rm, const uint64_t *O, cudaStream_t s);
+cudaError_t launch_label_quad(const Roadmap &rm, const uint64_t *O, int32_t P, uint64_t *L,
+                                const MonitorTables *mon, int depth, cudaStream_t s);
+cudaError_t launch_quad_count(const int64_t *rowptr, const int32_t *colidx, int64_t E, int32_t *count,
+                                cudaStream_t s);
+cudaError_t launch_quad_fill(const int64_t *rowptr, const int32_t *colidx, int64_t E, QuadOffsets off,
+                               const int64_t *drow, int32_t *idx, cudaStream_t s);
 
 cudaError_t launch_label_bittile(const Roadmap &rm, const uint64_t *O, int32_t P, uint64_t *L,
                                  const MonitorTables *mon, bool early_exit, int ctas_per_sm, cudaStream_t s);

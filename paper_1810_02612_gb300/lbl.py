@@ -30,6 +30,7 @@ LBL_ALGO_AUTO = 0
 LBL_ALGO_CSR = 1
 LBL_ALGO_BITTILE = 2
 LBL_ALGO_SECTOR = 3
+LBL_ALGO_QUAD = 4
 
 LBL_PIPE_REGISTERS = 1
 LBL_PIPE_BULK = 2
@@ -41,6 +42,7 @@ LBL_STAGE_LABEL = 2
 LBL_UPLOAD_DEVICE_PTRS = 1
 LBL_UPLOAD_BITTILE = 2
 LBL_UPLOAD_SECTOR = 4
+LBL_UPLOAD_QUAD = 8
 
 # every entry point declared in include/lbl.h
 EXPORTS = (
@@ -110,7 +112,7 @@ def load(build_if_needed: bool = True):
         "lbl_roadmap_rasterize": (ctypes.c_int, [G, p, i64, ctypes.c_double, u32, p, ctypes.POINTER(p)]),
         "lbl_roadmap_rows": (ctypes.c_int, [p, p, p, p]),
         "lbl_roadmap_free": (ctypes.c_int, [p]),
-        "lbl_roadmap_info": (ctypes.c_int, [p, p, p, p, p, p]),
+        "lbl_roadmap_info": (ctypes.c_int, [p, p, p, p, p, p, p]),
         "lbl_roadmap_status": (ctypes.c_int, [p, p]),
         "lbl_frame_transform": (ctypes.c_int, [G, p, i32, lbl_pose, G, p, p]),
         "lbl_monitor_create": (ctypes.c_int, [i32, i32, p, p, i32, ctypes.POINTER(p)]),
@@ -267,8 +269,8 @@ def lbl_roadmap_free(rm) -> None:
 
 
 def lbl_roadmap_info(rm):
-    """(n_edges, nnz, n_block_entries, n_sector_entries, device_bytes) of a roadmap."""
-    v = [ctypes.c_int64() for _ in range(5)]
+    """(n_edges, nnz, n_block_entries, n_sector_entries, n_qdadic_entries, device_bytes) of a roadmap."""
+    v = [ctypes.c_int64() for _ in range(6)]
     _check(load().lbl_roadmap_info(rm, *[ctypes.byref(x) for x in v]))
     return tuple(x.value for x in v)
 

@@ -36,8 +36,8 @@ def empty_u16(n):
 class Roadmap:
     def __init__(self, agent, rowptr, colidx, bittile=False):
         self.E = rowptr.shape[0] - 1
-        self.h = L.lbl_roadmap_upload(agent, rowptr, colidx,
-                                      flags=(L.LBL_UPLOAD_BITTILE | L.LBL_UPLOAD_SECTOR) if bittile else 0)
+        every_form = L.LBL_UPLOAD_BITTILE | L.LBL_UPLOAD_SECTOR | L.LBL_UPLOAD_QUAD
+        self.h = L.lbl_roadmap_upload(agent, rowptr, colidx, flags=every_form if bittile else 0)
 
     def __del__(self):
         if getattr(self, "h", None):
@@ -79,6 +79,10 @@ CFGS = [
     dict(algo=L.LBL_ALGO_CSR, depth=12),
     dict(algo=L.LBL_ALGO_CSR, depth=16),
     dict(algo=L.LBL_ALGO_BITTILE, early_exit=1),
+    dict(algo=L.LBL_ALGO_QUAD),
+    dict(algo=L.LBL_ALGO_QUAD, depth=12),
+    dict(algo=L.LBL_ALGO_QUAD, depth=16),
+    dict(algo=L.LBL_ALGO_QUAD, ctas_per_sm=1),
     dict(algo=L.LBL_ALGO_AUTO),
 ]
 
@@ -280,8 +284,8 @@ def test_upload_from_device_pointers_and_info(plain):
     wl = plain
     h = L.lbl_roadmap_upload(wl.agent, cuda(wl.rowptr), cuda(wl.colidx))
     try:
-        E, nnz, nbt, nsec, b = L.lbl_roadmap_info(h)
-        assert nbt == 0 and nsec == 0
+        E, nnz, nbt, nsec, ndy, b = L.lbl_roadmap_info(h)
+        assert nbt == 0 and nsec == 0 and ndy == 0
         assert (E, nnz) == (wl.n_edges, wl.nnz) and b >= 8 * (E + 1) + 4 * nnz
         O = gpu_O(wl)
         out = empty_u64(E)
@@ -289,6 +293,71 @@ def test_upload_from_device_pointers_and_info(plain):
         assert np.array_equal(host(out), oracle.label(wl.rowptr, wl.colidx, host(O), wl.P))
     finally:
         L.lbl_roadmap_free(h)
+
+
+def _quad_count(rowptr, colidx, levels=4):
+    """Maximal blocks of 4^j cells per row, counted by a plain scan (test helper)."""
+    counts = []
+    for e in range(rowptr.shape[0] - 1):
+        row = colidx[rowptr[e]:rowptr[e + 1]].astype(np.int64)
+        k, n = 0, 0
+        while k < row.shape[0]:
+            j = 0
+            while j < levels:
+                size = 4 << (2 * j)
+                if row[k] % size or k + size > row.shape[0] or row[k + size - 1] != row[k] + size - 1:
+                    break
+                j += 1
+            k += 1 << (2 * j)
+            n += 1
+        counts.append(n)
+    return np.array(counts, np.int64)
+
+
+@pytest.mark.parametrize("order", [synth.MORTON, synth.ROWMAJOR])
+def test_quad_runs_at_every_alignment(order):
+    """Rows made of runs of 1..700 consecutive cells at every offset modulo 256,
+    rows covering the whole grid, rows ending at its last cell and single
+    cells: quadtree-form labels equal the oracle's for every proposition
+    count, and the form holds exactly one entry per maximal block."""
+    rng = np.random.default_rng(91 + order)
+    agent = synth.agent_grid(64, 0.5, order) if order == synth.MORTON else synth.Grid(77, 53, 0.5, 0.0, 0.0, order)
+    cells = agent.cells
+    rows = [np.arange(cells), np.arange(cells - 300, cells), np.array([cells - 1]), np.array([0]), np.arange(0, 256),
+            np.arange(1, 257), np.arange(255, 512)]
+    for start in range(0, 256, 7):
+        for length in (1, 2, 3, 255, 256, 257, 700):
+            if start + length <= cells:
+                rows.append(np.arange(start, start + length))
+    for _ in range(200):  # a few random runs per row
+        parts = []
+        for _ in range(int(rng.integers(1, 5))):
+            a = int(rng.integers(0, cells - 1))
+            parts.append(np.arange(a, min(cells, a + int(rng.integers(1, 400)))))
+        rows.append(np.unique(np.concatenate(parts)))
+    rows.append(np.array([], np.int64))
+    rowptr = np.zeros(len(rows) + 1, np.int64)
+    rowptr[1:] = np.cumsum([r.shape[0] for r in rows])
+    colidx = np.concatenate(rows).astype(np.int32)
+    rm = Roadmap(agent, rowptr, colidx, bittile=True)
+    want_entries = int(_quad_count(rowptr, colidx).sum())
+    assert L.lbl_roadmap_info(rm.h)[4] == want_entries
+    assert want_entries < 0.3 * colidx.shape[0]
+    for P in (1, 2, 31, 64):
+        O_h = np.zeros(cells, np.uint64)
+        hit = rng.random(cells) < 0.01
+        O_h[hit] = rng.integers(1, 2**63, size=hit.sum(), dtype=np.uint64)
+        O_h[cells - 1] = np.uint64(1 << (P - 1))
+        want = oracle.label(rowptr, colidx, O_h, P)
+        for depth in (8, 12, 16):
+            assert np.array_equal(gpu_label(rm, cuda(O_h), P, dict(algo=L.LBL_ALGO_QUAD, depth=depth)), want), P
+
+
+def test_quad_needs_its_upload_flag(plain):
+    rm = Roadmap(plain.agent, plain.rowptr, plain.colidx, bittile=False)
+    with pytest.raises(L.LblError) as ei:
+        gpu_label(rm, gpu_O(plain), plain.P, dict(algo=L.LBL_ALGO_QUAD))
+    assert ei.value.code == L.LBL_EUNSUPPORTED
 
 
 def test_bittile_needs_its_upload_flag(plain):
@@ -351,7 +420,7 @@ def test_autotune_choice_is_exact_and_sticks(driving_small):
     want = oracle.label(wl.rowptr, wl.colidx, host(O), wl.P, threads=8)
     out = empty_u64(rm.E)
     chosen = L.lbl_roadmap_autotune(rm.h, O, wl.P, out, reps=2)
-    assert chosen["algo"] in (L.LBL_ALGO_CSR, L.LBL_ALGO_BITTILE, L.LBL_ALGO_SECTOR)
+    assert chosen["algo"] in (L.LBL_ALGO_CSR, L.LBL_ALGO_BITTILE, L.LBL_ALGO_SECTOR, L.LBL_ALGO_QUAD)
     assert np.array_equal(host(out), want)
     assert np.array_equal(gpu_label(rm, O, wl.P, dict(algo=L.LBL_ALGO_AUTO)), want)
     assert np.array_equal(gpu_label(rm, O, wl.P, None), want)
