@@ -65,6 +65,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS))
+    ap.add_argument("--requests", type=int, default=20_000, help="serving: requests at the first rate")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--algo", default="quad", choices=["auto", "csr", "bittile", "sector", "quad"],
                     help="labeling form; auto = measure every form on the first frame and keep the fastest")
@@ -78,7 +79,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
-    ap.add_argument("--rates", default="2000,3500,5000", help="serving: request rates (req/s); the first is the "
+    ap.add_argument("--rates", default="2000,5000,10000,15000", help="serving: request rates (req/s); the first is the "
                     "configured rate of the headline line, the others a saturation sweep")
     return ap.parse_args()
 
@@ -474,8 +475,10 @@ def run_batched(args, rank, world, local, dist, torch, L):
     t_gen = time.perf_counter() - t_gen
     stream = torch.cuda.Stream()
     rms, fr = [], []
+    quad = args.algo in ("quad", "auto")
     for f in frames:
-        rms.append(L.lbl_roadmap_upload(f.agent, f.rowptr, f.colidx, stream=stream))
+        rms.append(L.lbl_roadmap_upload(f.agent, f.rowptr, f.colidx, flags=L.LBL_UPLOAD_QUAD if quad else 0,
+                                        stream=stream))
     for f in frames:
         d_pl = torch.from_numpy(np.ascontiguousarray(f.planes)).cuda()
         fr.append(dict(world=f.world, d_planes=d_pl, pose=f.pose,
@@ -542,7 +545,10 @@ def run_batched(args, rank, world, local, dist, torch, L):
     value = job_throughput(world, units, 1, args.steps, total_b)
     plain_value = job_throughput(world, units, 1, args.steps, total_p)
     nnz = sum(f.nnz for f in frames)
-    bytes_step = sum(4 * f.nnz + 16 * f.n_edges + 8 * f.agent.cells + f.P * f.world.cells for f in frames)
+    entries = [L.lbl_roadmap_info(r)[4] if quad else f.nnz for f, r in zip(frames, rms)]
+    bytes_step = sum(4 * n + 16 * f.n_edges + 8 * f.agent.cells + f.P * f.world.cells
+                     + (16 * pyramid_words(f.agent.cells) if quad else 0) for f, n in zip(frames, entries))
+    launches = 3 if quad else 2  # transform, (pyramid,) label
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
     achieved = bytes_step / (total_b / args.steps / 1e3) / 1e9
@@ -552,11 +558,13 @@ def run_batched(args, rank, world, local, dist, torch, L):
             "warmup": args.warmup, "ms_per_step": total_b / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": WORKLOADS["batched"], "name": "batched", "frames": len(frames),
-                       "edges": sum(f.n_edges for f in frames), "nnz": nnz,
+                       "edges": sum(f.n_edges for f in frames), "nnz": nnz, "algo": "quad" if quad else "csr",
+                       "streamed_entries": int(sum(entries)),
                        "l2": "flushed before every step (256 MiB write)", "parallelism": f"replicas x{world}"},
             "batched_vs_plain": {"plain_value": plain_value, "plain_ms_per_step": total_p / args.steps,
                                  "speedup": total_p / total_b, "bit_exact_match": bool(match),
-                                 "plain_launches_per_step": 2 * len(frames), "batched_launches_per_step": 2,
+                                 "plain_launches_per_step": launches * len(frames),
+                                 "batched_launches_per_step": launches,
                                  "stage_ms": {"batched_transform": float(np.median(b_tr)),
                                               "batched_label": float(np.median(b_lb)),
                                               "plain_transform": float(np.median(p_tr)),
@@ -565,7 +573,7 @@ def run_batched(args, rank, world, local, dist, torch, L):
                            "batched_p99": float(np.percentile(batched_ms, 99)),
                            "plain_p50": float(np.percentile(plain_ms, 50)),
                            "plain_p99": float(np.percentile(plain_ms, 99))},
-            "gpu_launches": 2 * args.steps,
+            "gpu_launches": launches * args.steps,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": None, "kernel": "batched step (frame transforms + labels)",
                          "algorithmic_bytes_per_launch": bytes_step,
@@ -594,8 +602,10 @@ def run_serving(args, rank, world, local, dist, torch, L):
     P = 32
     plane_sets = [torch.from_numpy(synth.planes_mixed(rng, P, wgrid)).pin_memory() for _ in range(8)]
     t_gen = time.perf_counter() - t_gen
-    rms = [L.lbl_roadmap_upload(agent, rowptr[: n + 1], colidx[: int(rowptr[n])]) for n in sizes]
-    n_max = args.steps if args.steps >= 1000 else 20_000
+    quad = args.algo in ("quad", "auto")
+    rms = [L.lbl_roadmap_upload(agent, rowptr[: n + 1], colidx[: int(rowptr[n])],
+                                flags=L.LBL_UPLOAD_QUAD if quad else 0) for n in sizes]
+    n_max = args.requests
     unit_gaps = rng.exponential(1.0, size=n_max)  # scaled by 1/rate per run
     which = rng.integers(0, len(sizes), size=n_max)
     sets = rng.integers(0, len(plane_sets), size=n_max)
@@ -664,7 +674,8 @@ def run_serving(args, rank, world, local, dist, torch, L):
             "dtype": "u64", "data": "synthetic",
             "config": {"workload": WORKLOADS["serving"], "name": "serving", "requests": n_max, "rate_req_s": rate,
                        "roadmap_edges": sizes, "nnz_largest": int(rowptr[-1]), "props": P,
-                       "parallelism": f"replicas x{world}"},
+                       "algo": "quad" if quad else "csr", "parallelism": f"replicas x{world}"},
+            "gpu_launches": int(cont["batches"]) * (3 if quad else 2),
             "serving": {"continuous_batching": cont, "one_request_per_launch": plain,
                         "p99_gain": plain["p99_ms"] / cont["p99_ms"], "saturation_sweep": sweep},
             "latency_ms": {"p50": cont["p50_ms"], "p99": cont["p99_ms"]},

@@ -377,15 +377,16 @@ __global__ void __launch_bounds__(kThreads, 4) k_label_batch(const __grid_consta
 // Quadtree pyramid of O for the quadtree form (compressed A): level k holds,
 // for every block of 4^k consecutive cells in the grid's cell order that lies
 // wholly inside the grid, the OR of their words; level 0 is O itself.  Word of
-// block b at level k: pyr[off.at[k] + b].  One CTA covers 256 consecutive
-// cells: levels 1-2 (4 and 16 cells) by butterfly shuffles inside each warp,
-// levels 3-4 (64 and 256 cells) from the eight 32-cell warp words.
-__global__ void __launch_bounds__(kThreads) k_quad_pyramid(const uint64_t *__restrict__ O, int64_t cells,
-                                                           QuadOffsets off, uint64_t *__restrict__ pyr) {
+// block b at level k: pyr[off.at[k] + b].  One CTA covers the 256 consecutive
+// cells of top-level block `blk`: levels 1-2 (4 and 16 cells) by butterfly
+// shuffles inside each warp, levels 3-4 (64 and 256 cells) from the eight
+// 32-cell warp words.
+__device__ __forceinline__ void quad_pyramid_block(const uint64_t *__restrict__ O, int64_t cells,
+                                                   const QuadOffsets &off, uint64_t *__restrict__ pyr, int64_t blk,
+                                                   uint64_t *wsum) {
   static_assert(kThreads == 256 && kQuadLevels == 4, "one CTA = one block of the top level");
-  __shared__ uint64_t wsum[kThreads / 32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int64_t i = static_cast<int64_t>(blockIdx.x) * kThreads + threadIdx.x;
+  const int64_t i = blk * kThreads + threadIdx.x;
   uint64_t v = i < cells ? __ldg(O + i) : 0ull;
   if (i < cells) pyr[i] = v;
   v = or_xor(or_xor(v, 1), 2);  // every lane: OR of its aligned 4-cell block
@@ -397,14 +398,37 @@ __global__ void __launch_bounds__(kThreads) k_quad_pyramid(const uint64_t *__res
   __syncthreads();
   if (threadIdx.x < 4) {  // 64-cell blocks: warps (2t, 2t+1)
     const int t = threadIdx.x;
-    const int64_t b = static_cast<int64_t>(blockIdx.x) * 4 + t;
+    const int64_t b = blk * 4 + t;
     if (b < (cells >> 6)) pyr[off.at[3] + b] = wsum[2 * t] | wsum[2 * t + 1];
   } else if (threadIdx.x == 4) {  // the 256-cell block
     uint64_t a = 0;
 #pragma unroll
     for (int w = 0; w < kThreads / 32; ++w) a |= wsum[w];
-    if (static_cast<int64_t>(blockIdx.x) < (cells >> 8)) pyr[off.at[4] + blockIdx.x] = a;
+    if (blk < (cells >> 8)) pyr[off.at[4] + blk] = a;
   }
+}
+
+__global__ void __launch_bounds__(kThreads) k_quad_pyramid(const uint64_t *__restrict__ O, int64_t cells,
+                                                           QuadOffsets off, uint64_t *__restrict__ pyr) {
+  __shared__ uint64_t wsum[kThreads / 32];
+  quad_pyramid_block(O, cells, off, pyr, blockIdx.x, wsum);
+}
+
+// The same for many frames in one launch: CTA b finds its item (the last with
+// block0 <= b) and builds that item's top-level block b - block0.
+__global__ void __launch_bounds__(kThreads) k_quad_pyramid_batch(const __grid_constant__ PyrTable tab) {
+  __shared__ uint64_t wsum[kThreads / 32];
+  const int64_t b = blockIdx.x;
+  int lo = 0, hi = tab.n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (tab.items[mid].block0 <= b)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  const PyrItem &it = tab.items[lo];
+  quad_pyramid_block(it.O, it.cells, it.off, it.pyr, b - it.block0, wsum);
 }
 
 // ---------------------------------------------------------------------------
@@ -1035,6 +1059,12 @@ cudaError_t launch_quad_pyramid(const Roadmap &rm, const uint64_t *O, cudaStream
   if (rm.cells == 0) return cudaSuccess;
   const unsigned grid = static_cast<unsigned>((rm.cells + kThreads - 1) / kThreads);
   k_quad_pyramid<<<grid, kThreads, 0, s>>>(O, rm.cells, rm.qd_off, rm.pyr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_quad_pyramid_batch(const PyrTable &tab, cudaStream_t s) {
+  if (tab.n == 0 || tab.total == 0) return cudaSuccess;
+  k_quad_pyramid_batch<<<static_cast<unsigned>(tab.total), kThreads, 0, s>>>(tab);
   return cudaGetLastError();
 }
 

@@ -201,6 +201,10 @@ struct lbl_batch_s {
   int ctas = 1;
   BatchTable tab{};
   FrameTable ftab{};
+  // items whose roadmap has the quadtree form label from their own pyramid
+  uint64_t *pyr = nullptr;      // every such item's pyramid, concatenated
+  std::vector<int> pyr_slot;    // item -> entry of ptab, or -1
+  PyrTable ptab{};
   bool frames_set = false;
 };
 
@@ -861,15 +865,20 @@ int lbl_batch_create(int32_t n, const lbl_roadmap *rms, const int32_t *n_props, 
   b->ctas = ctas;
   constexpr int64_t kUnitsPerWarp = 8;
   const int64_t units_target = static_cast<int64_t>(b->num_sms) * ctas * (kThreads / 32) * kUnitsPerWarp;
+  // entries streamed per item: quadtree entries when the roadmap has them
+  auto entries = [](const Roadmap &r) { return r.has_qd ? r.n_qd : r.nnz; };
   double total = 0;
-  for (int i = 0; i < n; ++i) total += static_cast<double>(rms[i]->nnz + kEdgeCost * rms[i]->E);
+  for (int i = 0; i < n; ++i) total += static_cast<double>(entries(*rms[i]) + kEdgeCost * rms[i]->E);
   const double unit_cost = total > 0 ? total / static_cast<double>(units_target) : 1.0;
   std::vector<int64_t> W(n), off(n + 1, 0);
+  int64_t pyr_words = 0;
+  for (int i = 0; i < n; ++i)
+    if (rms[i]->has_qd && rms[i]->E > 0) pyr_words += rms[i]->pyr_words;
   for (int i = 0; i < n; ++i) {
     const Roadmap &r = *rms[i];
     W[i] = 0;
     if (r.E > 0) {
-      const double c = static_cast<double>(r.nnz + kEdgeCost * r.E);
+      const double c = static_cast<double>(entries(r) + kEdgeCost * r.E);
       W[i] = std::max<int64_t>(1, static_cast<int64_t>(std::ceil(c / unit_cost)));
       W[i] = std::min<int64_t>(W[i], r.E);  // never more units than edges
     }
@@ -877,15 +886,30 @@ int lbl_batch_create(int32_t n, const lbl_roadmap *rms, const int32_t *n_props, 
   }
   cudaError_t e = dev_alloc(&b->part, static_cast<size_t>(off[n]), nullptr);
   if (e == cudaSuccess) e = dev_alloc(&b->counter, 1, nullptr);
-  int64_t warp0 = 0;
+  if (e == cudaSuccess && pyr_words > 0) e = dev_alloc(&b->pyr, static_cast<size_t>(pyr_words), nullptr);
+  b->pyr_slot.assign(n, -1);
+  int64_t warp0 = 0, pyr0 = 0, block0 = 0;
   for (int i = 0; i < n && e == cudaSuccess; ++i) {
     const Roadmap &r = *rms[i];
-    e = launch_partition_into(r.rowptr, r.E, W[i], b->part + off[i], nullptr);
+    const bool quad = r.has_qd && r.E > 0;
+    e = launch_partition_into(quad ? r.qd_rowptr : r.rowptr, r.E, W[i], b->part + off[i], nullptr);
     BatchItem &it = b->tab.items[i];
     it = BatchItem{};
-    it.rowptr = r.rowptr;
-    it.colidx = r.colidx;
+    it.rowptr = quad ? r.qd_rowptr : r.rowptr;
+    it.colidx = quad ? r.qd_idx : r.colidx;
     it.part = b->part + off[i];
+    if (quad) {  // labels gather from the item's pyramid, built from its O at the label stage
+      PyrItem &pi = b->ptab.items[b->ptab.n];
+      pi = PyrItem{};
+      pi.pyr = b->pyr + pyr0;
+      pi.cells = r.cells;
+      pi.block0 = block0;
+      pi.off = r.qd_off;
+      it.O = pi.pyr;
+      b->pyr_slot[i] = b->ptab.n++;
+      pyr0 += r.pyr_words;
+      block0 += (r.cells + kThreads - 1) / kThreads;
+    }
     it.mask = n_props[i] >= 64 ? ~0ull : ((1ull << n_props[i]) - 1ull);
     it.warp0 = warp0;
     it.warps = W[i];
@@ -902,14 +926,16 @@ int lbl_batch_create(int32_t n, const lbl_roadmap *rms, const int32_t *n_props, 
   if (e != cudaSuccess) {
     cudaFree(b->part);
     cudaFree(b->counter);
+    cudaFree(b->pyr);
     delete b;
     return cuda_fail(e, "batch create: partitions");
   }
+  b->ptab.total = block0;
   b->tab.n = n;
   b->tab.total = warp0;
   b->tab.wide = 0;
   for (int i = 0; i < n; ++i)
-    if (rms[i]->nnz >= kNarrowLimit || rms[i]->E >= kNarrowLimit) b->tab.wide = 1;
+    if (entries(*rms[i]) >= kNarrowLimit || rms[i]->E >= kNarrowLimit) b->tab.wide = 1;
   b->ftab.n = n;
   *out = b;
   return LBL_OK;
@@ -937,7 +963,10 @@ int lbl_batch_set_frames(lbl_batch b, const lbl_frame *frames) {
     b->ftab.items[i] = frame_item(m, f.world, r.agent, f.d_planes, P, f.d_O, cell0);
     cell0 += r.cells;
     BatchItem &it = b->tab.items[i];
-    it.O = f.d_O;
+    if (b->pyr_slot[i] >= 0)
+      b->ptab.items[b->pyr_slot[i]].O = f.d_O;  // the item gathers from its pyramid
+    else
+      it.O = f.d_O;
     it.L = f.d_L;
     it.next = f.d_next;
     it.viol = f.d_viol;
@@ -956,7 +985,10 @@ int lbl_batch_launch(lbl_batch b, uint32_t stages, lbl_stream s) {
   cudaStream_t st = reinterpret_cast<cudaStream_t>(s);
   cudaError_t e = cudaSuccess;
   if (stages & LBL_STAGE_TRANSFORM) e = launch_frame_batch(b->ftab, b->num_sms, st);
-  if (e == cudaSuccess && (stages & LBL_STAGE_LABEL)) e = launch_label_batch(b->tab, b->counter, b->num_sms, b->ctas, st);
+  if (e == cudaSuccess && (stages & LBL_STAGE_LABEL)) {
+    e = launch_quad_pyramid_batch(b->ptab, st);
+    if (e == cudaSuccess) e = launch_label_batch(b->tab, b->counter, b->num_sms, b->ctas, st);
+  }
   if (e != cudaSuccess) return cuda_fail(e, "batch launch");
   return LBL_OK;
 }
@@ -967,6 +999,7 @@ int lbl_batch_free(lbl_batch b) {
   cudaDeviceSynchronize();
   cudaFree(b->part);
   cudaFree(b->counter);
+  cudaFree(b->pyr);
   delete b;
   return LBL_OK;
 }

@@ -91,6 +91,20 @@ struct QuadOffsets {
   int64_t at[kQuadLevels + 1];  // first pyramid word of each level
 };
 
+// One item of a batched pyramid launch: O of a frame -> that frame's pyramid.
+struct PyrItem {
+  const uint64_t *O;
+  uint64_t *pyr;
+  int64_t cells;
+  int64_t block0;  // first 256-cell block of this item in the launch
+  QuadOffsets off;
+};
+struct PyrTable {
+  PyrItem items[128];
+  int32_t n;
+  int64_t total;  // 256-cell blocks over all items
+};
+
 // One streamed row set: CSR rows over some gather base (cells, sectors or
 // pyramid words) with its warp partition.
 struct StreamRows {
@@ -212,6 +226,7 @@ cudaError_t launch_label_rows(const StreamRows &r, const uint64_t *base, int32_t
 cudaError_t launch_quad_pyramid(const Roadmap &rm, const uint64_t *O, cudaStream_t s);
 cudaError_t launch_label_quad(const Roadmap &rm, const uint64_t *O, int32_t P, uint64_t *L,
                                 const MonitorTables *mon, int depth, cudaStream_t s);
+cudaError_t launch_quad_pyramid_batch(const PyrTable &tab, cudaStream_t s);
 cudaError_t launch_quad_count(const int64_t *rowptr, const int32_t *colidx, int64_t E, int32_t *count,
                                 cudaStream_t s);
 cudaError_t launch_quad_fill(const int64_t *rowptr, const int32_t *colidx, int64_t E, QuadOffsets off,

@@ -85,6 +85,7 @@ struct Resident {
   lbl_roadmap rm = nullptr;
   lbl_monitor mon = nullptr;
   int32_t P = 0;
+  bool quad = false;        // label through the roadmap's quadtree form
   int64_t *part = nullptr;  // units + 1 entries
   int64_t units = 0;
 };
@@ -103,7 +104,7 @@ struct Request {
   int status = LBL_OK;
   size_t off = 0, bytes = 0;
   uint8_t *d_planes = nullptr;
-  uint64_t *d_O = nullptr, *d_L = nullptr, *d_next = nullptr;
+  uint64_t *d_O = nullptr, *d_pyr = nullptr, *d_L = nullptr, *d_next = nullptr;
   uint16_t *d_viol = nullptr;
 };
 
@@ -145,6 +146,7 @@ size_t request_bytes(const lbl_server_s &S, const Request &r) {
   const lbl::Roadmap &rm = *R.rm;
   size_t b = align_up(static_cast<size_t>(R.P) * lbl::grid_cells(r.world));
   b += align_up(static_cast<size_t>(rm.cells) * 8);
+  if (R.quad) b += align_up(static_cast<size_t>(rm.pyr_words) * 8);
   b += align_up(static_cast<size_t>(rm.E) * 8);
   if (R.mon) b += align_up(static_cast<size_t>(rm.E) * 8) + align_up(static_cast<size_t>(rm.E) * 2);
   return b;
@@ -158,6 +160,10 @@ void carve(lbl_server_s &S, Request &r) {
   p += align_up(static_cast<size_t>(R.P) * lbl::grid_cells(r.world));
   r.d_O = reinterpret_cast<uint64_t *>(p);
   p += align_up(static_cast<size_t>(rm.cells) * 8);
+  if (R.quad) {
+    r.d_pyr = reinterpret_cast<uint64_t *>(p);
+    p += align_up(static_cast<size_t>(rm.pyr_words) * 8);
+  }
   r.d_L = reinterpret_cast<uint64_t *>(p);
   p += align_up(static_cast<size_t>(rm.E) * 8);
   if (R.mon) {
@@ -172,7 +178,8 @@ void carve(lbl_server_s &S, Request &r) {
 cudaError_t launch_group(lbl_server_s &S, Lane &lane, std::vector<Request *> &group) {
   BatchTable tab{};
   FrameTable ftab{};
-  int64_t unit0 = 0, cell0 = 0;
+  lbl::PyrTable ptab{};
+  int64_t unit0 = 0, cell0 = 0, block0 = 0;
   cudaError_t e = cudaSuccess;
   for (size_t i = 0; i < group.size() && e == cudaSuccess; ++i) {
     Request &r = *group[i];
@@ -186,10 +193,21 @@ cudaError_t launch_group(lbl_server_s &S, Lane &lane, std::vector<Request *> &gr
     cell0 += rm.cells;
     BatchItem &it = tab.items[i];
     it = BatchItem{};
-    it.rowptr = rm.rowptr;
-    it.colidx = rm.colidx;
+    it.rowptr = R.quad ? rm.qd_rowptr : rm.rowptr;
+    it.colidx = R.quad ? rm.qd_idx : rm.colidx;
     it.part = R.part;
     it.O = r.d_O;
+    if (R.quad) {  // gather from the request's pyramid, built after its transform
+      lbl::PyrItem &pi = ptab.items[ptab.n++];
+      pi = lbl::PyrItem{};
+      pi.O = r.d_O;
+      pi.pyr = r.d_pyr;
+      pi.cells = rm.cells;
+      pi.block0 = block0;
+      pi.off = rm.qd_off;
+      block0 += (rm.cells + lbl::kThreads - 1) / lbl::kThreads;
+      it.O = r.d_pyr;
+    }
     it.L = r.d_L;
     it.next = r.d_next;
     it.viol = r.d_viol;
@@ -207,7 +225,14 @@ cudaError_t launch_group(lbl_server_s &S, Lane &lane, std::vector<Request *> &gr
   tab.n = ftab.n = static_cast<int32_t>(group.size());
   tab.total = unit0;
   ftab.total = cell0;
+  ptab.total = block0;
+  for (size_t i = 0; i < group.size(); ++i) {
+    const Resident &R = S.res[group[i]->res];
+    const int64_t ent = R.quad ? R.rm->n_qd : R.rm->nnz;
+    if (ent >= lbl::kNarrowLimit || R.rm->E >= lbl::kNarrowLimit) tab.wide = 1;
+  }
   if (e == cudaSuccess) e = lbl::launch_frame_batch(ftab, S.num_sms, lane.s);
+  if (e == cudaSuccess) e = lbl::launch_quad_pyramid_batch(ptab, lane.s);
   if (e == cudaSuccess) e = lbl::launch_label_batch(tab, lane.counter, S.num_sms, S.ctas, lane.s);
   for (size_t i = 0; i < group.size() && e == cudaSuccess; ++i) {
     Request &r = *group[i];
@@ -359,11 +384,13 @@ int lbl_server_create(int32_t n, const lbl_roadmap *rms, const int32_t *n_props,
     R.mon = mons ? mons[i] : nullptr;
     R.P = n_props[i];
     const lbl::Roadmap &rm = *R.rm;
-    const double cost = static_cast<double>(rm.nnz + lbl::kEdgeCost * rm.E);
+    R.quad = rm.has_qd && rm.E > 0;
+    const double cost = static_cast<double>((R.quad ? rm.n_qd : rm.nnz) + lbl::kEdgeCost * rm.E);
     R.units = rm.E > 0 ? std::min<int64_t>(rm.E, std::max<int64_t>(1, static_cast<int64_t>(std::ceil(cost / kUnitCost))))
                        : 0;
     e = cudaMalloc(reinterpret_cast<void **>(&R.part), sizeof(int64_t) * (R.units + 1));
-    if (e == cudaSuccess) e = lbl::launch_partition_into(rm.rowptr, rm.E, R.units, R.part, nullptr);
+    if (e == cudaSuccess)
+      e = lbl::launch_partition_into(R.quad ? rm.qd_rowptr : rm.rowptr, rm.E, R.units, R.part, nullptr);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&S->arena_base), static_cast<size_t>(mem_budget));

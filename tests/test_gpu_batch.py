@@ -1,6 +1,7 @@
 """Batched frames: one plan over roadmaps of uneven size, grid order, proposition
-count and monitor; every item's outputs equal the per-frame entry points' and
-the oracle's, also when the launch is captured in a CUDA graph and replayed."""
+count, monitor and form (CSR or quadtree, the same roadmap twice); every
+item's outputs equal the per-frame entry points' and the oracle's, also when
+the launch is captured in a CUDA graph and replayed."""
 import numpy as np
 import pytest
 
@@ -28,14 +29,18 @@ def _items():
     wl0.rowptr = np.zeros(1, np.int64)
     wl0.colidx = np.zeros(0, np.int32)
     items.append((wl0, 4, None))
+    items.append((items[0][0], 9, None))  # the first roadmap again
     return items
 
 
 def _run_batch(items, graph):
     rms, mons, frames, outs = [], [], [], []
     rng = np.random.default_rng(8)
-    for wl, P, mon in items:
-        rms.append(L.lbl_roadmap_upload(wl.agent, wl.rowptr, wl.colidx))
+    for k, (wl, P, mon) in enumerate(items):
+        if k == len(items) - 1 and wl is items[0][0]:
+            rms.append(rms[0])  # the same roadmap again, in its own frame
+        else:
+            rms.append(L.lbl_roadmap_upload(wl.agent, wl.rowptr, wl.colidx, flags=0 if k % 3 == 1 else L.LBL_UPLOAD_QUAD))
         mons.append(L.lbl_monitor_create(mon.n_states, mon.m, mon.relbits, mon.delta, mon.reject) if mon else None)
     b = L.lbl_batch_create(rms, [P for _, P, _ in items], mons)
     try:
@@ -104,7 +109,7 @@ def test_batch_matches_per_frame_calls_and_oracle(graph):
         for m in mons:
             if m:
                 L.lbl_monitor_free(m)
-        for rm in rms:
+        for rm in {id(r): r for r in rms}.values():
             L.lbl_roadmap_free(rm)
 
 

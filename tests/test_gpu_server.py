@@ -19,7 +19,8 @@ def resident():
     wls = [synth.make("plain", seed=21), synth.make("driving", seed=22, edges=15_000),
            synth.make("paper", seed=23, edges=20_000)]
     mons = [synth.random_monitor(rng, 5, 3, wls[0].P), None, None]
-    rms = [L.lbl_roadmap_upload(w.agent, w.rowptr, w.colidx) for w in wls]
+    flags = [L.LBL_UPLOAD_QUAD, 0, L.LBL_UPLOAD_QUAD]  # quadtree and CSR residents in one server
+    rms = [L.lbl_roadmap_upload(w.agent, w.rowptr, w.colidx, flags=f) for w, f in zip(wls, flags)]
     mhs = [L.lbl_monitor_create(m.n_states, m.m, m.relbits, m.delta, m.reject) if m else None for m in mons]
     yield wls, mons, rms, mhs
     for m in mhs:
