@@ -24,6 +24,13 @@ constexpr unsigned kFull = 0xffffffffu;
 
 __device__ __forceinline__ uint64_t or_xor(uint64_t v, int off) { return v | __shfl_xor_sync(kFull, v, off); }
 
+// OR of v over the whole warp, in every lane: one redux.sync per 32-bit half.
+__device__ __forceinline__ uint64_t warp_or(uint64_t v) {
+  const uint32_t lo = __reduce_or_sync(kFull, static_cast<uint32_t>(v));
+  const uint32_t hi = __reduce_or_sync(kFull, static_cast<uint32_t>(v >> 32));
+  return (static_cast<uint64_t>(hi) << 32) | lo;
+}
+
 struct EpiSmem {
   uint64_t T[256];
   uint16_t V[256];
@@ -175,9 +182,7 @@ __device__ __forceinline__ void stream_body(const int64_t *__restrict__ rowptr, 
   // lane keeps it; a complete window of 32 labels leaves in one coalesced
   // store, each lane running the epilogue for its own edge.
   auto flush = [&]() {
-    uint64_t r = acc;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) r = or_xor(r, off);
+    const uint64_t r = warp_or(acc);
     if (lane == static_cast<int>(cur - win)) mine = r;
     acc = 0;
     ++cur;
@@ -530,9 +535,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_label_tma(const int64_t *__rest
   uint64_t acc = 0;
 
   auto flush = [&]() {
-    uint64_t r = acc;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) r = or_xor(r, off);
+    uint64_t r = warp_or(acc);
     if (lane == 0) {
       r &= mask;
       L[cur] = r;
@@ -659,9 +662,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_label_async(const int64_t *__re
   uint64_t acc = 0;
 
   auto flush = [&]() {
-    uint64_t r = acc;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) r = or_xor(r, off);
+    uint64_t r = warp_or(acc);
     if (lane == 0) {
       r &= mask;
       L[cur] = r;
@@ -829,16 +830,14 @@ __global__ void __launch_bounds__(kThreads) k_label_bt(const int64_t *__restrict
         uint64_t r = 0;
 #pragma unroll
         for (int t = 0; t < T; ++t) r |= static_cast<uint64_t>(hit[t]) << (pl + t * LPB);
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) r = or_xor(r, off);
+        r = warp_or(r);
         if ((r & mask) == mask) break;  // warp-uniform: r is the same in every lane
       }
     }
     uint64_t word = 0;
 #pragma unroll
     for (int t = 0; t < T; ++t) word |= static_cast<uint64_t>(hit[t]) << (pl + t * LPB);
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) word = or_xor(word, off);
+    word = warp_or(word);
     if (lane == 0) {
       word &= mask;
       L[e] = word;
