@@ -409,7 +409,7 @@ int roadmap_finish(lbl_roadmap_s *rm, uint32_t flags, cudaStream_t st) {
         (e = launch_quad_fill(rm->rowptr, rm->colidx, n_edges, rm->qd_off, rm->qd_rowptr, rm->qd_idx, st)) !=
             cudaSuccess)
       return fail(cuda_fail(e, "roadmap: quadtree form"));
-    rm->qd_part_ctas = stream_ctas_per_sm(8);
+    rm->qd_part_ctas = stream_ctas_per_sm(kQuadDepth);
     const int64_t W = static_cast<int64_t>(rm->num_sms) * rm->qd_part_ctas * (kThreads / 32);
     if ((e = launch_partition_into(rm->qd_rowptr, n_edges, W, rm->qd_part, st)) != cudaSuccess)
       return fail(cuda_fail(e, "roadmap: quadtree partition"));
@@ -724,7 +724,7 @@ static int label_impl(lbl_roadmap rm, const uint64_t *d_O, int32_t n_props, uint
     }
     e = launch_label_sector(*rm, d_O, n_props, d_L, mon ? &t : nullptr, depth, st);
   } else if (algo == LBL_ALGO_QUAD) {
-    const int depth = cfg ? cfg->depth : 0;
+    const int depth = (cfg && cfg->depth) ? cfg->depth : kQuadDepth;
     if (rm->E > 0) {
       const int occ = stream_ctas_per_sm(depth);
       const int want = ctas > 0 ? std::min(ctas, occ) : occ;

@@ -87,6 +87,10 @@ struct FrameTable {
 
 // Levels of the quadtree form: blocks of up to 4^4 = 256 cells.
 constexpr int kQuadLevels = 4;
+// Default register pipeline depth of the quadtree stream (groups of 32 entries
+// in flight per warp): its rows are short, so deeper pipelines pay (measured
+// on all four single-frame workloads).
+constexpr int kQuadDepth = 12;
 struct QuadOffsets {
   int64_t at[kQuadLevels + 1];  // first pyramid word of each level
 };
