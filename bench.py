@@ -341,15 +341,18 @@ def main():
         flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     torch.cuda.synchronize()
 
-    def step():
+    def transform():
         L.lbl_frame_transform(wl.world, d_planes, P, wl.pose, wl.agent, d_O, stream=stream)
+
+    def step():
+        transform()
         L.lbl_label(rm, d_O, P, d_L, mon, d_next, d_viol, cfg, stream=stream)
 
     # AUTO: measure every labeling variant on this frame once (untimed) and
     # let the roadmap keep the fastest
     tuned = None
     if args.algo == "auto":
-        L.lbl_frame_transform(wl.world, d_planes, P, wl.pose, wl.agent, d_O, stream=stream)
+        transform()
         tuned = L.lbl_roadmap_autotune(rm, d_O, P, d_L, mon, d_next, d_viol, reps=5, stream=stream)
         used = {L.LBL_ALGO_BITTILE: "bittile", L.LBL_ALGO_SECTOR: "sector",
                 L.LBL_ALGO_QUAD: "quad"}.get(tuned["algo"], "csr")
@@ -374,7 +377,7 @@ def main():
         with torch.cuda.stream(stream):
             flush.fill_(i & 255)
         ev[i][0].record(stream)
-        L.lbl_frame_transform(wl.world, d_planes, P, wl.pose, wl.agent, d_O, stream=stream)
+        transform()
         ev[i][1].record(stream)
         L.lbl_label(rm, d_O, P, d_L, mon, d_next, d_viol, cfg, stream=stream)
         ev[i][2].record(stream)
@@ -484,6 +487,9 @@ def run_batched(args, rank, world, local, dist, torch, L):
         fr.append(dict(world=f.world, d_planes=d_pl, pose=f.pose,
                        d_O=torch.empty(f.agent.cells, dtype=torch.uint64, device="cuda"),
                        d_L=torch.empty(f.n_edges, dtype=torch.uint64, device="cuda")))
+
+    def frame_transform(f, d):
+        L.lbl_frame_transform(f.world, d["d_planes"], f.P, f.pose, f.agent, d["d_O"], stream=stream)
     b = L.lbl_batch_create(rms, [f.P for f in frames])
     L.lbl_batch_set_frames(b, fr)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -491,7 +497,7 @@ def run_batched(args, rank, world, local, dist, torch, L):
 
     def plain_step():
         for f, r, d in zip(frames, rms, fr):
-            L.lbl_frame_transform(f.world, d["d_planes"], f.P, f.pose, f.agent, d["d_O"], stream=stream)
+            frame_transform(f, d)
             L.lbl_label(r, d["d_O"], f.P, d["d_L"], stream=stream)
 
     # correctness: batched == frame by frame, bit for bit
@@ -536,8 +542,7 @@ def run_batched(args, rank, world, local, dist, torch, L):
     with torch.cuda.stream(stream):
         b_tr = timed(lambda: L.lbl_batch_launch(b, L.LBL_STAGE_TRANSFORM, stream=stream), n_br)
         b_lb = timed(lambda: L.lbl_batch_launch(b, L.LBL_STAGE_LABEL, stream=stream), n_br)
-    p_tr = timed(lambda: [L.lbl_frame_transform(f.world, d["d_planes"], f.P, f.pose, f.agent, d["d_O"],
-                                                 stream=stream) for f, d in zip(frames, fr)], n_br)
+    p_tr = timed(lambda: [frame_transform(f, d) for f, d in zip(frames, fr)], n_br)
     p_lb = timed(lambda: [L.lbl_label(r, d["d_O"], f.P, d["d_L"], stream=stream)
                           for f, r, d in zip(frames, rms, fr)], n_br)
     total_b = max_over_ranks(float(batched_ms.sum()), dist, "cuda")
@@ -549,6 +554,7 @@ def run_batched(args, rank, world, local, dist, torch, L):
     bytes_step = sum(4 * n + 16 * f.n_edges + 8 * f.agent.cells + f.P * f.world.cells
                      + (16 * pyramid_words(f.agent.cells) if quad else 0) for f, n in zip(frames, entries))
     launches = 3 if quad else 2  # transform, (pyramid,) label
+    plain_launches = len(frames) * launches
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
     achieved = bytes_step / (total_b / args.steps / 1e3) / 1e9
@@ -563,7 +569,7 @@ def run_batched(args, rank, world, local, dist, torch, L):
                        "l2": "flushed before every step (256 MiB write)", "parallelism": f"replicas x{world}"},
             "batched_vs_plain": {"plain_value": plain_value, "plain_ms_per_step": total_p / args.steps,
                                  "speedup": total_p / total_b, "bit_exact_match": bool(match),
-                                 "plain_launches_per_step": launches * len(frames),
+                                 "plain_launches_per_step": plain_launches,
                                  "batched_launches_per_step": launches,
                                  "stage_ms": {"batched_transform": float(np.median(b_tr)),
                                               "batched_label": float(np.median(b_lb)),

@@ -228,6 +228,28 @@ int lbl_roadmap_info(lbl_roadmap rm, int64_t *n_edges, int64_t *nnz, int64_t *n_
 int lbl_frame_transform(const lbl_grid *world, const uint8_t *d_planes, int32_t n_props, lbl_pose pose,
                         const lbl_grid *agent, uint64_t *d_O, lbl_stream s);
 
+/*
+ * lbl_pack_planes — the world planes as one word per world cell: bit p of
+ * d_words[c] is set iff d_planes[p][c] != 0 (c in the world grid's row-major
+ * cell order, time slabs outermost; the same cells lbl_frame_transform reads).
+ *   d_planes  uint8[n_props][cells of world]   (device)
+ *   d_words   uint64[cells of world]           (device, caller-owned; bits >= n_props zero)
+ * One coalesced pass over the planes; with lbl_frame_transform_words it gives
+ * exactly lbl_frame_transform's O.  LBL_EINVAL on a bad grid, n_props outside
+ * 0..64 or a NULL buffer.  Asynchronous on `s`.
+ */
+int lbl_pack_planes(const lbl_grid *world, const uint8_t *d_planes, int32_t n_props, uint64_t *d_words,
+                    lbl_stream s);
+
+/*
+ * lbl_frame_transform_words — lbl_frame_transform (Sec. 5, eq. 13) reading the
+ * packed words of lbl_pack_planes instead of the planes: one 8-byte gather per
+ * agent cell instead of n_props byte gathers.  Word bits >= n_props are
+ * ignored.  Same arguments, layouts and errors as lbl_frame_transform.
+ */
+int lbl_frame_transform_words(const lbl_grid *world, const uint64_t *d_words, int32_t n_props, lbl_pose pose,
+                              const lbl_grid *agent, uint64_t *d_O, lbl_stream s);
+
 /* --------------------------------------------------------------- monitor */
 
 /*

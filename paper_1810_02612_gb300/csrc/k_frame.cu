@@ -44,7 +44,9 @@ __device__ __forceinline__ uint64_t frame_word(const FrameItem &f, int64_t idx) 
   const int64_t wy = (f.A10 * ix + f.A11 * iy + f.B1) >> 32;
   const int64_t wt = f.wd > 1 ? ((f.At * it + f.Bt) >> 32) : 0;  // a 2-D world is static in time
   uint64_t word = 0;
-  if (wx >= 0 && wx < f.ww && wy >= 0 && wy < f.wh && wt >= 0 && wt < f.wd) {
+  if (wx >= 0 && wx < f.ww && wy >= 0 && wy < f.wh && wt >= 0 && wt < f.wd && f.words) {
+    word = __ldg(f.words + (wt * f.wh + wy) * f.ww + wx) & f.wmask;
+  } else if (wx >= 0 && wx < f.ww && wy >= 0 && wy < f.wh && wt >= 0 && wt < f.wd) {
     const uint8_t *p = f.planes + (wt * f.wh + wy) * f.ww + wx;
     int q = 0;
     for (; q + 8 <= f.P; q += 8) {
@@ -88,6 +90,60 @@ __global__ void __launch_bounds__(256) k_frame_batch(const __grid_constant__ Fra
   }
 }
 
+// Packing: lane quad (4 consecutive lanes) per group of four world cells;
+// lane q of the quad reads planes q, q+4, q+8, ... of the group (4 bytes at a
+// time when the planes are 4-byte aligned and the cell count divisible by 4),
+// so all of a lane's loads are in flight at once; the quad ORs its partial
+// words by two shuffles and lane j stores the word of cell 4g + j.
+// `t` is the global lane index; lanes past the last group only shuffle.
+__device__ __forceinline__ void pack_quad(const PackItem &it, int64_t t, bool valid) {
+  const int q = static_cast<int>(t & 3);
+  const int64_t g = t >> 2;
+  const int64_t c0 = 4 * g;
+  uint64_t w[4] = {0, 0, 0, 0};
+  if (valid) {
+    const bool vec = ((reinterpret_cast<uintptr_t>(it.planes) | static_cast<uintptr_t>(it.cells)) & 3u) == 0;
+    uint32_t v[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const int p = q + 4 * i;
+      uint32_t x = 0;
+      if (p < it.P) {
+        const uint8_t *pl = it.planes + p * it.cells;
+        if (vec) {
+          x = __ldg(reinterpret_cast<const uint32_t *>(pl + c0));
+        } else {
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (c0 + j < it.cells) x |= static_cast<uint32_t>(__ldg(pl + c0 + j)) << (8 * j);
+        }
+      }
+      v[i] = x;
+    }
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const int p = q + 4 * i;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) w[j] |= static_cast<uint64_t>((v[i] >> (8 * j)) & 0xFFu ? 1u : 0u) << p;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    w[j] |= __shfl_xor_sync(0xffffffffu, w[j], 1);
+    w[j] |= __shfl_xor_sync(0xffffffffu, w[j], 2);
+  }
+  if (valid && c0 + q < it.cells) it.words[c0 + q] = q == 0 ? w[0] : q == 1 ? w[1] : q == 2 ? w[2] : w[3];
+}
+
+__global__ void __launch_bounds__(256) k_pack_planes(const __grid_constant__ PackItem it) {
+  const int64_t lanes = 4 * ((it.cells + 3) / 4);
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  // the loop bound is tested on the warp's first lane, so whole warps iterate together
+  for (int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; t - (threadIdx.x & 31) < lanes;
+       t += stride)
+    pack_quad(it, t, t < lanes);
+}
+
 // letter = sum_j bit(L, rel[j]) << j ; next/viol from the per-letter tables.
 __global__ void __launch_bounds__(256) k_monitor_step(MonitorTables mon, const uint64_t *__restrict__ L, int64_t n) {
   __shared__ uint64_t sT[256];
@@ -117,6 +173,16 @@ cudaError_t launch_frame_transform(const FrameItem &f, int num_sms, cudaStream_t
   const int64_t cap = static_cast<int64_t>(num_sms) * 8;
   if (blocks > cap) blocks = cap;
   k_frame_transform<<<static_cast<unsigned>(blocks), 256, 0, s>>>(f);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_planes(const PackItem &it, int num_sms, cudaStream_t s) {
+  const int64_t lanes = 4 * ((it.cells + 3) / 4);
+  if (lanes == 0) return cudaSuccess;
+  int64_t blocks = (lanes + 255) / 256;
+  const int64_t cap = static_cast<int64_t>(num_sms) * 8;
+  if (blocks > cap) blocks = cap;
+  k_pack_planes<<<static_cast<unsigned>(blocks), 256, 0, s>>>(it);
   return cudaGetLastError();
 }
 

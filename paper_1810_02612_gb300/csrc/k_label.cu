@@ -338,8 +338,8 @@ __global__ void __launch_bounds__(kThreads, stream_min_blocks<2 * U>()) k_label_
 // global counter (zeroed before the launch), so the load stays balanced and
 // only the few items being worked on keep their O words hot in L2.  Monitor
 // tables, if any, are read through L1.
-template <typename Off>
-__global__ void __launch_bounds__(kThreads, 4) k_label_batch(const __grid_constant__ BatchTable tab,
+template <int U, typename Off>
+__global__ void __launch_bounds__(kThreads, stream_min_blocks<U>()) k_label_batch(const __grid_constant__ BatchTable tab,
                                                           unsigned long long *__restrict__ next_unit) {
   const uint64_t pol = evict_first_policy();
   const int lane = threadIdx.x & 31;
@@ -363,7 +363,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_label_batch(const __grid_consta
     const int64_t *part = it->part;
     const int64_t e_beg = __ldg(part + lu), e_end = __ldg(part + lu + 1);
     if (e_beg >= e_end) continue;
-    stream_range<8, Off>(it->rowptr, it->colidx, CsrGather{it->O}, e_beg, e_end, pol, lane,
+    stream_range<U, Off>(it->rowptr, it->colidx, CsrGather{it->O}, e_beg, e_end, pol, lane,
                          [&](int64_t e, uint64_t r) {
       r &= it->mask;
       it->L[e] = r;
@@ -736,17 +736,20 @@ __global__ void __launch_bounds__(kThreads, 4) k_label_async(const int64_t *__re
 }
 
 // Edge partition of the streaming kernel: part[w] = first edge e with
-// rowptr[e] + edge_cost * e >= w * total / W  (total = nnz + edge_cost * E).
+// (rowptr[e] - rowptr[0]) + edge_cost * e >= w * total / W
+// (total = rowptr[E] - rowptr[0] + edge_cost * E; rowptr may be a slice of a
+// roadmap's row pointer, so it need not start at 0).
 __global__ void k_partition(const int64_t *__restrict__ rowptr, int64_t E, int64_t W, int64_t edge_cost,
                             int64_t *__restrict__ part) {
   const int64_t w = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (w > W) return;
-  const int64_t total = rowptr[E] + edge_cost * E;
+  const int64_t r0 = rowptr[0];
+  const int64_t total = rowptr[E] - r0 + edge_cost * E;
   const int64_t target = w == W ? total : total / W * w + (total % W) * w / W;
   int64_t lo = 0, hi = E;
   while (lo < hi) {
     const int64_t mid = lo + (hi - lo) / 2;
-    if (rowptr[mid] + edge_cost * mid < target)
+    if (rowptr[mid] - r0 + edge_cost * mid < target)
       lo = mid + 1;
     else
       hi = mid;
@@ -947,9 +950,10 @@ cudaError_t launch_label_sector(const Roadmap &rm, const uint64_t *O, int32_t P,
   return cudaGetLastError();
 }
 
-int batch_ctas_per_sm() {
-  static const int occ = std::min(occupancy(k_label_batch<int32_t>), occupancy(k_label_batch<int64_t>));
-  return occ;
+int batch_ctas_per_sm(int depth) {
+  static const int o8 = std::min(occupancy(k_label_batch<8, int32_t>), occupancy(k_label_batch<8, int64_t>));
+  static const int o12 = occupancy(k_label_batch<12, int32_t>);
+  return depth == 12 ? o12 : o8;
 }
 
 cudaError_t launch_label_batch(const BatchTable &tab, unsigned long long *counter, int num_sms, int ctas_per_sm,
@@ -957,10 +961,13 @@ cudaError_t launch_label_batch(const BatchTable &tab, unsigned long long *counte
   if (tab.total == 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
+  const unsigned grid = static_cast<unsigned>(num_sms * ctas_per_sm);
   if (tab.wide)
-    k_label_batch<int64_t><<<static_cast<unsigned>(num_sms * ctas_per_sm), kThreads, 0, s>>>(tab, counter);
+    k_label_batch<8, int64_t><<<grid, kThreads, 0, s>>>(tab, counter);
+  else if (tab.depth == 12)
+    k_label_batch<12, int32_t><<<grid, kThreads, 0, s>>>(tab, counter);
   else
-    k_label_batch<int32_t><<<static_cast<unsigned>(num_sms * ctas_per_sm), kThreads, 0, s>>>(tab, counter);
+    k_label_batch<8, int32_t><<<grid, kThreads, 0, s>>>(tab, counter);
   return cudaGetLastError();
 }
 

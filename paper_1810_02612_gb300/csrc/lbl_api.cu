@@ -219,6 +219,17 @@ struct lbl_session_s {
   uint8_t *planes = nullptr;
   uint64_t *O = nullptr, *L = nullptr, *next = nullptr;
   uint16_t *viol = nullptr;
+  // Chunked labeling: the edges in kSessionChunks ranges, each labeled by the
+  // whole grid; a range's results go to the host on `cs` while the next range
+  // is labeled.  Used with the default form (quadtree, else streaming CSR).
+  bool chunked = false;
+  bool quad = false;
+  int depth = 8, ctas = 0;
+  int64_t edge0[lbl::kSessionChunks + 1] = {0};
+  int64_t *cpart = nullptr;  // kSessionChunks partitions of warps + 1 entries
+  int64_t warps = 0;
+  cudaStream_t cs = nullptr;
+  cudaEvent_t ev[lbl::kSessionChunks + 1] = {nullptr};
 };
 
 namespace lbl {
@@ -550,6 +561,53 @@ int lbl_frame_transform(const lbl_grid *world, const uint8_t *d_planes, int32_t 
   return LBL_OK;
 }
 
+int lbl_pack_planes(const lbl_grid *world, const uint8_t *d_planes, int32_t n_props, uint64_t *d_words,
+                    lbl_stream s) {
+  g_err.clear();
+  if (!valid_grid(world, "pack planes (world)", false)) return LBL_EINVAL;
+  if (n_props < 0 || n_props > 64) {
+    set_error("pack planes: n_props = %d outside 0..64", n_props);
+    return LBL_EINVAL;
+  }
+  if (!d_words || (n_props > 0 && !d_planes)) {
+    set_error("pack planes: NULL buffer");
+    return LBL_EINVAL;
+  }
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "pack planes: cudaGetDevice");
+  PackItem it{d_planes, d_words, grid_cells(*world), n_props};
+  e = launch_pack_planes(it, device_sms(dev), reinterpret_cast<cudaStream_t>(s));
+  if (e != cudaSuccess) return cuda_fail(e, "pack planes: launch");
+  return LBL_OK;
+}
+
+int lbl_frame_transform_words(const lbl_grid *world, const uint64_t *d_words, int32_t n_props, lbl_pose pose,
+                              const lbl_grid *agent, uint64_t *d_O, lbl_stream s) {
+  g_err.clear();
+  if (!valid_grid(world, "frame transform (world)", false) || !valid_grid(agent, "frame transform (agent)", true))
+    return LBL_EINVAL;
+  if (n_props < 0 || n_props > 64) {
+    set_error("frame transform: n_props = %d outside 0..64", n_props);
+    return LBL_EINVAL;
+  }
+  if (!d_O || !d_words) {
+    set_error("frame transform: NULL buffer");
+    return LBL_EINVAL;
+  }
+  FrameMap m;
+  if (!frame_map(*world, *agent, pose, &m)) return LBL_EINVAL;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "frame transform: cudaGetDevice");
+  FrameItem f = frame_item(m, *world, *agent, nullptr, n_props, d_O, 0);
+  f.words = d_words;
+  f.wmask = n_props >= 64 ? ~0ull : ((1ull << n_props) - 1ull);
+  e = launch_frame_transform(f, device_sms(dev), reinterpret_cast<cudaStream_t>(s));
+  if (e != cudaSuccess) return cuda_fail(e, "frame transform: launch");
+  return LBL_OK;
+}
+
 int lbl_monitor_create(int32_t n_states, int32_t m, const uint8_t *relbits, const uint8_t *delta, int32_t reject,
                        lbl_monitor *out) {
   g_err.clear();
@@ -860,7 +918,10 @@ int lbl_batch_create(int32_t n, const lbl_roadmap *rms, const int32_t *n_props, 
   // The persistent grid's warps take work units from a counter; items are
   // cut into units of about equal cost (nonzeros + kEdgeCost per edge),
   // kUnitsPerWarp per warp overall, at least one per item with edges.
-  const int occ = batch_ctas_per_sm();
+  bool all_quad = true;
+  for (int i = 0; i < n; ++i) all_quad = all_quad && (rms[i]->has_qd || rms[i]->E == 0);
+  b->tab.depth = all_quad ? kQuadDepth : 8;
+  const int occ = batch_ctas_per_sm(b->tab.depth);
   const int ctas = ctas_per_sm > 0 ? std::min<int>(ctas_per_sm, occ) : occ;
   b->ctas = ctas;
   constexpr int64_t kUnitsPerWarp = 8;
@@ -1042,13 +1103,37 @@ int lbl_session_create(lbl_roadmap rm, const lbl_grid *world, int32_t n_props, l
   if (e == cudaSuccess) e = dev_alloc(&ss->L, static_cast<size_t>(rm->E), nullptr);
   if (e == cudaSuccess && mon) e = dev_alloc(&ss->next, static_cast<size_t>(rm->E), nullptr);
   if (e == cudaSuccess && mon) e = dev_alloc(&ss->viol, static_cast<size_t>(rm->E), nullptr);
+  // Chunked labeling when the configuration resolves to a register-pipelined
+  // stream (quadtree, or CSR without lane groups, early exit or copy rings) on
+  // a roadmap big enough to pay.
+  lbl_config c{};
+  if (cfg) c = *cfg;
+  if (c.algo == LBL_ALGO_AUTO && rm->tuned_valid[n_props]) c = rm->tuned[n_props];
+  if (c.algo == LBL_ALGO_AUTO)  // as lbl_label resolves it
+    c.algo = rm->has_qd ? LBL_ALGO_QUAD : (rm->has_bt && n_props <= 8) ? LBL_ALGO_BITTILE : LBL_ALGO_CSR;
+  const bool stream_form = (c.algo == LBL_ALGO_QUAD && rm->has_qd) ||
+                           (c.algo == LBL_ALGO_CSR && c.lanes_per_edge == 0 && c.early_exit <= 0 &&
+                            (c.pipeline == 0 || c.pipeline == LBL_PIPE_REGISTERS));
+  if (e == cudaSuccess && stream_form && rm->E >= kSessionChunkMinEdges) {
+    ss->chunked = true;
+    ss->quad = c.algo == LBL_ALGO_QUAD;
+    ss->depth = c.depth ? c.depth : (ss->quad ? kQuadDepth : 8);
+    const int occ = stream_ctas_per_sm(ss->depth);
+    ss->ctas = c.ctas_per_sm > 0 ? std::min(c.ctas_per_sm, occ) : occ;
+    ss->warps = static_cast<int64_t>(rm->num_sms) * ss->ctas * (kThreads / 32);
+    for (int c = 0; c <= kSessionChunks; ++c) ss->edge0[c] = rm->E * c / kSessionChunks;
+    const int64_t *rows = ss->quad ? rm->qd_rowptr : rm->rowptr;
+    e = dev_alloc(&ss->cpart, static_cast<size_t>(kSessionChunks * (ss->warps + 1)), nullptr);
+    for (int c = 0; c < kSessionChunks && e == cudaSuccess; ++c)
+      e = launch_partition_into(rows + ss->edge0[c], ss->edge0[c + 1] - ss->edge0[c], ss->warps,
+                                ss->cpart + c * (ss->warps + 1), nullptr);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ss->cs, cudaStreamNonBlocking);
+    for (int c = 0; c <= kSessionChunks && e == cudaSuccess; ++c)
+      e = cudaEventCreateWithFlags(&ss->ev[c], cudaEventDisableTiming);
+  }
   if (e != cudaSuccess) {
-    cudaFree(ss->planes);
-    cudaFree(ss->O);
-    cudaFree(ss->L);
-    cudaFree(ss->next);
-    cudaFree(ss->viol);
-    delete ss;
+    lbl_session_free(ss);
     return cuda_fail(e, "session create");
   }
   *out = ss;
@@ -1075,6 +1160,35 @@ int lbl_session_run(lbl_session ss, const uint8_t *h_planes, lbl_pose pose, uint
   if (e != cudaSuccess) return cuda_fail(e, "session run: copy planes");
   int rc = lbl_frame_transform(&ss->world, ss->planes, ss->P, pose, &rm.agent, ss->O, s);
   if (rc != LBL_OK) return rc;
+  if (ss->chunked) {
+    const uint64_t *base = ss->O;
+    if (ss->quad) {
+      if ((e = launch_quad_pyramid(rm, ss->O, st)) != cudaSuccess) return cuda_fail(e, "session run: pyramid");
+      base = rm.pyr;
+    }
+    for (int c = 0; c < kSessionChunks; ++c) {
+      const int64_t e0 = ss->edge0[c], n = ss->edge0[c + 1] - e0;
+      if (n == 0) continue;
+      const StreamRows r{(ss->quad ? rm.qd_rowptr : rm.rowptr) + e0, ss->quad ? rm.qd_idx : rm.colidx,
+                         ss->cpart + c * (ss->warps + 1), ss->ctas, n, ss->quad ? rm.n_qd : rm.nnz};
+      MonitorTables t{};
+      if (ss->mon) t = tables_of(*ss->mon, ss->next + e0, ss->viol + e0);
+      e = launch_label_rows(r, base, ss->P, ss->L + e0, ss->mon ? &t : nullptr, ss->depth, rm.num_sms, st);
+      if (e == cudaSuccess) e = cudaEventRecord(ss->ev[c], st);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(ss->cs, ss->ev[c], 0);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(h_L + e0, ss->L + e0, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost, ss->cs);
+      if (e == cudaSuccess && ss->mon && h_next)
+        e = cudaMemcpyAsync(h_next + e0, ss->next + e0, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost, ss->cs);
+      if (e == cudaSuccess && ss->mon && h_viol)
+        e = cudaMemcpyAsync(h_viol + e0, ss->viol + e0, sizeof(uint16_t) * n, cudaMemcpyDeviceToHost, ss->cs);
+      if (e != cudaSuccess) return cuda_fail(e, "session run: chunk");
+    }
+    // the caller's stream sees the results once every copy has landed
+    if ((e = cudaEventRecord(ss->ev[kSessionChunks], ss->cs)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(st, ss->ev[kSessionChunks], 0)) != cudaSuccess)
+      return cuda_fail(e, "session run: join");
+    return LBL_OK;
+  }
   rc = label_impl(ss->rm, ss->O, ss->P, ss->L, ss->mon, ss->next, ss->viol, ss->has_cfg ? &ss->cfg : nullptr, st);
   if (rc != LBL_OK) return rc;
   if (rm.E > 0) {
@@ -1097,6 +1211,10 @@ int lbl_session_free(lbl_session ss) {
   cudaFree(ss->L);
   cudaFree(ss->next);
   cudaFree(ss->viol);
+  cudaFree(ss->cpart);
+  if (ss->cs) cudaStreamDestroy(ss->cs);
+  for (cudaEvent_t ev : ss->ev)
+    if (ev) cudaEventDestroy(ev);
   delete ss;
   return LBL_OK;
 }

@@ -69,6 +69,16 @@ struct FrameItem {
   int64_t plane_cells;  // ww * wh * wd
   int64_t cell0;        // first global cell of this frame
   int32_t ww, wh, wd, aw, ah, ad, P, order;
+  const uint64_t *words;  // packed world words (bit p = plane p), or NULL: read the planes
+  uint64_t wmask;         // 2^P - 1, applied to packed words
+};
+
+// Packing world planes into one word per world cell (bit p = plane p != 0).
+struct PackItem {
+  const uint8_t *planes;
+  uint64_t *words;
+  int64_t cells;  // world cells (w * h * d)
+  int32_t P;
 };
 
 // Batched launches take their whole item table as one kernel parameter.
@@ -77,6 +87,7 @@ struct BatchTable {
   BatchItem items[kMaxBatch];
   int32_t n;
   int32_t wide;   // some item has 2^31 - 4096 or more nonzeros or edges
+  int32_t depth;  // groups in flight per warp: 12 when every item streams quadtree rows, else 8
   int64_t total;  // work units
 };
 struct FrameTable {
@@ -91,6 +102,10 @@ constexpr int kQuadLevels = 4;
 // in flight per warp): its rows are short, so deeper pipelines pay (measured
 // on all four single-frame workloads).
 constexpr int kQuadDepth = 12;
+// Host-buffer sessions label big roadmaps in this many edge ranges and copy
+// each range's results to the host while the next one is labeled.
+constexpr int kSessionChunks = 4;
+constexpr int64_t kSessionChunkMinEdges = 1 << 16;
 struct QuadOffsets {
   int64_t at[kQuadLevels + 1];  // first pyramid word of each level
 };
@@ -208,6 +223,7 @@ FrameItem frame_item(const FrameMap &m, const lbl_grid &W, const lbl_grid &A, co
                      uint64_t *O, int64_t cell0);
 
 cudaError_t launch_frame_transform(const FrameItem &f, int num_sms, cudaStream_t s);
+cudaError_t launch_pack_planes(const PackItem &it, int num_sms, cudaStream_t s);
 
 cudaError_t launch_label_csr(const Roadmap &rm, const uint64_t *O, int32_t P, uint64_t *L, const MonitorTables *mon,
                              int lanes_per_edge, bool early_exit, int ctas_per_sm, cudaStream_t s);
@@ -249,7 +265,7 @@ cudaError_t launch_sector_count(const int64_t *rowptr, const int32_t *colidx, in
                                 cudaStream_t s);
 cudaError_t launch_sector_fill(const int64_t *rowptr, const int32_t *colidx, int64_t E, const int64_t *srow,
                                int32_t *sec, cudaStream_t s);
-int batch_ctas_per_sm();
+int batch_ctas_per_sm(int depth);
 cudaError_t launch_label_batch(const BatchTable &tab, unsigned long long *counter, int num_sms, int ctas_per_sm,
                                cudaStream_t s);
 cudaError_t launch_partition_into(const int64_t *rowptr, int64_t E, int64_t W, int64_t *part, cudaStream_t s);

@@ -122,6 +122,7 @@ struct lbl_server_s {
   int device = 0;
   int num_sms = 1;
   int ctas = 1;
+  int depth = 8;  // groups in flight per warp of the label launch (12 when every resident is quadtree)
   int max_batch = lbl::kMaxBatch;
   std::vector<Resident> res;
   uint8_t *arena_base = nullptr;
@@ -223,6 +224,7 @@ cudaError_t launch_group(lbl_server_s &S, Lane &lane, std::vector<Request *> &gr
     unit0 += it.warps;
   }
   tab.n = ftab.n = static_cast<int32_t>(group.size());
+  tab.depth = S.depth;
   tab.total = unit0;
   ftab.total = cell0;
   ptab.total = block0;
@@ -362,7 +364,7 @@ int lbl_server_create(int32_t n, const lbl_roadmap *rms, const int32_t *n_props,
   }
   S->device = dev;
   S->num_sms = rms[0]->num_sms;
-  S->ctas = lbl::batch_ctas_per_sm();
+  S->ctas = lbl::batch_ctas_per_sm(8);
   S->max_batch = max_batch;
   S->res.resize(n);
   // fixed work-unit size: 32k nonzero-equivalents (a unit takes a warp ~10 us)
@@ -393,6 +395,10 @@ int lbl_server_create(int32_t n, const lbl_roadmap *rms, const int32_t *n_props,
       e = lbl::launch_partition_into(R.quad ? rm.qd_rowptr : rm.rowptr, rm.E, R.units, R.part, nullptr);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
+  bool all_quad = true;
+  for (const Resident &R : S->res) all_quad = all_quad && (R.quad || R.rm->E == 0);
+  S->depth = all_quad ? lbl::kQuadDepth : 8;
+  S->ctas = lbl::batch_ctas_per_sm(S->depth);
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&S->arena_base), static_cast<size_t>(mem_budget));
   if (e != cudaSuccess) return cleanup(lbl::cuda_fail(e, "server create: resident state"));
   S->arena.init(static_cast<size_t>(mem_budget));

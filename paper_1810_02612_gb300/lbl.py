@@ -49,7 +49,7 @@ EXPORTS = (
     "lbl_last_error", "lbl_version",
     "lbl_roadmap_upload", "lbl_roadmap_rasterize", "lbl_roadmap_rows", "lbl_roadmap_free", "lbl_roadmap_info",
     "lbl_roadmap_status",
-    "lbl_frame_transform",
+    "lbl_frame_transform", "lbl_pack_planes", "lbl_frame_transform_words",
     "lbl_monitor_create", "lbl_monitor_free", "lbl_monitor_step",
     "lbl_label", "lbl_label_blocks_noalloc", "lbl_roadmap_autotune",
     "lbl_session_create", "lbl_session_run", "lbl_session_free",
@@ -115,6 +115,8 @@ def load(build_if_needed: bool = True):
         "lbl_roadmap_info": (ctypes.c_int, [p, p, p, p, p, p, p]),
         "lbl_roadmap_status": (ctypes.c_int, [p, p]),
         "lbl_frame_transform": (ctypes.c_int, [G, p, i32, lbl_pose, G, p, p]),
+        "lbl_pack_planes": (ctypes.c_int, [G, p, i32, p, p]),
+        "lbl_frame_transform_words": (ctypes.c_int, [G, p, i32, lbl_pose, G, p, p]),
         "lbl_monitor_create": (ctypes.c_int, [i32, i32, p, p, i32, ctypes.POINTER(p)]),
         "lbl_monitor_free": (ctypes.c_int, [p]),
         "lbl_monitor_step": (ctypes.c_int, [p, p, i64, p, p, p]),
@@ -285,6 +287,19 @@ def lbl_frame_transform(world, d_planes, n_props: int, pose, agent, d_O, stream=
     w, a = _grid(world), _grid(agent)
     _check(load().lbl_frame_transform(ctypes.byref(w), _dev(d_planes, "uint8", "planes"), int(n_props),
                                       _pose(pose), ctypes.byref(a), _dev(d_O, "uint64", "O"), _stream(stream)))
+
+
+def lbl_pack_planes(world, d_planes, n_props: int, d_words, stream=None) -> None:
+    w = _grid(world)
+    _check(load().lbl_pack_planes(ctypes.byref(w), _dev(d_planes, "uint8", "planes"), int(n_props),
+                                  _dev(d_words, "uint64", "words"), _stream(stream)))
+
+
+def lbl_frame_transform_words(world, d_words, n_props: int, pose, agent, d_O, stream=None) -> None:
+    w, a = _grid(world), _grid(agent)
+    _check(load().lbl_frame_transform_words(ctypes.byref(w), _dev(d_words, "uint64", "words"), int(n_props),
+                                            _pose(pose), ctypes.byref(a), _dev(d_O, "uint64", "O"),
+                                            _stream(stream)))
 
 
 def lbl_monitor_create(n_states: int, m: int, relbits, delta, reject: int) -> int:

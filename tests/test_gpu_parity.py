@@ -134,6 +134,53 @@ def test_frame_transform_prop_counts_and_odd_grids(P):
         assert np.array_equal(host(O), oracle.frame_transform(world, planes, pose, agent))
 
 
+def _packed(planes):
+    P = planes.shape[0]
+    flat = planes.reshape(P, int(np.prod(planes.shape[1:])))
+    w = np.zeros(flat.shape[1], np.uint64)
+    for p in range(P):
+        w |= (flat[p] != 0).astype(np.uint64) << np.uint64(p)
+    return w
+
+
+@pytest.mark.parametrize("P", [0, 1, 7, 16, 33, 64])
+def test_pack_planes_and_packed_transform(P):
+    """Packed words equal the plain definition for word-aligned and unaligned
+    planes and odd cell counts; the packed transform equals the oracle's."""
+    rng = np.random.default_rng(70 + P)
+    for world, misalign in ((synth.world_grid(53, 41, 0.37), 0), (synth.world_grid(64, 48, 0.37), 0),
+                            (synth.world_grid(64, 48, 0.37), 1)):
+        cells = world.cells
+        planes = (rng.random((P, world.h, world.w)) < 0.3).astype(np.uint8) * rng.integers(
+            1, 255, size=(P, world.h, world.w)).astype(np.uint8)
+        buf = torch.zeros(P * cells + 8, dtype=torch.uint8, device="cuda")
+        d_planes = buf[misalign:misalign + P * cells]
+        d_planes.copy_(torch.from_numpy(planes.reshape(-1)).cuda())
+        words = torch.full((cells,), 0x55, dtype=torch.int64, device="cuda").view(torch.uint64)
+        L.lbl_pack_planes(world, d_planes, P, words)
+        assert np.array_equal(host(words), _packed(planes)), (world.w, misalign)
+        for agent in (synth.agent_grid(32, 0.25, synth.MORTON), synth.Grid(37, 29, 0.3, -5.0, -4.0, synth.ROWMAJOR)):
+            pose = (9.0 + rng.random(), 7.5 + rng.random(), rng.random() * 6.3)
+            O = empty_u64(agent.cells)
+            L.lbl_frame_transform_words(world, words, P, pose, agent, O)
+            assert np.array_equal(host(O), oracle.frame_transform(world, planes, pose, agent))
+
+
+def test_packed_transform_time_augmented():
+    rng = np.random.default_rng(77)
+    world = synth.Grid(20, 17, 0.3, 0.0, 0.0, synth.ROWMAJOR, 12, 0.07, -0.1)
+    vols = (rng.random((40, 12, 17, 20)) < 0.5).astype(np.uint8)
+    agent = synth.agent_grid3(8, 0.25, 8, 0.05, synth.MORTON)
+    words = empty_u64(world.cells)
+    L.lbl_pack_planes(world, cuda(vols), 40, words)
+    assert np.array_equal(host(words), _packed(vols))
+    for _ in range(3):
+        pose = (2 + 2 * rng.random(), 2 + 2 * rng.random(), 6.3 * rng.random(), 0.3 * rng.random() - 0.1)
+        O = empty_u64(agent.cells)
+        L.lbl_frame_transform_words(world, words, 40, pose, agent, O)
+        assert np.array_equal(host(O), oracle.frame_transform3(world, vols, pose, agent))
+
+
 def test_frame_transform_rejects_out_of_range_pose():
     world = synth.world_grid(8, 8, 1.0)
     agent = synth.agent_grid(8, 1.0, synth.MORTON)
@@ -411,6 +458,37 @@ def test_session_run_from_host_memory(large_small):
     finally:
         L.lbl_session_free(ss)
         L.lbl_monitor_free(hm)
+
+
+@pytest.mark.parametrize("flags", [0, "quad"])
+def test_session_chunked_copies_match_oracle(flags):
+    """Roadmaps of 2^16 edges or more: the session labels them in edge ranges
+    and copies each range to the host while the next is labeled."""
+    wl = synth.make("large", seed=14, edges=90_000)
+    rm = L.lbl_roadmap_upload(wl.agent, wl.rowptr, wl.colidx, flags=L.LBL_UPLOAD_QUAD if flags else 0)
+    mon = wl.monitor
+    hm = L.lbl_monitor_create(mon.n_states, mon.m, mon.relbits, mon.delta, mon.reject)
+    ss = L.lbl_session_create(rm, wl.world, wl.P, hm)
+    try:
+        planes = torch.from_numpy(wl.planes).pin_memory()
+        outL = torch.full((wl.n_edges,), 7, dtype=torch.int64).view(torch.uint64).pin_memory()
+        outN = torch.empty(wl.n_edges, dtype=torch.uint64).pin_memory()
+        outV = torch.empty(wl.n_edges, dtype=torch.uint16).pin_memory()
+        rng = np.random.default_rng(15)
+        s = torch.cuda.Stream()
+        for _ in range(2):
+            pose = synth.random_pose(rng, wl.world)
+            L.lbl_session_run(ss, planes, pose, outL, outN, outV, stream=s)
+            s.synchronize()  # the caller's stream covers the copies made on the session's own stream
+            O = oracle.frame_transform(wl.world, wl.planes, pose, wl.agent)
+            want = oracle.label(wl.rowptr, wl.colidx, O, wl.P, threads=8)
+            wn, wv = oracle.monitor(mon.n_states, mon.m, mon.relbits, mon.delta, mon.reject, want)
+            assert np.array_equal(outL.numpy(), want)
+            assert np.array_equal(outN.numpy(), wn) and np.array_equal(outV.numpy(), wv)
+    finally:
+        L.lbl_session_free(ss)
+        L.lbl_monitor_free(hm)
+        L.lbl_roadmap_free(rm)
 
 
 def test_autotune_choice_is_exact_and_sticks(driving_small):
