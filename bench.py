@@ -78,6 +78,7 @@ def parse():
     ap.add_argument("--edges", type=int, default=None, help="shrink the workload (not for reported numbers)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-csr-form", action="store_true", help="skip timing the CSR form beside the quadtree form")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--rates", default="2000,5000,10000,15000", help="serving: request rates (req/s); the first is the "
                     "configured rate of the headline line, the others a saturation sweep")
@@ -392,6 +393,33 @@ def main():
     total_ms = max_over_ranks(float(step_ms.sum()), dist, "cuda")
     value = job_throughput(world, E, P, args.steps, total_ms)
 
+    # ---- the CSR form on the same frame and roadmap, for its roofline (the
+    # quadtree form moves five times fewer bytes, so its fraction is lower)
+    csr_line = None
+    if used == "quad" and not args.no_csr_form:
+        csr_cfg = lbl_config(L.LBL_ALGO_CSR, 0, 0, args.ctas, 0, 0)
+        n_csr = max(10, min(args.steps, 200))
+        cev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_csr)]
+        for _ in range(3):
+            L.lbl_label(rm, d_O, P, d_L, mon, d_next, d_viol, csr_cfg, stream=stream)
+        for i in range(n_csr):
+            with torch.cuda.stream(stream):
+                flush.fill_(i & 255)
+            cev[i][0].record(stream)
+            L.lbl_label(rm, d_O, P, d_L, mon, d_next, d_viol, csr_cfg, stream=stream)
+            cev[i][1].record(stream)
+        torch.cuda.synchronize()
+        csr_s = float(np.mean([a.elapsed_time(b) for a, b in cev])) / 1e3
+        csr_b = label_bytes(wl, "csr", None, mon is not None)
+        peaks0 = measured_peaks()
+        pk = peaks0["hbm_gbs"] if peaks0 else 6800.0
+        csr_line = {"bound": "hbm", "achieved": csr_b / csr_s / 1e9, "peak": pk, "unit": "GB/s",
+                    "frac": csr_b / csr_s / 1e9 / pk, "label_ms": csr_s * 1e3, "launches": n_csr,
+                    "traffic": committed_traffic(os.path.join(ROOT, "paper_1810_02612_gb300", "csrc", "k_label.cu"),
+                                                 args.workload, "csr"),
+                    "kernel": "label_csr", "algorithmic_bytes_per_launch": csr_b,
+                    "peak_source": "measured" if peaks0 else "fallback"}
+
     # ---- end to end through the session API with pinned host buffers
     ss = L.lbl_session_create(rm, wl.world, P, mon, cfg)
     h_planes = torch.from_numpy(wl.planes).pin_memory()
@@ -457,6 +485,7 @@ def main():
                          "kernel": f"label_{used}", "algorithmic_bytes_per_launch": lb,
                          "csr_equivalent_gbs": label_bytes(wl, "csr", None, mon is not None) / label_avg_s / 1e9,
                          "peak_source": "measured" if peaks else "fallback"},
+            "roofline_csr_form": csr_line,
             "cpu_baseline": cpu,
             "clocks": clk,
             "setup_s": {"generate": t_gen},
