@@ -449,12 +449,18 @@ int lbl_server_free(lbl_server srv);
  * monitor, if any) and copy the results out.
  *   lbl_session_create  allocates the device buffers (planes, O, labels,
  *                       monitor outputs) for `world` and n_props.
- *   lbl_session_run     enqueues H2D(h_planes) -> transform -> label -> D2H on
- *                       `s`.  h_planes: uint8[n_props][world.d][world.h][world.w];
- *                       h_L: uint64[E]; h_next/h_viol: uint64[E]/uint16[E] or
- *                       NULL.  Host buffers should be pinned for asynchronous
- *                       copies.  Results are valid after `s` completes; a
- *                       session runs one frame at a time.
+ *   lbl_session_run     enqueues H2D(h_planes) -> transform -> label -> D2H;
+ *                       everything is ordered before the end of `s`.  h_planes:
+ *                       uint8[n_props][world.d][world.h][world.w]; h_L: uint64[E];
+ *                       h_next/h_viol: uint64[E]/uint16[E] or NULL.  Host buffers
+ *                       should be pinned for asynchronous copies and stay
+ *                       untouched until `s` completes; results are valid then.
+ * Frames run back to back overlap their copies with the neighbouring frames'
+ * kernels: the planes go in on the session's own copy stream into one of two
+ * device buffers (frame i+1's copy runs while frame i is labeled), and on
+ * roadmaps of 2^16 edges or more the labels leave in four edge ranges on a
+ * second copy stream while the next range is labeled.  Calls on one session
+ * must not be made from several threads at once.
  */
 int lbl_session_create(lbl_roadmap rm, const lbl_grid *world, int32_t n_props, lbl_monitor mon,
                        const lbl_config *cfg, lbl_session *out);

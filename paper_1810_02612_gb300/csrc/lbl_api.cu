@@ -219,6 +219,13 @@ struct lbl_session_s {
   uint8_t *planes = nullptr;
   uint64_t *O = nullptr, *L = nullptr, *next = nullptr;
   uint16_t *viol = nullptr;
+  // Two plane buffers, filled on `cin` in turn: frame i+1's planes go to the
+  // device while frame i is transformed and labeled.  ev_in[k]: slot k filled;
+  // ev_free[k]: the transform that read slot k is done.
+  uint8_t *slot[2] = {nullptr, nullptr};
+  cudaStream_t cin = nullptr;
+  cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
+  int64_t frame = 0;
   // Chunked labeling: the edges in kSessionChunks ranges, each labeled by the
   // whole grid; a range's results go to the host on `cs` while the next range
   // is labeled.  Used with the default form (quadtree, else streaming CSR).
@@ -1098,7 +1105,14 @@ int lbl_session_create(lbl_roadmap rm, const lbl_grid *world, int32_t n_props, l
     ss->has_cfg = true;
   }
   const size_t plane_bytes = static_cast<size_t>(n_props) * grid_cells(*world);
-  cudaError_t e = dev_alloc(&ss->planes, plane_bytes, nullptr);
+  cudaError_t e = dev_alloc(&ss->planes, 2 * plane_bytes, nullptr);
+  ss->slot[0] = ss->planes;
+  ss->slot[1] = ss->planes + plane_bytes;
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ss->cin, cudaStreamNonBlocking);
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+    e = cudaEventCreateWithFlags(&ss->ev_in[k], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ss->ev_free[k], cudaEventDisableTiming);
+  }
   if (e == cudaSuccess) e = dev_alloc(&ss->O, static_cast<size_t>(rm->cells), nullptr);
   if (e == cudaSuccess) e = dev_alloc(&ss->L, static_cast<size_t>(rm->E), nullptr);
   if (e == cudaSuccess && mon) e = dev_alloc(&ss->next, static_cast<size_t>(rm->E), nullptr);
@@ -1155,11 +1169,17 @@ int lbl_session_run(lbl_session ss, const uint8_t *h_planes, lbl_pose pose, uint
   if (!same_device(ss->device)) return LBL_EINVAL;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(s);
   const size_t plane_bytes = static_cast<size_t>(ss->P) * grid_cells(ss->world);
-  cudaError_t e = cudaSuccess;
-  if (plane_bytes) e = cudaMemcpyAsync(ss->planes, h_planes, plane_bytes, cudaMemcpyHostToDevice, st);
+  const int k = static_cast<int>(ss->frame & 1);
+  cudaError_t e = cudaStreamWaitEvent(ss->cin, ss->ev_free[k], 0);  // slot k no longer read
+  if (e == cudaSuccess && plane_bytes)
+    e = cudaMemcpyAsync(ss->slot[k], h_planes, plane_bytes, cudaMemcpyHostToDevice, ss->cin);
+  if (e == cudaSuccess) e = cudaEventRecord(ss->ev_in[k], ss->cin);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ss->ev_in[k], 0);
   if (e != cudaSuccess) return cuda_fail(e, "session run: copy planes");
-  int rc = lbl_frame_transform(&ss->world, ss->planes, ss->P, pose, &rm.agent, ss->O, s);
+  int rc = lbl_frame_transform(&ss->world, ss->slot[k], ss->P, pose, &rm.agent, ss->O, s);
   if (rc != LBL_OK) return rc;
+  if ((e = cudaEventRecord(ss->ev_free[k], st)) != cudaSuccess) return cuda_fail(e, "session run: event");
+  ++ss->frame;
   if (ss->chunked) {
     const uint64_t *base = ss->O;
     if (ss->quad) {
@@ -1213,8 +1233,13 @@ int lbl_session_free(lbl_session ss) {
   cudaFree(ss->viol);
   cudaFree(ss->cpart);
   if (ss->cs) cudaStreamDestroy(ss->cs);
+  if (ss->cin) cudaStreamDestroy(ss->cin);
   for (cudaEvent_t ev : ss->ev)
     if (ev) cudaEventDestroy(ev);
+  for (int k = 0; k < 2; ++k) {
+    if (ss->ev_in[k]) cudaEventDestroy(ss->ev_in[k]);
+    if (ss->ev_free[k]) cudaEventDestroy(ss->ev_free[k]);
+  }
   delete ss;
   return LBL_OK;
 }

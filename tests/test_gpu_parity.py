@@ -491,6 +491,43 @@ def test_session_chunked_copies_match_oracle(flags):
         L.lbl_roadmap_free(rm)
 
 
+def test_session_frames_back_to_back():
+    """Frames enqueued without waiting: the plane copies of frame i+1 overlap
+    frame i (two device slots, reused every other frame) and every frame's
+    outputs still equal the oracle's."""
+    wl = synth.make("large", seed=16, edges=80_000)
+    rm = L.lbl_roadmap_upload(wl.agent, wl.rowptr, wl.colidx, flags=L.LBL_UPLOAD_QUAD)
+    mon = wl.monitor
+    hm = L.lbl_monitor_create(mon.n_states, mon.m, mon.relbits, mon.delta, mon.reject)
+    ss = L.lbl_session_create(rm, wl.world, wl.P, hm)
+    try:
+        rng = np.random.default_rng(17)
+        plane_sets = [np.ascontiguousarray(wl.planes), np.ascontiguousarray(wl.planes[::-1]),
+                      np.ascontiguousarray(np.roll(wl.planes, 5, axis=0))]
+        frames = []
+        for i in range(6):
+            planes = plane_sets[i % 3]
+            frames.append(dict(planes=planes, h_planes=torch.from_numpy(planes).pin_memory(),
+                               pose=synth.random_pose(rng, wl.world),
+                               L=torch.empty(wl.n_edges, dtype=torch.uint64).pin_memory(),
+                               N=torch.empty(wl.n_edges, dtype=torch.uint64).pin_memory(),
+                               V=torch.empty(wl.n_edges, dtype=torch.uint16).pin_memory()))
+        s = torch.cuda.Stream()
+        for f in frames:
+            L.lbl_session_run(ss, f["h_planes"], f["pose"], f["L"], f["N"], f["V"], stream=s)
+        s.synchronize()
+        for i, f in enumerate(frames):
+            O = oracle.frame_transform(wl.world, f["planes"], f["pose"], wl.agent)
+            want = oracle.label(wl.rowptr, wl.colidx, O, wl.P, threads=8)
+            wn, wv = oracle.monitor(mon.n_states, mon.m, mon.relbits, mon.delta, mon.reject, want)
+            assert np.array_equal(f["L"].numpy(), want), i
+            assert np.array_equal(f["N"].numpy(), wn) and np.array_equal(f["V"].numpy(), wv), i
+    finally:
+        L.lbl_session_free(ss)
+        L.lbl_monitor_free(hm)
+        L.lbl_roadmap_free(rm)
+
+
 def test_autotune_choice_is_exact_and_sticks(driving_small):
     wl = driving_small
     rm = Roadmap(wl.agent, wl.rowptr, wl.colidx, bittile=True)
