@@ -178,6 +178,11 @@ def pyramid_words(cells: int, levels: int = 4) -> int:
     return sum(cells >> (2 * k) for k in range(levels + 1))
 
 
+def pyramid_word_bytes(P: int) -> int:
+    """Width of the per-frame pyramid words the library uses for P propositions."""
+    return 1 if P <= 8 else 2 if P <= 16 else 4 if P <= 32 else 8
+
+
 def label_bytes(wl, algo: str, n_bt: int | None, with_monitor: bool, n_sec: int | None = None,
                 n_qd: int | None = None) -> int:
     """Algorithmic HBM bytes of one labeling call (each array read or written
@@ -186,7 +191,8 @@ def label_bytes(wl, algo: str, n_bt: int | None, with_monitor: bool, n_sec: int 
     E = wl.n_edges
     out = 8 * E + (10 * E if with_monitor else 0)
     if algo == "quad":  # pyramid: O read, pyramid written; stream: entries, rows, pyramid once
-        return 4 * n_qd + 8 * (E + 1) + 8 * wl.agent.cells + 16 * pyramid_words(wl.agent.cells) + out
+        return (4 * n_qd + 8 * (E + 1) + 8 * wl.agent.cells
+                + 2 * pyramid_word_bytes(wl.P) * pyramid_words(wl.agent.cells) + out)
     if algo == "sector":
         return 4 * n_sec + 8 * (E + 1) + 8 * wl.agent.cells + out
     if algo == "bittile":

@@ -147,13 +147,19 @@ __global__ void __launch_bounds__(kThreads) k_label_csr(const int64_t *__restric
 // of the current edge) flushes the current edge: its lanes' words are ORed in,
 // the warp reduces, lane 0 hands the label to `emit`, and the next edge starts.
 // Empty edges are flushed the same way with nothing ORed in.
-// Gather for the CSR stream: entry = cell index, -1 = no entry.
-struct CsrGather {
-  const uint64_t *__restrict__ O;
+// Gather for the CSR and quadtree streams: entry = index of a word, -1 = no
+// entry.  Words are uint64 proposition words, or narrower pyramid words when
+// every proposition fits (the label's bits >= P are masked anyway).
+template <typename T>
+struct WordGather {
+  const T *__restrict__ O;
   static constexpr int32_t kNone = -1;
-  __device__ __forceinline__ uint64_t full(int32_t c) const { return __ldg(O + c); }
-  __device__ __forceinline__ uint64_t masked(int32_t c) const { return c >= 0 ? __ldg(O + c) : 0ull; }
+  __device__ __forceinline__ uint64_t full(int32_t c) const { return static_cast<uint64_t>(__ldg(O + c)); }
+  __device__ __forceinline__ uint64_t masked(int32_t c) const {
+    return c >= 0 ? static_cast<uint64_t>(__ldg(O + c)) : 0ull;
+  }
 };
+using CsrGather = WordGather<uint64_t>;
 
 // Positions inside a warp's range are kept relative to its first entry `a`
 // and first edge in `Off` (int32_t whenever the range allows it: fewer
@@ -264,10 +270,10 @@ constexpr int stream_min_blocks() {
   return U <= 8 ? 4 : (U <= 12 ? 3 : 2);
 }
 
-template <int U, bool EPI, typename Off>
+template <int U, bool EPI, typename Off, typename T = uint64_t>
 __global__ void __launch_bounds__(kThreads, stream_min_blocks<U>()) k_label_stream(const int64_t *__restrict__ rowptr,
                                                            const int32_t *__restrict__ colidx,
-                                                           const uint64_t *__restrict__ O,
+                                                           const T *__restrict__ O,
                                                            const int64_t *__restrict__ part, uint64_t mask,
                                                            uint64_t *__restrict__ L, MonitorTables mon) {
   __shared__ EpiSmem sm;
@@ -277,7 +283,7 @@ __global__ void __launch_bounds__(kThreads, stream_min_blocks<U>()) k_label_stre
   const int64_t w = (static_cast<int64_t>(blockIdx.x) * kThreads + threadIdx.x) >> 5;
   const int64_t e_beg = __ldg(part + w), e_end = __ldg(part + w + 1);
   if (e_beg >= e_end) return;  // warp-uniform
-  stream_range<U, Off>(rowptr, colidx, CsrGather{O}, e_beg, e_end, pol, lane, [&](int64_t e, uint64_t r) {
+  stream_range<U, Off>(rowptr, colidx, WordGather<T>{O}, e_beg, e_end, pol, lane, [&](int64_t e, uint64_t r) {
     r &= mask;
     L[e] = r;
     if (EPI) epilogue(mon, sm, e, r);
@@ -386,37 +392,39 @@ __global__ void __launch_bounds__(kThreads, stream_min_blocks<U>()) k_label_batc
 // cells of top-level block `blk`: levels 1-2 (4 and 16 cells) by butterfly
 // shuffles inside each warp, levels 3-4 (64 and 256 cells) from the eight
 // 32-cell warp words.
+template <typename T>
 __device__ __forceinline__ void quad_pyramid_block(const uint64_t *__restrict__ O, int64_t cells,
-                                                   const QuadOffsets &off, uint64_t *__restrict__ pyr, int64_t blk,
+                                                   const QuadOffsets &off, T *__restrict__ pyr, int64_t blk,
                                                    uint64_t *wsum) {
   static_assert(kThreads == 256 && kQuadLevels == 4, "one CTA = one block of the top level");
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t i = blk * kThreads + threadIdx.x;
   uint64_t v = i < cells ? __ldg(O + i) : 0ull;
-  if (i < cells) pyr[i] = v;
+  if (i < cells) pyr[i] = static_cast<T>(v);
   v = or_xor(or_xor(v, 1), 2);  // every lane: OR of its aligned 4-cell block
-  if ((lane & 3) == 0 && (i >> 2) < (cells >> 2)) pyr[off.at[1] + (i >> 2)] = v;
+  if ((lane & 3) == 0 && (i >> 2) < (cells >> 2)) pyr[off.at[1] + (i >> 2)] = static_cast<T>(v);
   v = or_xor(or_xor(v, 4), 8);  // 16-cell block
-  if ((lane & 15) == 0 && (i >> 4) < (cells >> 4)) pyr[off.at[2] + (i >> 4)] = v;
+  if ((lane & 15) == 0 && (i >> 4) < (cells >> 4)) pyr[off.at[2] + (i >> 4)] = static_cast<T>(v);
   v = or_xor(v, 16);  // the warp's 32 cells
   if (lane == 0) wsum[wid] = v;
   __syncthreads();
   if (threadIdx.x < 4) {  // 64-cell blocks: warps (2t, 2t+1)
     const int t = threadIdx.x;
     const int64_t b = blk * 4 + t;
-    if (b < (cells >> 6)) pyr[off.at[3] + b] = wsum[2 * t] | wsum[2 * t + 1];
+    if (b < (cells >> 6)) pyr[off.at[3] + b] = static_cast<T>(wsum[2 * t] | wsum[2 * t + 1]);
   } else if (threadIdx.x == 4) {  // the 256-cell block
     uint64_t a = 0;
 #pragma unroll
     for (int w = 0; w < kThreads / 32; ++w) a |= wsum[w];
-    if (blk < (cells >> 8)) pyr[off.at[4] + blk] = a;
+    if (blk < (cells >> 8)) pyr[off.at[4] + blk] = static_cast<T>(a);
   }
 }
 
+template <typename T>
 __global__ void __launch_bounds__(kThreads) k_quad_pyramid(const uint64_t *__restrict__ O, int64_t cells,
-                                                           QuadOffsets off, uint64_t *__restrict__ pyr) {
+                                                           QuadOffsets off, T *__restrict__ pyr) {
   __shared__ uint64_t wsum[kThreads / 32];
-  quad_pyramid_block(O, cells, off, pyr, blockIdx.x, wsum);
+  quad_pyramid_block<T>(O, cells, off, pyr, blockIdx.x, wsum);
 }
 
 // The same for many frames in one launch: CTA b finds its item (the last with
@@ -433,7 +441,7 @@ __global__ void __launch_bounds__(kThreads) k_quad_pyramid_batch(const __grid_co
       hi = mid - 1;
   }
   const PyrItem &it = tab.items[lo];
-  quad_pyramid_block(it.O, it.cells, it.off, it.pyr, b - it.block0, wsum);
+  quad_pyramid_block<uint64_t>(it.O, it.cells, it.off, it.pyr, b - it.block0, wsum);
 }
 
 // ---------------------------------------------------------------------------
@@ -1029,42 +1037,67 @@ cudaError_t launch_partition(const Roadmap &rm, int ctas_per_sm, cudaStream_t s)
   return cudaGetLastError();
 }
 
-template <int U, typename Off>
-void rows_launch(const StreamRows &r, const uint64_t *base, uint64_t mask, uint64_t *L, const MonitorTables *mon,
+template <int U, typename Off, typename T>
+void rows_launch(const StreamRows &r, const T *base, uint64_t mask, uint64_t *L, const MonitorTables *mon,
                  int num_sms, cudaStream_t s) {
   const unsigned grid = static_cast<unsigned>(num_sms * r.part_ctas);
   MonitorTables none{};
   if (mon)
-    k_label_stream<U, true, Off><<<grid, kThreads, 0, s>>>(r.rowptr, r.idx, base, r.part, mask, L, *mon);
+    k_label_stream<U, true, Off, T><<<grid, kThreads, 0, s>>>(r.rowptr, r.idx, base, r.part, mask, L, *mon);
   else
-    k_label_stream<U, false, Off><<<grid, kThreads, 0, s>>>(r.rowptr, r.idx, base, r.part, mask, L, none);
+    k_label_stream<U, false, Off, T><<<grid, kThreads, 0, s>>>(r.rowptr, r.idx, base, r.part, mask, L, none);
 }
 
-cudaError_t launch_label_rows(const StreamRows &r, const uint64_t *base, int32_t P, uint64_t *L,
+template <typename T>
+void rows_launch_depth(const StreamRows &r, const T *base, uint64_t mask, uint64_t *L, const MonitorTables *mon,
+                       int depth, int num_sms, cudaStream_t s) {
+  if (depth == 16)
+    rows_launch<16, int32_t, T>(r, base, mask, L, mon, num_sms, s);
+  else if (depth == 12)
+    rows_launch<12, int32_t, T>(r, base, mask, L, mon, num_sms, s);
+  else
+    rows_launch<8, int32_t, T>(r, base, mask, L, mon, num_sms, s);
+}
+
+cudaError_t launch_label_rows(const StreamRows &r, const void *base, int word_bytes, int32_t P, uint64_t *L,
                               const MonitorTables *mon, int depth, int num_sms, cudaStream_t s) {
   if (r.E == 0) return cudaSuccess;
   const uint64_t mask = prop_mask(P);
-  if (r.entries >= kNarrowLimit || r.E >= kNarrowLimit)
-    rows_launch<8, int64_t>(r, base, mask, L, mon, num_sms, s);
-  else if (depth == 16)
-    rows_launch<16, int32_t>(r, base, mask, L, mon, num_sms, s);
-  else if (depth == 12)
-    rows_launch<12, int32_t>(r, base, mask, L, mon, num_sms, s);
-  else
-    rows_launch<8, int32_t>(r, base, mask, L, mon, num_sms, s);
+  if (r.entries >= kNarrowLimit || r.E >= kNarrowLimit) {  // wide rows gather 64-bit words only
+    if (word_bytes != 8) return cudaErrorInvalidValue;
+    rows_launch<8, int64_t, uint64_t>(r, static_cast<const uint64_t *>(base), mask, L, mon, num_sms, s);
+  } else if (word_bytes == 1) {
+    rows_launch_depth(r, static_cast<const uint8_t *>(base), mask, L, mon, depth, num_sms, s);
+  } else if (word_bytes == 2) {
+    rows_launch_depth(r, static_cast<const uint16_t *>(base), mask, L, mon, depth, num_sms, s);
+  } else if (word_bytes == 4) {
+    rows_launch_depth(r, static_cast<const uint32_t *>(base), mask, L, mon, depth, num_sms, s);
+  } else {
+    rows_launch_depth(r, static_cast<const uint64_t *>(base), mask, L, mon, depth, num_sms, s);
+  }
   return cudaGetLastError();
 }
 
 cudaError_t launch_label_stream(const Roadmap &rm, const uint64_t *O, int32_t P, uint64_t *L,
                                 const MonitorTables *mon, int depth, cudaStream_t s) {
   const StreamRows r{rm.rowptr, rm.colidx, rm.part, rm.part_ctas, rm.E, rm.nnz};
-  return launch_label_rows(r, O, P, L, mon, depth, rm.num_sms, s);
+  return launch_label_rows(r, O, 8, P, L, mon, depth, rm.num_sms, s);
 }
 
-cudaError_t launch_quad_pyramid(const Roadmap &rm, const uint64_t *O, cudaStream_t s) {
+int quad_word_bytes(const Roadmap &rm, int32_t P) {
+  if (rm.n_qd >= kNarrowLimit || rm.E >= kNarrowLimit) return 8;
+  return P <= 8 ? 1 : P <= 16 ? 2 : P <= 32 ? 4 : 8;
+}
+
+cudaError_t launch_quad_pyramid(const Roadmap &rm, const uint64_t *O, int word_bytes, cudaStream_t s) {
   if (rm.cells == 0) return cudaSuccess;
   const unsigned grid = static_cast<unsigned>((rm.cells + kThreads - 1) / kThreads);
-  k_quad_pyramid<<<grid, kThreads, 0, s>>>(O, rm.cells, rm.qd_off, rm.pyr);
+  switch (word_bytes) {
+    case 1: k_quad_pyramid<uint8_t><<<grid, kThreads, 0, s>>>(O, rm.cells, rm.qd_off, reinterpret_cast<uint8_t *>(rm.pyr)); break;
+    case 2: k_quad_pyramid<uint16_t><<<grid, kThreads, 0, s>>>(O, rm.cells, rm.qd_off, reinterpret_cast<uint16_t *>(rm.pyr)); break;
+    case 4: k_quad_pyramid<uint32_t><<<grid, kThreads, 0, s>>>(O, rm.cells, rm.qd_off, reinterpret_cast<uint32_t *>(rm.pyr)); break;
+    default: k_quad_pyramid<uint64_t><<<grid, kThreads, 0, s>>>(O, rm.cells, rm.qd_off, rm.pyr); break;
+  }
   return cudaGetLastError();
 }
 
@@ -1075,12 +1108,13 @@ cudaError_t launch_quad_pyramid_batch(const PyrTable &tab, cudaStream_t s) {
 }
 
 cudaError_t launch_label_quad(const Roadmap &rm, const uint64_t *O, int32_t P, uint64_t *L,
-                                const MonitorTables *mon, int depth, cudaStream_t s) {
+                              const MonitorTables *mon, int depth, cudaStream_t s) {
   if (rm.E == 0) return cudaSuccess;
-  cudaError_t e = launch_quad_pyramid(rm, O, s);
+  const int wb = quad_word_bytes(rm, P);
+  cudaError_t e = launch_quad_pyramid(rm, O, wb, s);
   if (e != cudaSuccess) return e;
   const StreamRows r{rm.qd_rowptr, rm.qd_idx, rm.qd_part, rm.qd_part_ctas, rm.E, rm.n_qd};
-  return launch_label_rows(r, rm.pyr, P, L, mon, depth, rm.num_sms, s);
+  return launch_label_rows(r, rm.pyr, wb, P, L, mon, depth, rm.num_sms, s);
 }
 
 cudaError_t launch_label_csr(const Roadmap &rm, const uint64_t *O, int32_t P, uint64_t *L, const MonitorTables *mon,

@@ -1181,9 +1181,11 @@ int lbl_session_run(lbl_session ss, const uint8_t *h_planes, lbl_pose pose, uint
   if ((e = cudaEventRecord(ss->ev_free[k], st)) != cudaSuccess) return cuda_fail(e, "session run: event");
   ++ss->frame;
   if (ss->chunked) {
-    const uint64_t *base = ss->O;
+    const void *base = ss->O;
+    int wb = 8;
     if (ss->quad) {
-      if ((e = launch_quad_pyramid(rm, ss->O, st)) != cudaSuccess) return cuda_fail(e, "session run: pyramid");
+      wb = quad_word_bytes(rm, ss->P);
+      if ((e = launch_quad_pyramid(rm, ss->O, wb, st)) != cudaSuccess) return cuda_fail(e, "session run: pyramid");
       base = rm.pyr;
     }
     for (int c = 0; c < kSessionChunks; ++c) {
@@ -1193,7 +1195,7 @@ int lbl_session_run(lbl_session ss, const uint8_t *h_planes, lbl_pose pose, uint
                          ss->cpart + c * (ss->warps + 1), ss->ctas, n, ss->quad ? rm.n_qd : rm.nnz};
       MonitorTables t{};
       if (ss->mon) t = tables_of(*ss->mon, ss->next + e0, ss->viol + e0);
-      e = launch_label_rows(r, base, ss->P, ss->L + e0, ss->mon ? &t : nullptr, ss->depth, rm.num_sms, st);
+      e = launch_label_rows(r, base, wb, ss->P, ss->L + e0, ss->mon ? &t : nullptr, ss->depth, rm.num_sms, st);
       if (e == cudaSuccess) e = cudaEventRecord(ss->ev[c], st);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(ss->cs, ss->ev[c], 0);
       if (e == cudaSuccess) e = cudaMemcpyAsync(h_L + e0, ss->L + e0, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost, ss->cs);

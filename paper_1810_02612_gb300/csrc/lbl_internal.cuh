@@ -239,11 +239,14 @@ cudaError_t launch_label_tma(const Roadmap &rm, const uint64_t *O, int32_t P, ui
 cudaError_t launch_partition(const Roadmap &rm, int ctas_per_sm, cudaStream_t s);
 cudaError_t launch_label_stream(const Roadmap &rm, const uint64_t *O, int32_t P, uint64_t *L,
                                 const MonitorTables *mon, int depth, cudaStream_t s);
-cudaError_t launch_label_rows(const StreamRows &r, const uint64_t *base, int32_t P, uint64_t *L,
+// base: words of word_bytes (1, 2, 4 or 8) each; rows of 2^31 entries or more need 8
+cudaError_t launch_label_rows(const StreamRows &r, const void *base, int word_bytes, int32_t P, uint64_t *L,
                               const MonitorTables *mon, int depth, int num_sms, cudaStream_t s);
 
 // quadtree form: pyramid of O, then the stream over the quadtree rows
-cudaError_t launch_quad_pyramid(const Roadmap &rm, const uint64_t *O, cudaStream_t s);
+// pyramid word width for n_props propositions: 1, 2, 4 or 8 bytes
+int quad_word_bytes(const Roadmap &rm, int32_t P);
+cudaError_t launch_quad_pyramid(const Roadmap &rm, const uint64_t *O, int word_bytes, cudaStream_t s);
 cudaError_t launch_label_quad(const Roadmap &rm, const uint64_t *O, int32_t P, uint64_t *L,
                                 const MonitorTables *mon, int depth, cudaStream_t s);
 cudaError_t launch_quad_pyramid_batch(const PyrTable &tab, cudaStream_t s);

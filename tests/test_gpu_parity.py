@@ -366,7 +366,9 @@ def test_quad_runs_at_every_alignment(order):
     """Rows made of runs of 1..700 consecutive cells at every offset modulo 256,
     rows covering the whole grid, rows ending at its last cell and single
     cells: quadtree-form labels equal the oracle's for every proposition
-    count, and the form holds exactly one entry per maximal block."""
+    count (8-, 16-, 32- and 64-bit pyramid words; O words carry bits above P,
+    which the labels must drop), and the form holds exactly one entry per
+    maximal block."""
     rng = np.random.default_rng(91 + order)
     agent = synth.agent_grid(64, 0.5, order) if order == synth.MORTON else synth.Grid(77, 53, 0.5, 0.0, 0.0, order)
     cells = agent.cells
@@ -390,7 +392,7 @@ def test_quad_runs_at_every_alignment(order):
     want_entries = int(_quad_count(rowptr, colidx).sum())
     assert L.lbl_roadmap_info(rm.h)[4] == want_entries
     assert want_entries < 0.3 * colidx.shape[0]
-    for P in (1, 2, 31, 64):
+    for P in (1, 2, 8, 9, 16, 17, 31, 32, 33, 64):  # every pyramid word width and its edges
         O_h = np.zeros(cells, np.uint64)
         hit = rng.random(cells) < 0.01
         O_h[hit] = rng.integers(1, 2**63, size=hit.sum(), dtype=np.uint64)
