@@ -460,7 +460,9 @@ int lbl_server_free(lbl_server srv);
  * device buffers (frame i+1's copy runs while frame i is labeled), and on
  * roadmaps of 2^16 edges or more the labels leave in four edge ranges on a
  * second copy stream while the next range is labeled.  Calls on one session
- * must not be made from several threads at once.
+ * must not be made from several threads at once, and sessions sharing a
+ * roadmap must not run at the same time on different streams (the roadmap's
+ * per-frame working memory is shared, as for lbl_label).
  */
 int lbl_session_create(lbl_roadmap rm, const lbl_grid *world, int32_t n_props, lbl_monitor mon,
                        const lbl_config *cfg, lbl_session *out);
