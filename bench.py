@@ -543,6 +543,7 @@ def run_batched(args, rank, world, local, dist, torch, L):
 
     def frame_transform(f, d):
         L.lbl_frame_transform(f.world, d["d_planes"], f.P, f.pose, f.agent, d["d_O"], stream=stream)
+    torch.cuda.synchronize()  # frame buffers were filled on the default stream; the launches use `stream`
     b = L.lbl_batch_create(rms, [f.P for f in frames])
     L.lbl_batch_set_frames(b, fr)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")

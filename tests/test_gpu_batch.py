@@ -55,6 +55,7 @@ def _run_batch(items, graph):
                 o["d_viol"] = torch.zeros(max(E, 1), dtype=torch.uint16, device="cuda")
             frames.append(o)
         L.lbl_batch_set_frames(b, frames)
+        torch.cuda.synchronize()  # the frames' buffers were filled on the default stream
         s = torch.cuda.Stream()
         L.lbl_batch_launch(b, stream=s)  # first launch outside any capture
         s.synchronize()
