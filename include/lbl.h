@@ -458,11 +458,16 @@ int lbl_server_free(lbl_server srv);
  * Frames run back to back overlap their copies with the neighbouring frames'
  * kernels: the planes go in on the session's own copy stream into one of two
  * device buffers (frame i+1's copy runs while frame i is labeled), and on
- * roadmaps of 2^16 edges or more the labels leave in four edge ranges on a
- * second copy stream while the next range is labeled.  Calls on one session
- * must not be made from several threads at once, and sessions sharing a
- * roadmap must not run at the same time on different streams (the roadmap's
- * per-frame working memory is shared, as for lbl_label).
+ * roadmaps of 2^16 edges or more labeled by a streamed form (quadtree, or CSR
+ * without lane groups) the labels leave in four edge ranges on a second copy
+ * stream while the next range is labeled.  Such a session keeps its own
+ * pyramid and output buffers (two sets), runs its kernels on its own stream
+ * and only makes `s` wait for each frame's end, so frame i+1 is computed while
+ * frame i is still being copied out; it reads nothing on the device that the
+ * caller writes.  Other sessions run their kernels on `s` and use the
+ * roadmap's working memory like lbl_label: sessions of that kind sharing a
+ * roadmap must not run at the same time.  Calls on one session must not be
+ * made from several threads at once.
  */
 int lbl_session_create(lbl_roadmap rm, const lbl_grid *world, int32_t n_props, lbl_monitor mon,
                        const lbl_config *cfg, lbl_session *out);

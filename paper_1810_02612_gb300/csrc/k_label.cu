@@ -1089,14 +1089,14 @@ int quad_word_bytes(const Roadmap &rm, int32_t P) {
   return P <= 8 ? 1 : P <= 16 ? 2 : P <= 32 ? 4 : 8;
 }
 
-cudaError_t launch_quad_pyramid(const Roadmap &rm, const uint64_t *O, int word_bytes, cudaStream_t s) {
+cudaError_t launch_quad_pyramid(const Roadmap &rm, const uint64_t *O, int word_bytes, void *pyr, cudaStream_t s) {
   if (rm.cells == 0) return cudaSuccess;
   const unsigned grid = static_cast<unsigned>((rm.cells + kThreads - 1) / kThreads);
   switch (word_bytes) {
-    case 1: k_quad_pyramid<uint8_t><<<grid, kThreads, 0, s>>>(O, rm.cells, rm.qd_off, reinterpret_cast<uint8_t *>(rm.pyr)); break;
-    case 2: k_quad_pyramid<uint16_t><<<grid, kThreads, 0, s>>>(O, rm.cells, rm.qd_off, reinterpret_cast<uint16_t *>(rm.pyr)); break;
-    case 4: k_quad_pyramid<uint32_t><<<grid, kThreads, 0, s>>>(O, rm.cells, rm.qd_off, reinterpret_cast<uint32_t *>(rm.pyr)); break;
-    default: k_quad_pyramid<uint64_t><<<grid, kThreads, 0, s>>>(O, rm.cells, rm.qd_off, rm.pyr); break;
+    case 1: k_quad_pyramid<uint8_t><<<grid, kThreads, 0, s>>>(O, rm.cells, rm.qd_off, static_cast<uint8_t *>(pyr)); break;
+    case 2: k_quad_pyramid<uint16_t><<<grid, kThreads, 0, s>>>(O, rm.cells, rm.qd_off, static_cast<uint16_t *>(pyr)); break;
+    case 4: k_quad_pyramid<uint32_t><<<grid, kThreads, 0, s>>>(O, rm.cells, rm.qd_off, static_cast<uint32_t *>(pyr)); break;
+    default: k_quad_pyramid<uint64_t><<<grid, kThreads, 0, s>>>(O, rm.cells, rm.qd_off, static_cast<uint64_t *>(pyr)); break;
   }
   return cudaGetLastError();
 }
@@ -1111,7 +1111,7 @@ cudaError_t launch_label_quad(const Roadmap &rm, const uint64_t *O, int32_t P, u
                               const MonitorTables *mon, int depth, cudaStream_t s) {
   if (rm.E == 0) return cudaSuccess;
   const int wb = quad_word_bytes(rm, P);
-  cudaError_t e = launch_quad_pyramid(rm, O, wb, s);
+  cudaError_t e = launch_quad_pyramid(rm, O, wb, rm.pyr, s);
   if (e != cudaSuccess) return e;
   const StreamRows r{rm.qd_rowptr, rm.qd_idx, rm.qd_part, rm.qd_part_ctas, rm.E, rm.n_qd};
   return launch_label_rows(r, rm.pyr, wb, P, L, mon, depth, rm.num_sms, s);

@@ -226,6 +226,14 @@ struct lbl_session_s {
   cudaStream_t cin = nullptr;
   cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
   int64_t frame = 0;
+  // The session's kernels run on `cc`, and its outputs go to one of two device
+  // buffer sets in turn, so frame i+1 computes while frame i's results are
+  // still being copied out; ev_out[k]: output set k copied to the host.
+  cudaStream_t cc = nullptr;
+  uint64_t *Ls[2] = {nullptr, nullptr}, *Ns[2] = {nullptr, nullptr};
+  uint16_t *Vs[2] = {nullptr, nullptr};
+  cudaEvent_t ev_out[2] = {nullptr, nullptr};
+  uint64_t *pyr = nullptr;  // the session's own quadtree pyramid (chunked quadtree sessions)
   // Chunked labeling: the edges in kSessionChunks ranges, each labeled by the
   // whole grid; a range's results go to the host on `cs` while the next range
   // is labeled.  Used with the default form (quadtree, else streaming CSR).
@@ -1114,9 +1122,17 @@ int lbl_session_create(lbl_roadmap rm, const lbl_grid *world, int32_t n_props, l
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ss->ev_free[k], cudaEventDisableTiming);
   }
   if (e == cudaSuccess) e = dev_alloc(&ss->O, static_cast<size_t>(rm->cells), nullptr);
-  if (e == cudaSuccess) e = dev_alloc(&ss->L, static_cast<size_t>(rm->E), nullptr);
-  if (e == cudaSuccess && mon) e = dev_alloc(&ss->next, static_cast<size_t>(rm->E), nullptr);
-  if (e == cudaSuccess && mon) e = dev_alloc(&ss->viol, static_cast<size_t>(rm->E), nullptr);
+  if (e == cudaSuccess) e = dev_alloc(&ss->L, static_cast<size_t>(2 * rm->E), nullptr);
+  if (e == cudaSuccess && mon) e = dev_alloc(&ss->next, static_cast<size_t>(2 * rm->E), nullptr);
+  if (e == cudaSuccess && mon) e = dev_alloc(&ss->viol, static_cast<size_t>(2 * rm->E), nullptr);
+  for (int k = 0; k < 2; ++k) {
+    ss->Ls[k] = ss->L ? ss->L + k * rm->E : nullptr;
+    ss->Ns[k] = ss->next ? ss->next + k * rm->E : nullptr;
+    ss->Vs[k] = ss->viol ? ss->viol + k * rm->E : nullptr;
+  }
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ss->cc, cudaStreamNonBlocking);
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&ss->ev_out[k], cudaEventDisableTiming);
+
   // Chunked labeling when the configuration resolves to a register-pipelined
   // stream (quadtree, or CSR without lane groups, early exit or copy rings) on
   // a roadmap big enough to pay.
@@ -1131,6 +1147,7 @@ int lbl_session_create(lbl_roadmap rm, const lbl_grid *world, int32_t n_props, l
   if (e == cudaSuccess && stream_form && rm->E >= kSessionChunkMinEdges) {
     ss->chunked = true;
     ss->quad = c.algo == LBL_ALGO_QUAD;
+    if (ss->quad) e = dev_alloc(&ss->pyr, static_cast<size_t>(rm->pyr_words), nullptr);
     ss->depth = c.depth ? c.depth : (ss->quad ? kQuadDepth : 8);
     const int occ = stream_ctas_per_sm(ss->depth);
     ss->ctas = c.ctas_per_sm > 0 ? std::min(c.ctas_per_sm, occ) : occ;
@@ -1142,10 +1159,10 @@ int lbl_session_create(lbl_roadmap rm, const lbl_grid *world, int32_t n_props, l
       e = launch_partition_into(rows + ss->edge0[c], ss->edge0[c + 1] - ss->edge0[c], ss->warps,
                                 ss->cpart + c * (ss->warps + 1), nullptr);
     if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ss->cs, cudaStreamNonBlocking);
-    for (int c = 0; c <= kSessionChunks && e == cudaSuccess; ++c)
-      e = cudaEventCreateWithFlags(&ss->ev[c], cudaEventDisableTiming);
   }
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ss->cs, cudaStreamNonBlocking);
+  for (int c = 0; c <= kSessionChunks && e == cudaSuccess; ++c)
+    e = cudaEventCreateWithFlags(&ss->ev[c], cudaEventDisableTiming);
   if (e != cudaSuccess) {
     lbl_session_free(ss);
     return cuda_fail(e, "session create");
@@ -1168,25 +1185,45 @@ int lbl_session_run(lbl_session ss, const uint8_t *h_planes, lbl_pose pose, uint
   }
   if (!same_device(ss->device)) return LBL_EINVAL;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(s);
+  // A chunked session touches only its own device memory (planes, O,
+  // pyramid, partitions, outputs) besides the roadmap's read-only rows, so
+  // its kernels run on its own stream `cc` and frame i+1 computes while frame
+  // i's results are still being copied out.  Other sessions label through
+  // lbl_label (roadmap-owned working memory), ordered on the caller's stream.
+  cudaStream_t cc = ss->chunked ? ss->cc : st;
   const size_t plane_bytes = static_cast<size_t>(ss->P) * grid_cells(ss->world);
-  const int k = static_cast<int>(ss->frame & 1);
-  cudaError_t e = cudaStreamWaitEvent(ss->cin, ss->ev_free[k], 0);  // slot k no longer read
+  const int k = static_cast<int>(ss->frame & 1);  // plane slot and output set of this frame
+  uint64_t *dL = ss->Ls[k], *dN = ss->Ns[k];
+  uint16_t *dV = ss->Vs[k];
+  // planes in on `cin` once slot k is no longer read
+  cudaError_t e = cudaStreamWaitEvent(ss->cin, ss->ev_free[k], 0);
   if (e == cudaSuccess && plane_bytes)
     e = cudaMemcpyAsync(ss->slot[k], h_planes, plane_bytes, cudaMemcpyHostToDevice, ss->cin);
   if (e == cudaSuccess) e = cudaEventRecord(ss->ev_in[k], ss->cin);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ss->ev_in[k], 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(cc, ss->ev_in[k], 0);
   if (e != cudaSuccess) return cuda_fail(e, "session run: copy planes");
-  int rc = lbl_frame_transform(&ss->world, ss->slot[k], ss->P, pose, &rm.agent, ss->O, s);
+  int rc = lbl_frame_transform(&ss->world, ss->slot[k], ss->P, pose, &rm.agent, ss->O, reinterpret_cast<lbl_stream>(cc));
   if (rc != LBL_OK) return rc;
-  if ((e = cudaEventRecord(ss->ev_free[k], st)) != cudaSuccess) return cuda_fail(e, "session run: event");
+  if ((e = cudaEventRecord(ss->ev_free[k], cc)) != cudaSuccess ||
+      (e = cudaStreamWaitEvent(cc, ss->ev_out[k], 0)) != cudaSuccess)  // output set k copied out (frame i-2)
+    return cuda_fail(e, "session run: event");
   ++ss->frame;
+  auto copy_out = [&](int64_t e0, int64_t n) {
+    cudaError_t r = cudaMemcpyAsync(h_L + e0, dL + e0, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost, ss->cs);
+    if (r == cudaSuccess && ss->mon && h_next)
+      r = cudaMemcpyAsync(h_next + e0, dN + e0, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost, ss->cs);
+    if (r == cudaSuccess && ss->mon && h_viol)
+      r = cudaMemcpyAsync(h_viol + e0, dV + e0, sizeof(uint16_t) * n, cudaMemcpyDeviceToHost, ss->cs);
+    return r;
+  };
   if (ss->chunked) {
     const void *base = ss->O;
     int wb = 8;
     if (ss->quad) {
       wb = quad_word_bytes(rm, ss->P);
-      if ((e = launch_quad_pyramid(rm, ss->O, wb, st)) != cudaSuccess) return cuda_fail(e, "session run: pyramid");
-      base = rm.pyr;
+      if ((e = launch_quad_pyramid(rm, ss->O, wb, ss->pyr, cc)) != cudaSuccess)
+        return cuda_fail(e, "session run: pyramid");
+      base = ss->pyr;
     }
     for (int c = 0; c < kSessionChunks; ++c) {
       const int64_t e0 = ss->edge0[c], n = ss->edge0[c + 1] - e0;
@@ -1194,33 +1231,25 @@ int lbl_session_run(lbl_session ss, const uint8_t *h_planes, lbl_pose pose, uint
       const StreamRows r{(ss->quad ? rm.qd_rowptr : rm.rowptr) + e0, ss->quad ? rm.qd_idx : rm.colidx,
                          ss->cpart + c * (ss->warps + 1), ss->ctas, n, ss->quad ? rm.n_qd : rm.nnz};
       MonitorTables t{};
-      if (ss->mon) t = tables_of(*ss->mon, ss->next + e0, ss->viol + e0);
-      e = launch_label_rows(r, base, wb, ss->P, ss->L + e0, ss->mon ? &t : nullptr, ss->depth, rm.num_sms, st);
-      if (e == cudaSuccess) e = cudaEventRecord(ss->ev[c], st);
+      if (ss->mon) t = tables_of(*ss->mon, dN + e0, dV + e0);
+      e = launch_label_rows(r, base, wb, ss->P, dL + e0, ss->mon ? &t : nullptr, ss->depth, rm.num_sms, cc);
+      if (e == cudaSuccess) e = cudaEventRecord(ss->ev[c], cc);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(ss->cs, ss->ev[c], 0);
-      if (e == cudaSuccess) e = cudaMemcpyAsync(h_L + e0, ss->L + e0, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost, ss->cs);
-      if (e == cudaSuccess && ss->mon && h_next)
-        e = cudaMemcpyAsync(h_next + e0, ss->next + e0, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost, ss->cs);
-      if (e == cudaSuccess && ss->mon && h_viol)
-        e = cudaMemcpyAsync(h_viol + e0, ss->viol + e0, sizeof(uint16_t) * n, cudaMemcpyDeviceToHost, ss->cs);
+      if (e == cudaSuccess) e = copy_out(e0, n);
       if (e != cudaSuccess) return cuda_fail(e, "session run: chunk");
     }
-    // the caller's stream sees the results once every copy has landed
-    if ((e = cudaEventRecord(ss->ev[kSessionChunks], ss->cs)) != cudaSuccess ||
-        (e = cudaStreamWaitEvent(st, ss->ev[kSessionChunks], 0)) != cudaSuccess)
-      return cuda_fail(e, "session run: join");
-    return LBL_OK;
+  } else {
+    rc = label_impl(ss->rm, ss->O, ss->P, dL, ss->mon, dN, dV, ss->has_cfg ? &ss->cfg : nullptr, cc);
+    if (rc != LBL_OK) return rc;
+    if ((e = cudaEventRecord(ss->ev[0], cc)) != cudaSuccess || (e = cudaStreamWaitEvent(ss->cs, ss->ev[0], 0)) != cudaSuccess ||
+        (rm.E > 0 && (e = copy_out(0, rm.E)) != cudaSuccess))
+      return cuda_fail(e, "session run: copy results");
   }
-  rc = label_impl(ss->rm, ss->O, ss->P, ss->L, ss->mon, ss->next, ss->viol, ss->has_cfg ? &ss->cfg : nullptr, st);
-  if (rc != LBL_OK) return rc;
-  if (rm.E > 0) {
-    e = cudaMemcpyAsync(h_L, ss->L, sizeof(uint64_t) * rm.E, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess && ss->mon && h_next)
-      e = cudaMemcpyAsync(h_next, ss->next, sizeof(uint64_t) * rm.E, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess && ss->mon && h_viol)
-      e = cudaMemcpyAsync(h_viol, ss->viol, sizeof(uint16_t) * rm.E, cudaMemcpyDeviceToHost, st);
-    if (e != cudaSuccess) return cuda_fail(e, "session run: copy results");
-  }
+  // output set k is free again once its copies land; the caller's stream sees
+  // the whole frame (copies in, kernels, copies out) before its next work
+  if ((e = cudaEventRecord(ss->ev_out[k], ss->cs)) != cudaSuccess ||
+      (e = cudaStreamWaitEvent(st, ss->ev_out[k], 0)) != cudaSuccess)
+    return cuda_fail(e, "session run: join");
   return LBL_OK;
 }
 
@@ -1236,6 +1265,10 @@ int lbl_session_free(lbl_session ss) {
   cudaFree(ss->cpart);
   if (ss->cs) cudaStreamDestroy(ss->cs);
   if (ss->cin) cudaStreamDestroy(ss->cin);
+  if (ss->cc) cudaStreamDestroy(ss->cc);
+  for (int k = 0; k < 2; ++k)
+    if (ss->ev_out[k]) cudaEventDestroy(ss->ev_out[k]);
+  cudaFree(ss->pyr);
   for (cudaEvent_t ev : ss->ev)
     if (ev) cudaEventDestroy(ev);
   for (int k = 0; k < 2; ++k) {

@@ -246,7 +246,8 @@ cudaError_t launch_label_rows(const StreamRows &r, const void *base, int word_by
 // quadtree form: pyramid of O, then the stream over the quadtree rows
 // pyramid word width for n_props propositions: 1, 2, 4 or 8 bytes
 int quad_word_bytes(const Roadmap &rm, int32_t P);
-cudaError_t launch_quad_pyramid(const Roadmap &rm, const uint64_t *O, int word_bytes, cudaStream_t s);
+// pyramid of O into `pyr` (rm.pyr, or a buffer of rm.pyr_words 64-bit words owned elsewhere)
+cudaError_t launch_quad_pyramid(const Roadmap &rm, const uint64_t *O, int word_bytes, void *pyr, cudaStream_t s);
 cudaError_t launch_label_quad(const Roadmap &rm, const uint64_t *O, int32_t P, uint64_t *L,
                                 const MonitorTables *mon, int depth, cudaStream_t s);
 cudaError_t launch_quad_pyramid_batch(const PyrTable &tab, cudaStream_t s);
