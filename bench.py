@@ -606,7 +606,8 @@ def run_batched(args, rank, world, local, dist, torch, L):
     nnz = sum(f.nnz for f in frames)
     entries = [L.lbl_roadmap_info(r)[4] if quad else f.nnz for f, r in zip(frames, rms)]
     bytes_step = sum(4 * n + 16 * f.n_edges + 8 * f.agent.cells + f.P * f.world.cells
-                     + (16 * pyramid_words(f.agent.cells) if quad else 0) for f, n in zip(frames, entries))
+                     + (2 * pyramid_word_bytes(f.P) * pyramid_words(f.agent.cells) if quad else 0)
+                     for f, n in zip(frames, entries))
     launches = 3 if quad else 2  # transform, (pyramid,) label
     plain_launches = len(frames) * launches
     peaks = measured_peaks()

@@ -344,7 +344,7 @@ __global__ void __launch_bounds__(kThreads, stream_min_blocks<2 * U>()) k_label_
 // global counter (zeroed before the launch), so the load stays balanced and
 // only the few items being worked on keep their O words hot in L2.  Monitor
 // tables, if any, are read through L1.
-template <int U, typename Off>
+template <int U, typename Off, typename W = uint64_t>
 __global__ void __launch_bounds__(kThreads, stream_min_blocks<U>()) k_label_batch(const __grid_constant__ BatchTable tab,
                                                           unsigned long long *__restrict__ next_unit) {
   const uint64_t pol = evict_first_policy();
@@ -369,8 +369,8 @@ __global__ void __launch_bounds__(kThreads, stream_min_blocks<U>()) k_label_batc
     const int64_t *part = it->part;
     const int64_t e_beg = __ldg(part + lu), e_end = __ldg(part + lu + 1);
     if (e_beg >= e_end) continue;
-    stream_range<U, Off>(it->rowptr, it->colidx, CsrGather{it->O}, e_beg, e_end, pol, lane,
-                         [&](int64_t e, uint64_t r) {
+    stream_range<U, Off>(it->rowptr, it->colidx, WordGather<W>{static_cast<const W *>(it->O)}, e_beg, e_end, pol,
+                         lane, [&](int64_t e, uint64_t r) {
       r &= it->mask;
       it->L[e] = r;
       const uint64_t *T = it->T;
@@ -441,7 +441,13 @@ __global__ void __launch_bounds__(kThreads) k_quad_pyramid_batch(const __grid_co
       hi = mid - 1;
   }
   const PyrItem &it = tab.items[lo];
-  quad_pyramid_block<uint64_t>(it.O, it.cells, it.off, it.pyr, b - it.block0, wsum);
+  const int64_t blk = b - it.block0;
+  switch (it.word_bytes) {  // CTA-uniform
+    case 1: quad_pyramid_block<uint8_t>(it.O, it.cells, it.off, static_cast<uint8_t *>(it.pyr), blk, wsum); break;
+    case 2: quad_pyramid_block<uint16_t>(it.O, it.cells, it.off, static_cast<uint16_t *>(it.pyr), blk, wsum); break;
+    case 4: quad_pyramid_block<uint32_t>(it.O, it.cells, it.off, static_cast<uint32_t *>(it.pyr), blk, wsum); break;
+    default: quad_pyramid_block<uint64_t>(it.O, it.cells, it.off, static_cast<uint64_t *>(it.pyr), blk, wsum);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -970,12 +976,25 @@ cudaError_t launch_label_batch(const BatchTable &tab, unsigned long long *counte
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
   const unsigned grid = static_cast<unsigned>(num_sms * ctas_per_sm);
-  if (tab.wide)
+  const int wb = tab.word_bytes ? tab.word_bytes : 8;
+  if (tab.wide) {
+    if (wb != 8) return cudaErrorInvalidValue;
     k_label_batch<8, int64_t><<<grid, kThreads, 0, s>>>(tab, counter);
-  else if (tab.depth == 12)
-    k_label_batch<12, int32_t><<<grid, kThreads, 0, s>>>(tab, counter);
-  else
-    k_label_batch<8, int32_t><<<grid, kThreads, 0, s>>>(tab, counter);
+  } else if (tab.depth == 12) {
+    switch (wb) {
+      case 1: k_label_batch<12, int32_t, uint8_t><<<grid, kThreads, 0, s>>>(tab, counter); break;
+      case 2: k_label_batch<12, int32_t, uint16_t><<<grid, kThreads, 0, s>>>(tab, counter); break;
+      case 4: k_label_batch<12, int32_t, uint32_t><<<grid, kThreads, 0, s>>>(tab, counter); break;
+      default: k_label_batch<12, int32_t><<<grid, kThreads, 0, s>>>(tab, counter);
+    }
+  } else {
+    switch (wb) {
+      case 1: k_label_batch<8, int32_t, uint8_t><<<grid, kThreads, 0, s>>>(tab, counter); break;
+      case 2: k_label_batch<8, int32_t, uint16_t><<<grid, kThreads, 0, s>>>(tab, counter); break;
+      case 4: k_label_batch<8, int32_t, uint32_t><<<grid, kThreads, 0, s>>>(tab, counter); break;
+      default: k_label_batch<8, int32_t><<<grid, kThreads, 0, s>>>(tab, counter);
+    }
+  }
   return cudaGetLastError();
 }
 

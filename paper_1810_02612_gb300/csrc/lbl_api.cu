@@ -197,9 +197,12 @@ struct lbl_batch_s {
   std::vector<int32_t> P;
   std::vector<lbl_monitor> mons;
   int64_t *part = nullptr;  // every item's partition, concatenated
-  unsigned long long *counter = nullptr;  // next work unit of the label launch
+  unsigned long long *counter = nullptr;  // next work unit of each class's label launch
   int ctas = 1;
-  BatchTable tab{};
+  // items grouped by gathered word width (class c = 1, 2, 4, 8 bytes); item i
+  // is entry slot[i] of tabs[cls[i]]
+  BatchTable tabs[kWordClasses]{};
+  std::vector<int> cls, slot;
   FrameTable ftab{};
   // items whose roadmap has the quadtree form label from their own pyramid
   uint64_t *pyr = nullptr;      // every such item's pyramid, concatenated
@@ -935,17 +938,20 @@ int lbl_batch_create(int32_t n, const lbl_roadmap *rms, const int32_t *n_props, 
   // kUnitsPerWarp per warp overall, at least one per item with edges.
   bool all_quad = true;
   for (int i = 0; i < n; ++i) all_quad = all_quad && (rms[i]->has_qd || rms[i]->E == 0);
-  b->tab.depth = all_quad ? kQuadDepth : 8;
-  const int occ = batch_ctas_per_sm(b->tab.depth);
+  const int depth = all_quad ? kQuadDepth : 8;
+  for (BatchTable &t : b->tabs) t.depth = depth;
+  const int occ = batch_ctas_per_sm(depth);
   const int ctas = ctas_per_sm > 0 ? std::min<int>(ctas_per_sm, occ) : occ;
   b->ctas = ctas;
   constexpr int64_t kUnitsPerWarp = 8;
   const int64_t units_target = static_cast<int64_t>(b->num_sms) * ctas * (kThreads / 32) * kUnitsPerWarp;
-  // entries streamed per item: quadtree entries when the roadmap has them
+  // entries streamed per item: quadtree entries when the roadmap has them;
+  // word width of its gathers (items of one width share a launch)
   auto entries = [](const Roadmap &r) { return r.has_qd ? r.n_qd : r.nnz; };
-  double total = 0;
-  for (int i = 0; i < n; ++i) total += static_cast<double>(entries(*rms[i]) + kEdgeCost * rms[i]->E);
-  const double unit_cost = total > 0 ? total / static_cast<double>(units_target) : 1.0;
+  auto width = [&](int i) { return rms[i]->has_qd && rms[i]->E > 0 ? quad_word_bytes(*rms[i], n_props[i]) : 8; };
+  // every class's launch gets about kUnitsPerWarp units per warp of its own
+  double total[kWordClasses] = {0, 0, 0, 0};
+  for (int i = 0; i < n; ++i) total[word_class(width(i))] += static_cast<double>(entries(*rms[i]) + kEdgeCost * rms[i]->E);
   std::vector<int64_t> W(n), off(n + 1, 0);
   int64_t pyr_words = 0;
   for (int i = 0; i < n; ++i)
@@ -955,21 +961,29 @@ int lbl_batch_create(int32_t n, const lbl_roadmap *rms, const int32_t *n_props, 
     W[i] = 0;
     if (r.E > 0) {
       const double c = static_cast<double>(entries(r) + kEdgeCost * r.E);
+      const double unit_cost = total[word_class(width(i))] / static_cast<double>(units_target);
       W[i] = std::max<int64_t>(1, static_cast<int64_t>(std::ceil(c / unit_cost)));
       W[i] = std::min<int64_t>(W[i], r.E);  // never more units than edges
     }
     off[i + 1] = off[i] + W[i] + 1;
   }
   cudaError_t e = dev_alloc(&b->part, static_cast<size_t>(off[n]), nullptr);
-  if (e == cudaSuccess) e = dev_alloc(&b->counter, 1, nullptr);
+  if (e == cudaSuccess) e = dev_alloc(&b->counter, kWordClasses, nullptr);
   if (e == cudaSuccess && pyr_words > 0) e = dev_alloc(&b->pyr, static_cast<size_t>(pyr_words), nullptr);
   b->pyr_slot.assign(n, -1);
-  int64_t warp0 = 0, pyr0 = 0, block0 = 0;
+  b->cls.assign(n, kWordClasses - 1);
+  b->slot.assign(n, 0);
+  int64_t pyr0 = 0, block0 = 0;
   for (int i = 0; i < n && e == cudaSuccess; ++i) {
     const Roadmap &r = *rms[i];
     const bool quad = r.has_qd && r.E > 0;
+    const int wb = width(i);
     e = launch_partition_into(quad ? r.qd_rowptr : r.rowptr, r.E, W[i], b->part + off[i], nullptr);
-    BatchItem &it = b->tab.items[i];
+    BatchTable &tb = b->tabs[word_class(wb)];
+    b->cls[i] = word_class(wb);
+    b->slot[i] = tb.n;
+    tb.word_bytes = wb;
+    BatchItem &it = tb.items[tb.n++];
     it = BatchItem{};
     it.rowptr = quad ? r.qd_rowptr : r.rowptr;
     it.colidx = quad ? r.qd_idx : r.colidx;
@@ -981,13 +995,14 @@ int lbl_batch_create(int32_t n, const lbl_roadmap *rms, const int32_t *n_props, 
       pi.cells = r.cells;
       pi.block0 = block0;
       pi.off = r.qd_off;
+      pi.word_bytes = wb;
       it.O = pi.pyr;
       b->pyr_slot[i] = b->ptab.n++;
       pyr0 += r.pyr_words;
       block0 += (r.cells + kThreads - 1) / kThreads;
     }
     it.mask = n_props[i] >= 64 ? ~0ull : ((1ull << n_props[i]) - 1ull);
-    it.warp0 = warp0;
+    it.warp0 = tb.total;  // work units of this class's launch
     it.warps = W[i];
     if (b->mons[i]) {
       const Monitor &m = *b->mons[i];
@@ -996,7 +1011,8 @@ int lbl_batch_create(int32_t n, const lbl_roadmap *rms, const int32_t *n_props, 
       it.m = m.m;
       for (int j = 0; j < 8; ++j) it.rel[j] = m.rel[j];
     }
-    warp0 += W[i];
+    tb.total += W[i];
+    if (entries(r) >= kNarrowLimit || r.E >= kNarrowLimit) tb.wide = 1;
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
   if (e != cudaSuccess) {
@@ -1007,11 +1023,6 @@ int lbl_batch_create(int32_t n, const lbl_roadmap *rms, const int32_t *n_props, 
     return cuda_fail(e, "batch create: partitions");
   }
   b->ptab.total = block0;
-  b->tab.n = n;
-  b->tab.total = warp0;
-  b->tab.wide = 0;
-  for (int i = 0; i < n; ++i)
-    if (entries(*rms[i]) >= kNarrowLimit || rms[i]->E >= kNarrowLimit) b->tab.wide = 1;
   b->ftab.n = n;
   *out = b;
   return LBL_OK;
@@ -1038,7 +1049,7 @@ int lbl_batch_set_frames(lbl_batch b, const lbl_frame *frames) {
     if (!frame_map(f.world, r.agent, f.pose, &m)) return LBL_EINVAL;
     b->ftab.items[i] = frame_item(m, f.world, r.agent, f.d_planes, P, f.d_O, cell0);
     cell0 += r.cells;
-    BatchItem &it = b->tab.items[i];
+    BatchItem &it = b->tabs[b->cls[i]].items[b->slot[i]];
     if (b->pyr_slot[i] >= 0)
       b->ptab.items[b->pyr_slot[i]].O = f.d_O;  // the item gathers from its pyramid
     else
@@ -1063,7 +1074,8 @@ int lbl_batch_launch(lbl_batch b, uint32_t stages, lbl_stream s) {
   if (stages & LBL_STAGE_TRANSFORM) e = launch_frame_batch(b->ftab, b->num_sms, st);
   if (e == cudaSuccess && (stages & LBL_STAGE_LABEL)) {
     e = launch_quad_pyramid_batch(b->ptab, st);
-    if (e == cudaSuccess) e = launch_label_batch(b->tab, b->counter, b->num_sms, b->ctas, st);
+    for (int c = 0; c < kWordClasses && e == cudaSuccess; ++c)
+      if (b->tabs[c].n > 0) e = launch_label_batch(b->tabs[c], b->counter + c, b->num_sms, b->ctas, st);
   }
   if (e != cudaSuccess) return cuda_fail(e, "batch launch");
   return LBL_OK;

@@ -49,7 +49,7 @@ struct BatchItem {
   const int64_t *rowptr;
   const int32_t *colidx;
   const int64_t *part;  // warps + 1 entries
-  const uint64_t *O;
+  const void *O;  // gather base: words of the table's word_bytes (O itself, or the item's pyramid)
   uint64_t *L, *next;
   uint16_t *viol;
   const uint64_t *T;  // monitor tables, NULL without a monitor
@@ -86,8 +86,9 @@ constexpr int kMaxBatch = 128;
 struct BatchTable {
   BatchItem items[kMaxBatch];
   int32_t n;
-  int32_t wide;   // some item has 2^31 - 4096 or more nonzeros or edges
+  int32_t wide;   // some item has 2^31 - 4096 or more nonzeros or edges (64-bit words only)
   int32_t depth;  // groups in flight per warp: 12 when every item streams quadtree rows, else 8
+  int32_t word_bytes;  // width of every item's gathered words: 1, 2, 4 or 8 (0 = 8)
   int64_t total;  // work units
 };
 struct FrameTable {
@@ -113,11 +114,15 @@ struct QuadOffsets {
 // One item of a batched pyramid launch: O of a frame -> that frame's pyramid.
 struct PyrItem {
   const uint64_t *O;
-  uint64_t *pyr;
+  void *pyr;       // words of word_bytes each
   int64_t cells;
   int64_t block0;  // first 256-cell block of this item in the launch
   QuadOffsets off;
+  int32_t word_bytes;  // 1, 2, 4 or 8
 };
+// Batched label launches group their items by gathered word width.
+constexpr int kWordClasses = 4;  // 1, 2, 4, 8 bytes
+inline int word_class(int word_bytes) { return word_bytes == 1 ? 0 : word_bytes == 2 ? 1 : word_bytes == 4 ? 2 : 3; }
 struct PyrTable {
   PyrItem items[128];
   int32_t n;
