@@ -224,9 +224,10 @@ def cpu_cores() -> int:
         return os.cpu_count() or 1
 
 
-def oracle_step_rate(wl, n_sample: int, threads: int):
-    """Oracle time for one frame on a sample of the workload's edges: frame
-    transform of the whole grid, labels of the first n_sample edges, monitor."""
+def oracle_step_times(wl, n_sample: int, threads: int):
+    """Oracle times on a sample of one frame: (total, transform) seconds for the
+    frame transform of the whole grid, labels of the first n_sample edges and
+    the monitor on them."""
     import oracle
     rp = wl.rowptr[: n_sample + 1]
     ci = wl.colidx[: int(rp[-1])]
@@ -235,11 +236,22 @@ def oracle_step_rate(wl, n_sample: int, threads: int):
         O = oracle.frame_transform3(wl.world, wl.planes, wl.pose, wl.agent)
     else:
         O = oracle.frame_transform(wl.world, wl.planes, wl.pose, wl.agent)
+    t_tr = time.perf_counter() - t
     Lw = oracle.label(rp, ci, O, wl.P, threads=threads)
     if wl.monitor is not None:
         m = wl.monitor
         oracle.monitor(m.n_states, m.m, m.relbits, m.delta, m.reject, Lw)
-    return time.perf_counter() - t
+    return time.perf_counter() - t, t_tr
+
+
+def oracle_step_rate(wl, n_sample: int, threads: int):
+    return oracle_step_times(wl, n_sample, threads)[0]
+
+
+def oracle_frame_seconds(wl, n_sample: int, t_total: float, t_transform: float) -> float:
+    """A whole frame's oracle time from a sample: the transform once, the
+    per-edge part scaled from n_sample edges to all of them."""
+    return t_transform + (t_total - t_transform) * wl.n_edges / max(n_sample, 1)
 
 
 def calibrate_sample(wl, seconds: float, threads: int) -> int:
@@ -265,14 +277,18 @@ def run_reference(args, rank, world):
     else:
         wl = synth.make(args.workload, seed=args.seed, edges=args.edges, threads=cpu_cores())
     threads = cpu_cores()
-    per_step = max(0.5, min(6.0, 120.0 / max(args.steps + args.warmup, 1)))
+    # about two minutes for the whole run: each step a sample of ~120 s / steps
+    # (at least 1,000 edges, at most the whole frame)
+    per_step = min(6.0, 120.0 / max(args.steps + args.warmup, 1))
     n = calibrate_sample(wl, per_step, threads)
     for _ in range(args.warmup):
         oracle_step_rate(wl, n, threads)
-    times = [oracle_step_rate(wl, n, threads) for _ in range(args.steps)]
-    tot = sum(times)
-    value = n * wl.P * args.steps / tot
-    sample = f"first {n} of {wl.n_edges} edges per step (whole-grid frame transform), {args.steps} steps"
+    samples = [oracle_step_times(wl, n, threads) for _ in range(args.steps)]
+    tot = sum(oracle_frame_seconds(wl, n, a, b) for a, b in samples)
+    value = wl.n_edges * wl.P * args.steps / tot
+    sample = (f"per step: whole-grid frame transform + labels (and monitor) of the first {n} of {wl.n_edges} "
+              f"edges; a whole frame's time = transform + label time x {wl.n_edges}/{n}; {args.steps} steps, "
+              f"{sum(a for a, b in samples):.1f} s of oracle work")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
@@ -481,10 +497,12 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         threads = cpu_cores()
         n = calibrate_sample(wl, args.cpu_seconds, threads)
-        dt = oracle_step_rate(wl, n, threads)
-        cpu = {"value": n * P / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+        dt, dtr = oracle_step_times(wl, n, threads)
+        cpu = {"value": E * P / oracle_frame_seconds(wl, n, dt, dtr), "unit": UNIT, "cores": threads,
+               "kind": "oracle",
                "sample": f"one frame: whole-grid frame transform + labels of the first {n} of {E} edges"
-                         + (" + monitor" if mon else "") + f" ({dt:.1f} s)"}
+                         + (" + monitor" if mon else "") + f" ({dt:.1f} s); a whole frame's time = transform"
+                         f" + label time x {E}/{n}"}
 
     if rank == 0:
         line = {
