@@ -26,6 +26,7 @@ import json
 import math
 import os
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -80,6 +81,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-csr-form", action="store_true", help="skip timing the CSR form beside the quadtree form")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--clocks-csv", default=None, help="keep the raw clock samples in this file")
     ap.add_argument("--rates", default="2000,5000,10000,15000", help="serving: request rates (req/s); the first is the "
                     "configured rate of the headline line, the others a saturation sweep")
     return ap.parse_args()
@@ -121,15 +123,22 @@ CLOCK_FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reaso
 
 
 class ClockSampler:
+    """nvidia-smi clock and throttle samples every 100 ms while the timed region
+    runs, into `path` (a temporary file unless --clocks-csv names one)."""
+
+    csv_path = None  # set from --clocks-csv
+
     def __init__(self, index: int, enabled: bool = True):
         self.proc = None
         self.path = None
         if not enabled:
             return
         try:
-            out = os.path.join(ROOT, "gpurun_out")
-            os.makedirs(out, exist_ok=True)
-            self.path = os.path.join(out, f"clocks_gpu{index}.csv")
+            if ClockSampler.csv_path:
+                self.path = ClockSampler.csv_path
+            else:
+                fd, self.path = tempfile.mkstemp(prefix=f"lbl_clocks_gpu{index}_", suffix=".csv")
+                os.close(fd)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={CLOCK_FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "100"],
@@ -156,6 +165,11 @@ class ClockSampler:
                 rows.append((ts, float(parts[1]), float(parts[2]), parts[5:9]))
             except ValueError:
                 continue
+        if not ClockSampler.csv_path:
+            try:
+                os.remove(self.path)
+            except OSError:
+                pass
         inside = [r for r in rows if t0 - 1.0 <= r[0] <= t1 + 1.0] or rows
         if not inside:
             return None
@@ -302,6 +316,7 @@ def run_reference(args, rank, world):
 
 def main():
     args = parse()
+    ClockSampler.csv_path = args.clocks_csv
     rank, world, local = dist_env()
     if args.impl == "reference":
         if world > 1:
