@@ -80,8 +80,12 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-csr-form", action="store_true", help="skip timing the CSR form beside the quadtree form")
+    ap.add_argument("--transform", default="auto", choices=["auto", "packed", "direct"],
+                    help="frame transform: planes packed into words, then one gather per agent cell; or byte "
+                         "gathers; auto packs as sessions do (planes of 8 MiB or more, world <= 4x agent cells)")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--clocks-csv", default=None, help="keep the raw clock samples in this file")
+    ap.add_argument("--steps-csv", default=None, help="write every timed step's device times (ms) to this file")
     ap.add_argument("--rates", default="2000,5000,10000,15000", help="serving: request rates (req/s); the first is the "
                     "configured rate of the headline line, the others a saturation sweep")
     return ap.parse_args()
@@ -377,10 +381,18 @@ def main():
         d_next = torch.empty(E, dtype=torch.uint64, device="cuda") if mon else None
         d_viol = torch.empty(E, dtype=torch.uint16, device="cuda") if mon else None
         flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+        d_words = torch.empty(wl.world.cells, dtype=getattr(torch, L.packed_word_dtype(P)), device="cuda")
     torch.cuda.synchronize()
+    if args.transform == "auto":
+        args.transform = ("packed" if P * wl.world.cells >= (8 << 20) and wl.world.cells <= 4 * wl.agent.cells
+                          else "direct")
 
     def transform():
-        L.lbl_frame_transform(wl.world, d_planes, P, wl.pose, wl.agent, d_O, stream=stream)
+        if args.transform == "packed":
+            L.lbl_pack_planes(wl.world, d_planes, P, d_words, stream=stream)
+            L.lbl_frame_transform_words(wl.world, d_words, P, wl.pose, wl.agent, d_O, stream=stream)
+        else:
+            L.lbl_frame_transform(wl.world, d_planes, P, wl.pose, wl.agent, d_O, stream=stream)
 
     def step():
         transform()
@@ -396,7 +408,8 @@ def main():
                 L.LBL_ALGO_QUAD: "quad"}.get(tuned["algo"], "csr")
     else:
         used = args.algo
-    launches_per_step = 2 + (1 if used in ("bittile", "quad") else 0)  # + planes / pyramid kernel
+    launches_per_step = (2 + (1 if used in ("bittile", "quad") else 0)  # + planes / pyramid kernel
+                         + (1 if args.transform == "packed" else 0))   # + packing kernel
 
     # ---- warm-up
     for _ in range(args.warmup):
@@ -427,6 +440,9 @@ def main():
     frame_ms = np.array([a.elapsed_time(b) for a, b, c in ev])
     label_ms = np.array([b.elapsed_time(c) for a, b, c in ev])
     clk = clocks.stop(t0, t1)
+    if args.steps_csv and rank == 0:
+        np.savetxt(args.steps_csv, np.stack([step_ms, frame_ms, label_ms], 1), fmt="%.5f",
+                   header="step_ms,transform_ms,label_ms", delimiter=",")
     total_ms = max_over_ranks(float(step_ms.sum()), dist, "cuda")
     value = job_throughput(world, E, P, args.steps, total_ms)
 
@@ -526,6 +542,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": WORKLOADS[args.workload], "name": args.workload, "edges": E, "nnz": wl.nnz,
                        "props": P, "grid": "x".join(str(v) for v in (wl.agent.w, wl.agent.h, wl.agent.d) if v > 1), "algo": used, "tuned": tuned,
+                       "transform": args.transform,
                        "monitor": bool(mon), "l2": "flushed before every step (256 MiB write); CSR "
                        f"{(4 * wl.nnz) / 1e9:.2f} GB > L2", "parallelism": f"replicas x{world}"},
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
@@ -641,8 +658,10 @@ def run_batched(args, rank, world, local, dist, torch, L):
     bytes_step = sum(4 * n + 16 * f.n_edges + 8 * f.agent.cells + f.P * f.world.cells
                      + (2 * pyramid_word_bytes(f.P) * pyramid_words(f.agent.cells) if quad else 0)
                      for f, n in zip(frames, entries))
-    launches = 3 if quad else 2  # transform, (pyramid,) label
-    plain_launches = len(frames) * launches
+    packs = any(f.P > 0 and f.world.cells <= 4 * f.agent.cells for f in frames)  # frames the batch packs
+    label_classes = len({pyramid_word_bytes(f.P) if quad else 8 for f in frames})  # one label launch per word width
+    launches = 1 + int(packs) + int(quad) + label_classes  # (pack,) transform, (pyramid,) labels
+    plain_launches = len(frames) * (3 if quad else 2)  # transform, (pyramid,) label per frame
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
     achieved = bytes_step / (total_b / args.steps / 1e3) / 1e9

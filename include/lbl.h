@@ -230,24 +230,30 @@ int lbl_frame_transform(const lbl_grid *world, const uint8_t *d_planes, int32_t 
 
 /*
  * lbl_pack_planes — the world planes as one word per world cell: bit p of
- * d_words[c] is set iff d_planes[p][c] != 0 (c in the world grid's row-major
- * cell order, time slabs outermost; the same cells lbl_frame_transform reads).
- *   d_planes  uint8[n_props][cells of world]   (device)
- *   d_words   uint64[cells of world]           (device, caller-owned; bits >= n_props zero)
- * One coalesced pass over the planes; with lbl_frame_transform_words it gives
- * exactly lbl_frame_transform's O.  LBL_EINVAL on a bad grid, n_props outside
- * 0..64 or a NULL buffer.  Asynchronous on `s`.
+ * word c is set iff d_planes[p][c] != 0 (c in the world grid's row-major cell
+ * order, time slabs outermost; the same cells lbl_frame_transform reads).
+ *   d_planes  uint8[n_props][cells of world]              (device)
+ *   d_words   cells of world words, each LBL_PACKED_WORD_BYTES(n_props)
+ *             bytes: uint8 for n_props <= 8, uint16 <= 16, uint32 <= 32,
+ *             else uint64 (device, caller-owned; bits >= n_props zero)
+ * One coalesced pass over the planes (whole 128-byte lines of a plane per
+ * warp load, with 4-byte aligned planes and a cell count divisible by 4; byte
+ * loads otherwise).  With lbl_frame_transform_words it gives exactly
+ * lbl_frame_transform's O.  LBL_EINVAL on a bad grid, n_props outside 0..64
+ * or a NULL buffer.  Asynchronous on `s`.
  */
-int lbl_pack_planes(const lbl_grid *world, const uint8_t *d_planes, int32_t n_props, uint64_t *d_words,
+#define LBL_PACKED_WORD_BYTES(n_props) ((n_props) <= 8 ? 1 : (n_props) <= 16 ? 2 : (n_props) <= 32 ? 4 : 8)
+int lbl_pack_planes(const lbl_grid *world, const uint8_t *d_planes, int32_t n_props, void *d_words,
                     lbl_stream s);
 
 /*
  * lbl_frame_transform_words — lbl_frame_transform (Sec. 5, eq. 13) reading the
- * packed words of lbl_pack_planes instead of the planes: one 8-byte gather per
- * agent cell instead of n_props byte gathers.  Word bits >= n_props are
- * ignored.  Same arguments, layouts and errors as lbl_frame_transform.
+ * packed words of lbl_pack_planes (LBL_PACKED_WORD_BYTES(n_props) bytes each)
+ * instead of the planes: one gather per agent cell instead of n_props byte
+ * gathers.  Word bits >= n_props are ignored.  Same arguments, layouts and
+ * errors as lbl_frame_transform.
  */
-int lbl_frame_transform_words(const lbl_grid *world, const uint64_t *d_words, int32_t n_props, lbl_pose pose,
+int lbl_frame_transform_words(const lbl_grid *world, const void *d_words, int32_t n_props, lbl_pose pose,
                               const lbl_grid *agent, uint64_t *d_O, lbl_stream s);
 
 /* --------------------------------------------------------------- monitor */
@@ -363,11 +369,18 @@ int lbl_roadmap_autotune(lbl_roadmap rm, const uint64_t *d_O, int32_t n_props, l
  *                     counter, so the load balances and few frames are live in
  *                     L2 at once.  ctas_per_sm 0 = as many as fit.
  *                     Synchronises the legacy default stream.
- * lbl_batch_set_frames  host-side only: frames[i] is item i's world planes,
- *                     pose and output buffers (see lbl_frame).  Checked here.
+ * lbl_batch_set_frames  frames[i] is item i's world planes, pose and output
+ *                     buffers (see lbl_frame).  Checked here.  Host-side, except
+ *                     that it allocates a larger packed-word buffer (cudaMalloc)
+ *                     when the packed worlds outgrow the batch's; the buffer it
+ *                     replaces stays allocated until lbl_batch_free, so graphs
+ *                     captured earlier remain valid.
  * lbl_batch_launch    enqueues on `s`, for the frames last set, the stages asked
- *                     for: LBL_STAGE_TRANSFORM (all frame transforms, one
- *                     launch) and/or LBL_STAGE_LABEL (all labels with the fused
+ *                     for: LBL_STAGE_TRANSFORM (all frame transforms: one launch
+ *                     packs the planes of every frame whose world has at most
+ *                     4x its agent's cells into 64-bit words, one launch
+ *                     transforms all frames, from those words or from the
+ *                     planes) and/or LBL_STAGE_LABEL (all labels with the fused
  *                     monitors, one launch after a 8-byte memset of the unit
  *                     counter; reads each frame's d_O).  It only enqueues
  *                     kernels and that memset, so it can be captured in a CUDA
@@ -448,7 +461,11 @@ int lbl_server_free(lbl_server srv);
  * copy the world planes in, transform them to the agent frame, label (with the
  * monitor, if any) and copy the results out.
  *   lbl_session_create  allocates the device buffers (planes, O, labels,
- *                       monitor outputs) for `world` and n_props.
+ *                       monitor outputs) for `world` and n_props; when the
+ *                       planes take 8 MiB or more and the world has at most
+ *                       4x the agent's cells, also a packed word per world
+ *                       cell, and each frame's transform is then
+ *                       lbl_pack_planes + lbl_frame_transform_words.
  *   lbl_session_run     enqueues H2D(h_planes) -> transform -> label -> D2H;
  *                       everything is ordered before the end of `s`.  h_planes:
  *                       uint8[n_props][world.d][world.h][world.w]; h_L: uint64[E];

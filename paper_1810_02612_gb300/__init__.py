@@ -4,4 +4,5 @@
 from . import lbl  # noqa: F401
 from .lbl import *  # noqa: F401,F403
 
-__all__ = list(lbl.EXPORTS) + ["LblError", "lbl_grid", "lbl_pose", "lbl_config"]
+__all__ = list(lbl.EXPORTS) + ["LblError", "lbl_grid", "lbl_pose", "lbl_config", "packed_word_bytes",
+                               "packed_word_dtype"]

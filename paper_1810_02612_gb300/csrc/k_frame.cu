@@ -17,15 +17,28 @@ __device__ __forceinline__ uint32_t gather_third_bits(uint64_t v) {
   return static_cast<uint32_t>(v);
 }
 
-// World word of agent cell idx of frame f (2-D or time-augmented).  The world
-// cell is the floor of exact Q32.32 affine maps of (ix, iy) and of the slab it.
-__device__ __forceinline__ uint64_t frame_word(const FrameItem &f, int64_t idx) {
-  int64_t ix, iy, it = 0;
+template <int WB> struct WordOf;
+template <> struct WordOf<1> { using T = uint8_t; };
+template <> struct WordOf<2> { using T = uint16_t; };
+template <> struct WordOf<4> { using T = uint32_t; };
+template <> struct WordOf<8> { using T = uint64_t; };
+
+// Coordinates (ix, iy, it) of agent cell idx of frame f in the grid's order.
+__device__ __forceinline__ void agent_coords(const FrameItem &f, int64_t idx, int64_t &ix, int64_t &iy,
+                                             int64_t &it) {
+  it = 0;
   if (f.ad > 1) {
     if (f.order == LBL_ORDER_MORTON) {
       ix = gather_third_bits(static_cast<uint64_t>(idx) >> 2);
       iy = gather_third_bits(static_cast<uint64_t>(idx) >> 1);
       it = gather_third_bits(static_cast<uint64_t>(idx));
+    } else if (f.small_index) {  // 32-bit division is several times cheaper than 64-bit
+      const uint32_t plane = static_cast<uint32_t>(f.aw) * static_cast<uint32_t>(f.ah);
+      const uint32_t i32 = static_cast<uint32_t>(idx);
+      const uint32_t t32 = i32 / plane, r = i32 - t32 * plane, y32 = r / static_cast<uint32_t>(f.aw);
+      it = t32;
+      iy = y32;
+      ix = r - y32 * static_cast<uint32_t>(f.aw);
     } else {
       const int64_t plane = static_cast<int64_t>(f.aw) * f.ah;
       it = idx / plane;
@@ -36,38 +49,86 @@ __device__ __forceinline__ uint64_t frame_word(const FrameItem &f, int64_t idx) 
   } else if (f.order == LBL_ORDER_MORTON) {
     ix = gather_even_bits(static_cast<uint64_t>(idx) >> 1);
     iy = gather_even_bits(static_cast<uint64_t>(idx));
+  } else if (f.small_index) {
+    const uint32_t i32 = static_cast<uint32_t>(idx), y32 = i32 / static_cast<uint32_t>(f.aw);
+    iy = y32;
+    ix = i32 - y32 * static_cast<uint32_t>(f.aw);
   } else {
     iy = idx / f.aw;
     ix = idx - iy * f.aw;
   }
+}
+
+// World word of agent cell (ix, iy, it) of frame f (2-D or time-augmented).
+// The world cell is the floor of exact Q32.32 affine maps of (ix, iy) and of
+// the slab it.  WB = 0 reads the P planes; WB = 1, 2, 4 or 8 reads packed
+// words that wide.
+template <int WB>
+__device__ __forceinline__ uint64_t world_word(const FrameItem &f, int64_t ix, int64_t iy, int64_t it) {
   const int64_t wx = (f.A00 * ix + f.A01 * iy + f.B0) >> 32;  // arithmetic shift: floor
   const int64_t wy = (f.A10 * ix + f.A11 * iy + f.B1) >> 32;
   const int64_t wt = f.wd > 1 ? ((f.At * it + f.Bt) >> 32) : 0;  // a 2-D world is static in time
   uint64_t word = 0;
-  if (wx >= 0 && wx < f.ww && wy >= 0 && wy < f.wh && wt >= 0 && wt < f.wd && f.words) {
-    word = __ldg(f.words + (wt * f.wh + wy) * f.ww + wx) & f.wmask;
-  } else if (wx >= 0 && wx < f.ww && wy >= 0 && wy < f.wh && wt >= 0 && wt < f.wd) {
-    const uint8_t *p = f.planes + (wt * f.wh + wy) * f.ww + wx;
-    int q = 0;
-    for (; q + 8 <= f.P; q += 8) {
-      uint8_t b[8];
+  if (wx >= 0 && wx < f.ww && wy >= 0 && wy < f.wh && wt >= 0 && wt < f.wd) {
+    const int64_t c = (wt * f.wh + wy) * f.ww + wx;
+    if constexpr (WB > 0) {
+      word = static_cast<uint64_t>(__ldg(static_cast<const typename WordOf<WB>::T *>(f.words) + c)) & f.wmask;
+    } else {
+      const uint8_t *p = f.planes + c;
+      int q = 0;
+      for (; q + 8 <= f.P; q += 8) {
+        uint8_t b[8];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) b[j] = __ldg(p + (q + j) * f.plane_cells);
+        for (int j = 0; j < 8; ++j) b[j] = __ldg(p + (q + j) * f.plane_cells);
 #pragma unroll
-      for (int j = 0; j < 8; ++j) word |= static_cast<uint64_t>(b[j] != 0) << (q + j);
+        for (int j = 0; j < 8; ++j) word |= static_cast<uint64_t>(b[j] != 0) << (q + j);
+      }
+      for (; q < f.P; ++q) word |= static_cast<uint64_t>(__ldg(p + q * f.plane_cells) != 0) << q;
     }
-    for (; q < f.P; ++q) word |= static_cast<uint64_t>(__ldg(p + q * f.plane_cells) != 0) << q;
   }
   return word;
 }
 
 // One thread per agent cell, in output (cell-order) index so the O stores are
 // coalesced.
+template <int WB>
+__device__ __forceinline__ uint64_t frame_word(const FrameItem &f, int64_t idx) {
+  int64_t ix, iy, it;
+  agent_coords(f, idx, ix, iy, it);
+  return world_word<WB>(f, ix, iy, it);
+}
+
+// Row-major agent grids: each warp takes an 8 x 4 tile of cells of one slab,
+// so under any rotation its world reads stay within a few rows (a warp along
+// one row would read a rotated line of up to 32 world rows); the tile's O
+// stores are four 64-byte runs.
+__device__ __forceinline__ uint32_t rowmajor_tiles(const FrameItem &f, uint32_t &tiles_x) {
+  tiles_x = (static_cast<uint32_t>(f.aw) + 7u) / 8u;
+  return tiles_x * ((static_cast<uint32_t>(f.ah) + 3u) / 4u);
+}
+
+// One thread per agent cell; Morton grids in cell order (a warp's 32 cells
+// are a 4 x 8 tile and its O stores coalesce), row-major grids by tiles.
+template <int WB>
 __global__ void __launch_bounds__(256) k_frame_transform(const __grid_constant__ FrameItem f) {
-  const int64_t n = static_cast<int64_t>(f.aw) * f.ah * f.ad;
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-  for (int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; idx < n; idx += stride)
-    f.O[idx] = frame_word(f, idx);
+  const int64_t t0 = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (f.order == LBL_ORDER_ROWMAJOR && f.small_index) {
+    uint32_t tx;
+    const uint32_t per_slab = rowmajor_tiles(f, tx);
+    const int64_t lanes = 32 * static_cast<int64_t>(per_slab) * f.ad;
+    for (int64_t t = t0; t < lanes; t += stride) {
+      const uint32_t tile = static_cast<uint32_t>(t >> 5), lane = static_cast<uint32_t>(t) & 31u;
+      const uint32_t slab = tile / per_slab, r = tile - slab * per_slab;
+      const uint32_t yt = r / tx, xt = r - yt * tx;
+      const uint32_t ix = 8u * xt + (lane & 7u), iy = 4u * yt + (lane >> 3);
+      if (ix < static_cast<uint32_t>(f.aw) && iy < static_cast<uint32_t>(f.ah))
+        f.O[(static_cast<int64_t>(slab) * f.ah + iy) * f.aw + ix] = world_word<WB>(f, ix, iy, slab);
+    }
+    return;
+  }
+  const int64_t n = static_cast<int64_t>(f.aw) * f.ah * f.ad;
+  for (int64_t idx = t0; idx < n; idx += stride) f.O[idx] = frame_word<WB>(f, idx);
 }
 
 // Batched frame transform: thread per (frame, agent cell) over all frames'
@@ -86,62 +147,101 @@ __global__ void __launch_bounds__(256) k_frame_batch(const __grid_constant__ Fra
     }
     const FrameItem &f = tab.items[lo];
     const int64_t idx = gidx - f.cell0;
-    f.O[idx] = frame_word(f, idx);
+    f.O[idx] = f.words ? frame_word<8>(f, idx) : frame_word<0>(f, idx);  // packed items: 64-bit words
   }
 }
 
-// Packing: lane quad (4 consecutive lanes) per group of four world cells;
-// lane q of the quad reads planes q, q+4, q+8, ... of the group (4 bytes at a
-// time when the planes are 4-byte aligned and the cell count divisible by 4),
-// so all of a lane's loads are in flight at once; the quad ORs its partial
-// words by two shuffles and lane j stores the word of cell 4g + j.
-// `t` is the global lane index; lanes past the last group only shuffle.
-__device__ __forceinline__ void pack_quad(const PackItem &it, int64_t t, bool valid) {
-  const int q = static_cast<int>(t & 3);
-  const int64_t g = t >> 2;
-  const int64_t c0 = 4 * g;
-  uint64_t w[4] = {0, 0, 0, 0};
-  if (valid) {
-    const bool vec = ((reinterpret_cast<uintptr_t>(it.planes) | static_cast<uintptr_t>(it.cells)) & 3u) == 0;
-    uint32_t v[16];
+// Packing: a lane per four consecutive world cells.  For each plane the lane
+// reads its cells' four bytes (one 4-byte load when the planes allow it), so a
+// warp reads a whole 128-byte line of a plane per load instruction and NB
+// planes are in flight per lane.  "byte != 0" becomes bit 7 of each byte
+// without carries between bytes, and the plane loop is unrolled so the bit
+// moves to position p of the cell's word by constant shifts.  Each lane stores
+// its four words as one vector (two for 8-byte words) when VEC holds.
+template <int WB, bool VEC>
+__device__ __forceinline__ void pack_lane(const PackItem &it, int64_t lane) {
+  using T = typename WordOf<WB>::T;
+  constexpr int NB = WB == 8 || WB == 4 ? 32 : 8 * WB;  // planes per batch of loads
+  constexpr int PMAX = 8 * WB;
+  const int64_t c0 = 4 * lane;
+  if (c0 >= it.cells) return;
+  uint32_t lo[4] = {0, 0, 0, 0}, hi[4] = {0, 0, 0, 0};
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      const int p = q + 4 * i;
+  for (int b = 0; b < PMAX / NB; ++b) {
+    if (b * NB >= it.P) break;
+    uint32_t v[NB];
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+      const int p = b * NB + i;
       uint32_t x = 0;
       if (p < it.P) {
-        const uint8_t *pl = it.planes + p * it.cells;
-        if (vec) {
-          x = __ldg(reinterpret_cast<const uint32_t *>(pl + c0));
+        const uint8_t *pl = it.planes + p * it.cells + c0;
+        if (VEC) {
+          x = __ldg(reinterpret_cast<const uint32_t *>(pl));
         } else {
 #pragma unroll
           for (int j = 0; j < 4; ++j)
-            if (c0 + j < it.cells) x |= static_cast<uint32_t>(__ldg(pl + c0 + j)) << (8 * j);
+            if (c0 + j < it.cells) x |= static_cast<uint32_t>(__ldg(pl + j)) << (8 * j);
         }
       }
       v[i] = x;
     }
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      const int p = q + 4 * i;
+    for (int i = 0; i < NB; ++i) {
+      const uint32_t x = v[i];
+      const uint32_t nz = (((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x) & 0x80808080u;
+      const int p = b * NB + i;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) w[j] |= static_cast<uint64_t>((v[i] >> (8 * j)) & 0xFFu ? 1u : 0u) << p;
+      for (int k = 0; k < 4; ++k) {
+        const uint32_t bit = (nz >> (8 * k + 7)) & 1u;
+        if (p < 32)
+          lo[k] |= bit << p;
+        else
+          hi[k] |= bit << (p - 32);
+      }
     }
   }
+  T *w = static_cast<T *>(it.words) + c0;
+  if (VEC) {
+    if constexpr (WB == 8) {
+      reinterpret_cast<uint4 *>(w)[0] = make_uint4(lo[0], hi[0], lo[1], hi[1]);
+      reinterpret_cast<uint4 *>(w)[1] = make_uint4(lo[2], hi[2], lo[3], hi[3]);
+    } else if constexpr (WB == 4) {
+      *reinterpret_cast<uint4 *>(w) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+    } else if constexpr (WB == 2) {
+      *reinterpret_cast<uint2 *>(w) = make_uint2(lo[0] | (lo[1] << 16), lo[2] | (lo[3] << 16));
+    } else {
+      *reinterpret_cast<uint32_t *>(w) = lo[0] | (lo[1] << 8) | (lo[2] << 16) | (lo[3] << 24);
+    }
+  } else {
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    w[j] |= __shfl_xor_sync(0xffffffffu, w[j], 1);
-    w[j] |= __shfl_xor_sync(0xffffffffu, w[j], 2);
+    for (int k = 0; k < 4; ++k)
+      if (c0 + k < it.cells) w[k] = static_cast<T>(lo[k] | (static_cast<uint64_t>(hi[k]) << 32));
   }
-  if (valid && c0 + q < it.cells) it.words[c0 + q] = q == 0 ? w[0] : q == 1 ? w[1] : q == 2 ? w[2] : w[3];
 }
 
+template <int WB, bool VEC>
 __global__ void __launch_bounds__(256) k_pack_planes(const __grid_constant__ PackItem it) {
-  const int64_t lanes = 4 * ((it.cells + 3) / 4);
-  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-  // the loop bound is tested on the warp's first lane, so whole warps iterate together
-  for (int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; t - (threadIdx.x & 31) < lanes;
-       t += stride)
-    pack_quad(it, t, t < lanes);
+  pack_lane<WB, VEC>(it, static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x);
+}
+
+// Batched packing: the item of a lane by binary search over the items' first
+// lanes; every item packs into 64-bit words.
+__global__ void __launch_bounds__(256) k_pack_batch(const __grid_constant__ PackTable tab) {
+  const int64_t g = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (g >= tab.lane0[tab.n]) return;
+  int lo = 0, hi = tab.n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (tab.lane0[mid] <= g)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  if (tab.vec[lo])
+    pack_lane<8, true>(tab.items[lo], g - tab.lane0[lo]);
+  else
+    pack_lane<8, false>(tab.items[lo], g - tab.lane0[lo]);
 }
 
 // letter = sum_j bit(L, rel[j]) << j ; next/viol from the per-letter tables.
@@ -172,17 +272,51 @@ cudaError_t launch_frame_transform(const FrameItem &f, int num_sms, cudaStream_t
   int64_t blocks = (n + 255) / 256;
   const int64_t cap = static_cast<int64_t>(num_sms) * 8;
   if (blocks > cap) blocks = cap;
-  k_frame_transform<<<static_cast<unsigned>(blocks), 256, 0, s>>>(f);
+  const unsigned g = static_cast<unsigned>(blocks);
+  switch (f.words ? f.word_bytes : 0) {
+    case 0: k_frame_transform<0><<<g, 256, 0, s>>>(f); break;
+    case 1: k_frame_transform<1><<<g, 256, 0, s>>>(f); break;
+    case 2: k_frame_transform<2><<<g, 256, 0, s>>>(f); break;
+    case 4: k_frame_transform<4><<<g, 256, 0, s>>>(f); break;
+    case 8: k_frame_transform<8><<<g, 256, 0, s>>>(f); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 
-cudaError_t launch_pack_planes(const PackItem &it, int num_sms, cudaStream_t s) {
-  const int64_t lanes = 4 * ((it.cells + 3) / 4);
+template <int WB>
+static void pack_launch(const PackItem &it, bool vec, unsigned blocks, cudaStream_t s) {
+  if (vec)
+    k_pack_planes<WB, true><<<blocks, 256, 0, s>>>(it);
+  else
+    k_pack_planes<WB, false><<<blocks, 256, 0, s>>>(it);
+}
+
+// vector loads and stores: 4-byte aligned planes, whole lanes, words aligned to the lane's store
+bool pack_vec_ok(const PackItem &it) {
+  const uintptr_t store_align = it.word_bytes >= 4 ? 16 : 4 * static_cast<uintptr_t>(it.word_bytes);
+  return (reinterpret_cast<uintptr_t>(it.planes) & 3u) == 0 && it.cells % 4 == 0 &&
+         (reinterpret_cast<uintptr_t>(it.words) & (store_align - 1)) == 0;
+}
+
+cudaError_t launch_pack_planes(const PackItem &it, cudaStream_t s) {
+  const int64_t lanes = (it.cells + 3) / 4;
   if (lanes == 0) return cudaSuccess;
-  int64_t blocks = (lanes + 255) / 256;
-  const int64_t cap = static_cast<int64_t>(num_sms) * 8;
-  if (blocks > cap) blocks = cap;
-  k_pack_planes<<<static_cast<unsigned>(blocks), 256, 0, s>>>(it);
+  const unsigned blocks = static_cast<unsigned>((lanes + 255) / 256);
+  const bool vec = pack_vec_ok(it);
+  switch (it.word_bytes) {
+    case 1: pack_launch<1>(it, vec, blocks, s); break;
+    case 2: pack_launch<2>(it, vec, blocks, s); break;
+    case 4: pack_launch<4>(it, vec, blocks, s); break;
+    case 8: pack_launch<8>(it, vec, blocks, s); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_batch(const PackTable &tab, cudaStream_t s) {
+  if (tab.n == 0 || tab.lane0[tab.n] == 0) return cudaSuccess;
+  k_pack_batch<<<static_cast<unsigned>((tab.lane0[tab.n] + 255) / 256), 256, 0, s>>>(tab);
   return cudaGetLastError();
 }
 

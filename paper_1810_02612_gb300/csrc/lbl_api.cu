@@ -168,8 +168,10 @@ bool frame_map(const lbl_grid &W, const lbl_grid &A, const lbl_pose &p, FrameMap
 
 FrameItem frame_item(const FrameMap &m, const lbl_grid &W, const lbl_grid &A, const uint8_t *planes, int32_t P,
                      uint64_t *O, int64_t cell0) {
-  return FrameItem{m.A00, m.A01, m.B0, m.A10, m.A11, m.B1, m.At, m.Bt, planes, O, grid_cells(W), cell0,
-                   W.w, W.h, grid_depth(W), A.w, A.h, grid_depth(A), P, A.order};
+  FrameItem f{m.A00, m.A01, m.B0, m.A10, m.A11, m.B1, m.At, m.Bt, planes, O, grid_cells(W), cell0,
+              W.w, W.h, grid_depth(W), A.w, A.h, grid_depth(A), P, A.order};
+  f.small_index = grid_cells(A) < (1ll << 32);
+  return f;
 }
 
 void set_error(const char *fmt, ...) {
@@ -208,6 +210,14 @@ struct lbl_batch_s {
   uint64_t *pyr = nullptr;      // every such item's pyramid, concatenated
   std::vector<int> pyr_slot;    // item -> entry of ptab, or -1
   PyrTable ptab{};
+  // frames whose world has at most kPackedWorldRatio times the agent's cells
+  // are packed (one launch) and transformed from 64-bit words; the words
+  // buffer grows on demand, and a replaced buffer is kept until the batch is
+  // freed so graphs captured before still see live memory
+  PackTable pktab{};
+  uint64_t *words = nullptr;
+  int64_t words_cap = 0;
+  std::vector<uint64_t *> retired;
   bool frames_set = false;
 };
 
@@ -237,6 +247,11 @@ struct lbl_session_s {
   uint16_t *Vs[2] = {nullptr, nullptr};
   cudaEvent_t ev_out[2] = {nullptr, nullptr};
   uint64_t *pyr = nullptr;  // the session's own quadtree pyramid (chunked quadtree sessions)
+  // Packed world words: the planes are packed (one coalesced pass) and the
+  // transform gathers one word per agent cell.  Used for planes of at least
+  // kPackedMinPlaneBytes on a world of at most kPackedWorldRatio times the
+  // agent's cells, so packing reads little the transform would not.
+  uint8_t *words = nullptr;
   // Chunked labeling: the edges in kSessionChunks ranges, each labeled by the
   // whole grid; a range's results go to the host on `cs` while the next range
   // is labeled.  Used with the default form (quadtree, else streaming CSR).
@@ -579,7 +594,7 @@ int lbl_frame_transform(const lbl_grid *world, const uint8_t *d_planes, int32_t 
   return LBL_OK;
 }
 
-int lbl_pack_planes(const lbl_grid *world, const uint8_t *d_planes, int32_t n_props, uint64_t *d_words,
+int lbl_pack_planes(const lbl_grid *world, const uint8_t *d_planes, int32_t n_props, void *d_words,
                     lbl_stream s) {
   g_err.clear();
   if (!valid_grid(world, "pack planes (world)", false)) return LBL_EINVAL;
@@ -591,16 +606,13 @@ int lbl_pack_planes(const lbl_grid *world, const uint8_t *d_planes, int32_t n_pr
     set_error("pack planes: NULL buffer");
     return LBL_EINVAL;
   }
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return cuda_fail(e, "pack planes: cudaGetDevice");
-  PackItem it{d_planes, d_words, grid_cells(*world), n_props};
-  e = launch_pack_planes(it, device_sms(dev), reinterpret_cast<cudaStream_t>(s));
+  const PackItem it{d_planes, d_words, grid_cells(*world), n_props, packed_word_bytes(n_props)};
+  cudaError_t e = launch_pack_planes(it, reinterpret_cast<cudaStream_t>(s));
   if (e != cudaSuccess) return cuda_fail(e, "pack planes: launch");
   return LBL_OK;
 }
 
-int lbl_frame_transform_words(const lbl_grid *world, const uint64_t *d_words, int32_t n_props, lbl_pose pose,
+int lbl_frame_transform_words(const lbl_grid *world, const void *d_words, int32_t n_props, lbl_pose pose,
                               const lbl_grid *agent, uint64_t *d_O, lbl_stream s) {
   g_err.clear();
   if (!valid_grid(world, "frame transform (world)", false) || !valid_grid(agent, "frame transform (agent)", true))
@@ -620,6 +632,7 @@ int lbl_frame_transform_words(const lbl_grid *world, const uint64_t *d_words, in
   if (e != cudaSuccess) return cuda_fail(e, "frame transform: cudaGetDevice");
   FrameItem f = frame_item(m, *world, *agent, nullptr, n_props, d_O, 0);
   f.words = d_words;
+  f.word_bytes = packed_word_bytes(n_props);
   f.wmask = n_props >= 64 ? ~0ull : ((1ull << n_props) - 1ull);
   e = launch_frame_transform(f, device_sms(dev), reinterpret_cast<cudaStream_t>(s));
   if (e != cudaSuccess) return cuda_fail(e, "frame transform: launch");
@@ -1059,6 +1072,41 @@ int lbl_batch_set_frames(lbl_batch b, const lbl_frame *frames) {
     it.viol = f.d_viol;
   }
   b->ftab.total = cell0;
+  // packed frames: 64-bit words at 4-word aligned offsets (vector stores)
+  int64_t need = 0;
+  std::vector<int64_t> woff(b->n, -1);
+  for (int i = 0; i < b->n; ++i) {
+    const int64_t wc = grid_cells(frames[i].world);
+    if (b->P[i] > 0 && wc > 0 && wc <= kPackedWorldRatio * b->rms[i]->cells) {
+      woff[i] = need;
+      need += (wc + 3) / 4 * 4;
+    }
+  }
+  if (need > b->words_cap) {
+    uint64_t *w = nullptr;
+    cudaError_t e = dev_alloc(&w, static_cast<size_t>(need), nullptr);
+    if (e != cudaSuccess) return cuda_fail(e, "batch frames: packed words");
+    if (b->words) b->retired.push_back(b->words);
+    b->words = w;
+    b->words_cap = need;
+  }
+  PackTable &pt = b->pktab;
+  pt.n = 0;
+  pt.lane0[0] = 0;
+  for (int i = 0; i < b->n; ++i) {
+    FrameItem &fi = b->ftab.items[i];
+    fi.words = nullptr;
+    if (woff[i] < 0) continue;
+    const int32_t P = b->P[i];
+    const PackItem it{frames[i].d_planes, b->words + woff[i], grid_cells(frames[i].world), P, 8};
+    pt.items[pt.n] = it;
+    pt.vec[pt.n] = pack_vec_ok(it) ? 1 : 0;
+    pt.lane0[pt.n + 1] = pt.lane0[pt.n] + (it.cells + 3) / 4;
+    ++pt.n;
+    fi.words = it.words;
+    fi.word_bytes = 8;
+    fi.wmask = P >= 64 ? ~0ull : ((1ull << P) - 1ull);
+  }
   b->frames_set = true;
   return LBL_OK;
 }
@@ -1071,7 +1119,10 @@ int lbl_batch_launch(lbl_batch b, uint32_t stages, lbl_stream s) {
   }
   cudaStream_t st = reinterpret_cast<cudaStream_t>(s);
   cudaError_t e = cudaSuccess;
-  if (stages & LBL_STAGE_TRANSFORM) e = launch_frame_batch(b->ftab, b->num_sms, st);
+  if (stages & LBL_STAGE_TRANSFORM) {
+    e = launch_pack_batch(b->pktab, st);
+    if (e == cudaSuccess) e = launch_frame_batch(b->ftab, b->num_sms, st);
+  }
   if (e == cudaSuccess && (stages & LBL_STAGE_LABEL)) {
     e = launch_quad_pyramid_batch(b->ptab, st);
     for (int c = 0; c < kWordClasses && e == cudaSuccess; ++c)
@@ -1088,6 +1139,8 @@ int lbl_batch_free(lbl_batch b) {
   cudaFree(b->part);
   cudaFree(b->counter);
   cudaFree(b->pyr);
+  cudaFree(b->words);
+  for (uint64_t *w : b->retired) cudaFree(w);
   delete b;
   return LBL_OK;
 }
@@ -1134,6 +1187,9 @@ int lbl_session_create(lbl_roadmap rm, const lbl_grid *world, int32_t n_props, l
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ss->ev_free[k], cudaEventDisableTiming);
   }
   if (e == cudaSuccess) e = dev_alloc(&ss->O, static_cast<size_t>(rm->cells), nullptr);
+  if (e == cudaSuccess && static_cast<int64_t>(plane_bytes) >= kPackedMinPlaneBytes &&
+      grid_cells(*world) <= kPackedWorldRatio * rm->cells)
+    e = dev_alloc(&ss->words, static_cast<size_t>(grid_cells(*world)) * packed_word_bytes(n_props), nullptr);
   if (e == cudaSuccess) e = dev_alloc(&ss->L, static_cast<size_t>(2 * rm->E), nullptr);
   if (e == cudaSuccess && mon) e = dev_alloc(&ss->next, static_cast<size_t>(2 * rm->E), nullptr);
   if (e == cudaSuccess && mon) e = dev_alloc(&ss->viol, static_cast<size_t>(2 * rm->E), nullptr);
@@ -1214,7 +1270,14 @@ int lbl_session_run(lbl_session ss, const uint8_t *h_planes, lbl_pose pose, uint
   if (e == cudaSuccess) e = cudaEventRecord(ss->ev_in[k], ss->cin);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(cc, ss->ev_in[k], 0);
   if (e != cudaSuccess) return cuda_fail(e, "session run: copy planes");
-  int rc = lbl_frame_transform(&ss->world, ss->slot[k], ss->P, pose, &rm.agent, ss->O, reinterpret_cast<lbl_stream>(cc));
+  int rc = LBL_OK;
+  if (ss->words) {
+    const PackItem it{ss->slot[k], ss->words, grid_cells(ss->world), ss->P, packed_word_bytes(ss->P)};
+    if ((e = launch_pack_planes(it, cc)) != cudaSuccess) return cuda_fail(e, "session run: pack planes");
+    rc = lbl_frame_transform_words(&ss->world, ss->words, ss->P, pose, &rm.agent, ss->O, reinterpret_cast<lbl_stream>(cc));
+  } else {
+    rc = lbl_frame_transform(&ss->world, ss->slot[k], ss->P, pose, &rm.agent, ss->O, reinterpret_cast<lbl_stream>(cc));
+  }
   if (rc != LBL_OK) return rc;
   if ((e = cudaEventRecord(ss->ev_free[k], cc)) != cudaSuccess ||
       (e = cudaStreamWaitEvent(cc, ss->ev_out[k], 0)) != cudaSuccess)  // output set k copied out (frame i-2)
@@ -1281,6 +1344,7 @@ int lbl_session_free(lbl_session ss) {
   for (int k = 0; k < 2; ++k)
     if (ss->ev_out[k]) cudaEventDestroy(ss->ev_out[k]);
   cudaFree(ss->pyr);
+  cudaFree(ss->words);
   for (cudaEvent_t ev : ss->ev)
     if (ev) cudaEventDestroy(ev);
   for (int k = 0; k < 2; ++k) {

@@ -69,17 +69,28 @@ struct FrameItem {
   int64_t plane_cells;  // ww * wh * wd
   int64_t cell0;        // first global cell of this frame
   int32_t ww, wh, wd, aw, ah, ad, P, order;
-  const uint64_t *words;  // packed world words (bit p = plane p), or NULL: read the planes
-  uint64_t wmask;         // 2^P - 1, applied to packed words
+  const void *words;  // packed world words (bit p = plane p), or NULL: read the planes
+  uint64_t wmask;     // 2^P - 1, applied to packed words
+  int32_t word_bytes; // width of a packed word: 1, 2, 4 or 8
+  bool small_index;   // agent cells < 2^32: cell coordinates by 32-bit division
 };
 
 // Packing world planes into one word per world cell (bit p = plane p != 0).
 struct PackItem {
   const uint8_t *planes;
-  uint64_t *words;
-  int64_t cells;  // world cells (w * h * d)
+  void *words;         // cells words of word_bytes each
+  int64_t cells;       // world cells (w * h * d)
   int32_t P;
+  int32_t word_bytes;  // 1, 2, 4 or 8, at least P bits
 };
+
+// Width of a packed world word: the narrowest of 1, 2, 4 and 8 bytes that holds P bits.
+inline int packed_word_bytes(int32_t P) { return P <= 8 ? 1 : P <= 16 ? 2 : P <= 32 ? 4 : 8; }
+// Sessions pack the planes when they hold at least kPackedMinPlaneBytes (below
+// that, a second small launch costs more than the byte gathers it saves) and
+// the world has at most kPackedWorldRatio times the agent's cells.
+constexpr int64_t kPackedMinPlaneBytes = 8ll << 20;
+constexpr int64_t kPackedWorldRatio = 4;
 
 // Batched launches take their whole item table as one kernel parameter.
 constexpr int kMaxBatch = 128;
@@ -95,6 +106,15 @@ struct FrameTable {
   FrameItem items[kMaxBatch];
   int32_t n;
   int64_t total;  // cells
+};
+
+// Batched packing: item i packs lanes [lane0[i], lane0[i+1]) of the launch, a
+// lane per four world cells, into 64-bit words.
+struct PackTable {
+  PackItem items[kMaxBatch];
+  int32_t vec[kMaxBatch];  // the item's planes and words allow vector loads and stores
+  int64_t lane0[kMaxBatch + 1];
+  int32_t n;
 };
 
 // Levels of the quadtree form: blocks of up to 4^4 = 256 cells.
@@ -228,7 +248,9 @@ FrameItem frame_item(const FrameMap &m, const lbl_grid &W, const lbl_grid &A, co
                      uint64_t *O, int64_t cell0);
 
 cudaError_t launch_frame_transform(const FrameItem &f, int num_sms, cudaStream_t s);
-cudaError_t launch_pack_planes(const PackItem &it, int num_sms, cudaStream_t s);
+cudaError_t launch_pack_planes(const PackItem &it, cudaStream_t s);
+cudaError_t launch_pack_batch(const PackTable &tab, cudaStream_t s);
+bool pack_vec_ok(const PackItem &it);
 
 cudaError_t launch_label_csr(const Roadmap &rm, const uint64_t *O, int32_t P, uint64_t *L, const MonitorTables *mon,
                              int lanes_per_edge, bool early_exit, int ctas_per_sm, cudaStream_t s);

@@ -289,15 +289,42 @@ def lbl_frame_transform(world, d_planes, n_props: int, pose, agent, d_O, stream=
                                       _pose(pose), ctypes.byref(a), _dev(d_O, "uint64", "O"), _stream(stream)))
 
 
+def packed_word_bytes(n_props: int) -> int:
+    """Bytes of one packed world word (LBL_PACKED_WORD_BYTES)."""
+    return 1 if n_props <= 8 else 2 if n_props <= 16 else 4 if n_props <= 32 else 8
+
+
+_PACKED_DTYPES = {1: "uint8", 2: "int16", 4: "int32", 8: "uint64"}
+
+
+def packed_word_dtype(n_props: int) -> str:
+    """torch dtype name for a buffer of packed world words (the bits are what
+    count: 16- and 32-bit words use the signed types torch supports everywhere)."""
+    return _PACKED_DTYPES[packed_word_bytes(n_props)]
+
+
+def _words(x, n_props: int, what: str):
+    if isinstance(x, int) or x is None:
+        return x
+    wb = packed_word_bytes(n_props)
+    if not _is_torch(x) or not x.is_cuda:
+        raise TypeError(f"{what}: expected a CUDA tensor")
+    if x.element_size() != wb or x.is_floating_point() or x.is_complex() or str(x.dtype) == "torch.bool":
+        raise TypeError(f"{what}: expected {wb}-byte integer words for {n_props} propositions, got {x.dtype}")
+    if not x.is_contiguous():
+        raise ValueError(f"{what}: tensor must be contiguous")
+    return x.data_ptr()
+
+
 def lbl_pack_planes(world, d_planes, n_props: int, d_words, stream=None) -> None:
     w = _grid(world)
     _check(load().lbl_pack_planes(ctypes.byref(w), _dev(d_planes, "uint8", "planes"), int(n_props),
-                                  _dev(d_words, "uint64", "words"), _stream(stream)))
+                                  _words(d_words, n_props, "words"), _stream(stream)))
 
 
 def lbl_frame_transform_words(world, d_words, n_props: int, pose, agent, d_O, stream=None) -> None:
     w, a = _grid(world), _grid(agent)
-    _check(load().lbl_frame_transform_words(ctypes.byref(w), _dev(d_words, "uint64", "words"), int(n_props),
+    _check(load().lbl_frame_transform_words(ctypes.byref(w), _words(d_words, n_props, "words"), int(n_props),
                                             _pose(pose), ctypes.byref(a), _dev(d_O, "uint64", "O"),
                                             _stream(stream)))
 

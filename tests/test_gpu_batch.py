@@ -1,7 +1,9 @@
 """Batched frames: one plan over roadmaps of uneven size, grid order, proposition
-count, monitor and form (CSR or quadtree, the same roadmap twice); every
-item's outputs equal the per-frame entry points' and the oracle's, also when
-the launch is captured in a CUDA graph and replayed."""
+count, monitor and form (CSR or quadtree, the same roadmap twice), frames
+packed or transformed from their planes (a world of more than 4x the agent's
+cells; an odd world with planes off alignment); every item's outputs equal the
+per-frame entry points' and the oracle's, also when the launch is captured in
+a CUDA graph and replayed."""
 import numpy as np
 import pytest
 
@@ -29,6 +31,17 @@ def _items():
     wl0.rowptr = np.zeros(1, np.int64)
     wl0.colidx = np.zeros(0, np.int32)
     items.append((wl0, 4, None))
+    # a world of more than 4x the agent's cells: the batch transforms it from the planes
+    wl1 = synth.make("plain", seed=41, edges=800)
+    wl1.world = synth.world_grid(160, 120, 0.5)
+    wl1.planes = (rng.random((wl1.P, 120, 160)) < 0.2).astype(np.uint8)
+    items.append((wl1, wl1.P, None))
+    # an odd world cell count and planes one byte past alignment: the batch packs with byte loads
+    wl2 = synth.make("plain", seed=42, edges=600)
+    wl2.world = synth.world_grid(61, 37, 0.6)
+    wl2.planes = (rng.random((wl2.P, 37, 61)) < 0.3).astype(np.uint8) * 7
+    wl2.misalign = 1
+    items.append((wl2, 3, synth.random_monitor(rng, 5, 2, 3)))
     items.append((items[0][0], 9, None))  # the first roadmap again
     return items
 
@@ -46,7 +59,11 @@ def _run_batch(items, graph):
     try:
         for (wl, P, mon) in items:
             E = wl.rowptr.shape[0] - 1
-            o = dict(world=wl.world, d_planes=torch.from_numpy(np.ascontiguousarray(wl.planes[:P])).cuda(),
+            off = getattr(wl, "misalign", 0)
+            flat = torch.from_numpy(np.ascontiguousarray(wl.planes[:P]).reshape(-1))
+            buf = torch.zeros(flat.numel() + off, dtype=torch.uint8, device="cuda")
+            buf[off:].copy_(flat.cuda())
+            o = dict(world=wl.world, d_planes=buf[off:],
                      pose=synth.random_pose(rng, wl.world),
                      d_O=torch.zeros(wl.agent.cells, dtype=torch.uint64, device="cuda"),
                      d_L=torch.zeros(max(E, 1), dtype=torch.uint64, device="cuda"))
@@ -131,4 +148,47 @@ def test_batch_argument_checks():
                                             d_L=torch.zeros(50, dtype=torch.uint64, device="cuda"))])
         L.lbl_batch_free(b)
     finally:
+        L.lbl_roadmap_free(rm)
+
+
+def test_batch_words_buffer_grows_and_old_graphs_stay_valid():
+    """Frames with a larger world replace the batch's packed-word buffer; a
+    graph captured with the earlier frames still runs on them afterwards."""
+    wl = synth.make("plain", seed=51, edges=400)
+    rm = L.lbl_roadmap_upload(wl.agent, wl.rowptr, wl.colidx, flags=L.LBL_UPLOAD_QUAD)
+    b = L.lbl_batch_create([rm], [wl.P])
+    rng = np.random.default_rng(3)
+    E = wl.n_edges
+
+    def frame(world):
+        planes = (rng.random((wl.P, world.h, world.w)) < 0.3).astype(np.uint8)
+        return planes, dict(world=world, d_planes=torch.from_numpy(planes.reshape(-1)).cuda(),
+                            pose=synth.random_pose(rng, world),
+                            d_O=torch.zeros(wl.agent.cells, dtype=torch.uint64, device="cuda"),
+                            d_L=torch.zeros(E, dtype=torch.uint64, device="cuda"))
+
+    try:
+        p1, f1 = frame(synth.world_grid(32, 32, 0.5))     # packed (1,024 world cells)
+        p2, f2 = frame(synth.world_grid(120, 100, 0.5))   # packed, a larger buffer (12,000 cells)
+        s = torch.cuda.Stream()
+        L.lbl_batch_set_frames(b, [f1])
+        torch.cuda.synchronize()
+        L.lbl_batch_launch(b, stream=s)  # first launch outside any capture
+        s.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            L.lbl_batch_launch(b, stream=torch.cuda.current_stream())
+        L.lbl_batch_set_frames(b, [f2])
+        f1["d_O"].zero_()
+        f1["d_L"].zero_()
+        torch.cuda.synchronize()
+        g.replay()
+        L.lbl_batch_launch(b, stream=s)
+        torch.cuda.synchronize()
+        for planes, f in ((p1, f1), (p2, f2)):
+            want_O = oracle.frame_transform(f["world"], planes, f["pose"], wl.agent)
+            assert np.array_equal(f["d_O"].cpu().numpy(), want_O)
+            assert np.array_equal(f["d_L"].cpu().numpy(), oracle.label(wl.rowptr, wl.colidx, want_O, wl.P))
+    finally:
+        L.lbl_batch_free(b)
         L.lbl_roadmap_free(rm)

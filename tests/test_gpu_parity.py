@@ -143,42 +143,81 @@ def _packed(planes):
     return w
 
 
-@pytest.mark.parametrize("P", [0, 1, 7, 16, 33, 64])
+def _words_buf(cells, P, fill=0x55):
+    """a packed-word buffer of the width lbl_pack_planes writes, every byte `fill`"""
+    dt = getattr(torch, L.packed_word_dtype(P))
+    return torch.full((cells * L.packed_word_bytes(P),), fill, dtype=torch.uint8, device="cuda").view(dt)
+
+
+def _words_host(words):
+    w = words.cpu().numpy()
+    return w.view({1: np.uint8, 2: np.uint16, 4: np.uint32, 8: np.uint64}[w.itemsize]).astype(np.uint64)
+
+
+@pytest.mark.parametrize("P", [0, 1, 2, 7, 8, 9, 16, 17, 31, 32, 33, 63, 64])
 def test_pack_planes_and_packed_transform(P):
-    """Packed words equal the plain definition for word-aligned and unaligned
-    planes and odd cell counts; the packed transform equals the oracle's."""
+    """Packed words (as narrow as P allows) equal the plain definition for
+    4-byte aligned and unaligned planes, cell counts divisible by 4 or not, and
+    words at and off their vector alignment; the packed transform equals the
+    oracle's."""
     rng = np.random.default_rng(70 + P)
-    for world, misalign in ((synth.world_grid(53, 41, 0.37), 0), (synth.world_grid(64, 48, 0.37), 0),
-                            (synth.world_grid(64, 48, 0.37), 1)):
+    wb = L.packed_word_bytes(P)
+    for world, misalign, woff in ((synth.world_grid(53, 41, 0.37), 0, 0), (synth.world_grid(64, 48, 0.37), 0, 0),
+                                  (synth.world_grid(64, 48, 0.37), 1, 0), (synth.world_grid(64, 48, 0.37), 0, 1),
+                                  (synth.world_grid(3, 1, 0.37), 0, 0), (synth.world_grid(1, 1, 0.37), 0, 0)):
         cells = world.cells
         planes = (rng.random((P, world.h, world.w)) < 0.3).astype(np.uint8) * rng.integers(
             1, 255, size=(P, world.h, world.w)).astype(np.uint8)
         buf = torch.zeros(P * cells + 8, dtype=torch.uint8, device="cuda")
         d_planes = buf[misalign:misalign + P * cells]
         d_planes.copy_(torch.from_numpy(planes.reshape(-1)).cuda())
-        words = torch.full((cells,), 0x55, dtype=torch.int64, device="cuda").view(torch.uint64)
+        words = _words_buf(cells + 1, P)[woff:woff + cells]  # woff = 1: one word past a 16-byte boundary
         L.lbl_pack_planes(world, d_planes, P, words)
-        assert np.array_equal(host(words), _packed(planes)), (world.w, misalign)
+        torch.cuda.synchronize()
+        assert np.array_equal(_words_host(words), _packed(planes)), (world.w, misalign, woff)
         for agent in (synth.agent_grid(32, 0.25, synth.MORTON), synth.Grid(37, 29, 0.3, -5.0, -4.0, synth.ROWMAJOR)):
             pose = (9.0 + rng.random(), 7.5 + rng.random(), rng.random() * 6.3)
             O = empty_u64(agent.cells)
             L.lbl_frame_transform_words(world, words, P, pose, agent, O)
             assert np.array_equal(host(O), oracle.frame_transform(world, planes, pose, agent))
+    assert wb == (1 if P <= 8 else 2 if P <= 16 else 4 if P <= 32 else 8)
+
+
+def test_pack_planes_all_byte_values():
+    """every byte value 0..255 in every plane position packs to (value != 0)"""
+    world = synth.world_grid(256, 4, 1.0)
+    for P in (8, 64):
+        planes = np.zeros((P, 4, 256), np.uint8)
+        for p in range(P):
+            planes[p] = np.roll(np.arange(256, dtype=np.uint8), 7 * p)[None, :]
+        words = _words_buf(world.cells, P)
+        L.lbl_pack_planes(world, cuda(planes), P, words)
+        torch.cuda.synchronize()
+        assert np.array_equal(_words_host(words), _packed(planes))
+
+
+def test_packed_words_must_match_width():
+    world = synth.world_grid(8, 8, 1.0)
+    planes = torch.zeros(9 * 64, dtype=torch.uint8, device="cuda")
+    with pytest.raises(TypeError):
+        L.lbl_pack_planes(world, planes, 9, empty_u64(64))  # 9 propositions pack into 16-bit words
 
 
 def test_packed_transform_time_augmented():
     rng = np.random.default_rng(77)
     world = synth.Grid(20, 17, 0.3, 0.0, 0.0, synth.ROWMAJOR, 12, 0.07, -0.1)
-    vols = (rng.random((40, 12, 17, 20)) < 0.5).astype(np.uint8)
     agent = synth.agent_grid3(8, 0.25, 8, 0.05, synth.MORTON)
-    words = empty_u64(world.cells)
-    L.lbl_pack_planes(world, cuda(vols), 40, words)
-    assert np.array_equal(host(words), _packed(vols))
-    for _ in range(3):
-        pose = (2 + 2 * rng.random(), 2 + 2 * rng.random(), 6.3 * rng.random(), 0.3 * rng.random() - 0.1)
-        O = empty_u64(agent.cells)
-        L.lbl_frame_transform_words(world, words, 40, pose, agent, O)
-        assert np.array_equal(host(O), oracle.frame_transform3(world, vols, pose, agent))
+    for P in (5, 40):
+        vols = (rng.random((P, 12, 17, 20)) < 0.5).astype(np.uint8)
+        words = _words_buf(world.cells, P)
+        L.lbl_pack_planes(world, cuda(vols), P, words)
+        torch.cuda.synchronize()
+        assert np.array_equal(_words_host(words), _packed(vols))
+        for _ in range(3):
+            pose = (2 + 2 * rng.random(), 2 + 2 * rng.random(), 6.3 * rng.random(), 0.3 * rng.random() - 0.1)
+            O = empty_u64(agent.cells)
+            L.lbl_frame_transform_words(world, words, P, pose, agent, O)
+            assert np.array_equal(host(O), oracle.frame_transform3(world, vols, pose, agent))
 
 
 def test_frame_transform_rejects_out_of_range_pose():
