@@ -239,8 +239,8 @@ int lbl_frame_transform(const lbl_grid *world, const uint8_t *d_planes, int32_t 
  * One coalesced pass over the planes (whole 128-byte lines of a plane per
  * warp load, with 4-byte aligned planes and a cell count divisible by 4; byte
  * loads otherwise).  With lbl_frame_transform_words it gives exactly
- * lbl_frame_transform's O.  LBL_EINVAL on a bad grid, n_props outside 0..64
- * or a NULL buffer.  Asynchronous on `s`.
+ * lbl_frame_transform's O.  LBL_EINVAL on a bad grid, n_props outside 0..64,
+ * a NULL buffer or words not aligned to their width.  Asynchronous on `s`.
  */
 #define LBL_PACKED_WORD_BYTES(n_props) ((n_props) <= 8 ? 1 : (n_props) <= 16 ? 2 : (n_props) <= 32 ? 4 : 8)
 int lbl_pack_planes(const lbl_grid *world, const uint8_t *d_planes, int32_t n_props, void *d_words,
@@ -251,7 +251,8 @@ int lbl_pack_planes(const lbl_grid *world, const uint8_t *d_planes, int32_t n_pr
  * packed words of lbl_pack_planes (LBL_PACKED_WORD_BYTES(n_props) bytes each)
  * instead of the planes: one gather per agent cell instead of n_props byte
  * gathers.  Word bits >= n_props are ignored.  Same arguments, layouts and
- * errors as lbl_frame_transform.
+ * errors as lbl_frame_transform, and LBL_EINVAL for words or d_O not aligned
+ * to their width.
  */
 int lbl_frame_transform_words(const lbl_grid *world, const void *d_words, int32_t n_props, lbl_pose pose,
                               const lbl_grid *agent, uint64_t *d_O, lbl_stream s);

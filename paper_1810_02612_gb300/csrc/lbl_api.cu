@@ -606,6 +606,10 @@ int lbl_pack_planes(const lbl_grid *world, const uint8_t *d_planes, int32_t n_pr
     set_error("pack planes: NULL buffer");
     return LBL_EINVAL;
   }
+  if (reinterpret_cast<uintptr_t>(d_words) % static_cast<uintptr_t>(packed_word_bytes(n_props))) {
+    set_error("pack planes: words not aligned to their %d-byte width", packed_word_bytes(n_props));
+    return LBL_EINVAL;
+  }
   const PackItem it{d_planes, d_words, grid_cells(*world), n_props, packed_word_bytes(n_props)};
   cudaError_t e = launch_pack_planes(it, reinterpret_cast<cudaStream_t>(s));
   if (e != cudaSuccess) return cuda_fail(e, "pack planes: launch");
@@ -623,6 +627,11 @@ int lbl_frame_transform_words(const lbl_grid *world, const void *d_words, int32_
   }
   if (!d_O || !d_words) {
     set_error("frame transform: NULL buffer");
+    return LBL_EINVAL;
+  }
+  if (reinterpret_cast<uintptr_t>(d_words) % static_cast<uintptr_t>(packed_word_bytes(n_props)) ||
+      reinterpret_cast<uintptr_t>(d_O) % 8u) {
+    set_error("frame transform: words or O not aligned to their width");
     return LBL_EINVAL;
   }
   FrameMap m;

@@ -201,6 +201,11 @@ def test_packed_words_must_match_width():
     planes = torch.zeros(9 * 64, dtype=torch.uint8, device="cuda")
     with pytest.raises(TypeError):
         L.lbl_pack_planes(world, planes, 9, empty_u64(64))  # 9 propositions pack into 16-bit words
+    words = torch.zeros(2 * 64 + 2, dtype=torch.uint8, device="cuda")
+    with pytest.raises(L.LblError):  # a raw pointer one byte past a 16-bit boundary
+        L.lbl_pack_planes(world, planes, 9, words.data_ptr() + 1)
+    with pytest.raises(L.LblError):
+        L.lbl_frame_transform_words(world, words.data_ptr() + 1, 9, (1.0, 1.0, 0.0), world, empty_u64(64))
 
 
 def test_packed_transform_time_augmented():
