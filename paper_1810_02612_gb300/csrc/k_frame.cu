@@ -1,5 +1,7 @@
 // Frame transform (equivariant re-use of the roadmap, Sec. 5 / eq. 13) and the
 // stand-alone safety-monitor step (Sec. 3.2).
+#include <algorithm>
+
 #include "lbl_internal.cuh"
 
 namespace lbl {
@@ -59,38 +61,59 @@ __device__ __forceinline__ void agent_coords(const FrameItem &f, int64_t idx, in
   }
 }
 
+// Word of world cell c (row-major, time slabs outermost) of frame f: WB = 0
+// reads the P planes, WB = 1, 2, 4 or 8 reads packed words that wide.
+template <int WB>
+__device__ __forceinline__ uint64_t cell_word(const FrameItem &f, int64_t c) {
+  uint64_t word = 0;
+  if constexpr (WB > 0) {
+    word = static_cast<uint64_t>(__ldg(static_cast<const typename WordOf<WB>::T *>(f.words) + c)) & f.wmask;
+  } else {
+    const uint8_t *p = f.planes + c;
+    int q = 0;
+    for (; q + 8 <= f.P; q += 8) {
+      uint8_t b[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) b[j] = __ldg(p + (q + j) * f.plane_cells);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) word |= static_cast<uint64_t>(b[j] != 0) << (q + j);
+    }
+    for (; q < f.P; ++q) word |= static_cast<uint64_t>(__ldg(p + q * f.plane_cells) != 0) << q;
+  }
+  return word;
+}
+
 // World word of agent cell (ix, iy, it) of frame f (2-D or time-augmented).
 // The world cell is the floor of exact Q32.32 affine maps of (ix, iy) and of
-// the slab it.  WB = 0 reads the P planes; WB = 1, 2, 4 or 8 reads packed
-// words that wide.
+// the slab it.
 template <int WB>
 __device__ __forceinline__ uint64_t world_word(const FrameItem &f, int64_t ix, int64_t iy, int64_t it) {
   const int64_t wx = (f.A00 * ix + f.A01 * iy + f.B0) >> 32;  // arithmetic shift: floor
   const int64_t wy = (f.A10 * ix + f.A11 * iy + f.B1) >> 32;
   const int64_t wt = f.wd > 1 ? ((f.At * it + f.Bt) >> 32) : 0;  // a 2-D world is static in time
-  uint64_t word = 0;
-  if (wx >= 0 && wx < f.ww && wy >= 0 && wy < f.wh && wt >= 0 && wt < f.wd) {
-    const int64_t c = (wt * f.wh + wy) * f.ww + wx;
-    if constexpr (WB > 0) {
-      word = static_cast<uint64_t>(__ldg(static_cast<const typename WordOf<WB>::T *>(f.words) + c)) & f.wmask;
-    } else {
-      const uint8_t *p = f.planes + c;
-      int q = 0;
-      for (; q + 8 <= f.P; q += 8) {
-        uint8_t b[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) b[j] = __ldg(p + (q + j) * f.plane_cells);
-#pragma unroll
-        for (int j = 0; j < 8; ++j) word |= static_cast<uint64_t>(b[j] != 0) << (q + j);
-      }
-      for (; q < f.P; ++q) word |= static_cast<uint64_t>(__ldg(p + q * f.plane_cells) != 0) << q;
-    }
-  }
-  return word;
+  if (wx >= 0 && wx < f.ww && wy >= 0 && wy < f.wh && wt >= 0 && wt < f.wd)
+    return cell_word<WB>(f, (wt * f.wh + wy) * f.ww + wx);
+  return 0;
 }
 
-// One thread per agent cell, in output (cell-order) index so the O stores are
-// coalesced.
+// The same for agent and world grids of fewer than 2^32 cells: coordinates
+// zero-extend from 32 bits (each Q32.32 product needs one multiply-add fewer)
+// and the world cell index is 32-bit.  Same products, same floor: same cells.
+template <int WB>
+__device__ __forceinline__ uint64_t world_word32(const FrameItem &f, uint32_t ix, uint32_t iy, uint32_t it) {
+  const int64_t x = ix, y = iy;
+  const int64_t wx = (f.A00 * x + f.A01 * y + f.B0) >> 32;
+  const int64_t wy = (f.A10 * x + f.A11 * y + f.B1) >> 32;
+  const int64_t wt = f.wd > 1 ? ((f.At * static_cast<int64_t>(it) + f.Bt) >> 32) : 0;
+  if (wx >= 0 && wx < f.ww && wy >= 0 && wy < f.wh && wt >= 0 && wt < f.wd) {
+    const uint32_t c = (static_cast<uint32_t>(wt) * static_cast<uint32_t>(f.wh) + static_cast<uint32_t>(wy)) *
+                           static_cast<uint32_t>(f.ww) +
+                       static_cast<uint32_t>(wx);
+    return cell_word<WB>(f, c);
+  }
+  return 0;
+}
+
 template <int WB>
 __device__ __forceinline__ uint64_t frame_word(const FrameItem &f, int64_t idx) {
   int64_t ix, iy, it;
@@ -98,37 +121,60 @@ __device__ __forceinline__ uint64_t frame_word(const FrameItem &f, int64_t idx) 
   return world_word<WB>(f, ix, iy, it);
 }
 
-// Row-major agent grids: each warp takes an 8 x 4 tile of cells of one slab,
-// so under any rotation its world reads stay within a few rows (a warp along
-// one row would read a rotated line of up to 32 world rows); the tile's O
-// stores are four 64-byte runs.
-__device__ __forceinline__ uint32_t rowmajor_tiles(const FrameItem &f, uint32_t &tiles_x) {
-  tiles_x = (static_cast<uint32_t>(f.aw) + 7u) / 8u;
-  return tiles_x * ((static_cast<uint32_t>(f.ah) + 3u) / 4u);
+// Every third / every second bit of a 32-bit z-order index, packed: the
+// 32-bit forms of the decodes above, for indices below 2^32.
+__device__ __forceinline__ uint32_t third_bits32(uint32_t v) {
+  v &= 0x49249249u;
+  v = (v | (v >> 2)) & 0xC30C30C3u;
+  v = (v | (v >> 4)) & 0x0F00F00Fu;
+  v = (v | (v >> 8)) & 0xFF0000FFu;
+  return (v | (v >> 16)) & 0x000007FFu;
+}
+__device__ __forceinline__ uint32_t even_bits32(uint32_t v) {
+  v &= 0x55555555u;
+  v = (v | (v >> 1)) & 0x33333333u;
+  v = (v | (v >> 2)) & 0x0F0F0F0Fu;
+  v = (v | (v >> 4)) & 0x00FF00FFu;
+  return (v | (v >> 8)) & 0x0000FFFFu;
 }
 
-// One thread per agent cell; Morton grids in cell order (a warp's 32 cells
-// are a 4 x 8 tile and its O stores coalesce), row-major grids by tiles.
+// Grids of fewer than 2^32 cells, z-order: a thread per agent cell in cell
+// order (a warp's 32 cells are a 4 x 8 tile and its O stores coalesce).
+template <int WB>
+__global__ void __launch_bounds__(256) k_frame_z32(const __grid_constant__ FrameItem f, uint32_t n) {
+  const uint32_t idx = blockIdx.x * 256u + threadIdx.x;
+  if (idx >= n) return;
+  uint32_t ix, iy, it = 0;
+  if (f.ad > 1) {
+    ix = third_bits32(idx >> 2);
+    iy = third_bits32(idx >> 1);
+    it = third_bits32(idx);
+  } else {
+    ix = even_bits32(idx >> 1);
+    iy = even_bits32(idx);
+  }
+  f.O[idx] = world_word32<WB>(f, ix, iy, it);
+}
+
+// Grids of fewer than 2^32 cells, row-major: a warp per 8 x 4 tile of one slab
+// (grid: x tiles / 8, y tiles, slabs), so under any rotation a warp's world
+// reads stay within a few rows (a warp along one row would read a rotated line
+// of up to 32 world rows); the tile's O stores are four 64-byte runs.
+template <int WB>
+__global__ void __launch_bounds__(256) k_frame_tiles32(const __grid_constant__ FrameItem f) {
+  const uint32_t xt = blockIdx.x * 8u + (threadIdx.x >> 5), lane = threadIdx.x & 31u;
+  const uint32_t ix = 8u * xt + (lane & 7u), iy = 4u * blockIdx.y + (lane >> 3), it = blockIdx.z;
+  if (ix >= static_cast<uint32_t>(f.aw) || iy >= static_cast<uint32_t>(f.ah)) return;
+  f.O[(it * static_cast<uint32_t>(f.ah) + iy) * static_cast<uint32_t>(f.aw) + ix] = world_word32<WB>(f, ix, iy, it);
+}
+
+// Any grid: a thread per agent cell in cell order, 64-bit indices.
 template <int WB>
 __global__ void __launch_bounds__(256) k_frame_transform(const __grid_constant__ FrameItem f) {
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-  const int64_t t0 = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (f.order == LBL_ORDER_ROWMAJOR && f.small_index) {
-    uint32_t tx;
-    const uint32_t per_slab = rowmajor_tiles(f, tx);
-    const int64_t lanes = 32 * static_cast<int64_t>(per_slab) * f.ad;
-    for (int64_t t = t0; t < lanes; t += stride) {
-      const uint32_t tile = static_cast<uint32_t>(t >> 5), lane = static_cast<uint32_t>(t) & 31u;
-      const uint32_t slab = tile / per_slab, r = tile - slab * per_slab;
-      const uint32_t yt = r / tx, xt = r - yt * tx;
-      const uint32_t ix = 8u * xt + (lane & 7u), iy = 4u * yt + (lane >> 3);
-      if (ix < static_cast<uint32_t>(f.aw) && iy < static_cast<uint32_t>(f.ah))
-        f.O[(static_cast<int64_t>(slab) * f.ah + iy) * f.aw + ix] = world_word<WB>(f, ix, iy, slab);
-    }
-    return;
-  }
   const int64_t n = static_cast<int64_t>(f.aw) * f.ah * f.ad;
-  for (int64_t idx = t0; idx < n; idx += stride) f.O[idx] = frame_word<WB>(f, idx);
+  for (int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; idx < n; idx += stride)
+    f.O[idx] = frame_word<WB>(f, idx);
 }
 
 // Batched frame transform: thread per (frame, agent cell) over all frames'
@@ -266,19 +312,31 @@ __global__ void __launch_bounds__(256) k_monitor_step(MonitorTables mon, const u
 
 }  // namespace
 
+template <int WB>
+static void transform_launch(const FrameItem &f, int num_sms, cudaStream_t s) {
+  const int64_t n = static_cast<int64_t>(f.aw) * f.ah * f.ad;
+  const bool small = n < (1ll << 32) && f.plane_cells < (1ll << 32);
+  const int64_t tx = (f.aw + 7) / 8, ty = (f.ah + 3) / 4;
+  if (small && f.order == LBL_ORDER_MORTON) {
+    k_frame_z32<WB><<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(f, static_cast<uint32_t>(n));
+  } else if (small && ty <= 65535 && f.ad <= 65535) {
+    const dim3 grid(static_cast<unsigned>((tx + 7) / 8), static_cast<unsigned>(ty), static_cast<unsigned>(f.ad));
+    k_frame_tiles32<WB><<<grid, 256, 0, s>>>(f);
+  } else {
+    const int64_t blocks = std::min<int64_t>((n + 255) / 256, static_cast<int64_t>(num_sms) * 8);
+    k_frame_transform<WB><<<static_cast<unsigned>(blocks), 256, 0, s>>>(f);
+  }
+}
+
 cudaError_t launch_frame_transform(const FrameItem &f, int num_sms, cudaStream_t s) {
   const int64_t n = static_cast<int64_t>(f.aw) * f.ah * f.ad;
   if (n == 0) return cudaSuccess;
-  int64_t blocks = (n + 255) / 256;
-  const int64_t cap = static_cast<int64_t>(num_sms) * 8;
-  if (blocks > cap) blocks = cap;
-  const unsigned g = static_cast<unsigned>(blocks);
   switch (f.words ? f.word_bytes : 0) {
-    case 0: k_frame_transform<0><<<g, 256, 0, s>>>(f); break;
-    case 1: k_frame_transform<1><<<g, 256, 0, s>>>(f); break;
-    case 2: k_frame_transform<2><<<g, 256, 0, s>>>(f); break;
-    case 4: k_frame_transform<4><<<g, 256, 0, s>>>(f); break;
-    case 8: k_frame_transform<8><<<g, 256, 0, s>>>(f); break;
+    case 0: transform_launch<0>(f, num_sms, s); break;
+    case 1: transform_launch<1>(f, num_sms, s); break;
+    case 2: transform_launch<2>(f, num_sms, s); break;
+    case 4: transform_launch<4>(f, num_sms, s); break;
+    case 8: transform_launch<8>(f, num_sms, s); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
