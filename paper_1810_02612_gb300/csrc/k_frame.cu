@@ -1,23 +1,9 @@
 // Frame transform (equivariant re-use of the roadmap, Sec. 5 / eq. 13) and the
 // stand-alone safety-monitor step (Sec. 3.2).
-#include <algorithm>
-
 #include "lbl_internal.cuh"
 
 namespace lbl {
 namespace {
-
-// Every third bit of v (positions 0, 3, ..., 60) packed into the low 21 bits:
-// the inverse of the 3-D z-order interleave for one coordinate.
-__device__ __forceinline__ uint32_t gather_third_bits(uint64_t v) {
-  v &= 0x1249249249249249ull;
-  v = (v | (v >> 2)) & 0x10C30C30C30C30C3ull;
-  v = (v | (v >> 4)) & 0x100F00F00F00F00Full;
-  v = (v | (v >> 8)) & 0x001F0000FF0000FFull;
-  v = (v | (v >> 16)) & 0x001F00000000FFFFull;
-  v = (v | (v >> 32)) & 0x00000000001FFFFFull;
-  return static_cast<uint32_t>(v);
-}
 
 template <int WB> struct WordOf;
 template <> struct WordOf<1> { using T = uint8_t; };
@@ -25,46 +11,52 @@ template <> struct WordOf<2> { using T = uint16_t; };
 template <> struct WordOf<4> { using T = uint32_t; };
 template <> struct WordOf<8> { using T = uint64_t; };
 
+// Grids have at most 32768 cells a side and fewer than 2^31 cells (checked on
+// the host), so cell indices and coordinates are 32-bit throughout.
+
+// Every third / every second bit of a z-order index, packed: the inverse of
+// the 3-D / 2-D bit interleave for one coordinate.
+__device__ __forceinline__ uint32_t third_bits(uint32_t v) {
+  v &= 0x49249249u;
+  v = (v | (v >> 2)) & 0xC30C30C3u;
+  v = (v | (v >> 4)) & 0x0F00F00Fu;
+  v = (v | (v >> 8)) & 0xFF0000FFu;
+  return (v | (v >> 16)) & 0x000007FFu;
+}
+__device__ __forceinline__ uint32_t even_bits(uint32_t v) {
+  v &= 0x55555555u;
+  v = (v | (v >> 1)) & 0x33333333u;
+  v = (v | (v >> 2)) & 0x0F0F0F0Fu;
+  v = (v | (v >> 4)) & 0x00FF00FFu;
+  return (v | (v >> 8)) & 0x0000FFFFu;
+}
+
 // Coordinates (ix, iy, it) of agent cell idx of frame f in the grid's order.
-__device__ __forceinline__ void agent_coords(const FrameItem &f, int64_t idx, int64_t &ix, int64_t &iy,
-                                             int64_t &it) {
+__device__ __forceinline__ void agent_coords(const FrameItem &f, uint32_t idx, uint32_t &ix, uint32_t &iy,
+                                             uint32_t &it) {
   it = 0;
-  if (f.ad > 1) {
-    if (f.order == LBL_ORDER_MORTON) {
-      ix = gather_third_bits(static_cast<uint64_t>(idx) >> 2);
-      iy = gather_third_bits(static_cast<uint64_t>(idx) >> 1);
-      it = gather_third_bits(static_cast<uint64_t>(idx));
-    } else if (f.small_index) {  // 32-bit division is several times cheaper than 64-bit
-      const uint32_t plane = static_cast<uint32_t>(f.aw) * static_cast<uint32_t>(f.ah);
-      const uint32_t i32 = static_cast<uint32_t>(idx);
-      const uint32_t t32 = i32 / plane, r = i32 - t32 * plane, y32 = r / static_cast<uint32_t>(f.aw);
-      it = t32;
-      iy = y32;
-      ix = r - y32 * static_cast<uint32_t>(f.aw);
+  if (f.order == LBL_ORDER_MORTON) {
+    if (f.ad > 1) {
+      ix = third_bits(idx >> 2);
+      iy = third_bits(idx >> 1);
+      it = third_bits(idx);
     } else {
-      const int64_t plane = static_cast<int64_t>(f.aw) * f.ah;
-      it = idx / plane;
-      const int64_t r = idx - it * plane;
-      iy = r / f.aw;
-      ix = r - iy * f.aw;
+      ix = even_bits(idx >> 1);
+      iy = even_bits(idx);
     }
-  } else if (f.order == LBL_ORDER_MORTON) {
-    ix = gather_even_bits(static_cast<uint64_t>(idx) >> 1);
-    iy = gather_even_bits(static_cast<uint64_t>(idx));
-  } else if (f.small_index) {
-    const uint32_t i32 = static_cast<uint32_t>(idx), y32 = i32 / static_cast<uint32_t>(f.aw);
-    iy = y32;
-    ix = i32 - y32 * static_cast<uint32_t>(f.aw);
   } else {
-    iy = idx / f.aw;
-    ix = idx - iy * f.aw;
+    const uint32_t aw = static_cast<uint32_t>(f.aw), plane = aw * static_cast<uint32_t>(f.ah);
+    it = idx / plane;
+    const uint32_t r = idx - it * plane;
+    iy = r / aw;
+    ix = r - iy * aw;
   }
 }
 
 // Word of world cell c (row-major, time slabs outermost) of frame f: WB = 0
 // reads the P planes, WB = 1, 2, 4 or 8 reads packed words that wide.
 template <int WB>
-__device__ __forceinline__ uint64_t cell_word(const FrameItem &f, int64_t c) {
+__device__ __forceinline__ uint64_t cell_word(const FrameItem &f, uint32_t c) {
   uint64_t word = 0;
   if constexpr (WB > 0) {
     word = static_cast<uint64_t>(__ldg(static_cast<const typename WordOf<WB>::T *>(f.words) + c)) & f.wmask;
@@ -84,27 +76,14 @@ __device__ __forceinline__ uint64_t cell_word(const FrameItem &f, int64_t c) {
 }
 
 // World word of agent cell (ix, iy, it) of frame f (2-D or time-augmented).
-// The world cell is the floor of exact Q32.32 affine maps of (ix, iy) and of
-// the slab it.
+// The world cell is the floor (arithmetic shift) of exact Q32.32 affine maps
+// of (ix, iy) and of the slab it; coordinates zero-extend to 64 bits.
 template <int WB>
-__device__ __forceinline__ uint64_t world_word(const FrameItem &f, int64_t ix, int64_t iy, int64_t it) {
-  const int64_t wx = (f.A00 * ix + f.A01 * iy + f.B0) >> 32;  // arithmetic shift: floor
-  const int64_t wy = (f.A10 * ix + f.A11 * iy + f.B1) >> 32;
-  const int64_t wt = f.wd > 1 ? ((f.At * it + f.Bt) >> 32) : 0;  // a 2-D world is static in time
-  if (wx >= 0 && wx < f.ww && wy >= 0 && wy < f.wh && wt >= 0 && wt < f.wd)
-    return cell_word<WB>(f, (wt * f.wh + wy) * f.ww + wx);
-  return 0;
-}
-
-// The same for agent and world grids of fewer than 2^32 cells: coordinates
-// zero-extend from 32 bits (each Q32.32 product needs one multiply-add fewer)
-// and the world cell index is 32-bit.  Same products, same floor: same cells.
-template <int WB>
-__device__ __forceinline__ uint64_t world_word32(const FrameItem &f, uint32_t ix, uint32_t iy, uint32_t it) {
+__device__ __forceinline__ uint64_t world_word(const FrameItem &f, uint32_t ix, uint32_t iy, uint32_t it) {
   const int64_t x = ix, y = iy;
   const int64_t wx = (f.A00 * x + f.A01 * y + f.B0) >> 32;
   const int64_t wy = (f.A10 * x + f.A11 * y + f.B1) >> 32;
-  const int64_t wt = f.wd > 1 ? ((f.At * static_cast<int64_t>(it) + f.Bt) >> 32) : 0;
+  const int64_t wt = f.wd > 1 ? ((f.At * static_cast<int64_t>(it) + f.Bt) >> 32) : 0;  // a 2-D world is static
   if (wx >= 0 && wx < f.ww && wy >= 0 && wy < f.wh && wt >= 0 && wt < f.wd) {
     const uint32_t c = (static_cast<uint32_t>(wt) * static_cast<uint32_t>(f.wh) + static_cast<uint32_t>(wy)) *
                            static_cast<uint32_t>(f.ww) +
@@ -115,66 +94,30 @@ __device__ __forceinline__ uint64_t world_word32(const FrameItem &f, uint32_t ix
 }
 
 template <int WB>
-__device__ __forceinline__ uint64_t frame_word(const FrameItem &f, int64_t idx) {
-  int64_t ix, iy, it;
+__device__ __forceinline__ uint64_t frame_word(const FrameItem &f, uint32_t idx) {
+  uint32_t ix, iy, it;
   agent_coords(f, idx, ix, iy, it);
   return world_word<WB>(f, ix, iy, it);
 }
 
-// Every third / every second bit of a 32-bit z-order index, packed: the
-// 32-bit forms of the decodes above, for indices below 2^32.
-__device__ __forceinline__ uint32_t third_bits32(uint32_t v) {
-  v &= 0x49249249u;
-  v = (v | (v >> 2)) & 0xC30C30C3u;
-  v = (v | (v >> 4)) & 0x0F00F00Fu;
-  v = (v | (v >> 8)) & 0xFF0000FFu;
-  return (v | (v >> 16)) & 0x000007FFu;
-}
-__device__ __forceinline__ uint32_t even_bits32(uint32_t v) {
-  v &= 0x55555555u;
-  v = (v | (v >> 1)) & 0x33333333u;
-  v = (v | (v >> 2)) & 0x0F0F0F0Fu;
-  v = (v | (v >> 4)) & 0x00FF00FFu;
-  return (v | (v >> 8)) & 0x0000FFFFu;
-}
-
-// Grids of fewer than 2^32 cells, z-order: a thread per agent cell in cell
-// order (a warp's 32 cells are a 4 x 8 tile and its O stores coalesce).
+// z-order grids: a thread per agent cell in cell order (a warp's 32 cells are
+// a 4 x 8 tile and its O stores coalesce).
 template <int WB>
-__global__ void __launch_bounds__(256) k_frame_z32(const __grid_constant__ FrameItem f, uint32_t n) {
+__global__ void __launch_bounds__(256) k_frame_z(const __grid_constant__ FrameItem f, uint32_t n) {
   const uint32_t idx = blockIdx.x * 256u + threadIdx.x;
-  if (idx >= n) return;
-  uint32_t ix, iy, it = 0;
-  if (f.ad > 1) {
-    ix = third_bits32(idx >> 2);
-    iy = third_bits32(idx >> 1);
-    it = third_bits32(idx);
-  } else {
-    ix = even_bits32(idx >> 1);
-    iy = even_bits32(idx);
-  }
-  f.O[idx] = world_word32<WB>(f, ix, iy, it);
+  if (idx < n) f.O[idx] = frame_word<WB>(f, idx);
 }
 
-// Grids of fewer than 2^32 cells, row-major: a warp per 8 x 4 tile of one slab
-// (grid: x tiles / 8, y tiles, slabs), so under any rotation a warp's world
-// reads stay within a few rows (a warp along one row would read a rotated line
-// of up to 32 world rows); the tile's O stores are four 64-byte runs.
+// Row-major grids: a warp per 8 x 4 tile of one slab (grid: x tiles / 8, y
+// tiles, slabs), so under any rotation a warp's world reads stay within a few
+// rows (a warp along one row would read a rotated line of up to 32 world
+// rows); the tile's O stores are four 64-byte runs.
 template <int WB>
-__global__ void __launch_bounds__(256) k_frame_tiles32(const __grid_constant__ FrameItem f) {
+__global__ void __launch_bounds__(256) k_frame_tiles(const __grid_constant__ FrameItem f) {
   const uint32_t xt = blockIdx.x * 8u + (threadIdx.x >> 5), lane = threadIdx.x & 31u;
   const uint32_t ix = 8u * xt + (lane & 7u), iy = 4u * blockIdx.y + (lane >> 3), it = blockIdx.z;
   if (ix >= static_cast<uint32_t>(f.aw) || iy >= static_cast<uint32_t>(f.ah)) return;
-  f.O[(it * static_cast<uint32_t>(f.ah) + iy) * static_cast<uint32_t>(f.aw) + ix] = world_word32<WB>(f, ix, iy, it);
-}
-
-// Any grid: a thread per agent cell in cell order, 64-bit indices.
-template <int WB>
-__global__ void __launch_bounds__(256) k_frame_transform(const __grid_constant__ FrameItem f) {
-  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-  const int64_t n = static_cast<int64_t>(f.aw) * f.ah * f.ad;
-  for (int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; idx < n; idx += stride)
-    f.O[idx] = frame_word<WB>(f, idx);
+  f.O[(it * static_cast<uint32_t>(f.ah) + iy) * static_cast<uint32_t>(f.aw) + ix] = world_word<WB>(f, ix, iy, it);
 }
 
 // Batched frame transform: thread per (frame, agent cell) over all frames'
@@ -192,7 +135,7 @@ __global__ void __launch_bounds__(256) k_frame_batch(const __grid_constant__ Fra
         hi = mid - 1;
     }
     const FrameItem &f = tab.items[lo];
-    const int64_t idx = gidx - f.cell0;
+    const uint32_t idx = static_cast<uint32_t>(gidx - f.cell0);
     f.O[idx] = f.words ? frame_word<8>(f, idx) : frame_word<0>(f, idx);  // packed items: 64-bit words
   }
 }
@@ -313,30 +256,27 @@ __global__ void __launch_bounds__(256) k_monitor_step(MonitorTables mon, const u
 }  // namespace
 
 template <int WB>
-static void transform_launch(const FrameItem &f, int num_sms, cudaStream_t s) {
-  const int64_t n = static_cast<int64_t>(f.aw) * f.ah * f.ad;
-  const bool small = n < (1ll << 32) && f.plane_cells < (1ll << 32);
-  const int64_t tx = (f.aw + 7) / 8, ty = (f.ah + 3) / 4;
-  if (small && f.order == LBL_ORDER_MORTON) {
-    k_frame_z32<WB><<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(f, static_cast<uint32_t>(n));
-  } else if (small && ty <= 65535 && f.ad <= 65535) {
-    const dim3 grid(static_cast<unsigned>((tx + 7) / 8), static_cast<unsigned>(ty), static_cast<unsigned>(f.ad));
-    k_frame_tiles32<WB><<<grid, 256, 0, s>>>(f);
-  } else {
-    const int64_t blocks = std::min<int64_t>((n + 255) / 256, static_cast<int64_t>(num_sms) * 8);
-    k_frame_transform<WB><<<static_cast<unsigned>(blocks), 256, 0, s>>>(f);
+static void transform_launch(const FrameItem &f, cudaStream_t s) {
+  const uint32_t n = static_cast<uint32_t>(f.aw) * static_cast<uint32_t>(f.ah) * static_cast<uint32_t>(f.ad);
+  if (f.order == LBL_ORDER_MORTON) {
+    k_frame_z<WB><<<(n + 255u) / 256u, 256, 0, s>>>(f, n);
+  } else {  // at most 32768 / 4 tile rows and 32768 slabs: within the grid's y and z limits
+    const dim3 grid((static_cast<unsigned>(f.aw) + 63u) / 64u, (static_cast<unsigned>(f.ah) + 3u) / 4u,
+                    static_cast<unsigned>(f.ad));
+    k_frame_tiles<WB><<<grid, 256, 0, s>>>(f);
   }
 }
 
-cudaError_t launch_frame_transform(const FrameItem &f, int num_sms, cudaStream_t s) {
+cudaError_t launch_frame_transform(const FrameItem &f, cudaStream_t s) {
   const int64_t n = static_cast<int64_t>(f.aw) * f.ah * f.ad;
   if (n == 0) return cudaSuccess;
+  if (n >= (1ll << 31) || f.plane_cells >= (1ll << 31)) return cudaErrorInvalidValue;  // grids are checked on the host
   switch (f.words ? f.word_bytes : 0) {
-    case 0: transform_launch<0>(f, num_sms, s); break;
-    case 1: transform_launch<1>(f, num_sms, s); break;
-    case 2: transform_launch<2>(f, num_sms, s); break;
-    case 4: transform_launch<4>(f, num_sms, s); break;
-    case 8: transform_launch<8>(f, num_sms, s); break;
+    case 0: transform_launch<0>(f, s); break;
+    case 1: transform_launch<1>(f, s); break;
+    case 2: transform_launch<2>(f, s); break;
+    case 4: transform_launch<4>(f, s); break;
+    case 8: transform_launch<8>(f, s); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -170,7 +170,6 @@ FrameItem frame_item(const FrameMap &m, const lbl_grid &W, const lbl_grid &A, co
                      uint64_t *O, int64_t cell0) {
   FrameItem f{m.A00, m.A01, m.B0, m.A10, m.A11, m.B1, m.At, m.Bt, planes, O, grid_cells(W), cell0,
               W.w, W.h, grid_depth(W), A.w, A.h, grid_depth(A), P, A.order};
-  f.small_index = grid_cells(A) < (1ll << 32);
   return f;
 }
 
@@ -588,8 +587,7 @@ int lbl_frame_transform(const lbl_grid *world, const uint8_t *d_planes, int32_t 
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "frame transform: cudaGetDevice");
-  e = launch_frame_transform(frame_item(m, *world, *agent, d_planes, n_props, d_O, 0), device_sms(dev),
-                             reinterpret_cast<cudaStream_t>(s));
+  e = launch_frame_transform(frame_item(m, *world, *agent, d_planes, n_props, d_O, 0), reinterpret_cast<cudaStream_t>(s));
   if (e != cudaSuccess) return cuda_fail(e, "frame transform: launch");
   return LBL_OK;
 }
@@ -643,7 +641,7 @@ int lbl_frame_transform_words(const lbl_grid *world, const void *d_words, int32_
   f.words = d_words;
   f.word_bytes = packed_word_bytes(n_props);
   f.wmask = n_props >= 64 ? ~0ull : ((1ull << n_props) - 1ull);
-  e = launch_frame_transform(f, device_sms(dev), reinterpret_cast<cudaStream_t>(s));
+  e = launch_frame_transform(f, reinterpret_cast<cudaStream_t>(s));
   if (e != cudaSuccess) return cuda_fail(e, "frame transform: launch");
   return LBL_OK;
 }

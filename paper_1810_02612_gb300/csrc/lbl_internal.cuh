@@ -72,7 +72,6 @@ struct FrameItem {
   const void *words;  // packed world words (bit p = plane p), or NULL: read the planes
   uint64_t wmask;     // 2^P - 1, applied to packed words
   int32_t word_bytes; // width of a packed word: 1, 2, 4 or 8
-  bool small_index;   // agent cells < 2^32: cell coordinates by 32-bit division
 };
 
 // Packing world planes into one word per world cell (bit p = plane p != 0).
@@ -247,7 +246,7 @@ struct FrameItem;
 FrameItem frame_item(const FrameMap &m, const lbl_grid &W, const lbl_grid &A, const uint8_t *planes, int32_t P,
                      uint64_t *O, int64_t cell0);
 
-cudaError_t launch_frame_transform(const FrameItem &f, int num_sms, cudaStream_t s);
+cudaError_t launch_frame_transform(const FrameItem &f, cudaStream_t s);
 cudaError_t launch_pack_planes(const PackItem &it, cudaStream_t s);
 cudaError_t launch_pack_batch(const PackTable &tab, cudaStream_t s);
 bool pack_vec_ok(const PackItem &it);

@@ -127,3 +127,17 @@ def test_random_frames_both_transforms(seed):
         L.lbl_frame_transform_words(world, words, P, pose, agent, O2)
         torch.cuda.synchronize()
         assert np.array_equal(O2.cpu().numpy(), want), (world, agent, P, pose)
+
+
+def test_grids_past_32768_a_side_are_rejected():
+    """Grids have at most 32768 cells a side (and slabs) and fewer than 2^31
+    cells, which keeps every transform index 32-bit; larger grids are refused
+    before any device work."""
+    buf = torch.zeros(64, dtype=torch.uint64, device="cuda")
+    small = synth.world_grid(4, 4, 0.3)
+    for agent in (synth.Grid(3, 40_000, 0.01, 0.0, 0.0, synth.ROWMAJOR),
+                  synth.Grid(2, 3, 0.4, -0.4, -0.6, synth.ROWMAJOR, 40_000, 0.001, 0.0)):
+        with pytest.raises(L.LblError):
+            L.lbl_frame_transform(small, buf.view(torch.uint8), 1, (0.0, 0.0, 0.0, 0.0), agent, buf)
+    with pytest.raises(L.LblError):
+        L.lbl_pack_planes(synth.world_grid(40_000, 2, 0.3), buf.view(torch.uint8), 1, buf.view(torch.uint8))
