@@ -275,7 +275,8 @@ __global__ void __launch_bounds__(kThreads, stream_min_blocks<U>()) k_label_stre
                                                            const int32_t *__restrict__ colidx,
                                                            const T *__restrict__ O,
                                                            const int64_t *__restrict__ part, uint64_t mask,
-                                                           uint64_t *__restrict__ L, MonitorTables mon) {
+                                                           uint64_t *__restrict__ L, MonitorTables mon,
+                                                           const int32_t *__restrict__ perm) {
   __shared__ EpiSmem sm;
   if (EPI) load_tables(mon, sm);
   const uint64_t pol = evict_first_policy();
@@ -285,8 +286,9 @@ __global__ void __launch_bounds__(kThreads, stream_min_blocks<U>()) k_label_stre
   if (e_beg >= e_end) return;  // warp-uniform
   stream_range<U, Off>(rowptr, colidx, WordGather<T>{O}, e_beg, e_end, pol, lane, [&](int64_t e, uint64_t r) {
     r &= mask;
-    L[e] = r;
-    if (EPI) epilogue(mon, sm, e, r);
+    const int64_t o = perm ? static_cast<int64_t>(__ldg(perm + e)) : e;  // the caller's edge
+    L[o] = r;
+    if (EPI) epilogue(mon, sm, o, r);
   });
 }
 
@@ -372,14 +374,16 @@ __global__ void __launch_bounds__(kThreads, stream_min_blocks<U>()) k_label_batc
     stream_range<U, Off>(it->rowptr, it->colidx, WordGather<W>{static_cast<const W *>(it->O)}, e_beg, e_end, pol,
                          lane, [&](int64_t e, uint64_t r) {
       r &= it->mask;
-      it->L[e] = r;
+      const int32_t *perm = it->perm;
+      const int64_t o = perm ? static_cast<int64_t>(__ldg(perm + e)) : e;  // the caller's edge
+      it->L[o] = r;
       const uint64_t *T = it->T;
       if (T) {
         uint32_t letter = 0;
         const int m = it->m;
         for (int j = 0; j < m; ++j) letter |= static_cast<uint32_t>((r >> it->rel[j]) & 1u) << j;
-        it->next[e] = __ldg(T + letter);
-        it->viol[e] = __ldg(it->V + letter);
+        it->next[o] = __ldg(T + letter);
+        it->viol[o] = __ldg(it->V + letter);
       }
     });
   }
@@ -1062,9 +1066,9 @@ void rows_launch(const StreamRows &r, const T *base, uint64_t mask, uint64_t *L,
   const unsigned grid = static_cast<unsigned>(num_sms * r.part_ctas);
   MonitorTables none{};
   if (mon)
-    k_label_stream<U, true, Off, T><<<grid, kThreads, 0, s>>>(r.rowptr, r.idx, base, r.part, mask, L, *mon);
+    k_label_stream<U, true, Off, T><<<grid, kThreads, 0, s>>>(r.rowptr, r.idx, base, r.part, mask, L, *mon, r.perm);
   else
-    k_label_stream<U, false, Off, T><<<grid, kThreads, 0, s>>>(r.rowptr, r.idx, base, r.part, mask, L, none);
+    k_label_stream<U, false, Off, T><<<grid, kThreads, 0, s>>>(r.rowptr, r.idx, base, r.part, mask, L, none, r.perm);
 }
 
 template <typename T>
@@ -1099,7 +1103,7 @@ cudaError_t launch_label_rows(const StreamRows &r, const void *base, int word_by
 
 cudaError_t launch_label_stream(const Roadmap &rm, const uint64_t *O, int32_t P, uint64_t *L,
                                 const MonitorTables *mon, int depth, cudaStream_t s) {
-  const StreamRows r{rm.rowptr, rm.colidx, rm.part, rm.part_ctas, rm.E, rm.nnz};
+  const StreamRows r{rm.rowptr, rm.colidx, rm.part, rm.part_ctas, rm.E, rm.nnz, nullptr};
   return launch_label_rows(r, O, 8, P, L, mon, depth, rm.num_sms, s);
 }
 
@@ -1132,7 +1136,7 @@ cudaError_t launch_label_quad(const Roadmap &rm, const uint64_t *O, int32_t P, u
   const int wb = quad_word_bytes(rm, P);
   cudaError_t e = launch_quad_pyramid(rm, O, wb, rm.pyr, s);
   if (e != cudaSuccess) return e;
-  const StreamRows r{rm.qd_rowptr, rm.qd_idx, rm.qd_part, rm.qd_part_ctas, rm.E, rm.n_qd};
+  const StreamRows r{rm.qd_rowptr, rm.qd_idx, rm.qd_part, rm.qd_part_ctas, rm.E, rm.n_qd, rm.qd_perm};
   return launch_label_rows(r, rm.pyr, wb, P, L, mon, depth, rm.num_sms, s);
 }
 

@@ -123,14 +123,27 @@ __device__ __forceinline__ int quad_level(const int32_t *__restrict__ colidx, in
   return j;
 }
 
-__global__ void __launch_bounds__(256) k_quad_count(const int64_t *__restrict__ rowptr,
-                                                    const int32_t *__restrict__ colidx, int64_t E,
-                                                    int32_t *__restrict__ count) {
+// Locality key of row e: its middle cell in the grid's order (0 for an empty row).
+__global__ void __launch_bounds__(256) k_row_keys(const int64_t *__restrict__ rowptr,
+                                                  const int32_t *__restrict__ colidx, int64_t E,
+                                                  uint32_t *__restrict__ key) {
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < E; e += stride) {
-    const int64_t end = rowptr[e + 1];
+    const int64_t beg = rowptr[e], n = rowptr[e + 1] - beg;
+    key[e] = n > 0 ? static_cast<uint32_t>(colidx[beg + n / 2]) : 0u;
+  }
+}
+
+// Quadtree row e is built from CSR row rowmap[e] (rowmap NULL: row e).
+__global__ void __launch_bounds__(256) k_quad_count(const int64_t *__restrict__ rowptr,
+                                                    const int32_t *__restrict__ colidx, int64_t E,
+                                                    const int32_t *__restrict__ rowmap, int32_t *__restrict__ count) {
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < E; e += stride) {
+    const int64_t src = rowmap ? rowmap[e] : e;
+    const int64_t end = rowptr[src + 1];
     int32_t n = 0;
-    for (int64_t k = rowptr[e]; k < end; ++n) k += 1LL << (2 * quad_level(colidx, k, end, colidx[k]));
+    for (int64_t k = rowptr[src]; k < end; ++n) k += 1LL << (2 * quad_level(colidx, k, end, colidx[k]));
     count[e] = n;
   }
 }
@@ -139,11 +152,13 @@ __global__ void __launch_bounds__(256) k_quad_count(const int64_t *__restrict__ 
 // inside a level, i.e. ascending pyramid index: neighbouring lanes then
 // gather neighbouring words of one level.
 __global__ void __launch_bounds__(256) k_quad_fill(const int64_t *__restrict__ rowptr,
-                                                   const int32_t *__restrict__ colidx, int64_t E, QuadOffsets off,
+                                                   const int32_t *__restrict__ colidx, int64_t E,
+                                                   const int32_t *__restrict__ rowmap, QuadOffsets off,
                                                    const int64_t *__restrict__ qrow, int32_t *__restrict__ idx) {
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < E; e += stride) {
-    const int64_t beg = rowptr[e], end = rowptr[e + 1];
+    const int64_t src = rowmap ? rowmap[e] : e;
+    const int64_t beg = rowptr[src], end = rowptr[src + 1];
     int64_t out = qrow[e];
     for (int lev = 0; lev <= kQuadLevels; ++lev) {
       for (int64_t k = beg; k < end;) {
@@ -196,17 +211,23 @@ cudaError_t launch_bt_fill(const int64_t *rowptr, const int32_t *colidx, int64_t
 
 namespace lbl {
 
-cudaError_t launch_quad_count(const int64_t *rowptr, const int32_t *colidx, int64_t E, int32_t *count,
-                              cudaStream_t s) {
+cudaError_t launch_row_keys(const int64_t *rowptr, const int32_t *colidx, int64_t E, uint32_t *key, cudaStream_t s) {
   if (E == 0) return cudaSuccess;
-  k_quad_count<<<blocks_for(E), 256, 0, s>>>(rowptr, colidx, E, count);
+  k_row_keys<<<blocks_for(E), 256, 0, s>>>(rowptr, colidx, E, key);
   return cudaGetLastError();
 }
 
-cudaError_t launch_quad_fill(const int64_t *rowptr, const int32_t *colidx, int64_t E, QuadOffsets off,
-                             const int64_t *qrow, int32_t *idx, cudaStream_t s) {
+cudaError_t launch_quad_count(const int64_t *rowptr, const int32_t *colidx, int64_t E, const int32_t *rowmap,
+                              int32_t *count, cudaStream_t s) {
   if (E == 0) return cudaSuccess;
-  k_quad_fill<<<blocks_for(E), 256, 0, s>>>(rowptr, colidx, E, off, qrow, idx);
+  k_quad_count<<<blocks_for(E), 256, 0, s>>>(rowptr, colidx, E, rowmap, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_quad_fill(const int64_t *rowptr, const int32_t *colidx, int64_t E, const int32_t *rowmap,
+                             QuadOffsets off, const int64_t *qrow, int32_t *idx, cudaStream_t s) {
+  if (E == 0) return cudaSuccess;
+  k_quad_fill<<<blocks_for(E), 256, 0, s>>>(rowptr, colidx, E, rowmap, off, qrow, idx);
   return cudaGetLastError();
 }
 

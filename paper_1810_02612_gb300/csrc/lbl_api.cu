@@ -94,6 +94,7 @@ void free_roadmap(Roadmap *rm) {
   cudaFree(rm->sec);
   cudaFree(rm->sec_part);
   cudaFree(rm->qd_rowptr);
+  cudaFree(rm->qd_perm);
   cudaFree(rm->qd_idx);
   cudaFree(rm->qd_part);
   cudaFree(rm->pyr);
@@ -116,6 +117,24 @@ int resolve_lpe(const Roadmap &rm, const lbl_config *cfg) {
 // from world point q = (X, Y) + R(theta) * centre(ix, iy) (Sec. 5, eq. 13).
 // The double expressions are evaluated exactly as written (the library is built
 // without floating-point contraction) and each is rounded half to even.
+// perm[a..b) = a..b-1 ordered by key (stable): LSD radix sort, two 16-bit digits.
+void sort_range_by_key(const uint32_t *key, int64_t a, int64_t b, int32_t *perm) {
+  const int64_t n = b - a;
+  if (n <= 0) return;
+  std::vector<int32_t> tmp(static_cast<size_t>(n));
+  int32_t *src = perm + a, *dst = tmp.data();
+  for (int64_t i = 0; i < n; ++i) src[i] = static_cast<int32_t>(a + i);
+  std::vector<int64_t> count(65537);
+  for (int shift = 0; shift < 32; shift += 16) {
+    std::fill(count.begin(), count.end(), 0);
+    for (int64_t i = 0; i < n; ++i) ++count[((key[src[i]] >> shift) & 0xFFFFu) + 1];
+    for (int d = 0; d < 65536; ++d) count[d + 1] += count[d];
+    for (int64_t i = 0; i < n; ++i) dst[count[(key[src[i]] >> shift) & 0xFFFFu]++] = src[i];
+    std::swap(src, dst);
+  }
+  // two passes: the sorted order is back in perm + a
+}
+
 bool frame_map(const lbl_grid &W, const lbl_grid &A, const lbl_pose &p, FrameMap *out) {
   if (!std::isfinite(p.x) || !std::isfinite(p.y) || !std::isfinite(p.theta) || !std::isfinite(p.t)) {
     set_error("frame transform: pose must be finite");
@@ -428,11 +447,33 @@ int roadmap_finish(lbl_roadmap_s *rm, uint32_t flags, cudaStream_t st) {
       words += rm->cells >> (2 * k);
     }
     rm->pyr_words = words;
+    if (n_edges > 1 && n_edges < (1LL << 31)) {
+      // locality order: inside each session edge range, rows by their middle cell
+      std::vector<uint32_t> key(static_cast<size_t>(n_edges));
+      uint32_t *d_key = nullptr;
+      if ((e = dev_alloc(&d_key, static_cast<size_t>(n_edges), nullptr)) != cudaSuccess ||
+          (e = launch_row_keys(rm->rowptr, rm->colidx, n_edges, d_key, st)) != cudaSuccess ||
+          (e = cudaMemcpyAsync(key.data(), d_key, sizeof(uint32_t) * n_edges, cudaMemcpyDeviceToHost, st)) !=
+              cudaSuccess ||
+          (e = cudaStreamSynchronize(st)) != cudaSuccess) {
+        cudaFree(d_key);
+        return fail(cuda_fail(e, "roadmap: quadtree order"));
+      }
+      cudaFree(d_key);
+      std::vector<int32_t> perm(static_cast<size_t>(n_edges));
+      for (int c = 0; c < kSessionChunks; ++c)
+        sort_range_by_key(key.data(), n_edges * c / kSessionChunks, n_edges * (c + 1) / kSessionChunks, perm.data());
+      if ((e = dev_alloc(&rm->qd_perm, static_cast<size_t>(n_edges), &rm->bytes)) != cudaSuccess ||
+          (e = cudaMemcpyAsync(rm->qd_perm, perm.data(), sizeof(int32_t) * n_edges, cudaMemcpyHostToDevice, st)) !=
+              cudaSuccess ||
+          (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return fail(cuda_fail(e, "roadmap: quadtree order"));
+    }
     std::vector<int32_t> cnt(static_cast<size_t>(n_edges));
     std::vector<int64_t> drow(static_cast<size_t>(n_edges + 1));
     int32_t *d_dc = nullptr;
     if ((e = dev_alloc(&d_dc, static_cast<size_t>(n_edges), nullptr)) != cudaSuccess ||
-        (e = launch_quad_count(rm->rowptr, rm->colidx, n_edges, d_dc, st)) != cudaSuccess ||
+        (e = launch_quad_count(rm->rowptr, rm->colidx, n_edges, rm->qd_perm, d_dc, st)) != cudaSuccess ||
         (e = cudaMemcpyAsync(cnt.data(), d_dc, sizeof(int32_t) * n_edges, cudaMemcpyDeviceToHost, st)) !=
             cudaSuccess ||
         (e = cudaStreamSynchronize(st)) != cudaSuccess) {
@@ -449,8 +490,8 @@ int roadmap_finish(lbl_roadmap_s *rm, uint32_t flags, cudaStream_t st) {
         (e = dev_alloc(&rm->pyr, static_cast<size_t>(words), &rm->bytes)) != cudaSuccess ||
         (e = cudaMemcpyAsync(rm->qd_rowptr, drow.data(), sizeof(int64_t) * (n_edges + 1), cudaMemcpyHostToDevice,
                              st)) != cudaSuccess ||
-        (e = launch_quad_fill(rm->rowptr, rm->colidx, n_edges, rm->qd_off, rm->qd_rowptr, rm->qd_idx, st)) !=
-            cudaSuccess)
+        (e = launch_quad_fill(rm->rowptr, rm->colidx, n_edges, rm->qd_perm, rm->qd_off, rm->qd_rowptr, rm->qd_idx,
+                              st)) != cudaSuccess)
       return fail(cuda_fail(e, "roadmap: quadtree form"));
     rm->qd_part_ctas = stream_ctas_per_sm(kQuadDepth);
     const int64_t W = static_cast<int64_t>(rm->num_sms) * rm->qd_part_ctas * (kThreads / 32);
@@ -1007,6 +1048,7 @@ int lbl_batch_create(int32_t n, const lbl_roadmap *rms, const int32_t *n_props, 
     it = BatchItem{};
     it.rowptr = quad ? r.qd_rowptr : r.rowptr;
     it.colidx = quad ? r.qd_idx : r.colidx;
+    it.perm = quad ? r.qd_perm : nullptr;
     it.part = b->part + off[i];
     if (quad) {  // labels gather from the item's pyramid, built from its O at the label stage
       PyrItem &pi = b->ptab.items[b->ptab.n];
@@ -1310,11 +1352,15 @@ int lbl_session_run(lbl_session ss, const uint8_t *h_planes, lbl_pose pose, uint
     for (int c = 0; c < kSessionChunks; ++c) {
       const int64_t e0 = ss->edge0[c], n = ss->edge0[c + 1] - e0;
       if (n == 0) continue;
+      // quadtree rows in locality order write to the caller's edges of the
+      // same range: the outputs are addressed from their start, not from e0
+      const int32_t *perm = ss->quad && rm.qd_perm ? rm.qd_perm + e0 : nullptr;
+      const int64_t o0 = perm ? 0 : e0;
       const StreamRows r{(ss->quad ? rm.qd_rowptr : rm.rowptr) + e0, ss->quad ? rm.qd_idx : rm.colidx,
-                         ss->cpart + c * (ss->warps + 1), ss->ctas, n, ss->quad ? rm.n_qd : rm.nnz};
+                         ss->cpart + c * (ss->warps + 1), ss->ctas, n, ss->quad ? rm.n_qd : rm.nnz, perm};
       MonitorTables t{};
-      if (ss->mon) t = tables_of(*ss->mon, dN + e0, dV + e0);
-      e = launch_label_rows(r, base, wb, ss->P, dL + e0, ss->mon ? &t : nullptr, ss->depth, rm.num_sms, cc);
+      if (ss->mon) t = tables_of(*ss->mon, dN + o0, dV + o0);
+      e = launch_label_rows(r, base, wb, ss->P, dL + o0, ss->mon ? &t : nullptr, ss->depth, rm.num_sms, cc);
       if (e == cudaSuccess) e = cudaEventRecord(ss->ev[c], cc);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(ss->cs, ss->ev[c], 0);
       if (e == cudaSuccess) e = copy_out(e0, n);

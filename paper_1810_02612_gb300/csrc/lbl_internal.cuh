@@ -56,6 +56,7 @@ struct BatchItem {
   const uint16_t *V;
   uint64_t mask;
   int64_t warp0, warps;  // work units [warp0, warp0 + warps) of the batch
+  const int32_t *perm;   // output index of row e (NULL: e)
   int32_t m;
   uint8_t rel[8];
 };
@@ -156,6 +157,7 @@ struct StreamRows {
   const int64_t *part;
   int part_ctas;
   int64_t E, entries;
+  const int32_t *perm;  // output index of row e (NULL: e); with perm the outputs are not offset
 };
 
 struct Roadmap {
@@ -185,6 +187,11 @@ struct Roadmap {
   int64_t n_qd = 0;
   int64_t *qd_rowptr = nullptr;
   int32_t *qd_idx = nullptr;    // n_qd entries, padded like colidx
+  // Quadtree row i is the caller's edge qd_perm[i]: inside each of the
+  // kSessionChunks edge ranges the rows are sorted by their middle cell, so a
+  // CTA's edges lie close together and share pyramid lines in L1; NULL keeps
+  // the caller's order (roadmaps of 2^31 edges or more)
+  int32_t *qd_perm = nullptr;
   int64_t *qd_part = nullptr;   // partition of the quadtree stream's grid
   int qd_part_ctas = 0;
   QuadOffsets qd_off{};
@@ -277,10 +284,12 @@ cudaError_t launch_quad_pyramid(const Roadmap &rm, const uint64_t *O, int word_b
 cudaError_t launch_label_quad(const Roadmap &rm, const uint64_t *O, int32_t P, uint64_t *L,
                                 const MonitorTables *mon, int depth, cudaStream_t s);
 cudaError_t launch_quad_pyramid_batch(const PyrTable &tab, cudaStream_t s);
-cudaError_t launch_quad_count(const int64_t *rowptr, const int32_t *colidx, int64_t E, int32_t *count,
-                                cudaStream_t s);
-cudaError_t launch_quad_fill(const int64_t *rowptr, const int32_t *colidx, int64_t E, QuadOffsets off,
-                               const int64_t *drow, int32_t *idx, cudaStream_t s);
+// quadtree row e from CSR row rowmap[e] (rowmap NULL: row e); key[e] = middle cell of row e
+cudaError_t launch_row_keys(const int64_t *rowptr, const int32_t *colidx, int64_t E, uint32_t *key, cudaStream_t s);
+cudaError_t launch_quad_count(const int64_t *rowptr, const int32_t *colidx, int64_t E, const int32_t *rowmap,
+                                int32_t *count, cudaStream_t s);
+cudaError_t launch_quad_fill(const int64_t *rowptr, const int32_t *colidx, int64_t E, const int32_t *rowmap,
+                               QuadOffsets off, const int64_t *drow, int32_t *idx, cudaStream_t s);
 
 cudaError_t launch_label_bittile(const Roadmap &rm, const uint64_t *O, int32_t P, uint64_t *L,
                                  const MonitorTables *mon, bool early_exit, int ctas_per_sm, cudaStream_t s);

@@ -196,6 +196,7 @@ cudaError_t launch_group(lbl_server_s &S, Lane &lane, std::vector<Request *> &gr
     it = BatchItem{};
     it.rowptr = R.quad ? rm.qd_rowptr : rm.rowptr;
     it.colidx = R.quad ? rm.qd_idx : rm.colidx;
+    it.perm = R.quad ? rm.qd_perm : nullptr;
     it.part = R.part;
     it.O = r.d_O;
     if (R.quad) {  // gather from the request's pyramid, built after its transform
