@@ -208,8 +208,9 @@ def label_bytes(wl, algo: str, n_bt: int | None, with_monitor: bool, n_sec: int 
     re-read from L2)."""
     E = wl.n_edges
     out = 8 * E + (10 * E if with_monitor else 0)
-    if algo == "quad":  # pyramid: O read, pyramid written; stream: entries, rows, pyramid once
-        return (4 * n_qd + 8 * (E + 1) + 8 * wl.agent.cells
+    if algo == "quad":  # pyramid: O read, pyramid written; stream: entries, rows, row order, pyramid once
+        perm = 4 * E if 1 < E < 2**31 else 0  # the caller's edge of each row (rows are in locality order)
+        return (4 * n_qd + 8 * (E + 1) + perm + 8 * wl.agent.cells
                 + 2 * pyramid_word_bytes(wl.P) * pyramid_words(wl.agent.cells) + out)
     if algo == "sector":
         return 4 * n_sec + 8 * (E + 1) + 8 * wl.agent.cells + out
