@@ -144,7 +144,15 @@ int lbl_version(void);
                                      at most 2^30 cells) */
 #define LBL_UPLOAD_QUAD 8u        /* also derive the quadtree form used by LBL_ALGO_QUAD
                                      (4 B per maximal block of a row, plus a pyramid of
-                                     ~11 B per cell; grids of fewer than 2^30 cells) */
+                                     ~11 B per cell; grids of fewer than 2^30 cells).
+                                     On 2-D grids its rows are stored in locality order:
+                                     inside each quarter of the edges (E*c/4 .. E*(c+1)/4),
+                                     sorted by the z-order of the (x, y) of the row's
+                                     middle cell, 4 B per edge; outputs still land at the
+                                     caller's edge positions */
+#define LBL_UPLOAD_KEEP_ORDER 16u /* with LBL_UPLOAD_QUAD: keep the caller's edge order
+                                     for the quadtree rows (for roadmaps already ordered
+                                     for locality) */
 
 /*
  * lbl_roadmap_upload — make a roadmap resident on the device.

@@ -123,14 +123,34 @@ __device__ __forceinline__ int quad_level(const int32_t *__restrict__ colidx, in
   return j;
 }
 
-// Locality key of row e: its middle cell in the grid's order (0 for an empty row).
+// Bits 0..15 of v spread to the even positions 0, 2, ..., 30.
+__device__ __forceinline__ uint32_t spread_even(uint32_t v) {
+  v &= 0x0000FFFFu;
+  v = (v | (v << 8)) & 0x00FF00FFu;
+  v = (v | (v << 4)) & 0x0F0F0F0Fu;
+  v = (v | (v << 2)) & 0x33333333u;
+  return (v | (v << 1)) & 0x55555555u;
+}
+
+// Locality key of row e of a 2-D grid: the z-order index of its middle cell's
+// (x, y) (the cell index itself on a z-order grid; 0 for an empty row).
 __global__ void __launch_bounds__(256) k_row_keys(const int64_t *__restrict__ rowptr,
-                                                  const int32_t *__restrict__ colidx, int64_t E,
-                                                  uint32_t *__restrict__ key) {
+                                                  const int32_t *__restrict__ colidx, int64_t E, int32_t order,
+                                                  int32_t w, uint32_t *__restrict__ key) {
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < E; e += stride) {
     const int64_t beg = rowptr[e], n = rowptr[e + 1] - beg;
-    key[e] = n > 0 ? static_cast<uint32_t>(colidx[beg + n / 2]) : 0u;
+    uint32_t k = 0;
+    if (n > 0) {
+      const uint32_t c = static_cast<uint32_t>(colidx[beg + n / 2]);
+      if (order == LBL_ORDER_MORTON) {
+        k = c;
+      } else {
+        const uint32_t y = c / static_cast<uint32_t>(w), x = c - y * static_cast<uint32_t>(w);
+        k = (spread_even(x) << 1) | spread_even(y);
+      }
+    }
+    key[e] = k;
   }
 }
 
@@ -211,9 +231,10 @@ cudaError_t launch_bt_fill(const int64_t *rowptr, const int32_t *colidx, int64_t
 
 namespace lbl {
 
-cudaError_t launch_row_keys(const int64_t *rowptr, const int32_t *colidx, int64_t E, uint32_t *key, cudaStream_t s) {
+cudaError_t launch_row_keys(const int64_t *rowptr, const int32_t *colidx, int64_t E, int32_t order, int32_t w,
+                            uint32_t *key, cudaStream_t s) {
   if (E == 0) return cudaSuccess;
-  k_row_keys<<<blocks_for(E), 256, 0, s>>>(rowptr, colidx, E, key);
+  k_row_keys<<<blocks_for(E), 256, 0, s>>>(rowptr, colidx, E, order, w, key);
   return cudaGetLastError();
 }
 

@@ -305,7 +305,7 @@ extern "C" int lbl_roadmap_rasterize(const lbl_grid *agent, const double *h_arcs
     set_error("rasterize: need n_edges >= 0, arcs and a positive radius");
     return LBL_EINVAL;
   }
-  if (flags & ~(LBL_UPLOAD_BITTILE | LBL_UPLOAD_SECTOR | LBL_UPLOAD_QUAD)) {
+  if (flags & ~(LBL_UPLOAD_BITTILE | LBL_UPLOAD_SECTOR | LBL_UPLOAD_QUAD | LBL_UPLOAD_KEEP_ORDER)) {
     set_error("rasterize: unknown flags 0x%x", flags);
     return LBL_EINVAL;
   }

@@ -447,12 +447,15 @@ int roadmap_finish(lbl_roadmap_s *rm, uint32_t flags, cudaStream_t st) {
       words += rm->cells >> (2 * k);
     }
     rm->pyr_words = words;
-    if (n_edges > 1 && n_edges < (1LL << 31)) {
-      // locality order: inside each session edge range, rows by their middle cell
+    if (n_edges > 1 && n_edges < (1LL << 31) && !(flags & LBL_UPLOAD_KEEP_ORDER) && grid_depth(rm->agent) == 1) {
+      // locality order: inside each session edge range, rows by the z-order of
+      // their middle cell's (x, y); time-augmented grids keep the caller's
+      // order, which measured faster than every key tried there
       std::vector<uint32_t> key(static_cast<size_t>(n_edges));
       uint32_t *d_key = nullptr;
       if ((e = dev_alloc(&d_key, static_cast<size_t>(n_edges), nullptr)) != cudaSuccess ||
-          (e = launch_row_keys(rm->rowptr, rm->colidx, n_edges, d_key, st)) != cudaSuccess ||
+          (e = launch_row_keys(rm->rowptr, rm->colidx, n_edges, rm->agent.order, rm->agent.w, d_key, st)) !=
+              cudaSuccess ||
           (e = cudaMemcpyAsync(key.data(), d_key, sizeof(uint32_t) * n_edges, cudaMemcpyDeviceToHost, st)) !=
               cudaSuccess ||
           (e = cudaStreamSynchronize(st)) != cudaSuccess) {
@@ -530,7 +533,8 @@ int lbl_roadmap_upload(const lbl_grid *agent, const int64_t *rowptr, const int32
     set_error("roadmap upload: rowptr/colidx is NULL");
     return LBL_EINVAL;
   }
-  if (flags & ~(LBL_UPLOAD_DEVICE_PTRS | LBL_UPLOAD_BITTILE | LBL_UPLOAD_SECTOR | LBL_UPLOAD_QUAD)) {
+  if (flags & ~(LBL_UPLOAD_DEVICE_PTRS | LBL_UPLOAD_BITTILE | LBL_UPLOAD_SECTOR | LBL_UPLOAD_QUAD |
+                LBL_UPLOAD_KEEP_ORDER)) {
     set_error("roadmap upload: unknown flags 0x%x", flags);
     return LBL_EINVAL;
   }

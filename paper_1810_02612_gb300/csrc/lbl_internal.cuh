@@ -188,9 +188,10 @@ struct Roadmap {
   int64_t *qd_rowptr = nullptr;
   int32_t *qd_idx = nullptr;    // n_qd entries, padded like colidx
   // Quadtree row i is the caller's edge qd_perm[i]: inside each of the
-  // kSessionChunks edge ranges the rows are sorted by their middle cell, so a
-  // CTA's edges lie close together and share pyramid lines in L1; NULL keeps
-  // the caller's order (roadmaps of 2^31 edges or more)
+  // kSessionChunks edge ranges the rows of a 2-D grid are sorted by the z-order
+  // of their middle cell's (x, y), so a CTA's edges lie close together and
+  // share pyramid lines in L1; NULL keeps the caller's order (time-augmented
+  // grids, LBL_UPLOAD_KEEP_ORDER, roadmaps of 2^31 edges or more)
   int32_t *qd_perm = nullptr;
   int64_t *qd_part = nullptr;   // partition of the quadtree stream's grid
   int qd_part_ctas = 0;
@@ -284,8 +285,10 @@ cudaError_t launch_quad_pyramid(const Roadmap &rm, const uint64_t *O, int word_b
 cudaError_t launch_label_quad(const Roadmap &rm, const uint64_t *O, int32_t P, uint64_t *L,
                                 const MonitorTables *mon, int depth, cudaStream_t s);
 cudaError_t launch_quad_pyramid_batch(const PyrTable &tab, cudaStream_t s);
-// quadtree row e from CSR row rowmap[e] (rowmap NULL: row e); key[e] = middle cell of row e
-cudaError_t launch_row_keys(const int64_t *rowptr, const int32_t *colidx, int64_t E, uint32_t *key, cudaStream_t s);
+// quadtree row e from CSR row rowmap[e] (rowmap NULL: row e); key[e] = z-order
+// of the (x, y) of row e's middle cell (2-D grids of w columns in `order`)
+cudaError_t launch_row_keys(const int64_t *rowptr, const int32_t *colidx, int64_t E, int32_t order, int32_t w,
+                            uint32_t *key, cudaStream_t s);
 cudaError_t launch_quad_count(const int64_t *rowptr, const int32_t *colidx, int64_t E, const int32_t *rowmap,
                                 int32_t *count, cudaStream_t s);
 cudaError_t launch_quad_fill(const int64_t *rowptr, const int32_t *colidx, int64_t E, const int32_t *rowmap,

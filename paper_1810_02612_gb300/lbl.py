@@ -43,6 +43,7 @@ LBL_UPLOAD_DEVICE_PTRS = 1
 LBL_UPLOAD_BITTILE = 2
 LBL_UPLOAD_SECTOR = 4
 LBL_UPLOAD_QUAD = 8
+LBL_UPLOAD_KEEP_ORDER = 16
 
 # every entry point declared in include/lbl.h
 EXPORTS = (

@@ -586,3 +586,28 @@ def test_autotune_choice_is_exact_and_sticks(driving_small):
     assert np.array_equal(gpu_label(rm, O, wl.P, dict(algo=L.LBL_ALGO_AUTO)), want)
     assert np.array_equal(gpu_label(rm, O, wl.P, None), want)
     L.lbl_roadmap_status(rm.h)
+
+
+@pytest.mark.parametrize("order", [synth.MORTON, synth.ROWMAJOR])
+def test_quad_rows_in_locality_order_or_the_callers(order):
+    """The quadtree rows of a 2-D roadmap are stored sorted for locality (labels
+    and monitor outputs written back to the caller's edges) unless
+    LBL_UPLOAD_KEEP_ORDER keeps the caller's order; both equal the oracle."""
+    wl = synth.make("large", seed=21, edges=40_000, order=order)
+    mon = wl.monitor
+    hm = L.lbl_monitor_create(mon.n_states, mon.m, mon.relbits, mon.delta, mon.reject)
+    O_h = oracle.frame_transform(wl.world, wl.planes, wl.pose, wl.agent)
+    want = oracle.label(wl.rowptr, wl.colidx, O_h, wl.P, threads=8)
+    wn, wv = oracle.monitor(mon.n_states, mon.m, mon.relbits, mon.delta, mon.reject, want)
+    try:
+        for flags in (L.LBL_UPLOAD_QUAD, L.LBL_UPLOAD_QUAD | L.LBL_UPLOAD_KEEP_ORDER):
+            rm = L.lbl_roadmap_upload(wl.agent, wl.rowptr, wl.colidx, flags=flags)
+            try:
+                out, nx, vi = empty_u64(wl.n_edges), empty_u64(wl.n_edges), empty_u16(wl.n_edges)
+                L.lbl_label(rm, cuda(O_h), wl.P, out, hm, nx, vi, dict(algo=L.LBL_ALGO_QUAD))
+                assert np.array_equal(host(out), want), flags
+                assert np.array_equal(host(nx), wn) and np.array_equal(host(vi), wv), flags
+            finally:
+                L.lbl_roadmap_free(rm)
+    finally:
+        L.lbl_monitor_free(hm)
