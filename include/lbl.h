@@ -112,7 +112,7 @@ typedef struct {
   int32_t pipeline;       /* streaming CSR index stream (LBL_PIPE_*), 0 = default */
   int32_t depth;          /* register pipelines: groups of 32 entries in flight per
                              warp, 0 = the form's default: CSR 8 (default), 12 or 16;
-                             quadtree 8, 12 (default) or 16; sector form 4 (default)
+                             quadtree 8 (default), 12 or 16; sector form 4 (default)
                              or 8.  Deeper variants run fewer CTAs per SM */
 } lbl_config;
 

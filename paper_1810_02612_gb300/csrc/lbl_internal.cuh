@@ -120,9 +120,10 @@ struct PackTable {
 // Levels of the quadtree form: blocks of up to 4^4 = 256 cells.
 constexpr int kQuadLevels = 4;
 // Default register pipeline depth of the quadtree stream (groups of 32 entries
-// in flight per warp): its rows are short, so deeper pipelines pay (measured
-// on all four single-frame workloads).
-constexpr int kQuadDepth = 12;
+// in flight per warp).  With the rows in locality order a third of the
+// gathers hit L1, and four CTAs per SM at depth 8 beat three at depth 12
+// (and five or six at depths 6 or 4) on every single-frame workload.
+constexpr int kQuadDepth = 8;
 // Host-buffer sessions label big roadmaps in this many edge ranges and copy
 // each range's results to the host while the next one is labeled.
 constexpr int kSessionChunks = 4;
