@@ -98,3 +98,52 @@ def test_binding_refuses_host_arrays_for_device_arguments():
     g = B.lbl_grid(8, 8, 1.0, 0.0, 0.0, 0)
     with pytest.raises(TypeError):
         L.lbl_frame_transform(g, np.zeros((1, 8, 8), np.uint8), 1, (0, 0, 0), g, np.zeros(64, np.uint64), stream=0)
+
+
+def header_constants():
+    """Integer #defines of include/lbl.h (function-like macros excluded)."""
+    out = {}
+    for m in re.finditer(r"^#define\s+(LBL_[A-Z0-9_]+)\s+\(?(-?\d+)u?\)?", open(os.path.join(ROOT, "include", "lbl.h")).read(),
+                         flags=re.M):
+        out[m.group(1)] = int(m.group(2))
+    return out
+
+
+def test_binding_constants_equal_the_header():
+    consts = header_constants()
+    assert {"LBL_OK", "LBL_EINVAL", "LBL_ALGO_QUAD", "LBL_UPLOAD_QUAD", "LBL_UPLOAD_KEEP_ORDER"} <= set(consts)
+    for name, value in consts.items():
+        if hasattr(B, name):
+            assert getattr(B, name) == value, name
+    for name in ("LBL_ALGO_AUTO", "LBL_ALGO_CSR", "LBL_ALGO_BITTILE", "LBL_ALGO_SECTOR", "LBL_ALGO_QUAD",
+                 "LBL_UPLOAD_DEVICE_PTRS", "LBL_UPLOAD_BITTILE", "LBL_UPLOAD_SECTOR", "LBL_UPLOAD_QUAD",
+                 "LBL_UPLOAD_KEEP_ORDER", "LBL_STAGE_TRANSFORM", "LBL_STAGE_LABEL", "LBL_ORDER_MORTON"):
+        assert getattr(B, name) == consts[name], name
+
+
+def test_packed_word_width_follows_the_header_macro():
+    src = open(os.path.join(ROOT, "include", "lbl.h")).read()
+    m = re.search(r"#define LBL_PACKED_WORD_BYTES\(n_props\)\s*(.+)", src)
+    expr = m.group(1).replace("(n_props)", "P")
+    # the C conditional chain ((P) <= 8 ? 1 : ...) read as nested Python conditionals
+    py = re.sub(r"\(?P <= (\d+) \? (\d+) : ", r"(\2 if P <= \1 else ", expr).rstrip(")") + ")" * expr.count("?")
+    for P in range(0, 65):
+        assert L.packed_word_bytes(P) == eval(py, {"P": P}), P  # noqa: S307
+    assert [L.packed_word_bytes(P) for P in (0, 8, 9, 16, 17, 32, 33, 64)] == [1, 1, 2, 2, 4, 4, 8, 8]
+
+
+def test_transform_and_packing_refuse_bad_arguments_before_device_work():
+    """Grids past 32768 cells a side, and packed words off their width's
+    alignment, are refused by the host checks (the pointers here are never
+    dereferenced)."""
+    world = B.lbl_grid(4, 4, 0.3, 0.0, 0.0, 0)
+    tall = B.lbl_grid(3, 40_000, 0.01, 0.0, 0.0, 0)
+    with pytest.raises(L.LblError) as ei:
+        L.lbl_frame_transform(world, 4096, 1, (0.0, 0.0, 0.0), tall, 8192, stream=0)
+    assert ei.value.code == L.LBL_EINVAL
+    with pytest.raises(L.LblError) as ei:
+        L.lbl_pack_planes(world, 4096, 9, 8193, stream=0)  # 16-bit words at an odd address
+    assert ei.value.code == L.LBL_EINVAL and "aligned" in L.lbl_last_error()
+    with pytest.raises(L.LblError) as ei:
+        L.lbl_frame_transform_words(world, 8194, 33, (0.0, 0.0, 0.0), world, 8192, stream=0)  # 32-bit words
+    assert ei.value.code == L.LBL_EINVAL
