@@ -11,6 +11,11 @@ template <> struct WordOf<2> { using T = uint16_t; };
 template <> struct WordOf<4> { using T = uint32_t; };
 template <> struct WordOf<8> { using T = uint64_t; };
 
+// Plane bytes a thread has in flight in the byte-gather transform: with 16
+// rather than 8 the small grids, whose few threads wait on each batch in turn,
+// transform faster (driving 9.1 -> 8.4 us; 32 is no better; large grids unchanged).
+constexpr int kPlaneBatch = 16;
+
 // Grids have at most 32768 cells a side and fewer than 2^31 cells (checked on
 // the host), so cell indices and coordinates are 32-bit throughout.
 
@@ -63,6 +68,13 @@ __device__ __forceinline__ uint64_t cell_word(const FrameItem &f, uint32_t c) {
   } else {
     const uint8_t *p = f.planes + c;
     int q = 0;
+    for (; q + kPlaneBatch <= f.P; q += kPlaneBatch) {
+      uint8_t b[kPlaneBatch];
+#pragma unroll
+      for (int j = 0; j < kPlaneBatch; ++j) b[j] = __ldg(p + (q + j) * f.plane_cells);
+#pragma unroll
+      for (int j = 0; j < kPlaneBatch; ++j) word |= static_cast<uint64_t>(b[j] != 0) << (q + j);
+    }
     for (; q + 8 <= f.P; q += 8) {
       uint8_t b[8];
 #pragma unroll
