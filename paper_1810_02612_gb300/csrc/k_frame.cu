@@ -332,9 +332,9 @@ cudaError_t launch_pack_batch(const PackTable &tab, cudaStream_t s) {
 
 cudaError_t launch_frame_batch(const FrameTable &tab, int num_sms, cudaStream_t s) {
   if (tab.total == 0) return cudaSuccess;
+  (void)num_sms;  // a thread per cell: each thread's gathers are its only latency, no serial grid stride
   int64_t blocks = (tab.total + 255) / 256;
-  const int64_t cap = static_cast<int64_t>(num_sms) * 8;
-  if (blocks > cap) blocks = cap;
+  if (blocks > 2147483647LL) blocks = 2147483647LL;
   k_frame_batch<<<static_cast<unsigned>(blocks), 256, 0, s>>>(tab);
   return cudaGetLastError();
 }
