@@ -296,7 +296,7 @@ extern "C" int lbl_roadmap_rasterize(const lbl_grid *agent, const double *h_arcs
     return LBL_EINVAL;
   }
   *out = nullptr;
-  if (!valid_grid_public(agent, "rasterize", true)) return LBL_EINVAL;
+  if (!valid_grid(agent, "rasterize", true)) return LBL_EINVAL;
   if (grid_depth(*agent) > 1) {
     set_error("rasterize: time-augmented grids are not rasterised on the device (upload their rows)");
     return LBL_EUNSUPPORTED;
@@ -335,7 +335,7 @@ extern "C" int lbl_roadmap_rasterize(const lbl_grid *agent, const double *h_arcs
   if (e == cudaSuccess) e = cudaGetDevice(&dev);
   const int64_t warps = n_edges;
   int64_t blocks = (warps + 7) / 8;
-  const int64_t cap = static_cast<int64_t>(device_sms_public(dev)) * 16;
+  const int64_t cap = static_cast<int64_t>(device_sms(dev)) * 16;
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
   if (e == cudaSuccess && n_edges) {
@@ -376,7 +376,7 @@ extern "C" int lbl_roadmap_rasterize(const lbl_grid *agent, const double *h_arcs
   cudaFree(d_arcs);
   cudaFree(d_counts);
   if (e != cudaSuccess) {
-    free_roadmap_public(rm);
+    free_roadmap(rm);
     return cuda_fail(e, "rasterize: fill");
   }
   rc = roadmap_finish(rm, flags, st);

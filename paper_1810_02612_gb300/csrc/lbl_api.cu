@@ -1,5 +1,7 @@
-// C ABI of liblbl (declared in include/lbl.h): argument checks, handles,
-// device memory of roadmaps and sessions, and kernel dispatch.
+// C ABI of liblbl (declared in include/lbl.h): argument checks, roadmap and
+// monitor handles with their device memory, frame transforms and labeling
+// dispatch.  Batches live in lbl_batch.cu, sessions in lbl_session.cu, the
+// server in lbl_server.cu.
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -15,6 +17,17 @@ namespace lbl {
 namespace {
 thread_local std::string g_err;
 constexpr int kDefaultPipeline = LBL_PIPE_REGISTERS;  // measured fastest on GB300
+
+int resolve_lpe(const Roadmap &rm, const lbl_config *cfg) {
+  int lpe = cfg ? cfg->lanes_per_edge : 0;
+  if (lpe == 4 || lpe == 8 || lpe == 16 || lpe == 32) return lpe;
+  const double avg = rm.E ? static_cast<double>(rm.nnz) / static_cast<double>(rm.E) : 0.0;
+  lpe = 4;
+  while (lpe < 32 && lpe * 16 < avg) lpe *= 2;
+  return lpe;
+}
+
+}  // namespace
 
 int device_sms(int dev) {
   static int cache[64] = {0};
@@ -72,14 +85,6 @@ bool same_device(int dev) {
   return true;
 }
 
-template <typename T>
-cudaError_t dev_alloc(T **p, size_t count, int64_t *bytes) {
-  const size_t b = count * sizeof(T);
-  cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), b ? b : 16);
-  if (e == cudaSuccess && bytes) *bytes += static_cast<int64_t>(b);
-  return e;
-}
-
 void free_roadmap(Roadmap *rm) {
   if (!rm) return;
   cudaFree(rm->rowptr);
@@ -101,22 +106,7 @@ void free_roadmap(Roadmap *rm) {
   delete rm;
 }
 
-int resolve_lpe(const Roadmap &rm, const lbl_config *cfg) {
-  int lpe = cfg ? cfg->lanes_per_edge : 0;
-  if (lpe == 4 || lpe == 8 || lpe == 16 || lpe == 32) return lpe;
-  const double avg = rm.E ? static_cast<double>(rm.nnz) / static_cast<double>(rm.E) : 0.0;
-  lpe = 4;
-  while (lpe < 32 && lpe * 16 < avg) lpe *= 2;
-  return lpe;
-}
 
-}  // namespace
-
-// Q32.32 coefficients of (ix, iy) -> continuous world-cell coordinates:
-//   u = a00*ix + a01*iy + b0,  v = a10*ix + a11*iy + b1,
-// from world point q = (X, Y) + R(theta) * centre(ix, iy) (Sec. 5, eq. 13).
-// The double expressions are evaluated exactly as written (the library is built
-// without floating-point contraction) and each is rounded half to even.
 // perm[a..b) = a..b-1 ordered by key (stable): LSD radix sort, two 16-bit digits.
 void sort_range_by_key(const uint32_t *key, int64_t a, int64_t b, int32_t *perm) {
   const int64_t n = b - a;
@@ -135,6 +125,11 @@ void sort_range_by_key(const uint32_t *key, int64_t a, int64_t b, int32_t *perm)
   // two passes: the sorted order is back in perm + a
 }
 
+// Q32.32 coefficients of (ix, iy) -> continuous world-cell coordinates:
+//   u = a00*ix + a01*iy + b0,  v = a10*ix + a11*iy + b1,
+// from world point q = (X, Y) + R(theta) * centre(ix, iy) (Sec. 5, eq. 13).
+// The double expressions are evaluated exactly as written (the library is built
+// without floating-point contraction) and each is rounded half to even.
 bool frame_map(const lbl_grid &W, const lbl_grid &A, const lbl_pose &p, FrameMap *out) {
   if (!std::isfinite(p.x) || !std::isfinite(p.y) || !std::isfinite(p.theta) || !std::isfinite(p.t)) {
     set_error("frame transform: pose must be finite");
@@ -201,6 +196,8 @@ void set_error(const char *fmt, ...) {
   g_err = buf;
 }
 
+void clear_error() { g_err.clear(); }
+
 int cuda_fail(cudaError_t e, const char *what) {
   set_error("%s: %s", what, cudaGetErrorString(e));
   return e == cudaErrorMemoryAllocation ? LBL_ENOMEM : LBL_ECUDA;
@@ -209,87 +206,10 @@ int cuda_fail(cudaError_t e, const char *what) {
 }  // namespace lbl
 
 using namespace lbl;
-struct lbl_batch_s {
-  int device = 0;
-  int num_sms = 1;
-  int32_t n = 0;
-  std::vector<lbl_roadmap> rms;
-  std::vector<int32_t> P;
-  std::vector<lbl_monitor> mons;
-  int64_t *part = nullptr;  // every item's partition, concatenated
-  unsigned long long *counter = nullptr;  // next work unit of each class's label launch
-  int ctas = 1;
-  // items grouped by gathered word width (class c = 1, 2, 4, 8 bytes); item i
-  // is entry slot[i] of tabs[cls[i]]
-  BatchTable tabs[kWordClasses]{};
-  std::vector<int> cls, slot;
-  FrameTable ftab{};
-  // items whose roadmap has the quadtree form label from their own pyramid
-  uint64_t *pyr = nullptr;      // every such item's pyramid, concatenated
-  std::vector<int> pyr_slot;    // item -> entry of ptab, or -1
-  PyrTable ptab{};
-  // frames whose world has at most kPackedWorldRatio times the agent's cells
-  // are packed (one launch) and transformed from 64-bit words; the words
-  // buffer grows on demand, and a replaced buffer is kept until the batch is
-  // freed so graphs captured before still see live memory
-  PackTable pktab{};
-  uint64_t *words = nullptr;
-  int64_t words_cap = 0;
-  std::vector<uint64_t *> retired;
-  bool frames_set = false;
-};
 
-struct lbl_session_s {
-  int device = 0;
-  lbl_roadmap rm = nullptr;
-  lbl_monitor mon = nullptr;
-  lbl_grid world{};
-  int32_t P = 0;
-  lbl_config cfg{};
-  bool has_cfg = false;
-  uint8_t *planes = nullptr;
-  uint64_t *O = nullptr, *L = nullptr, *next = nullptr;
-  uint16_t *viol = nullptr;
-  // Two plane buffers, filled on `cin` in turn: frame i+1's planes go to the
-  // device while frame i is transformed and labeled.  ev_in[k]: slot k filled;
-  // ev_free[k]: the transform that read slot k is done.
-  uint8_t *slot[2] = {nullptr, nullptr};
-  cudaStream_t cin = nullptr;
-  cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
-  int64_t frame = 0;
-  // The session's kernels run on `cc`, and its outputs go to one of two device
-  // buffer sets in turn, so frame i+1 computes while frame i's results are
-  // still being copied out; ev_out[k]: output set k copied to the host.
-  cudaStream_t cc = nullptr;
-  uint64_t *Ls[2] = {nullptr, nullptr}, *Ns[2] = {nullptr, nullptr};
-  uint16_t *Vs[2] = {nullptr, nullptr};
-  cudaEvent_t ev_out[2] = {nullptr, nullptr};
-  uint64_t *pyr = nullptr;  // the session's own quadtree pyramid (chunked quadtree sessions)
-  // Packed world words: the planes are packed (one coalesced pass) and the
-  // transform gathers one word per agent cell.  Used for planes of at least
-  // kPackedMinPlaneBytes on a world of at most kPackedWorldRatio times the
-  // agent's cells, so packing reads little the transform would not.
-  uint8_t *words = nullptr;
-  // Chunked labeling: the edges in kSessionChunks ranges, each labeled by the
-  // whole grid; a range's results go to the host on `cs` while the next range
-  // is labeled.  Used with the default form (quadtree, else streaming CSR).
-  bool chunked = false;
-  bool quad = false;
-  int depth = 8, ctas = 0;
-  int64_t edge0[lbl::kSessionChunks + 1] = {0};
-  int64_t *cpart = nullptr;  // kSessionChunks partitions of warps + 1 entries
-  int64_t warps = 0;
-  cudaStream_t cs = nullptr;
-  cudaEvent_t ev[lbl::kSessionChunks + 1] = {nullptr};
-};
 
 namespace lbl {
 
-bool valid_grid_public(const lbl_grid *g, const char *name, bool need_order) {
-  return valid_grid(g, name, need_order);
-}
-int device_sms_public(int dev) { return device_sms(dev); }
-void free_roadmap_public(lbl_roadmap_s *rm) { free_roadmap(rm); }
 
 // A roadmap with device arrays for its CSR (rowptr int64[E+1], colidx padded
 // to whole 16-byte vectors plus one, the padding zeroed); contents to be
@@ -765,7 +685,11 @@ int lbl_monitor_free(lbl_monitor mon) {
   return LBL_OK;
 }
 
-static MonitorTables tables_of(const Monitor &mon, uint64_t *next, uint16_t *viol) {
+}  // extern "C"
+
+namespace lbl {
+
+MonitorTables tables_of(const Monitor &mon, uint64_t *next, uint16_t *viol) {
   MonitorTables t{};
   t.T = mon.T;
   t.V = mon.V;
@@ -775,6 +699,10 @@ static MonitorTables tables_of(const Monitor &mon, uint64_t *next, uint16_t *vio
   for (int j = 0; j < 8; ++j) t.rel[j] = mon.rel[j];
   return t;
 }
+
+}  // namespace lbl
+
+extern "C" {
 
 int lbl_monitor_step(lbl_monitor mon, const uint64_t *d_L, int64_t n, uint64_t *d_next, uint16_t *d_viol,
                      lbl_stream s) {
@@ -790,8 +718,12 @@ int lbl_monitor_step(lbl_monitor mon, const uint64_t *d_L, int64_t n, uint64_t *
   return LBL_OK;
 }
 
-static int label_impl(lbl_roadmap rm, const uint64_t *d_O, int32_t n_props, uint64_t *d_L, lbl_monitor mon,
-                      uint64_t *d_next, uint16_t *d_viol, const lbl_config *cfg, cudaStream_t st) {
+}  // extern "C"
+
+namespace lbl {
+
+int label_impl(lbl_roadmap rm, const uint64_t *d_O, int32_t n_props, uint64_t *d_L, lbl_monitor mon,
+               uint64_t *d_next, uint16_t *d_viol, const lbl_config *cfg, cudaStream_t st) {
   if (!rm) {
     set_error("label: NULL roadmap");
     return LBL_EINVAL;
@@ -908,6 +840,10 @@ static int label_impl(lbl_roadmap rm, const uint64_t *d_O, int32_t n_props, uint
   return LBL_OK;
 }
 
+}  // namespace lbl
+
+extern "C" {
+
 int lbl_label(lbl_roadmap rm, const uint64_t *d_O, int32_t n_props, uint64_t *d_L, lbl_monitor mon, uint64_t *d_next,
               uint16_t *d_viol, const lbl_config *cfg, lbl_stream s) {
   g_err.clear();
@@ -960,455 +896,6 @@ int lbl_roadmap_autotune(lbl_roadmap rm, const uint64_t *d_O, int32_t n_props, l
   rm->tuned[n_props] = cand[best_i];
   rm->tuned_valid[n_props] = true;
   if (chosen) *chosen = cand[best_i];
-  return LBL_OK;
-}
-
-int lbl_batch_create(int32_t n, const lbl_roadmap *rms, const int32_t *n_props, const lbl_monitor *mons,
-                     int32_t ctas_per_sm, lbl_batch *out) {
-  g_err.clear();
-  if (!out) {
-    set_error("batch create: out is NULL");
-    return LBL_EINVAL;
-  }
-  *out = nullptr;
-  if (n < 1 || n > kMaxBatch || !rms || !n_props) {
-    set_error("batch create: need 1 <= n <= %d roadmaps and their proposition counts", kMaxBatch);
-    return LBL_EINVAL;
-  }
-  for (int i = 0; i < n; ++i) {
-    if (!rms[i] || n_props[i] < 0 || n_props[i] > 64) {
-      set_error("batch create: item %d has no roadmap or n_props outside 0..64", i);
-      return LBL_EINVAL;
-    }
-    if (rms[i]->device != rms[0]->device || (mons && mons[i] && mons[i]->device != rms[0]->device)) {
-      set_error("batch create: items live on different devices");
-      return LBL_EINVAL;
-    }
-  }
-  if (!same_device(rms[0]->device)) return LBL_EINVAL;
-  lbl_batch_s *b = new (std::nothrow) lbl_batch_s();
-  if (!b) {
-    set_error("batch create: out of host memory");
-    return LBL_ENOMEM;
-  }
-  b->device = rms[0]->device;
-  b->num_sms = rms[0]->num_sms;
-  b->n = n;
-  b->rms.assign(rms, rms + n);
-  b->P.assign(n_props, n_props + n);
-  b->mons.assign(n, nullptr);
-  if (mons) b->mons.assign(mons, mons + n);
-  // The persistent grid's warps take work units from a counter; items are
-  // cut into units of about equal cost (nonzeros + kEdgeCost per edge),
-  // kUnitsPerWarp per warp overall, at least one per item with edges.
-  bool all_quad = true;
-  for (int i = 0; i < n; ++i) all_quad = all_quad && (rms[i]->has_qd || rms[i]->E == 0);
-  const int depth = all_quad ? kQuadDepth : 8;
-  for (BatchTable &t : b->tabs) t.depth = depth;
-  const int occ = batch_ctas_per_sm(depth);
-  const int ctas = ctas_per_sm > 0 ? std::min<int>(ctas_per_sm, occ) : occ;
-  b->ctas = ctas;
-  constexpr int64_t kUnitsPerWarp = 8;
-  const int64_t units_target = static_cast<int64_t>(b->num_sms) * ctas * (kThreads / 32) * kUnitsPerWarp;
-  // entries streamed per item: quadtree entries when the roadmap has them;
-  // word width of its gathers (items of one width share a launch)
-  auto entries = [](const Roadmap &r) { return r.has_qd ? r.n_qd : r.nnz; };
-  auto width = [&](int i) { return rms[i]->has_qd && rms[i]->E > 0 ? quad_word_bytes(*rms[i], n_props[i]) : 8; };
-  // every class's launch gets about kUnitsPerWarp units per warp of its own
-  double total[kWordClasses] = {0, 0, 0, 0};
-  for (int i = 0; i < n; ++i) total[word_class(width(i))] += static_cast<double>(entries(*rms[i]) + kEdgeCost * rms[i]->E);
-  std::vector<int64_t> W(n), off(n + 1, 0);
-  int64_t pyr_words = 0;
-  for (int i = 0; i < n; ++i)
-    if (rms[i]->has_qd && rms[i]->E > 0) pyr_words += rms[i]->pyr_words;
-  for (int i = 0; i < n; ++i) {
-    const Roadmap &r = *rms[i];
-    W[i] = 0;
-    if (r.E > 0) {
-      const double c = static_cast<double>(entries(r) + kEdgeCost * r.E);
-      const double unit_cost = total[word_class(width(i))] / static_cast<double>(units_target);
-      W[i] = std::max<int64_t>(1, static_cast<int64_t>(std::ceil(c / unit_cost)));
-      W[i] = std::min<int64_t>(W[i], r.E);  // never more units than edges
-    }
-    off[i + 1] = off[i] + W[i] + 1;
-  }
-  cudaError_t e = dev_alloc(&b->part, static_cast<size_t>(off[n]), nullptr);
-  if (e == cudaSuccess) e = dev_alloc(&b->counter, kWordClasses, nullptr);
-  if (e == cudaSuccess && pyr_words > 0) e = dev_alloc(&b->pyr, static_cast<size_t>(pyr_words), nullptr);
-  b->pyr_slot.assign(n, -1);
-  b->cls.assign(n, kWordClasses - 1);
-  b->slot.assign(n, 0);
-  int64_t pyr0 = 0, block0 = 0;
-  for (int i = 0; i < n && e == cudaSuccess; ++i) {
-    const Roadmap &r = *rms[i];
-    const bool quad = r.has_qd && r.E > 0;
-    const int wb = width(i);
-    e = launch_partition_into(quad ? r.qd_rowptr : r.rowptr, r.E, W[i], b->part + off[i], nullptr);
-    BatchTable &tb = b->tabs[word_class(wb)];
-    b->cls[i] = word_class(wb);
-    b->slot[i] = tb.n;
-    tb.word_bytes = wb;
-    BatchItem &it = tb.items[tb.n++];
-    it = BatchItem{};
-    it.rowptr = quad ? r.qd_rowptr : r.rowptr;
-    it.colidx = quad ? r.qd_idx : r.colidx;
-    it.perm = quad ? r.qd_perm : nullptr;
-    it.part = b->part + off[i];
-    if (quad) {  // labels gather from the item's pyramid, built from its O at the label stage
-      PyrItem &pi = b->ptab.items[b->ptab.n];
-      pi = PyrItem{};
-      pi.pyr = b->pyr + pyr0;
-      pi.cells = r.cells;
-      pi.block0 = block0;
-      pi.off = r.qd_off;
-      pi.word_bytes = wb;
-      it.O = pi.pyr;
-      b->pyr_slot[i] = b->ptab.n++;
-      pyr0 += r.pyr_words;
-      block0 += (r.cells + kThreads - 1) / kThreads;
-    }
-    it.mask = n_props[i] >= 64 ? ~0ull : ((1ull << n_props[i]) - 1ull);
-    it.warp0 = tb.total;  // work units of this class's launch
-    it.warps = W[i];
-    if (b->mons[i]) {
-      const Monitor &m = *b->mons[i];
-      it.T = m.T;
-      it.V = m.V;
-      it.m = m.m;
-      for (int j = 0; j < 8; ++j) it.rel[j] = m.rel[j];
-    }
-    tb.total += W[i];
-    if (entries(r) >= kNarrowLimit || r.E >= kNarrowLimit) tb.wide = 1;
-  }
-  if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
-  if (e != cudaSuccess) {
-    cudaFree(b->part);
-    cudaFree(b->counter);
-    cudaFree(b->pyr);
-    delete b;
-    return cuda_fail(e, "batch create: partitions");
-  }
-  b->ptab.total = block0;
-  b->ftab.n = n;
-  *out = b;
-  return LBL_OK;
-}
-
-int lbl_batch_set_frames(lbl_batch b, const lbl_frame *frames) {
-  g_err.clear();
-  if (!b || !frames) {
-    set_error("batch frames: NULL batch or frames");
-    return LBL_EINVAL;
-  }
-  int64_t cell0 = 0;
-  for (int i = 0; i < b->n; ++i) {
-    const lbl_frame &f = frames[i];
-    const Roadmap &r = *b->rms[i];
-    const int32_t P = b->P[i];
-    if (!valid_grid(&f.world, "batch frames (world)", false)) return LBL_EINVAL;
-    if ((P > 0 && !f.d_planes) || !f.d_O || (r.E > 0 && !f.d_L) ||
-        (b->mons[i] && r.E > 0 && (!f.d_next || !f.d_viol))) {
-      set_error("batch frames: frame %d is missing a buffer", i);
-      return LBL_EINVAL;
-    }
-    FrameMap m;
-    if (!frame_map(f.world, r.agent, f.pose, &m)) return LBL_EINVAL;
-    b->ftab.items[i] = frame_item(m, f.world, r.agent, f.d_planes, P, f.d_O, cell0);
-    cell0 += r.cells;
-    BatchItem &it = b->tabs[b->cls[i]].items[b->slot[i]];
-    if (b->pyr_slot[i] >= 0)
-      b->ptab.items[b->pyr_slot[i]].O = f.d_O;  // the item gathers from its pyramid
-    else
-      it.O = f.d_O;
-    it.L = f.d_L;
-    it.next = f.d_next;
-    it.viol = f.d_viol;
-  }
-  b->ftab.total = cell0;
-  // packed frames: 64-bit words at 4-word aligned offsets (vector stores)
-  int64_t need = 0;
-  std::vector<int64_t> woff(b->n, -1);
-  for (int i = 0; i < b->n; ++i) {
-    const int64_t wc = grid_cells(frames[i].world);
-    if (b->P[i] > 0 && wc > 0 && wc <= kPackedWorldRatio * b->rms[i]->cells) {
-      woff[i] = need;
-      need += (wc + 3) / 4 * 4;
-    }
-  }
-  if (need > b->words_cap) {
-    uint64_t *w = nullptr;
-    cudaError_t e = dev_alloc(&w, static_cast<size_t>(need), nullptr);
-    if (e != cudaSuccess) return cuda_fail(e, "batch frames: packed words");
-    if (b->words) b->retired.push_back(b->words);
-    b->words = w;
-    b->words_cap = need;
-  }
-  PackTable &pt = b->pktab;
-  pt.n = 0;
-  pt.lane0[0] = 0;
-  for (int i = 0; i < b->n; ++i) {
-    FrameItem &fi = b->ftab.items[i];
-    fi.words = nullptr;
-    if (woff[i] < 0) continue;
-    const int32_t P = b->P[i];
-    const PackItem it{frames[i].d_planes, b->words + woff[i], grid_cells(frames[i].world), P, 8};
-    pt.items[pt.n] = it;
-    pt.vec[pt.n] = pack_vec_ok(it) ? 1 : 0;
-    pt.lane0[pt.n + 1] = pt.lane0[pt.n] + (it.cells + 3) / 4;
-    ++pt.n;
-    fi.words = it.words;
-    fi.word_bytes = 8;
-    fi.wmask = P >= 64 ? ~0ull : ((1ull << P) - 1ull);
-  }
-  b->frames_set = true;
-  return LBL_OK;
-}
-
-int lbl_batch_launch(lbl_batch b, uint32_t stages, lbl_stream s) {
-  g_err.clear();
-  if (!b || !b->frames_set || (stages & ~(LBL_STAGE_TRANSFORM | LBL_STAGE_LABEL))) {
-    set_error("batch launch: NULL batch, no frames set, or unknown stages");
-    return LBL_EINVAL;
-  }
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(s);
-  cudaError_t e = cudaSuccess;
-  if (stages & LBL_STAGE_TRANSFORM) {
-    e = launch_pack_batch(b->pktab, st);
-    if (e == cudaSuccess) e = launch_frame_batch(b->ftab, b->num_sms, st);
-  }
-  if (e == cudaSuccess && (stages & LBL_STAGE_LABEL)) {
-    e = launch_quad_pyramid_batch(b->ptab, st);
-    for (int c = 0; c < kWordClasses && e == cudaSuccess; ++c)
-      if (b->tabs[c].n > 0) e = launch_label_batch(b->tabs[c], b->counter + c, b->num_sms, b->ctas, st);
-  }
-  if (e != cudaSuccess) return cuda_fail(e, "batch launch");
-  return LBL_OK;
-}
-
-int lbl_batch_free(lbl_batch b) {
-  g_err.clear();
-  if (!b) return LBL_OK;
-  cudaDeviceSynchronize();
-  cudaFree(b->part);
-  cudaFree(b->counter);
-  cudaFree(b->pyr);
-  cudaFree(b->words);
-  for (uint64_t *w : b->retired) cudaFree(w);
-  delete b;
-  return LBL_OK;
-}
-
-int lbl_session_create(lbl_roadmap rm, const lbl_grid *world, int32_t n_props, lbl_monitor mon,
-                       const lbl_config *cfg, lbl_session *out) {
-  g_err.clear();
-  if (!out) {
-    set_error("session create: out is NULL");
-    return LBL_EINVAL;
-  }
-  *out = nullptr;
-  if (!rm) {
-    set_error("session create: NULL roadmap");
-    return LBL_EINVAL;
-  }
-  if (!valid_grid(world, "session create (world)", false)) return LBL_EINVAL;
-  if (n_props < 0 || n_props > 64) {
-    set_error("session create: n_props = %d outside 0..64", n_props);
-    return LBL_EINVAL;
-  }
-  if (!same_device(rm->device)) return LBL_EINVAL;
-  lbl_session_s *ss = new (std::nothrow) lbl_session_s();
-  if (!ss) {
-    set_error("session create: out of host memory");
-    return LBL_ENOMEM;
-  }
-  ss->device = rm->device;
-  ss->rm = rm;
-  ss->mon = mon;
-  ss->world = *world;
-  ss->P = n_props;
-  if (cfg) {
-    ss->cfg = *cfg;
-    ss->has_cfg = true;
-  }
-  const size_t plane_bytes = static_cast<size_t>(n_props) * grid_cells(*world);
-  cudaError_t e = dev_alloc(&ss->planes, 2 * plane_bytes, nullptr);
-  ss->slot[0] = ss->planes;
-  ss->slot[1] = ss->planes + plane_bytes;
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ss->cin, cudaStreamNonBlocking);
-  for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
-    e = cudaEventCreateWithFlags(&ss->ev_in[k], cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ss->ev_free[k], cudaEventDisableTiming);
-  }
-  if (e == cudaSuccess) e = dev_alloc(&ss->O, static_cast<size_t>(rm->cells), nullptr);
-  if (e == cudaSuccess && static_cast<int64_t>(plane_bytes) >= kPackedMinPlaneBytes &&
-      grid_cells(*world) <= kPackedWorldRatio * rm->cells)
-    e = dev_alloc(&ss->words, static_cast<size_t>(grid_cells(*world)) * packed_word_bytes(n_props), nullptr);
-  if (e == cudaSuccess) e = dev_alloc(&ss->L, static_cast<size_t>(2 * rm->E), nullptr);
-  if (e == cudaSuccess && mon) e = dev_alloc(&ss->next, static_cast<size_t>(2 * rm->E), nullptr);
-  if (e == cudaSuccess && mon) e = dev_alloc(&ss->viol, static_cast<size_t>(2 * rm->E), nullptr);
-  for (int k = 0; k < 2; ++k) {
-    ss->Ls[k] = ss->L ? ss->L + k * rm->E : nullptr;
-    ss->Ns[k] = ss->next ? ss->next + k * rm->E : nullptr;
-    ss->Vs[k] = ss->viol ? ss->viol + k * rm->E : nullptr;
-  }
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ss->cc, cudaStreamNonBlocking);
-  for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&ss->ev_out[k], cudaEventDisableTiming);
-
-  // Chunked labeling when the configuration resolves to a register-pipelined
-  // stream (quadtree, or CSR without lane groups, early exit or copy rings) on
-  // a roadmap big enough to pay.
-  lbl_config c{};
-  if (cfg) c = *cfg;
-  if (c.algo == LBL_ALGO_AUTO && rm->tuned_valid[n_props]) c = rm->tuned[n_props];
-  if (c.algo == LBL_ALGO_AUTO)  // as lbl_label resolves it
-    c.algo = rm->has_qd ? LBL_ALGO_QUAD : (rm->has_bt && n_props <= 8) ? LBL_ALGO_BITTILE : LBL_ALGO_CSR;
-  const bool stream_form = (c.algo == LBL_ALGO_QUAD && rm->has_qd) ||
-                           (c.algo == LBL_ALGO_CSR && c.lanes_per_edge == 0 && c.early_exit <= 0 &&
-                            (c.pipeline == 0 || c.pipeline == LBL_PIPE_REGISTERS));
-  if (e == cudaSuccess && stream_form && rm->E >= kSessionChunkMinEdges) {
-    ss->chunked = true;
-    ss->quad = c.algo == LBL_ALGO_QUAD;
-    if (ss->quad) e = dev_alloc(&ss->pyr, static_cast<size_t>(rm->pyr_words), nullptr);
-    ss->depth = c.depth ? c.depth : (ss->quad ? kQuadDepth : 8);
-    const int occ = stream_ctas_per_sm(ss->depth);
-    ss->ctas = c.ctas_per_sm > 0 ? std::min(c.ctas_per_sm, occ) : occ;
-    ss->warps = static_cast<int64_t>(rm->num_sms) * ss->ctas * (kThreads / 32);
-    for (int c = 0; c <= kSessionChunks; ++c) ss->edge0[c] = rm->E * c / kSessionChunks;
-    const int64_t *rows = ss->quad ? rm->qd_rowptr : rm->rowptr;
-    e = dev_alloc(&ss->cpart, static_cast<size_t>(kSessionChunks * (ss->warps + 1)), nullptr);
-    for (int c = 0; c < kSessionChunks && e == cudaSuccess; ++c)
-      e = launch_partition_into(rows + ss->edge0[c], ss->edge0[c + 1] - ss->edge0[c], ss->warps,
-                                ss->cpart + c * (ss->warps + 1), nullptr);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
-  }
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ss->cs, cudaStreamNonBlocking);
-  for (int c = 0; c <= kSessionChunks && e == cudaSuccess; ++c)
-    e = cudaEventCreateWithFlags(&ss->ev[c], cudaEventDisableTiming);
-  if (e != cudaSuccess) {
-    lbl_session_free(ss);
-    return cuda_fail(e, "session create");
-  }
-  *out = ss;
-  return LBL_OK;
-}
-
-int lbl_session_run(lbl_session ss, const uint8_t *h_planes, lbl_pose pose, uint64_t *h_L, uint64_t *h_next,
-                    uint16_t *h_viol, lbl_stream s) {
-  g_err.clear();
-  if (!ss) {
-    set_error("session run: NULL session");
-    return LBL_EINVAL;
-  }
-  const Roadmap &rm = *ss->rm;
-  if ((ss->P > 0 && !h_planes) || (rm.E > 0 && !h_L)) {
-    set_error("session run: NULL host buffer");
-    return LBL_EINVAL;
-  }
-  if (!same_device(ss->device)) return LBL_EINVAL;
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(s);
-  // A chunked session touches only its own device memory (planes, O,
-  // pyramid, partitions, outputs) besides the roadmap's read-only rows, so
-  // its kernels run on its own stream `cc` and frame i+1 computes while frame
-  // i's results are still being copied out.  Other sessions label through
-  // lbl_label (roadmap-owned working memory), ordered on the caller's stream.
-  cudaStream_t cc = ss->chunked ? ss->cc : st;
-  const size_t plane_bytes = static_cast<size_t>(ss->P) * grid_cells(ss->world);
-  const int k = static_cast<int>(ss->frame & 1);  // plane slot and output set of this frame
-  uint64_t *dL = ss->Ls[k], *dN = ss->Ns[k];
-  uint16_t *dV = ss->Vs[k];
-  // planes in on `cin` once slot k is no longer read
-  cudaError_t e = cudaStreamWaitEvent(ss->cin, ss->ev_free[k], 0);
-  if (e == cudaSuccess && plane_bytes)
-    e = cudaMemcpyAsync(ss->slot[k], h_planes, plane_bytes, cudaMemcpyHostToDevice, ss->cin);
-  if (e == cudaSuccess) e = cudaEventRecord(ss->ev_in[k], ss->cin);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(cc, ss->ev_in[k], 0);
-  if (e != cudaSuccess) return cuda_fail(e, "session run: copy planes");
-  int rc = LBL_OK;
-  if (ss->words) {
-    const PackItem it{ss->slot[k], ss->words, grid_cells(ss->world), ss->P, packed_word_bytes(ss->P)};
-    if ((e = launch_pack_planes(it, cc)) != cudaSuccess) return cuda_fail(e, "session run: pack planes");
-    rc = lbl_frame_transform_words(&ss->world, ss->words, ss->P, pose, &rm.agent, ss->O, reinterpret_cast<lbl_stream>(cc));
-  } else {
-    rc = lbl_frame_transform(&ss->world, ss->slot[k], ss->P, pose, &rm.agent, ss->O, reinterpret_cast<lbl_stream>(cc));
-  }
-  if (rc != LBL_OK) return rc;
-  if ((e = cudaEventRecord(ss->ev_free[k], cc)) != cudaSuccess ||
-      (e = cudaStreamWaitEvent(cc, ss->ev_out[k], 0)) != cudaSuccess)  // output set k copied out (frame i-2)
-    return cuda_fail(e, "session run: event");
-  ++ss->frame;
-  auto copy_out = [&](int64_t e0, int64_t n) {
-    cudaError_t r = cudaMemcpyAsync(h_L + e0, dL + e0, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost, ss->cs);
-    if (r == cudaSuccess && ss->mon && h_next)
-      r = cudaMemcpyAsync(h_next + e0, dN + e0, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost, ss->cs);
-    if (r == cudaSuccess && ss->mon && h_viol)
-      r = cudaMemcpyAsync(h_viol + e0, dV + e0, sizeof(uint16_t) * n, cudaMemcpyDeviceToHost, ss->cs);
-    return r;
-  };
-  if (ss->chunked) {
-    const void *base = ss->O;
-    int wb = 8;
-    if (ss->quad) {
-      wb = quad_word_bytes(rm, ss->P);
-      if ((e = launch_quad_pyramid(rm, ss->O, wb, ss->pyr, cc)) != cudaSuccess)
-        return cuda_fail(e, "session run: pyramid");
-      base = ss->pyr;
-    }
-    for (int c = 0; c < kSessionChunks; ++c) {
-      const int64_t e0 = ss->edge0[c], n = ss->edge0[c + 1] - e0;
-      if (n == 0) continue;
-      // quadtree rows in locality order write to the caller's edges of the
-      // same range: the outputs are addressed from their start, not from e0
-      const int32_t *perm = ss->quad && rm.qd_perm ? rm.qd_perm + e0 : nullptr;
-      const int64_t o0 = perm ? 0 : e0;
-      const StreamRows r{(ss->quad ? rm.qd_rowptr : rm.rowptr) + e0, ss->quad ? rm.qd_idx : rm.colidx,
-                         ss->cpart + c * (ss->warps + 1), ss->ctas, n, ss->quad ? rm.n_qd : rm.nnz, perm};
-      MonitorTables t{};
-      if (ss->mon) t = tables_of(*ss->mon, dN + o0, dV + o0);
-      e = launch_label_rows(r, base, wb, ss->P, dL + o0, ss->mon ? &t : nullptr, ss->depth, rm.num_sms, cc);
-      if (e == cudaSuccess) e = cudaEventRecord(ss->ev[c], cc);
-      if (e == cudaSuccess) e = cudaStreamWaitEvent(ss->cs, ss->ev[c], 0);
-      if (e == cudaSuccess) e = copy_out(e0, n);
-      if (e != cudaSuccess) return cuda_fail(e, "session run: chunk");
-    }
-  } else {
-    rc = label_impl(ss->rm, ss->O, ss->P, dL, ss->mon, dN, dV, ss->has_cfg ? &ss->cfg : nullptr, cc);
-    if (rc != LBL_OK) return rc;
-    if ((e = cudaEventRecord(ss->ev[0], cc)) != cudaSuccess || (e = cudaStreamWaitEvent(ss->cs, ss->ev[0], 0)) != cudaSuccess ||
-        (rm.E > 0 && (e = copy_out(0, rm.E)) != cudaSuccess))
-      return cuda_fail(e, "session run: copy results");
-  }
-  // output set k is free again once its copies land; the caller's stream sees
-  // the whole frame (copies in, kernels, copies out) before its next work
-  if ((e = cudaEventRecord(ss->ev_out[k], ss->cs)) != cudaSuccess ||
-      (e = cudaStreamWaitEvent(st, ss->ev_out[k], 0)) != cudaSuccess)
-    return cuda_fail(e, "session run: join");
-  return LBL_OK;
-}
-
-int lbl_session_free(lbl_session ss) {
-  g_err.clear();
-  if (!ss) return LBL_OK;
-  cudaDeviceSynchronize();
-  cudaFree(ss->planes);
-  cudaFree(ss->O);
-  cudaFree(ss->L);
-  cudaFree(ss->next);
-  cudaFree(ss->viol);
-  cudaFree(ss->cpart);
-  if (ss->cs) cudaStreamDestroy(ss->cs);
-  if (ss->cin) cudaStreamDestroy(ss->cin);
-  if (ss->cc) cudaStreamDestroy(ss->cc);
-  for (int k = 0; k < 2; ++k)
-    if (ss->ev_out[k]) cudaEventDestroy(ss->ev_out[k]);
-  cudaFree(ss->pyr);
-  cudaFree(ss->words);
-  for (cudaEvent_t ev : ss->ev)
-    if (ev) cudaEventDestroy(ev);
-  for (int k = 0; k < 2; ++k) {
-    if (ss->ev_in[k]) cudaEventDestroy(ss->ev_in[k]);
-    if (ss->ev_free[k]) cudaEventDestroy(ss->ev_free[k]);
-  }
-  delete ss;
   return LBL_OK;
 }
 

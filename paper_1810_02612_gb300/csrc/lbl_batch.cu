@@ -1,0 +1,278 @@
+// Batched frames (lbl_batch_*, include/lbl.h): many frames' transforms and
+// labels in a few graph-capturable launches shared by all of them.
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "lbl_internal.cuh"
+
+using namespace lbl;
+
+struct lbl_batch_s {
+  int device = 0;
+  int num_sms = 1;
+  int32_t n = 0;
+  std::vector<lbl_roadmap> rms;
+  std::vector<int32_t> P;
+  std::vector<lbl_monitor> mons;
+  int64_t *part = nullptr;  // every item's partition, concatenated
+  unsigned long long *counter = nullptr;  // next work unit of each class's label launch
+  int ctas = 1;
+  // items grouped by gathered word width (class c = 1, 2, 4, 8 bytes); item i
+  // is entry slot[i] of tabs[cls[i]]
+  BatchTable tabs[kWordClasses]{};
+  std::vector<int> cls, slot;
+  FrameTable ftab{};
+  // items whose roadmap has the quadtree form label from their own pyramid
+  uint64_t *pyr = nullptr;      // every such item's pyramid, concatenated
+  std::vector<int> pyr_slot;    // item -> entry of ptab, or -1
+  PyrTable ptab{};
+  // frames whose world has at most kPackedWorldRatio times the agent's cells
+  // are packed (one launch) and transformed from 64-bit words; the words
+  // buffer grows on demand, and a replaced buffer is kept until the batch is
+  // freed so graphs captured before still see live memory
+  PackTable pktab{};
+  uint64_t *words = nullptr;
+  int64_t words_cap = 0;
+  std::vector<uint64_t *> retired;
+  bool frames_set = false;
+};
+
+extern "C" {
+
+int lbl_batch_create(int32_t n, const lbl_roadmap *rms, const int32_t *n_props, const lbl_monitor *mons,
+                     int32_t ctas_per_sm, lbl_batch *out) {
+  clear_error();
+  if (!out) {
+    set_error("batch create: out is NULL");
+    return LBL_EINVAL;
+  }
+  *out = nullptr;
+  if (n < 1 || n > kMaxBatch || !rms || !n_props) {
+    set_error("batch create: need 1 <= n <= %d roadmaps and their proposition counts", kMaxBatch);
+    return LBL_EINVAL;
+  }
+  for (int i = 0; i < n; ++i) {
+    if (!rms[i] || n_props[i] < 0 || n_props[i] > 64) {
+      set_error("batch create: item %d has no roadmap or n_props outside 0..64", i);
+      return LBL_EINVAL;
+    }
+    if (rms[i]->device != rms[0]->device || (mons && mons[i] && mons[i]->device != rms[0]->device)) {
+      set_error("batch create: items live on different devices");
+      return LBL_EINVAL;
+    }
+  }
+  if (!same_device(rms[0]->device)) return LBL_EINVAL;
+  lbl_batch_s *b = new (std::nothrow) lbl_batch_s();
+  if (!b) {
+    set_error("batch create: out of host memory");
+    return LBL_ENOMEM;
+  }
+  b->device = rms[0]->device;
+  b->num_sms = rms[0]->num_sms;
+  b->n = n;
+  b->rms.assign(rms, rms + n);
+  b->P.assign(n_props, n_props + n);
+  b->mons.assign(n, nullptr);
+  if (mons) b->mons.assign(mons, mons + n);
+  // The persistent grid's warps take work units from a counter; items are
+  // cut into units of about equal cost (nonzeros + kEdgeCost per edge),
+  // kUnitsPerWarp per warp overall, at least one per item with edges.
+  bool all_quad = true;
+  for (int i = 0; i < n; ++i) all_quad = all_quad && (rms[i]->has_qd || rms[i]->E == 0);
+  const int depth = all_quad ? kQuadDepth : 8;
+  for (BatchTable &t : b->tabs) t.depth = depth;
+  const int occ = batch_ctas_per_sm(depth);
+  const int ctas = ctas_per_sm > 0 ? std::min<int>(ctas_per_sm, occ) : occ;
+  b->ctas = ctas;
+  constexpr int64_t kUnitsPerWarp = 8;
+  const int64_t units_target = static_cast<int64_t>(b->num_sms) * ctas * (kThreads / 32) * kUnitsPerWarp;
+  // entries streamed per item: quadtree entries when the roadmap has them;
+  // word width of its gathers (items of one width share a launch)
+  auto entries = [](const Roadmap &r) { return r.has_qd ? r.n_qd : r.nnz; };
+  auto width = [&](int i) { return rms[i]->has_qd && rms[i]->E > 0 ? quad_word_bytes(*rms[i], n_props[i]) : 8; };
+  // every class's launch gets about kUnitsPerWarp units per warp of its own
+  double total[kWordClasses] = {0, 0, 0, 0};
+  for (int i = 0; i < n; ++i) total[word_class(width(i))] += static_cast<double>(entries(*rms[i]) + kEdgeCost * rms[i]->E);
+  std::vector<int64_t> W(n), off(n + 1, 0);
+  int64_t pyr_words = 0;
+  for (int i = 0; i < n; ++i)
+    if (rms[i]->has_qd && rms[i]->E > 0) pyr_words += rms[i]->pyr_words;
+  for (int i = 0; i < n; ++i) {
+    const Roadmap &r = *rms[i];
+    W[i] = 0;
+    if (r.E > 0) {
+      const double c = static_cast<double>(entries(r) + kEdgeCost * r.E);
+      const double unit_cost = total[word_class(width(i))] / static_cast<double>(units_target);
+      W[i] = std::max<int64_t>(1, static_cast<int64_t>(std::ceil(c / unit_cost)));
+      W[i] = std::min<int64_t>(W[i], r.E);  // never more units than edges
+    }
+    off[i + 1] = off[i] + W[i] + 1;
+  }
+  cudaError_t e = dev_alloc(&b->part, static_cast<size_t>(off[n]), nullptr);
+  if (e == cudaSuccess) e = dev_alloc(&b->counter, kWordClasses, nullptr);
+  if (e == cudaSuccess && pyr_words > 0) e = dev_alloc(&b->pyr, static_cast<size_t>(pyr_words), nullptr);
+  b->pyr_slot.assign(n, -1);
+  b->cls.assign(n, kWordClasses - 1);
+  b->slot.assign(n, 0);
+  int64_t pyr0 = 0, block0 = 0;
+  for (int i = 0; i < n && e == cudaSuccess; ++i) {
+    const Roadmap &r = *rms[i];
+    const bool quad = r.has_qd && r.E > 0;
+    const int wb = width(i);
+    e = launch_partition_into(quad ? r.qd_rowptr : r.rowptr, r.E, W[i], b->part + off[i], nullptr);
+    BatchTable &tb = b->tabs[word_class(wb)];
+    b->cls[i] = word_class(wb);
+    b->slot[i] = tb.n;
+    tb.word_bytes = wb;
+    BatchItem &it = tb.items[tb.n++];
+    it = BatchItem{};
+    it.rowptr = quad ? r.qd_rowptr : r.rowptr;
+    it.colidx = quad ? r.qd_idx : r.colidx;
+    it.perm = quad ? r.qd_perm : nullptr;
+    it.part = b->part + off[i];
+    if (quad) {  // labels gather from the item's pyramid, built from its O at the label stage
+      PyrItem &pi = b->ptab.items[b->ptab.n];
+      pi = PyrItem{};
+      pi.pyr = b->pyr + pyr0;
+      pi.cells = r.cells;
+      pi.block0 = block0;
+      pi.off = r.qd_off;
+      pi.word_bytes = wb;
+      it.O = pi.pyr;
+      b->pyr_slot[i] = b->ptab.n++;
+      pyr0 += r.pyr_words;
+      block0 += (r.cells + kThreads - 1) / kThreads;
+    }
+    it.mask = n_props[i] >= 64 ? ~0ull : ((1ull << n_props[i]) - 1ull);
+    it.warp0 = tb.total;  // work units of this class's launch
+    it.warps = W[i];
+    if (b->mons[i]) {
+      const Monitor &m = *b->mons[i];
+      it.T = m.T;
+      it.V = m.V;
+      it.m = m.m;
+      for (int j = 0; j < 8; ++j) it.rel[j] = m.rel[j];
+    }
+    tb.total += W[i];
+    if (entries(r) >= kNarrowLimit || r.E >= kNarrowLimit) tb.wide = 1;
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
+  if (e != cudaSuccess) {
+    cudaFree(b->part);
+    cudaFree(b->counter);
+    cudaFree(b->pyr);
+    delete b;
+    return cuda_fail(e, "batch create: partitions");
+  }
+  b->ptab.total = block0;
+  b->ftab.n = n;
+  *out = b;
+  return LBL_OK;
+}
+
+int lbl_batch_set_frames(lbl_batch b, const lbl_frame *frames) {
+  clear_error();
+  if (!b || !frames) {
+    set_error("batch frames: NULL batch or frames");
+    return LBL_EINVAL;
+  }
+  int64_t cell0 = 0;
+  for (int i = 0; i < b->n; ++i) {
+    const lbl_frame &f = frames[i];
+    const Roadmap &r = *b->rms[i];
+    const int32_t P = b->P[i];
+    if (!valid_grid(&f.world, "batch frames (world)", false)) return LBL_EINVAL;
+    if ((P > 0 && !f.d_planes) || !f.d_O || (r.E > 0 && !f.d_L) ||
+        (b->mons[i] && r.E > 0 && (!f.d_next || !f.d_viol))) {
+      set_error("batch frames: frame %d is missing a buffer", i);
+      return LBL_EINVAL;
+    }
+    FrameMap m;
+    if (!frame_map(f.world, r.agent, f.pose, &m)) return LBL_EINVAL;
+    b->ftab.items[i] = frame_item(m, f.world, r.agent, f.d_planes, P, f.d_O, cell0);
+    cell0 += r.cells;
+    BatchItem &it = b->tabs[b->cls[i]].items[b->slot[i]];
+    if (b->pyr_slot[i] >= 0)
+      b->ptab.items[b->pyr_slot[i]].O = f.d_O;  // the item gathers from its pyramid
+    else
+      it.O = f.d_O;
+    it.L = f.d_L;
+    it.next = f.d_next;
+    it.viol = f.d_viol;
+  }
+  b->ftab.total = cell0;
+  // packed frames: 64-bit words at 4-word aligned offsets (vector stores)
+  int64_t need = 0;
+  std::vector<int64_t> woff(b->n, -1);
+  for (int i = 0; i < b->n; ++i) {
+    const int64_t wc = grid_cells(frames[i].world);
+    if (b->P[i] > 0 && wc > 0 && wc <= kPackedWorldRatio * b->rms[i]->cells) {
+      woff[i] = need;
+      need += (wc + 3) / 4 * 4;
+    }
+  }
+  if (need > b->words_cap) {
+    uint64_t *w = nullptr;
+    cudaError_t e = dev_alloc(&w, static_cast<size_t>(need), nullptr);
+    if (e != cudaSuccess) return cuda_fail(e, "batch frames: packed words");
+    if (b->words) b->retired.push_back(b->words);
+    b->words = w;
+    b->words_cap = need;
+  }
+  PackTable &pt = b->pktab;
+  pt.n = 0;
+  pt.lane0[0] = 0;
+  for (int i = 0; i < b->n; ++i) {
+    FrameItem &fi = b->ftab.items[i];
+    fi.words = nullptr;
+    if (woff[i] < 0) continue;
+    const int32_t P = b->P[i];
+    const PackItem it{frames[i].d_planes, b->words + woff[i], grid_cells(frames[i].world), P, 8};
+    pt.items[pt.n] = it;
+    pt.vec[pt.n] = pack_vec_ok(it) ? 1 : 0;
+    pt.lane0[pt.n + 1] = pt.lane0[pt.n] + (it.cells + 3) / 4;
+    ++pt.n;
+    fi.words = it.words;
+    fi.word_bytes = 8;
+    fi.wmask = P >= 64 ? ~0ull : ((1ull << P) - 1ull);
+  }
+  b->frames_set = true;
+  return LBL_OK;
+}
+
+int lbl_batch_launch(lbl_batch b, uint32_t stages, lbl_stream s) {
+  clear_error();
+  if (!b || !b->frames_set || (stages & ~(LBL_STAGE_TRANSFORM | LBL_STAGE_LABEL))) {
+    set_error("batch launch: NULL batch, no frames set, or unknown stages");
+    return LBL_EINVAL;
+  }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(s);
+  cudaError_t e = cudaSuccess;
+  if (stages & LBL_STAGE_TRANSFORM) {
+    e = launch_pack_batch(b->pktab, st);
+    if (e == cudaSuccess) e = launch_frame_batch(b->ftab, b->num_sms, st);
+  }
+  if (e == cudaSuccess && (stages & LBL_STAGE_LABEL)) {
+    e = launch_quad_pyramid_batch(b->ptab, st);
+    for (int c = 0; c < kWordClasses && e == cudaSuccess; ++c)
+      if (b->tabs[c].n > 0) e = launch_label_batch(b->tabs[c], b->counter + c, b->num_sms, b->ctas, st);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "batch launch");
+  return LBL_OK;
+}
+
+int lbl_batch_free(lbl_batch b) {
+  clear_error();
+  if (!b) return LBL_OK;
+  cudaDeviceSynchronize();
+  cudaFree(b->part);
+  cudaFree(b->counter);
+  cudaFree(b->pyr);
+  cudaFree(b->words);
+  for (uint64_t *w : b->retired) cudaFree(w);
+  delete b;
+  return LBL_OK;
+}
+
+}  // extern "C"

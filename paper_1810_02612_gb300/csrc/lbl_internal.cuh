@@ -326,10 +326,28 @@ cudaError_t launch_bt_fill(const int64_t *rowptr, const int32_t *colidx, int64_t
 struct lbl_roadmap_s : lbl::Roadmap {};
 struct lbl_monitor_s : lbl::Monitor {};
 
+// Host helpers shared by the entry points (defined in lbl_api.cu).
 namespace lbl {
 int roadmap_new(const lbl_grid &agent, int64_t n_edges, int64_t nnz, lbl_roadmap_s **out);
 int roadmap_finish(lbl_roadmap_s *rm, uint32_t flags, cudaStream_t st);
-bool valid_grid_public(const lbl_grid *g, const char *name, bool need_order);
-int device_sms_public(int dev);
-void free_roadmap_public(lbl_roadmap_s *rm);
+void free_roadmap(Roadmap *rm);
+// a grid the entry points accept: 1..32768 cells a side, < 2^31 cells, finite
+// geometry; need_order also checks the cell order (z-order: a power-of-two square or cube)
+bool valid_grid(const lbl_grid *g, const char *name, bool need_order);
+int device_sms(int dev);    // SM count (cached per device)
+bool same_device(int dev);  // the current device is `dev` (else sets the error)
+void clear_error();         // empty lbl_last_error at the start of an entry point
+MonitorTables tables_of(const Monitor &mon, uint64_t *next, uint16_t *viol);
+// lbl_label's body: argument checks, form resolution, re-partitioning, launch
+int label_impl(lbl_roadmap rm, const uint64_t *d_O, int32_t n_props, uint64_t *d_L, lbl_monitor mon,
+               uint64_t *d_next, uint16_t *d_viol, const lbl_config *cfg, cudaStream_t st);
+
+// cudaMalloc of `count` elements (at least 16 bytes), adding the bytes to *bytes if given
+template <typename T>
+cudaError_t dev_alloc(T **p, size_t count, int64_t *bytes) {
+  const size_t b = count * sizeof(T);
+  cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), b ? b : 16);
+  if (e == cudaSuccess && bytes) *bytes += static_cast<int64_t>(b);
+  return e;
+}
 }  // namespace lbl
