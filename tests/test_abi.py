@@ -147,3 +147,15 @@ def test_transform_and_packing_refuse_bad_arguments_before_device_work():
     with pytest.raises(L.LblError) as ei:
         L.lbl_frame_transform_words(world, 8194, 33, (0.0, 0.0, 0.0), world, 8192, stream=0)  # 32-bit words
     assert ei.value.code == L.LBL_EINVAL
+
+
+def test_binding_refuses_to_run_without_the_library():
+    """No fallback: with the CUDA library absent, loading it raises."""
+    import subprocess
+    import sys
+    missing = os.path.join(ROOT, "_no_such_liblbl.so")
+    code = ("import paper_1810_02612_gb300.lbl as B, paper_1810_02612_gb300.build as Bd\n"
+            f"B._lib = None\nBd.LIB = {missing!r}\n"
+            "try:\n    B.load(build_if_needed=False)\nexcept ImportError as e:\n    print('refused:', e)\n")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and "refused:" in r.stdout, r.stdout + r.stderr
