@@ -48,7 +48,7 @@ typedef struct CUstream_st *lbl_stream;
 #define LBL_ENOMEM (-2)      /* device or host allocation failed */
 #define LBL_ECUDA (-3)       /* a CUDA runtime call or kernel launch failed */
 #define LBL_ETIMEOUT (-4)    /* a bounded wait ran out */
-#define LBL_EUNSUPPORTED (-5)/* valid request this build does not implement */
+#define LBL_EUNSUPPORTED (-5)/* valid request the library does not implement */
 
 /* ------------------------------------------------------------ cell order */
 #define LBL_ORDER_ROWMAJOR 0 /* index = iy * w + ix */

@@ -1047,7 +1047,7 @@ cudaError_t launch_label_async(const Roadmap &rm, const uint64_t *O, int32_t P, 
 // The stream kernels use shared memory only for the monitor tables (2.5 KB a
 // CTA).  The smallest carveout that still holds four CTAs' tables leaves the
 // rest of the SM's 256 KB to L1, which serves the pyramid gathers: 1M-edge
-// labeling call 0.282 vs 0.285 ms with the driver's choice, 0.308 ms at a
+// labeling call 0.282 vs 0.285 ms with the default carveout, 0.308 ms at a
 // 25 % carveout, 0.346 ms at 50 %.
 constexpr int kStreamCarveoutPct = 5;
 
