@@ -119,7 +119,7 @@ def frame_transform(world, planes: np.ndarray, pose, agent) -> np.ndarray:
 
 
 def label(rowptr: np.ndarray, colidx: np.ndarray, O: np.ndarray, P: int, threads: int = 1) -> np.ndarray:
-    """L = (M.O > 0) packed as one word per edge (eq. 10, Algorithm 2)."""
+    """L = (M.O > 0) packed as one word per edge (eq. 10 over the CSR rows of eq. 11)."""
     rowptr = np.ascontiguousarray(rowptr, np.int64)
     colidx = np.ascontiguousarray(colidx, np.int32)
     O = np.ascontiguousarray(O, np.uint64)

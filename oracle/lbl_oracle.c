@@ -15,8 +15,7 @@
  *                                frame; the perceived world grids are re-expressed
  *                                there at the planning pose
  *   orc_label / orc_label_rows   Boolean matrix product L = M.P over the CSR
- *                                rows of M, eq. 10 with Algorithm 2's loop nest
- *                                (proposition, row, nonzero)
+ *                                rows of M (eq. 10, rows stored as in eq. 11)
  *   orc_monitor                  safety-monitor transition delta(q, L(e)) for every
  *                                monitor state, Sec. 3.2
  *   orc_arc_geometry / orc_arc_dist / orc_sweep
@@ -150,25 +149,26 @@ int orc_frame_transform(int32_t ww, int32_t wh, double wres, double wx0, double 
 /* ------------------------------------------------------------------ labels */
 
 /*
- * L(e, p) = OR over the nonzeros k of row e of bit p of O[colidx[k]].
- * Loop nest as in Algorithm 2: propositions outermost, then rows, then the
- * row's nonzeros.  No early exit.  Rows are independent, so the row loop may be
- * split across n_threads OpenMP threads without changing any result.
+ * L(e, p) = OR over the nonzeros k of row e of P(colidx[k], p)  (eq. 10).
+ * Bit p of an OR of words is the OR of their bits p, so each row ORs the whole
+ * words of its cells and then clears the bits at positions >= P.  No early
+ * exit.  Rows are independent, so the row loop may be split across n_threads
+ * OpenMP threads without changing any result.
  */
 void orc_label(int64_t n_edges, const int64_t *rowptr, const int32_t *colidx, const uint64_t *O, int32_t P,
                uint64_t *L, int32_t n_threads) {
-  for (int64_t e = 0; e < n_edges; e++) L[e] = 0;
-  for (int32_t p = 0; p < P; p++) {
-#pragma omp parallel for schedule(dynamic, 256) num_threads(n_threads > 0 ? n_threads : 1)
-    for (int64_t e = 0; e < n_edges; e++) {
-      uint64_t hit = 0;
-      for (int64_t k = rowptr[e]; k < rowptr[e + 1]; k++) hit |= (O[colidx[k]] >> p) & 1u;
-      L[e] |= hit << p;
-    }
+  const uint64_t keep = P <= 0 ? 0 : (P >= 64 ? ~(uint64_t)0 : (((uint64_t)1 << P) - 1));
+#pragma omp parallel for schedule(dynamic, 1024) num_threads(n_threads > 0 ? n_threads : 1)
+  for (int64_t e = 0; e < n_edges; e++) {
+    uint64_t word = 0;
+    for (int64_t k = rowptr[e]; k < rowptr[e + 1]; k++) word |= O[colidx[k]];
+    L[e] = word & keep;
   }
 }
 
-/* The same definition for a list of rows (for spot checks of large inputs). */
+/* The same product for a list of rows, one element (edge, proposition) at a
+   time: bit p of L[i] is set iff some nonzero k of row rows[i] has bit p of
+   O[colidx[k]] set. */
 void orc_label_rows(int64_t n_rows, const int64_t *rows, const int64_t *rowptr, const int32_t *colidx,
                     const uint64_t *O, int32_t P, uint64_t *L) {
   for (int64_t i = 0; i < n_rows; i++) {

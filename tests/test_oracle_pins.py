@@ -115,6 +115,8 @@ def test_label_bits_at_or_above_P_are_zero():
     O = np.array([0xFFFFFFFFFFFFFFFF, 0xF0], np.uint64)
     assert int(oracle.label(rowptr, colidx, O, 3)[0]) == 0b111
     assert int(oracle.label(rowptr, colidx, O, 64)[0]) == 0xFFFFFFFFFFFFFFFF
+    assert int(oracle.label(rowptr, colidx, O, 0)[0]) == 0
+    assert int(oracle.label(rowptr, colidx, O, 5, threads=3)[0]) == 0b11111
 
 
 # ------------------------------------------------------ Algorithm 1 z-order
