@@ -23,11 +23,16 @@ std::mutex g_setup_mutex;
 uint64_t *g_planes_addr[kMaxDevices] = {nullptr};  // device address of g_noalloc_planes, per device
 int g_num_sms[kMaxDevices] = {0};
 
-// Once per device, with that device current: in host code the array's name is
-// only a stand-in, so ask the runtime for its device address.
-int setup(int dev, uint64_t **planes, int *num_sms) {
+// With the device current: in host code the array's name is only a stand-in,
+// so ask the runtime for its device address.  The address is looked up again
+// on every call whose stream is not being captured (a host application may
+// have reset the device since, which reloads the module and can move the
+// array); a call on a capturing stream reuses the address of the last lookup
+// on this device, so the first call on a device, and the first after a
+// cudaDeviceReset, must come before any capture.
+int setup(int dev, bool lookup, uint64_t **planes, int *num_sms) {
   std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_planes_addr[dev]) {
+  if (lookup || !g_planes_addr[dev]) {
     void *p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_planes);
     if (e != cudaSuccess) return lbl::cuda_fail(e, "label blocks (no alloc): cudaGetSymbolAddress");
@@ -72,12 +77,19 @@ extern "C" int lbl_label_blocks_noalloc(const int64_t *d_block_rowptr, const uin
     lbl::set_error("label blocks (no alloc): device %d beyond the %d supported", dev, kMaxDevices);
     return LBL_EUNSUPPORTED;
   }
+  const cudaStream_t st = reinterpret_cast<cudaStream_t>(s);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+    (void)cudaGetLastError();  // e.g. the legacy stream while another stream captures: treat as capturing
+    cap = cudaStreamCaptureStatusActive;
+  }
   uint64_t *planes = nullptr;
   int num_sms = 1;
-  int rc = setup(dev, &planes, &num_sms);
+  int rc = setup(dev, cap == cudaStreamCaptureStatusNone, &planes, &num_sms);
   if (rc != LBL_OK) return rc;
   // A roadmap view over the caller's arrays: the same launch as lbl_label with
-  // LBL_ALGO_BITTILE, with the fixed array as its bit-plane memory.
+  // LBL_ALGO_BITTILE and its default (no early exit), with the fixed array as
+  // its bit-plane memory.
   lbl::Roadmap view;
   view.device = dev;
   view.num_sms = num_sms;
@@ -89,7 +101,7 @@ extern "C" int lbl_label_blocks_noalloc(const int64_t *d_block_rowptr, const uin
   view.bt_block = const_cast<uint32_t *>(d_block_id);
   view.bt_mask = const_cast<uint64_t *>(d_block_mask);
   view.planes = planes;
-  e = lbl::launch_label_bittile(view, d_O, n_props, d_L, nullptr, n_props <= 4, 0, reinterpret_cast<cudaStream_t>(s));
+  e = lbl::launch_label_bittile(view, d_O, n_props, d_L, nullptr, false, 0, st);
   if (e != cudaSuccess) return lbl::cuda_fail(e, "label blocks (no alloc): launch");
   return LBL_OK;
 }
