@@ -109,7 +109,9 @@ typedef struct {
                              early termination; lane-group CSR and block forms);
                              0 or -1 = off */
   int32_t ctas_per_sm;    /* persistent grid size per SM, 0 = auto */
-  int32_t pipeline;       /* streaming CSR index stream (LBL_PIPE_*), 0 = default */
+  int32_t pipeline;       /* streaming CSR: index stream (LBL_PIPE_REGISTERS/BULK/ASYNC);
+                             quadtree: LBL_PIPE_FRONT or LBL_PIPE_REGISTERS (below);
+                             0 = the form's default */
   int32_t depth;          /* register pipelines: groups of 32 entries in flight per
                              warp, 0 = the form's default: CSR 8 (default), 12 or 16;
                              quadtree 8 (default), 12 or 16; sector form 4 (default)
@@ -120,6 +122,13 @@ typedef struct {
 #define LBL_PIPE_REGISTERS 1 /* loads into registers, 8 groups of 32 ahead */
 #define LBL_PIPE_BULK 2      /* cp.async.bulk (TMA engine) into a shared-memory ring */
 #define LBL_PIPE_ASYNC 3     /* per-lane cp.async into a shared-memory ring */
+/* How the quadtree form spreads edges over warps.  LBL_PIPE_REGISTERS: every
+   warp streams a fixed contiguous range of edges.  LBL_PIPE_FRONT (depth 8):
+   one CTA per SM takes the SM's range and its warps take chunks of
+   neighbouring edges in order, so the rows labeled at the same time on an SM
+   share pyramid words in its L1.  0 (default): the front on ranges of about
+   3,000 edges per SM or more, else the fixed ranges. */
+#define LBL_PIPE_FRONT 4
 
 typedef struct lbl_roadmap_s *lbl_roadmap;
 typedef struct lbl_monitor_s *lbl_monitor;
@@ -318,7 +327,8 @@ int lbl_label(lbl_roadmap rm, const uint64_t *d_O, int32_t n_props, uint64_t *d_
  * (LBL_ALGO_BITTILE) for callers that cannot allocate device memory: planning
  * loops under real-time or safety rules that forbid allocation once the system
  * runs, and host frameworks that own every device allocation.  The paper has no
- * counterpart; it is the same product (eq. 10) on the same kernels.
+ * counterpart: it is lbl_label's block form on the same kernels, with its
+ * working memory moved into the library.
  *
  * The kernels' one piece of working memory, the bit-plane copy of d_O (one word
  * per 64-cell block and proposition), is a fixed device array of
@@ -335,9 +345,11 @@ int lbl_label(lbl_roadmap rm, const uint64_t *d_O, int32_t n_props, uint64_t *d_
  * The block form is not checked (malformed entries are undefined behaviour);
  * it equals what lbl_roadmap_upload derives with LBL_UPLOAD_BITTILE.
  * Returns LBL_EINVAL when ceil(n_cells / 64) * n_props exceeds
- * LBL_NOALLOC_MAX_PLANE_WORDS.  The first call on a device looks up the array's
- * device address (once per device, under a lock), so make that first call
- * before any stream capture.  Every call uses the same array: calls that can
+ * LBL_NOALLOC_MAX_PLANE_WORDS.  A call looks up the array's device address
+ * (under a lock) unless its stream is being captured; a call on a capturing
+ * stream reuses the last address looked up on that device.  So make the first
+ * call on a device, and the first after a cudaDeviceReset (which can move the
+ * array), before any stream capture.  Every call uses the same array: calls that can
  * overlap on the GPU (on different streams, or from several threads) race and
  * must be serialised by the caller.  Nothing in the array needs clearing: each
  * call writes every word it reads.
@@ -414,6 +426,37 @@ int lbl_batch_set_frames(lbl_batch b, const lbl_frame *frames);
 #define LBL_STAGE_LABEL 2u
 int lbl_batch_launch(lbl_batch b, uint32_t stages, lbl_stream s);
 int lbl_batch_free(lbl_batch b);
+
+/*
+ * lbl_batch_autotune — choose the batched labeling launch by measurement, as
+ * lbl_roadmap_autotune does for one roadmap (Sec. 4.3: every variant computes
+ * the same eq. 10; which is fastest depends on the rows, the grids and the
+ * proposition counts).  The batch's items are labeled in one launch per class
+ * of gathered word width (1, 2, 4, 8 bytes: the bins of the batch); for each
+ * class with items the call times, on the frames last set, the stream depth
+ * (8 or 12 groups of 32 entries in flight per warp), CTAs per SM (the most
+ * that fit and up to two fewer) and the work-unit size (2, 4, 8, 16 or 32
+ * units per warp, the items cut into units of equal cost), `reps` launches
+ * each (CUDA events on `s`, after one untimed launch), and keeps the fastest
+ * plan for later lbl_batch_launch calls.  Labels written meanwhile are the
+ * frames' labels.  A CUDA graph captured before keeps the plan it captured
+ * (its memory stays allocated until lbl_batch_free); capture after tuning to
+ * replay the tuned plan.  out[LBL_BATCH_CLASSES] (may be NULL) receives, per
+ * class (index 0..3 = 1, 2, 4, 8-byte words), the choice and its time next to
+ * the time of the plan lbl_batch_create made.  Synchronises `s`;
+ * 1 <= reps <= 1000.
+ */
+#define LBL_BATCH_CLASSES 4
+typedef struct {
+  int32_t word_bytes;     /* 1, 2, 4 or 8; 0 = the class has no items */
+  int32_t items;          /* items labeled by the class's launch */
+  int32_t depth;          /* groups of 32 entries in flight per warp */
+  int32_t ctas_per_sm;    /* CTAs per SM of the launch */
+  int32_t units_per_warp; /* work units per warp */
+  float ms;               /* measured label-launch time of the chosen plan, ms */
+  float ms_default;       /* the same for the plan lbl_batch_create made, ms */
+} lbl_batch_tuning;
+int lbl_batch_autotune(lbl_batch b, int32_t reps, lbl_stream s, lbl_batch_tuning *out);
 
 /* ---------------------------------------------------------------- server */
 

@@ -292,6 +292,51 @@ __global__ void __launch_bounds__(kThreads, stream_min_blocks<U>()) k_label_stre
   });
 }
 
+// Moving-front form of the streaming gather-OR (quadtree rows in locality
+// order, large roadmaps): one CTA of kFrontWarps warps per SM owns the edges
+// its SM's warps would own in the stream partition (a contiguous range), cut
+// into chunks of `chunk` edges; the warps take chunks in order from a
+// shared-memory counter.  The warps of an SM then label neighbouring edges at
+// the same time, so the pyramid words their rows share are gathered while
+// they are still in the SM's L1 (1M-edge workload: gather misses per edge
+// 33 -> 19 sectors).  Each chunk is streamed by stream_range as a range of
+// its own.
+constexpr int kFrontWarps = 32;
+template <int U, bool EPI, typename T>
+__global__ void __launch_bounds__(kFrontWarps * 32, 1) k_label_front(const int64_t *__restrict__ rowptr,
+                                                                    const int32_t *__restrict__ idx,
+                                                                    const T *__restrict__ O,
+                                                                    const int64_t *__restrict__ part, int stride,
+                                                                    int chunk, uint64_t mask,
+                                                                    uint64_t *__restrict__ L, MonitorTables mon,
+                                                                    const int32_t *__restrict__ perm) {
+  __shared__ EpiSmem sm;
+  __shared__ int next_chunk;
+  if (threadIdx.x == 0) next_chunk = 0;
+  if (EPI)
+    load_tables(mon, sm);  // contains __syncthreads
+  else
+    __syncthreads();
+  const uint64_t pol = evict_first_policy();
+  const int lane = threadIdx.x & 31;
+  const int64_t r0 = __ldg(part + static_cast<int64_t>(blockIdx.x) * stride);
+  const int64_t r1 = __ldg(part + static_cast<int64_t>(blockIdx.x + 1) * stride);
+  for (;;) {
+    int c = 0;
+    if (lane == 0) c = atomicAdd(&next_chunk, 1);
+    c = __shfl_sync(kFull, c, 0);
+    const int64_t e_beg = r0 + static_cast<int64_t>(c) * chunk;
+    if (e_beg >= r1) return;  // warp-uniform
+    const int64_t e_end = min(r1, e_beg + chunk);
+    stream_range<U, int32_t>(rowptr, idx, WordGather<T>{O}, e_beg, e_end, pol, lane, [&](int64_t e, uint64_t r) {
+      r &= mask;
+      const int64_t o = perm ? static_cast<int64_t>(__ldg(perm + e)) : e;  // the caller's edge
+      L[o] = r;
+      if (EPI) epilogue(mon, sm, o, r);
+    });
+  }
+}
+
 // Sector form (compressed A at L2-sector granularity): an entry is
 // (sector << 4) | mask, sector = 4 consecutive cells of O (32 bytes), mask
 // bit i = cell 4*sector + i is in the row; 0 = no entry (a real entry has a
@@ -1109,9 +1154,49 @@ void rows_launch(const StreamRows &r, const T *base, uint64_t mask, uint64_t *L,
     k_label_stream<U, false, Off, T><<<grid, kThreads, 0, s>>>(r.rowptr, r.idx, base, r.part, mask, L, none, r.perm);
 }
 
+// Chunk size of the moving front for a range of E edges (0: the per-warp
+// stream instead).  Measured on quadtree rows in locality order (1M, 500k and
+// 250k edges of the 512x512, 64-proposition workload; 1.1M edges of the
+// 2^21-cell workload): 24 edges per chunk from ~6,000 edges per SM (-7 % on
+// 1M edges), 16 from ~3,000 (-2 % on 500k); below that too few chunks per
+// warp to balance the CTA (250k: +3 %, 100k: +20 %).
+int front_chunk_for(int64_t E, int num_sms) {
+  const int64_t per_sm = E / (num_sms > 0 ? num_sms : 1);
+  return per_sm >= 6000 ? 24 : per_sm >= 3000 ? 16 : 0;
+}
+
+template <typename T>
+void front_launch(const StreamRows &r, const T *base, uint64_t mask, uint64_t *L, const MonitorTables *mon,
+                  int chunk, int num_sms, cudaStream_t s) {
+  static const bool carved = [] {
+    cudaFuncSetAttribute(k_label_front<8, true, T>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         kStreamCarveoutPct);
+    cudaFuncSetAttribute(k_label_front<8, false, T>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         kStreamCarveoutPct);
+    cudaGetLastError();  // an attribute the device ignores is not an error of any later call
+    return true;
+  }();
+  (void)carved;
+  const int stride = r.part_ctas * (kThreads / 32);  // partition entries (warps) per SM = per front CTA
+  const unsigned grid = static_cast<unsigned>(num_sms);
+  MonitorTables none{};
+  if (mon)
+    k_label_front<8, true, T><<<grid, kFrontWarps * 32, 0, s>>>(r.rowptr, r.idx, base, r.part, stride, chunk, mask,
+                                                                 L, *mon, r.perm);
+  else
+    k_label_front<8, false, T><<<grid, kFrontWarps * 32, 0, s>>>(r.rowptr, r.idx, base, r.part, stride, chunk, mask,
+                                                                  L, none, r.perm);
+}
+
 template <typename T>
 void rows_launch_depth(const StreamRows &r, const T *base, uint64_t mask, uint64_t *L, const MonitorTables *mon,
                        int depth, int num_sms, cudaStream_t s) {
+  // the front reads the stream partition of depth 8 (kFrontWarps warps per SM)
+  const int chunk = r.front_chunk < 0 ? front_chunk_for(r.E, num_sms) : r.front_chunk;
+  if (chunk > 0 && depth == 8 && r.part_ctas * (kThreads / 32) == kFrontWarps) {
+    front_launch<T>(r, base, mask, L, mon, chunk, num_sms, s);
+    return;
+  }
   if (depth == 16)
     rows_launch<16, int32_t, T>(r, base, mask, L, mon, num_sms, s);
   else if (depth == 12)
@@ -1169,12 +1254,13 @@ cudaError_t launch_quad_pyramid_batch(const PyrTable &tab, cudaStream_t s) {
 }
 
 cudaError_t launch_label_quad(const Roadmap &rm, const uint64_t *O, int32_t P, uint64_t *L,
-                              const MonitorTables *mon, int depth, cudaStream_t s) {
+                              const MonitorTables *mon, int depth, cudaStream_t s, int front_chunk) {
   if (rm.E == 0) return cudaSuccess;
   const int wb = quad_word_bytes(rm, P);
   cudaError_t e = launch_quad_pyramid(rm, O, wb, rm.pyr, s);
   if (e != cudaSuccess) return e;
-  const StreamRows r{rm.qd_rowptr, rm.qd_idx, rm.qd_part, rm.qd_part_ctas, rm.E, rm.n_qd, rm.qd_perm};
+  StreamRows r{rm.qd_rowptr, rm.qd_idx, rm.qd_part, rm.qd_part_ctas, rm.E, rm.n_qd, rm.qd_perm};
+  r.front_chunk = front_chunk;
   return launch_label_rows(r, rm.pyr, wb, P, L, mon, depth, rm.num_sms, s);
 }
 

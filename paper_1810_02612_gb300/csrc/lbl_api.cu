@@ -797,6 +797,11 @@ int label_impl(lbl_roadmap rm, const uint64_t *d_O, int32_t n_props, uint64_t *d
     }
     e = launch_label_sector(*rm, d_O, n_props, d_L, mon ? &t : nullptr, depth, st);
   } else if (algo == LBL_ALGO_QUAD) {
+    const int qpipe = cfg ? cfg->pipeline : 0;
+    if (qpipe != 0 && qpipe != LBL_PIPE_REGISTERS && qpipe != LBL_PIPE_FRONT) {
+      set_error("label: pipeline %d does not apply to the quadtree form", qpipe);
+      return LBL_EINVAL;
+    }
     const int depth = (cfg && cfg->depth) ? cfg->depth : kQuadDepth;
     if (rm->E > 0) {
       const int occ = stream_ctas_per_sm(depth);
@@ -808,7 +813,11 @@ int label_impl(lbl_roadmap rm, const uint64_t *d_O, int32_t n_props, uint64_t *d
         rm->qd_part_ctas = want;
       }
     }
-    e = launch_label_quad(*rm, d_O, n_props, d_L, mon ? &t : nullptr, depth, st);
+    // pipeline: 0 = the moving front on large roadmaps (by size), LBL_PIPE_FRONT
+    // = the front whatever the size, anything else = the per-warp stream
+    const int pipe = cfg ? cfg->pipeline : 0;
+    const int fchunk = pipe == 0 ? -1 : pipe == LBL_PIPE_FRONT ? std::max(front_chunk_for(rm->E, rm->num_sms), 8) : 0;
+    e = launch_label_quad(*rm, d_O, n_props, d_L, mon ? &t : nullptr, depth, st, fchunk);
   } else if (early || lpe > 0) {
     // lanes-per-edge form (one edge per lane group; supports early exit)
     e = launch_label_csr(*rm, d_O, n_props, d_L, mon ? &t : nullptr, resolve_lpe(*rm, cfg), early, ctas, st);
@@ -866,7 +875,8 @@ int lbl_roadmap_autotune(lbl_roadmap rm, const uint64_t *d_O, int32_t n_props, l
   if (rm->has_sec && !(reinterpret_cast<uintptr_t>(d_O) & 31u))
     for (int depth : {4, 8}) cand.push_back(lbl_config{LBL_ALGO_SECTOR, 0, 0, 0, 0, depth});
   if (rm->has_qd)
-    for (int depth : {8, 12}) cand.push_back(lbl_config{LBL_ALGO_QUAD, 0, 0, 0, 0, depth});
+    for (int depth : {8, 12}) cand.push_back(lbl_config{LBL_ALGO_QUAD, 0, 0, 0, LBL_PIPE_REGISTERS, depth});
+    cand.push_back(lbl_config{LBL_ALGO_QUAD, 0, 0, 0, LBL_PIPE_FRONT, 8});
   cudaEvent_t t0, t1;
   cudaError_t e = cudaEventCreate(&t0);
   if (e == cudaSuccess) e = cudaEventCreate(&t1);

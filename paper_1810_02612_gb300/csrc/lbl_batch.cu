@@ -18,6 +18,13 @@ struct lbl_batch_s {
   int64_t *part = nullptr;  // every item's partition, concatenated
   unsigned long long *counter = nullptr;  // next work unit of each class's label launch
   int ctas = 1;
+  // per class: CTAs per SM of its label launch and work units per warp (set
+  // by lbl_batch_create, replaced by lbl_batch_autotune, whose partitions are
+  // kept in tuned_parts; partitions they replace stay allocated until
+  // lbl_batch_free, so graphs captured before still read live memory)
+  int ctas_c[kWordClasses] = {1, 1, 1, 1};
+  int upw_c[kWordClasses] = {0, 0, 0, 0};
+  std::vector<int64_t *> tuned_parts;
   // items grouped by gathered word width (class c = 1, 2, 4, 8 bytes); item i
   // is entry slot[i] of tabs[cls[i]]
   BatchTable tabs[kWordClasses]{};
@@ -37,6 +44,60 @@ struct lbl_batch_s {
   std::vector<uint64_t *> retired;
   bool frames_set = false;
 };
+
+namespace {
+
+// Work units of the batch: the persistent grid's warps take them from a
+// counter.  Items are cut into units of about equal cost (nonzeros, or
+// quadtree entries, + kEdgeCost per edge), about `upw` per warp overall, at
+// least one per item with edges and never more than its edges.
+constexpr int64_t kUnitsPerWarp = 8;
+
+int64_t item_cost(const Roadmap &r) { return (r.has_qd ? r.n_qd : r.nnz) + kEdgeCost * r.E; }
+
+// A new plan for the items of class c: partitions in a fresh device buffer
+// (*part_out, the caller's to free) and the table's unit ranges rewritten.
+cudaError_t plan_class(const lbl_batch_s *b, int c, int ctas, int upw, BatchTable *tab, int64_t **part_out) {
+  *part_out = nullptr;
+  const int64_t units_target = static_cast<int64_t>(b->num_sms) * ctas * (kThreads / 32) * upw;
+  double total = 0.0;
+  for (int i = 0; i < b->n; ++i)
+    if (b->cls[i] == c) total += static_cast<double>(item_cost(*b->rms[i]));
+  const double unit_cost = std::max(total / static_cast<double>(units_target), 1.0);
+  std::vector<int64_t> W(b->n, 0), off(b->n + 1, 0);
+  for (int i = 0; i < b->n; ++i) {
+    const Roadmap &r = *b->rms[i];
+    if (b->cls[i] == c && r.E > 0) {
+      W[i] = std::max<int64_t>(1, static_cast<int64_t>(std::ceil(static_cast<double>(item_cost(r)) / unit_cost)));
+      W[i] = std::min<int64_t>(W[i], r.E);
+    }
+    off[i + 1] = off[i] + (b->cls[i] == c ? W[i] + 1 : 0);
+  }
+  int64_t *part = nullptr;
+  cudaError_t e = dev_alloc(&part, static_cast<size_t>(std::max<int64_t>(off[b->n], 1)), nullptr);
+  if (e != cudaSuccess) return e;
+  tab->total = 0;
+  for (int i = 0; i < b->n && e == cudaSuccess; ++i) {
+    if (b->cls[i] != c) continue;
+    const Roadmap &r = *b->rms[i];
+    const bool quad = r.has_qd && r.E > 0;
+    e = launch_partition_into(quad ? r.qd_rowptr : r.rowptr, r.E, W[i], part + off[i], nullptr);
+    BatchItem &it = tab->items[b->slot[i]];
+    it.part = part + off[i];
+    it.warp0 = tab->total;
+    it.warps = W[i];
+    tab->total += W[i];
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);  // the partitions, made on the legacy stream
+  if (e != cudaSuccess) {
+    cudaFree(part);
+    return e;
+  }
+  *part_out = part;
+  return cudaSuccess;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -85,7 +146,10 @@ int lbl_batch_create(int32_t n, const lbl_roadmap *rms, const int32_t *n_props, 
   const int occ = batch_ctas_per_sm(depth);
   const int ctas = ctas_per_sm > 0 ? std::min<int>(ctas_per_sm, occ) : occ;
   b->ctas = ctas;
-  constexpr int64_t kUnitsPerWarp = 8;
+  for (int c = 0; c < kWordClasses; ++c) {
+    b->ctas_c[c] = ctas;
+    b->upw_c[c] = static_cast<int>(kUnitsPerWarp);
+  }
   const int64_t units_target = static_cast<int64_t>(b->num_sms) * ctas * (kThreads / 32) * kUnitsPerWarp;
   // entries streamed per item: quadtree entries when the roadmap has them;
   // word width of its gathers (items of one width share a launch)
@@ -256,7 +320,7 @@ int lbl_batch_launch(lbl_batch b, uint32_t stages, lbl_stream s) {
   if (e == cudaSuccess && (stages & LBL_STAGE_LABEL)) {
     e = launch_quad_pyramid_batch(b->ptab, st);
     for (int c = 0; c < kWordClasses && e == cudaSuccess; ++c)
-      if (b->tabs[c].n > 0) e = launch_label_batch(b->tabs[c], b->counter + c, b->num_sms, b->ctas, st);
+      if (b->tabs[c].n > 0) e = launch_label_batch(b->tabs[c], b->counter + c, b->num_sms, b->ctas_c[c], st);
   }
   if (e != cudaSuccess) return cuda_fail(e, "batch launch");
   return LBL_OK;
@@ -271,7 +335,92 @@ int lbl_batch_free(lbl_batch b) {
   cudaFree(b->pyr);
   cudaFree(b->words);
   for (uint64_t *w : b->retired) cudaFree(w);
+  for (int64_t *q : b->tuned_parts) cudaFree(q);
   delete b;
+  return LBL_OK;
+}
+
+int lbl_batch_autotune(lbl_batch b, int32_t reps, lbl_stream s, lbl_batch_tuning *out) {
+  clear_error();
+  if (!b || !b->frames_set || reps < 1 || reps > 1000) {
+    set_error("batch autotune: NULL batch, no frames set, or reps outside 1..1000");
+    return LBL_EINVAL;
+  }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(s);
+  // the frames' agent words and pyramids, which every candidate reads
+  int rc = lbl_batch_launch(b, LBL_STAGE_TRANSFORM | LBL_STAGE_LABEL, s);
+  if (rc != LBL_OK) return rc;
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  cudaError_t e = cudaEventCreate(&t0);
+  if (e == cudaSuccess) e = cudaEventCreate(&t1);
+  // mean time of `reps` launches of one class's labels under a candidate plan
+  auto time_class = [&](int c, const BatchTable &tab, int ctas, float *ms) {
+    cudaError_t r = launch_label_batch(tab, b->counter + c, b->num_sms, ctas, st);  // untimed
+    if (r == cudaSuccess) r = cudaEventRecord(t0, st);
+    for (int i = 0; i < reps && r == cudaSuccess; ++i) r = launch_label_batch(tab, b->counter + c, b->num_sms, ctas, st);
+    if (r == cudaSuccess) r = cudaEventRecord(t1, st);
+    if (r == cudaSuccess) r = cudaEventSynchronize(t1);
+    if (r == cudaSuccess) r = cudaEventElapsedTime(ms, t0, t1);
+    *ms /= static_cast<float>(reps);
+    return r;
+  };
+  for (int c = 0; c < kWordClasses && e == cudaSuccess; ++c) {
+    lbl_batch_tuning res{};
+    BatchTable &cur = b->tabs[c];
+    if (cur.n == 0) {
+      if (out) out[c] = res;
+      continue;
+    }
+    res.word_bytes = cur.word_bytes ? cur.word_bytes : 8;
+    res.items = cur.n;
+    float best_ms = 0.0f;
+    e = time_class(c, cur, b->ctas_c[c], &best_ms);
+    res.ms_default = best_ms;
+    int best_depth = cur.depth, best_ctas = b->ctas_c[c], best_upw = b->upw_c[c];
+    int64_t *best_part = nullptr;
+    BatchTable best_tab = cur;
+    // candidates: register depth, CTAs per SM (up to what fits), work units per warp
+    for (int depth : {8, 12}) {
+      if (depth == 12 && cur.wide) continue;  // the 64-bit range kernel exists at depth 8 only
+      const int occ = batch_ctas_per_sm(depth);
+      for (int ctas = occ; ctas >= std::max(1, occ - 2) && e == cudaSuccess; --ctas) {
+        for (int upw : {2, 4, 8, 16, 32}) {
+          BatchTable tab = cur;
+          tab.depth = depth;
+          int64_t *part = nullptr;
+          e = plan_class(b, c, ctas, upw, &tab, &part);
+          float ms = 0.0f;
+          if (e == cudaSuccess) e = time_class(c, tab, ctas, &ms);
+          if (e == cudaSuccess && ms < best_ms) {
+            best_ms = ms;
+            best_depth = depth;
+            best_ctas = ctas;
+            best_upw = upw;
+            best_tab = tab;
+            std::swap(best_part, part);
+          }
+          if (part) cudaFree(part);
+          if (e != cudaSuccess) break;
+        }
+      }
+    }
+    if (e == cudaSuccess && best_part) {  // adopt the winner; the plan it replaces stays allocated
+      cur = best_tab;
+      b->ctas_c[c] = best_ctas;
+      b->upw_c[c] = best_upw;
+      b->tuned_parts.push_back(best_part);
+      best_part = nullptr;
+    }
+    if (best_part) cudaFree(best_part);
+    res.depth = best_depth;
+    res.ctas_per_sm = best_ctas;
+    res.units_per_warp = best_upw;
+    res.ms = best_ms;
+    if (out) out[c] = res;
+  }
+  if (t0) cudaEventDestroy(t0);
+  if (t1) cudaEventDestroy(t1);
+  if (e != cudaSuccess) return cuda_fail(e, "batch autotune");
   return LBL_OK;
 }
 

@@ -159,6 +159,7 @@ struct StreamRows {
   int part_ctas;
   int64_t E, entries;
   const int32_t *perm;  // output index of row e (NULL: e); with perm the outputs are not offset
+  int front_chunk = -1;  // moving front over chunks of this many edges; 0 = per-warp stream, -1 = by range size
 };
 
 struct Roadmap {
@@ -281,10 +282,11 @@ cudaError_t launch_label_rows(const StreamRows &r, const void *base, int word_by
 // quadtree form: pyramid of O, then the stream over the quadtree rows
 // pyramid word width for n_props propositions: 1, 2, 4 or 8 bytes
 int quad_word_bytes(const Roadmap &rm, int32_t P);
+int front_chunk_for(int64_t E, int num_sms);
 // pyramid of O into `pyr` (rm.pyr, or a buffer of rm.pyr_words 64-bit words owned elsewhere)
 cudaError_t launch_quad_pyramid(const Roadmap &rm, const uint64_t *O, int word_bytes, void *pyr, cudaStream_t s);
 cudaError_t launch_label_quad(const Roadmap &rm, const uint64_t *O, int32_t P, uint64_t *L,
-                                const MonitorTables *mon, int depth, cudaStream_t s);
+                                const MonitorTables *mon, int depth, cudaStream_t s, int front_chunk = -1);
 cudaError_t launch_quad_pyramid_batch(const PyrTable &tab, cudaStream_t s);
 // quadtree row e from CSR row rowmap[e] (rowmap NULL: row e); key[e] = z-order
 // of the (x, y) of row e's middle cell (2-D grids of w columns in `order`)

@@ -35,6 +35,9 @@ LBL_ALGO_QUAD = 4
 LBL_PIPE_REGISTERS = 1
 LBL_PIPE_BULK = 2
 LBL_PIPE_ASYNC = 3
+LBL_PIPE_FRONT = 4
+
+LBL_NOALLOC_MAX_PLANE_WORDS = 524288
 
 LBL_STAGE_TRANSFORM = 1
 LBL_STAGE_LABEL = 2
@@ -54,7 +57,7 @@ EXPORTS = (
     "lbl_monitor_create", "lbl_monitor_free", "lbl_monitor_step",
     "lbl_label", "lbl_label_blocks_noalloc", "lbl_roadmap_autotune",
     "lbl_session_create", "lbl_session_run", "lbl_session_free",
-    "lbl_batch_create", "lbl_batch_set_frames", "lbl_batch_launch", "lbl_batch_free",
+    "lbl_batch_create", "lbl_batch_set_frames", "lbl_batch_launch", "lbl_batch_free", "lbl_batch_autotune",
     "lbl_server_create", "lbl_server_submit", "lbl_server_wait", "lbl_server_stats", "lbl_server_free",
 )
 
@@ -79,6 +82,15 @@ class lbl_pose(ctypes.Structure):
 class lbl_frame(ctypes.Structure):
     _fields_ = [("world", lbl_grid), ("d_planes", ctypes.c_void_p), ("pose", lbl_pose), ("d_O", ctypes.c_void_p),
                 ("d_L", ctypes.c_void_p), ("d_next", ctypes.c_void_p), ("d_viol", ctypes.c_void_p)]
+
+
+LBL_BATCH_CLASSES = 4
+
+
+class lbl_batch_tuning(ctypes.Structure):
+    _fields_ = [("word_bytes", ctypes.c_int32), ("items", ctypes.c_int32), ("depth", ctypes.c_int32),
+                ("ctas_per_sm", ctypes.c_int32), ("units_per_warp", ctypes.c_int32), ("ms", ctypes.c_float),
+                ("ms_default", ctypes.c_float)]
 
 
 class lbl_config(ctypes.Structure):
@@ -131,6 +143,7 @@ def load(build_if_needed: bool = True):
         "lbl_batch_set_frames": (ctypes.c_int, [p, ctypes.POINTER(lbl_frame)]),
         "lbl_batch_launch": (ctypes.c_int, [p, u32, p]),
         "lbl_batch_free": (ctypes.c_int, [p]),
+        "lbl_batch_autotune": (ctypes.c_int, [p, i32, p, ctypes.POINTER(lbl_batch_tuning)]),
         "lbl_server_create": (ctypes.c_int, [i32, p, p, p, i32, i32, i64, ctypes.POINTER(p)]),
         "lbl_server_submit": (ctypes.c_int, [p, i32, G, p, lbl_pose, p, p, p, i64, ctypes.POINTER(i64)]),
         "lbl_server_wait": (ctypes.c_int, [p, i64, i64, ctypes.POINTER(i64)]),
@@ -421,6 +434,13 @@ def lbl_batch_set_frames(b, frames) -> None:
 def lbl_batch_launch(b, stages: int = 3, stream=None) -> None:
     """stages: LBL_STAGE_TRANSFORM | LBL_STAGE_LABEL (default both)."""
     _check(load().lbl_batch_launch(b, int(stages), _stream(stream)))
+
+
+def lbl_batch_autotune(b, reps: int = 5, stream=None) -> list:
+    """Per word-width class (1, 2, 4, 8 bytes): the chosen plan and its time."""
+    out = (lbl_batch_tuning * LBL_BATCH_CLASSES)()
+    _check(load().lbl_batch_autotune(b, int(reps), _stream(stream), out))
+    return [{f: getattr(t, f) for f, _ in lbl_batch_tuning._fields_} for t in out]
 
 
 def lbl_batch_free(b) -> None:

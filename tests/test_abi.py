@@ -44,6 +44,7 @@ def test_struct_layouts_match_the_header():
     assert B.lbl_grid.d.offset == 36 and B.lbl_grid.tres.offset == 40 and B.lbl_grid.t0.offset == 48
     assert ctypes.sizeof(B.lbl_pose) == 32
     assert ctypes.sizeof(B.lbl_config) == 24
+    assert ctypes.sizeof(B.lbl_batch_tuning) == 28 and B.lbl_batch_tuning.ms.offset == 20
 
 
 def test_version_and_empty_error():

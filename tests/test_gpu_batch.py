@@ -46,7 +46,7 @@ def _items():
     return items
 
 
-def _run_batch(items, graph):
+def _run_batch(items, graph, tune=False):
     rms, mons, frames, outs = [], [], [], []
     rng = np.random.default_rng(8)
     for k, (wl, P, mon) in enumerate(items):
@@ -76,6 +76,13 @@ def _run_batch(items, graph):
         s = torch.cuda.Stream()
         L.lbl_batch_launch(b, stream=s)  # first launch outside any capture
         s.synchronize()
+        if tune:  # measured plan per word-width class, adopted by the launches below
+            res = L.lbl_batch_autotune(b, reps=2, stream=s)
+            used = [r for r in res if r["items"] > 0]
+            assert used and sum(r["items"] for r in used) == len(items)
+            for r in used:
+                assert r["depth"] in (8, 12) and r["ctas_per_sm"] >= 1 and r["units_per_warp"] in (2, 4, 8, 16, 32)
+                assert 0 < r["ms"] <= r["ms_default"]
         if graph:
             for f in frames:
                 f["d_L"].zero_()
@@ -101,9 +108,10 @@ def _run_batch(items, graph):
 
 
 @pytest.mark.parametrize("graph", [False, True])
-def test_batch_matches_per_frame_calls_and_oracle(graph):
+@pytest.mark.parametrize("tune", [False, True])
+def test_batch_matches_per_frame_calls_and_oracle(graph, tune):
     items = _items()
-    rms, mons, frames, b = _run_batch(items, graph)
+    rms, mons, frames, b = _run_batch(items, graph, tune)
     try:
         for k, ((wl, P, mon), f, rm, mh) in enumerate(zip(items, frames, rms, mons)):
             E = wl.rowptr.shape[0] - 1
@@ -192,3 +200,39 @@ def test_batch_words_buffer_grows_and_old_graphs_stay_valid():
     finally:
         L.lbl_batch_free(b)
         L.lbl_roadmap_free(rm)
+
+
+def test_graph_captured_before_tuning_stays_valid():
+    """lbl_batch_autotune replaces the label plans; a graph captured before
+    keeps its own plan, whose memory stays allocated, and still labels right;
+    the launches after tuning use the tuned plan and label the same."""
+    items = _items()[:4]
+    rms, mons, frames, b = _run_batch(items, graph=False)
+    try:
+        s = torch.cuda.Stream()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            L.lbl_batch_launch(b, stream=torch.cuda.current_stream())
+        L.lbl_batch_autotune(b, reps=2, stream=s)
+        for f in frames:
+            f["d_L"].zero_()
+        torch.cuda.synchronize()
+        g.replay()
+        torch.cuda.synchronize()
+        before = [f["d_L"].cpu().numpy().copy() for f in frames]
+        for f in frames:
+            f["d_L"].zero_()
+        torch.cuda.synchronize()
+        L.lbl_batch_launch(b, stream=s)
+        torch.cuda.synchronize()
+        for k, ((wl, P, mon), f, old) in enumerate(zip(items, frames, before)):
+            E = wl.rowptr.shape[0] - 1
+            want = oracle.label(wl.rowptr, wl.colidx, f["d_O"].cpu().numpy(), P, threads=8)
+            assert np.array_equal(old[:E], want) and np.array_equal(f["d_L"].cpu().numpy()[:E], want), k
+    finally:
+        L.lbl_batch_free(b)
+        for m in mons:
+            if m:
+                L.lbl_monitor_free(m)
+        for rm in {id(r): r for r in rms}.values():
+            L.lbl_roadmap_free(rm)

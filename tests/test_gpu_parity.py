@@ -83,6 +83,8 @@ CFGS = [
     dict(algo=L.LBL_ALGO_QUAD, depth=12),
     dict(algo=L.LBL_ALGO_QUAD, depth=16),
     dict(algo=L.LBL_ALGO_QUAD, ctas_per_sm=1),
+    dict(algo=L.LBL_ALGO_QUAD, pipeline=L.LBL_PIPE_FRONT),      # moving front, whatever the size
+    dict(algo=L.LBL_ALGO_QUAD, pipeline=L.LBL_PIPE_REGISTERS),  # fixed per-warp ranges
     dict(algo=L.LBL_ALGO_AUTO),
 ]
 
@@ -444,6 +446,16 @@ def test_quad_runs_at_every_alignment(order):
         want = oracle.label(rowptr, colidx, O_h, P)
         for depth in (8, 12, 16):
             assert np.array_equal(gpu_label(rm, cuda(O_h), P, dict(algo=L.LBL_ALGO_QUAD, depth=depth)), want), P
+        front = dict(algo=L.LBL_ALGO_QUAD, pipeline=L.LBL_PIPE_FRONT)
+        assert np.array_equal(gpu_label(rm, cuda(O_h), P, front), want), P
+
+
+def test_quad_rejects_csr_pipelines(plain):
+    rm = Roadmap(plain.agent, plain.rowptr, plain.colidx, bittile=True)
+    for pipe in (L.LBL_PIPE_BULK, L.LBL_PIPE_ASYNC, 7):
+        with pytest.raises(L.LblError) as ei:
+            gpu_label(rm, gpu_O(plain), plain.P, dict(algo=L.LBL_ALGO_QUAD, pipeline=pipe))
+        assert ei.value.code == L.LBL_EINVAL
 
 
 def test_quad_needs_its_upload_flag(plain):
