@@ -36,6 +36,36 @@ def _arcs(rng, grid, n):
 
 
 @pytest.mark.parametrize("order", [synth.MORTON, synth.ROWMAJOR])
+@pytest.mark.parametrize("radius", [0.4, 1.3])
+def test_rasterized_rows_within_dense_arc_sampling_bounds(order, radius):
+    """eq. 7 without the oracle's closed form: the device rows lie between the
+    cells whose centres are within the radius of densely sampled arc points
+    (lower set) and those within radius + half the sampling step (upper set),
+    so a mistake the rasteriser shared with the oracle's geometry would still
+    show.  Rows are strictly increasing."""
+    from test_oracle_pins import _arc_points, _centres
+    rng = np.random.default_rng(70 + order + int(radius * 10))
+    grid = synth.agent_grid(32, 0.25, order)
+    arcs = _arcs(rng, grid, 60)
+    arcs[7:, 3] = rng.uniform(-1.5, 1.5, size=arcs.shape[0] - 7)  # tighter turns than _arcs draws
+    rm = L.lbl_roadmap_rasterize(grid, arcs, radius)
+    try:
+        rp, ci = _rows(rm)
+    finally:
+        L.lbl_roadmap_free(rm)
+    cx, cy, keys = _centres(grid)
+    for e in range(arcs.shape[0]):
+        pts = _arc_points(arcs[e], 20000)
+        h = arcs[e, 4] / (pts.shape[0] - 1)
+        d = np.sqrt(((cx[:, None] - pts[None, :, 0]) ** 2 + (cy[:, None] - pts[None, :, 1]) ** 2).min(1))
+        row = ci[rp[e]:rp[e + 1]]
+        lower = set(keys[d <= radius - 1e-9].tolist())
+        upper = set(keys[d <= radius + h / 2 + 1e-9].tolist())
+        assert lower <= set(row.tolist()) <= upper, e
+        assert (np.diff(row) > 0).all(), e
+
+
+@pytest.mark.parametrize("order", [synth.MORTON, synth.ROWMAJOR])
 @pytest.mark.parametrize("radius", [0.3, 1.0, 2.7])
 def test_rasterized_rows_equal_the_oracle(order, radius):
     rng = np.random.default_rng(int(radius * 10) + order)

@@ -44,34 +44,46 @@ def _alone(wl, rm, mh, planes, pose):
 
 
 def test_results_in_the_mix_equal_results_alone(resident):
+    """60 requests submitted back to back (every buffer made beforehand), so
+    that most arrive while earlier batches are on the device: the server must
+    put several requests into one batch (max_batch >= 2, fewer batches than
+    requests), and every request's labels and monitor outputs equal the same
+    request run alone and the oracle's."""
     wls, mons, rms, mhs = resident
-    srv = L.lbl_server_create(rms, [w.P for w in wls], mhs, lanes=2, mem_budget=512 << 20)
     rng = np.random.default_rng(3)
+    prepared = []
+    for i in range(60):
+        k = int(rng.integers(0, 3))
+        wl = wls[k]
+        planes = torch.from_numpy(wl.planes).pin_memory()
+        pose = synth.random_pose(rng, wl.world)
+        out = torch.zeros(wl.n_edges, dtype=torch.uint64).pin_memory()
+        nxt = torch.zeros(wl.n_edges, dtype=torch.uint64).pin_memory() if mhs[k] else None
+        viol = torch.zeros(wl.n_edges, dtype=torch.uint16).pin_memory() if mhs[k] else None
+        prepared.append((k, planes, pose, out, nxt, viol))
+    srv = L.lbl_server_create(rms, [w.P for w in wls], mhs, lanes=2, mem_budget=512 << 20)
     reqs = []
     try:
-        for i in range(60):
-            k = int(rng.integers(0, 3))
-            wl = wls[k]
-            planes = torch.from_numpy(wl.planes).pin_memory()
-            pose = synth.random_pose(rng, wl.world)
-            out = torch.zeros(wl.n_edges, dtype=torch.uint64).pin_memory()
-            nxt = torch.zeros(wl.n_edges, dtype=torch.uint64).pin_memory() if mhs[k] else None
-            viol = torch.zeros(wl.n_edges, dtype=torch.uint16).pin_memory() if mhs[k] else None
-            t = L.lbl_server_submit(srv, k, wl.world, planes, pose, out, nxt, viol)
-            reqs.append((t, k, planes, pose, out, nxt, viol))
+        for k, planes, pose, out, nxt, viol in prepared:
+            reqs.append((L.lbl_server_submit(srv, k, wls[k].world, planes, pose, out, nxt, viol),) + (k, planes, pose,
+                                                                                                      out, nxt, viol))
         lats = [L.lbl_server_wait(srv, r[0], 20000) for r in reqs]
         assert all(x > 0 for x in lats)
         st = L.lbl_server_stats(srv)
-        assert st["completed"] == 60 and st["batches"] >= 1 and st["arena_used"] == 0
+        assert st["completed"] == 60 and st["arena_used"] == 0
+        assert st["max_batch"] >= 2 and st["batches"] < st["completed"], st  # requests were batched together
         for j, (t, k, planes, pose, out, nxt, viol) in enumerate(reqs):
-            wl, rm, mh = wls[k], rms[k], mhs[k]
+            wl, rm, mh, m = wls[k], rms[k], mhs[k], mons[k]
             aL, aN, aV = _alone(wl, rm, mh, planes, pose)
             assert np.array_equal(out.numpy(), aL), j
             if mh:
                 assert np.array_equal(nxt.numpy(), aN) and np.array_equal(viol.numpy(), aV), j
-            if j % 10 == 0:
-                O = oracle.frame_transform(wl.world, wl.planes, pose, wl.agent)
-                assert np.array_equal(out.numpy(), oracle.label(wl.rowptr, wl.colidx, O, wl.P, threads=8)), j
+            O = oracle.frame_transform(wl.world, wl.planes, pose, wl.agent)
+            want = oracle.label(wl.rowptr, wl.colidx, O, wl.P, threads=8)
+            assert np.array_equal(out.numpy(), want), j
+            if mh:
+                wn, wv = oracle.monitor(m.n_states, m.m, m.relbits, m.delta, m.reject, want)
+                assert np.array_equal(nxt.numpy(), wn) and np.array_equal(viol.numpy(), wv), j
     finally:
         L.lbl_server_free(srv)
 
