@@ -83,6 +83,8 @@ def parse():
     ap.add_argument("--transform", default="auto", choices=["auto", "packed", "direct"],
                     help="frame transform: planes packed into words, then one gather per agent cell; or byte "
                          "gathers; auto packs as sessions do (planes of 8 MiB or more, world <= 4x agent cells)")
+    ap.add_argument("--no-extras", action="store_true", help="skip the reduced batched and serving measurements "
+                    "of the default line")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--clocks-csv", default=None, help="keep the raw clock samples in this file")
     ap.add_argument("--steps-csv", default=None, help="write every timed step's device times (ms) to this file")
@@ -234,6 +236,40 @@ def committed_traffic(kernel_src: str, workload: str, algo: str):
     return None
 
 
+def workload_config(args, wl, world: int) -> dict:
+    """The `config` of both arms' JSON lines: the workload alone (which form
+    and transform the GPU arm ran is reported beside it, under `path`)."""
+    return {"workload": WORKLOADS[args.workload], "name": args.workload, "edges": int(wl.n_edges), "nnz": int(wl.nnz),
+            "props": int(wl.P), "grid": "x".join(str(v) for v in (wl.agent.w, wl.agent.h, wl.agent.d) if v > 1),
+            "monitor": wl.monitor is not None,
+            "l2": f"flushed before every step (256 MiB write); CSR {(4 * wl.nnz) / 1e9:.3f} GB "
+                  + ("> L2" if 4 * wl.nnz > (129 << 20) else "< L2 (each step starts with a flushed L2)"),
+            "parallelism": f"replicas x{world}"}
+
+
+def l1_roofline(kernel_src: str, workload: str, algo: str, E: int, label_s: float, clk, peaks):
+    """The labeling call against its L1 ceiling: LSU data-pipe wavefronts per
+    edge from the committed ncu capture (taken on a cut of the same workload,
+    on the current kernel source: matching hash), scaled to E edges, per SM
+    and clock, against the pipe's one wavefront per clock per SM."""
+    path = os.path.join(ROOT, "profiles", "l1.txt")
+    if not os.path.exists(path):
+        return None
+    h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+    for line in open(path):
+        t = line.split()
+        if len(t) >= 6 and t[0] == workload and t[1] == algo and t[2] == h:
+            wpe, spe, sms = float(t[3]), float(t[4]), int(t[5])
+            mhz = (clk or {}).get("sm_mhz") or (peaks or {}).get("sm_max_mhz") or 2070.0
+            per_launch = wpe * E
+            achieved = per_launch / label_s / (sms * mhz * 1e6)
+            return {"unit": "LSU data-pipe wavefronts per SM-clock", "achieved": achieved, "peak": 1.0,
+                    "frac": achieved, "wavefronts_per_launch": per_launch, "wavefronts_per_edge": wpe,
+                    "l1_sectors_per_edge": spe, "sm_mhz": mhz, "sms": sms,
+                    "source": "profiles/l1.txt (ncu, cut of the workload, scaled by edges)"}
+    return None
+
+
 # ------------------------------------------------------------------ reference
 
 def cpu_cores() -> int:
@@ -288,6 +324,25 @@ def calibrate_sample(wl, seconds: float, threads: int) -> int:
     return int(min(wl.n_edges, max(1000, (seconds - fixed) / per_edge)))
 
 
+def cpu_baseline(wl, seconds: float, with_monitor: bool) -> dict:
+    """The oracle on the host: OpenMP over edges on every core this process may
+    use (the baseline), and on one thread (a second, single-thread figure),
+    each on a bounded sample of one frame."""
+    E, P = wl.n_edges, wl.P
+    threads = cpu_cores()
+    n = calibrate_sample(wl, seconds, threads)
+    dt, dtr = oracle_step_times(wl, n, threads)
+    n1 = calibrate_sample(wl, seconds / 3.0, 1)
+    dt1, dtr1 = oracle_step_times(wl, n1, 1)
+    what = " + monitor" if with_monitor else ""
+    return {"value": E * P / oracle_frame_seconds(wl, n, dt, dtr), "unit": UNIT, "cores": threads,
+            "cores_total": os.cpu_count(), "kind": "oracle",
+            "sample": f"one frame: whole-grid frame transform + labels of the first {n} of {E} edges{what} "
+                      f"({dt:.1f} s on {threads} threads); a whole frame's time = transform + label time x {E}/{n}",
+            "single_thread": {"value": E * P / oracle_frame_seconds(wl, n1, dt1, dtr1), "unit": UNIT, "cores": 1,
+                              "sample": f"the same on one thread, first {n1} edges ({dt1:.1f} s)"}}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -311,8 +366,9 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": WORKLOADS[args.workload], "name": args.workload},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "config": workload_config(args, wl, world),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "cores_total": os.cpu_count(),
+                             "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -470,7 +526,7 @@ def main():
         csr_line = {"bound": "hbm", "achieved": csr_b / csr_s / 1e9, "peak": pk, "unit": "GB/s",
                     "frac": csr_b / csr_s / 1e9 / pk, "label_ms": csr_s * 1e3, "launches": n_csr,
                     "traffic": committed_traffic(os.path.join(ROOT, "paper_1810_02612_gb300", "csrc", "k_label.cu"),
-                                                 args.workload, "csr"),
+                                                 args.workload, "csr") if args.edges is None else None,
                     "kernel": "label_csr", "algorithmic_bytes_per_launch": csr_b,
                     "peak_source": "measured" if peaks0 else "fallback"}
 
@@ -522,30 +578,28 @@ def main():
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
     achieved = lb / label_avg_s / 1e9
-    traffic = committed_traffic(os.path.join(ROOT, "paper_1810_02612_gb300", "csrc", "k_label.cu"),
-                                args.workload, used)
+    kernel_src = os.path.join(ROOT, "paper_1810_02612_gb300", "csrc", "k_label.cu")
+    full_size = args.edges is None
+    traffic = committed_traffic(kernel_src, args.workload, used) if full_size else None
+    l1 = l1_roofline(kernel_src, args.workload, used, E, label_avg_s, clk, peaks)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        threads = cpu_cores()
-        n = calibrate_sample(wl, args.cpu_seconds, threads)
-        dt, dtr = oracle_step_times(wl, n, threads)
-        cpu = {"value": E * P / oracle_frame_seconds(wl, n, dt, dtr), "unit": UNIT, "cores": threads,
-               "kind": "oracle",
-               "sample": f"one frame: whole-grid frame transform + labels of the first {n} of {E} edges"
-                         + (" + monitor" if mon else "") + f" ({dt:.1f} s); a whole frame's time = transform"
-                         f" + label time x {E}/{n}"}
+        cpu = cpu_baseline(wl, args.cpu_seconds, mon is not None)
+
+    more = {}
+    if world == 1 and args.workload == "large" and not args.no_extras:
+        more = extras(args, rank, torch, L)
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": WORKLOADS[args.workload], "name": args.workload, "edges": E, "nnz": wl.nnz,
-                       "props": P, "grid": "x".join(str(v) for v in (wl.agent.w, wl.agent.h, wl.agent.d) if v > 1), "algo": used, "tuned": tuned,
-                       "transform": args.transform,
-                       "monitor": bool(mon), "l2": "flushed before every step (256 MiB write); CSR "
-                       f"{(4 * wl.nnz) / 1e9:.2f} GB > L2", "parallelism": f"replicas x{world}"},
+            "config": workload_config(args, wl, world),
+            "path": {"algo": used, "tuned": tuned, "transform": args.transform,
+                     "cfg": {"lanes_per_edge": args.lanes, "early_exit": args.early_exit, "ctas_per_sm": args.ctas,
+                             "pipeline": args.pipeline, "depth": args.depth}},
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
                            "frame_transform_avg": float(frame_ms.mean()), "label_avg": float(label_ms.mean()),
                            "e2e_p50": float(np.percentile(e2e_ms_steps, 50)),
@@ -555,16 +609,17 @@ def main():
                     "mode": "lbl_session_run frames back to back from pinned host memory; each frame's "
                             "H2D planes and D2H labels/monitor outputs inside the timed region"},
             "gpu_launches": launches_per_step * args.steps,
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "roofline": {"bound": "l1" if l1 else "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": f"label_{used}", "algorithmic_bytes_per_launch": lb,
                          "csr_equivalent_gbs": label_bytes(wl, "csr", None, mon is not None) / label_avg_s / 1e9,
-                         "peak_source": "measured" if peaks else "fallback"},
+                         "peak_source": "measured" if peaks else "fallback", "l1": l1},
             "roofline_csr_form": csr_line,
             "cpu_baseline": cpu,
             "clocks": clk,
             "setup_s": {"generate": t_gen},
         }
+        line.update(more)
         print(json.dumps(line), flush=True)
 
     if mon:
@@ -574,15 +629,15 @@ def main():
         dist.destroy_process_group()
 
 
-def run_batched(args, rank, world, local, dist, torch, L):
-    """64 frames of uneven roadmaps: one graph replay of the batched launch per
-    step against 64 frame-by-frame call pairs, same frames and buffers."""
-    t_gen = time.perf_counter()
-    frames = synth.make_batch(seed=rank_seed(args.seed, rank), threads=cpu_cores())
-    t_gen = time.perf_counter() - t_gen
+def measure_batched(torch, L, frames, steps: int, warmup: int, algo: str, dist=None, clocks=None, tune=True):
+    """Batched frames: one graph replay of the batched launches per step against
+    the same frames labeled by frame-by-frame transform + label call pairs (same
+    buffers, L2 flushed before every step), checked bit for bit.  With `tune`
+    the batch's label plan is chosen by lbl_batch_autotune before the graph is
+    captured (and checked bit for bit again)."""
     stream = torch.cuda.Stream()
     rms, fr = [], []
-    quad = args.algo in ("quad", "auto")
+    quad = algo in ("quad", "auto")
     for f in frames:
         rms.append(L.lbl_roadmap_upload(f.agent, f.rowptr, f.colidx, flags=L.LBL_UPLOAD_QUAD if quad else 0,
                                         stream=stream))
@@ -598,7 +653,6 @@ def run_batched(args, rank, world, local, dist, torch, L):
     b = L.lbl_batch_create(rms, [f.P for f in frames])
     L.lbl_batch_set_frames(b, fr)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    units = sum(f.n_edges * f.P for f in frames)
 
     def plain_step():
         for f, r, d in zip(frames, rms, fr):
@@ -614,6 +668,15 @@ def run_batched(args, rank, world, local, dist, torch, L):
     L.lbl_batch_launch(b, stream=stream)
     torch.cuda.synchronize()
     match = all(torch.equal(a.view(torch.int64), d["d_L"].view(torch.int64)) for a, d in zip(ref, fr))
+    tuning = None
+    if tune:
+        tuning = [t for t in L.lbl_batch_autotune(b, reps=5, stream=stream) if t["items"] > 0]
+        for d in fr:
+            d["d_L"].zero_()
+        torch.cuda.synchronize()
+        L.lbl_batch_launch(b, stream=stream)
+        torch.cuda.synchronize()
+        match = match and all(torch.equal(a.view(torch.int64), d["d_L"].view(torch.int64)) for a, d in zip(ref, fr))
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g, stream=stream):
         L.lbl_batch_launch(b, stream=torch.cuda.current_stream())
@@ -629,167 +692,210 @@ def run_batched(args, rank, world, local, dist, torch, L):
         torch.cuda.synchronize()
         return np.array([a.elapsed_time(c) for a, c in ev])
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         plain_step()
         g.replay()
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    clocks = ClockSampler(local, enabled=not args.no_clocks and rank == 0)
     t0 = time.time()
     with torch.cuda.stream(stream):
-        batched_ms = timed(lambda: g.replay(), args.steps)
+        batched_ms = timed(lambda: g.replay(), steps)
     t1 = time.time()
-    clk = clocks.stop(t0, t1)
-    plain_ms = timed(plain_step, args.steps)
+    clk = clocks.stop(t0, t1) if clocks else None
+    plain_ms = timed(plain_step, steps)
     # where the time goes: each stage alone, batched and frame by frame
-    n_br = max(5, args.steps // 5)
+    n_br = max(5, steps // 5)
     with torch.cuda.stream(stream):
         b_tr = timed(lambda: L.lbl_batch_launch(b, L.LBL_STAGE_TRANSFORM, stream=stream), n_br)
         b_lb = timed(lambda: L.lbl_batch_launch(b, L.LBL_STAGE_LABEL, stream=stream), n_br)
     p_tr = timed(lambda: [frame_transform(f, d) for f, d in zip(frames, fr)], n_br)
     p_lb = timed(lambda: [L.lbl_label(r, d["d_O"], f.P, d["d_L"], stream=stream)
                           for f, r, d in zip(frames, rms, fr)], n_br)
-    total_b = max_over_ranks(float(batched_ms.sum()), dist, "cuda")
-    total_p = max_over_ranks(float(plain_ms.sum()), dist, "cuda")
-    value = job_throughput(world, units, 1, args.steps, total_b)
-    plain_value = job_throughput(world, units, 1, args.steps, total_p)
-    nnz = sum(f.nnz for f in frames)
     entries = [L.lbl_roadmap_info(r)[4] if quad else f.nnz for f, r in zip(frames, rms)]
+    L.lbl_batch_free(b)
+    for r in rms:
+        L.lbl_roadmap_free(r)
+    packs = any(f.P > 0 and f.world.cells <= 4 * f.agent.cells for f in frames)  # frames the batch packs
+    label_classes = len({pyramid_word_bytes(f.P) if quad else 8 for f in frames})  # one label launch per word width
     bytes_step = sum(4 * n + 16 * f.n_edges + 8 * f.agent.cells + f.P * f.world.cells
                      + (2 * pyramid_word_bytes(f.P) * pyramid_words(f.agent.cells) if quad else 0)
                      for f, n in zip(frames, entries))
-    packs = any(f.P > 0 and f.world.cells <= 4 * f.agent.cells for f in frames)  # frames the batch packs
-    label_classes = len({pyramid_word_bytes(f.P) if quad else 8 for f in frames})  # one label launch per word width
-    launches = 1 + int(packs) + int(quad) + label_classes  # (pack,) transform, (pyramid,) labels
-    plain_launches = len(frames) * (3 if quad else 2)  # transform, (pyramid,) label per frame
+    return {"batched_ms": batched_ms, "plain_ms": plain_ms, "match": bool(match), "clk": clk, "tuning": tuning,
+            "units": sum(f.n_edges * f.P for f in frames), "entries": int(sum(entries)), "bytes_step": bytes_step,
+            "launches": 1 + int(packs) + int(quad) + label_classes,  # (pack,) transform, (pyramid,) labels
+            "plain_launches": len(frames) * (3 if quad else 2),  # transform, (pyramid,) label per frame
+            "stage_ms": {"batched_transform": float(np.median(b_tr)), "batched_label": float(np.median(b_lb)),
+                         "plain_transform": float(np.median(p_tr)), "plain_label": float(np.median(p_lb))}}
+
+
+def batched_summary(m: dict, frames, steps: int) -> dict:
+    """The batched-vs-plain comparison as one JSON object."""
+    units = m["units"]
+    tb, tp = float(m["batched_ms"].sum()), float(m["plain_ms"].sum())
+    return {"frames": len(frames), "edges": int(sum(f.n_edges for f in frames)), "steps": steps,
+            "value": units * steps / (tb / 1e3), "plain_value": units * steps / (tp / 1e3), "unit": UNIT,
+            "batched_ms_per_step": tb / steps, "plain_ms_per_step": tp / steps, "speedup": tp / tb,
+            "bit_exact_match": m["match"],
+            "batched_p50_ms": float(np.percentile(m["batched_ms"], 50)),
+            "batched_p99_ms": float(np.percentile(m["batched_ms"], 99)),
+            "plain_p50_ms": float(np.percentile(m["plain_ms"], 50)),
+            "plain_p99_ms": float(np.percentile(m["plain_ms"], 99)),
+            "batched_launches_per_step": m["launches"], "plain_launches_per_step": m["plain_launches"],
+            "stage_ms": m["stage_ms"], "tuning": m["tuning"]}
+
+
+def run_batched(args, rank, world, local, dist, torch, L):
+    """64 frames of uneven roadmaps: one graph replay of the batched launch per
+    step against 64 frame-by-frame call pairs, same frames and buffers."""
+    t_gen = time.perf_counter()
+    frames = synth.make_batch(seed=rank_seed(args.seed, rank), threads=cpu_cores())
+    t_gen = time.perf_counter() - t_gen
+    clocks = ClockSampler(local, enabled=not args.no_clocks and rank == 0)
+    m = measure_batched(torch, L, frames, args.steps, args.warmup, args.algo, dist, clocks)
+    quad = args.algo in ("quad", "auto")
+    total_b = max_over_ranks(float(m["batched_ms"].sum()), dist, "cuda")
+    total_p = max_over_ranks(float(m["plain_ms"].sum()), dist, "cuda")
+    value = job_throughput(world, m["units"], 1, args.steps, total_b)
+    plain_value = job_throughput(world, m["units"], 1, args.steps, total_p)
+    nnz = sum(f.nnz for f in frames)
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
-    achieved = bytes_step / (total_b / args.steps / 1e3) / 1e9
+    achieved = m["bytes_step"] / (total_b / args.steps / 1e3) / 1e9
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_b / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": WORKLOADS["batched"], "name": "batched", "frames": len(frames),
-                       "edges": sum(f.n_edges for f in frames), "nnz": nnz, "algo": "quad" if quad else "csr",
-                       "streamed_entries": int(sum(entries)),
+                       "edges": sum(f.n_edges for f in frames), "nnz": nnz,
                        "l2": "flushed before every step (256 MiB write)", "parallelism": f"replicas x{world}"},
+            "path": {"algo": "quad" if quad else "csr", "streamed_entries": m["entries"]},
             "batched_vs_plain": {"plain_value": plain_value, "plain_ms_per_step": total_p / args.steps,
-                                 "speedup": total_p / total_b, "bit_exact_match": bool(match),
-                                 "plain_launches_per_step": plain_launches,
-                                 "batched_launches_per_step": launches,
-                                 "stage_ms": {"batched_transform": float(np.median(b_tr)),
-                                              "batched_label": float(np.median(b_lb)),
-                                              "plain_transform": float(np.median(p_tr)),
-                                              "plain_label": float(np.median(p_lb))}},
-            "latency_ms": {"batched_p50": float(np.percentile(batched_ms, 50)),
-                           "batched_p99": float(np.percentile(batched_ms, 99)),
-                           "plain_p50": float(np.percentile(plain_ms, 50)),
-                           "plain_p99": float(np.percentile(plain_ms, 99))},
-            "gpu_launches": launches * args.steps,
+                                 "speedup": total_p / total_b, "bit_exact_match": m["match"],
+                                 "plain_launches_per_step": m["plain_launches"],
+                                 "batched_launches_per_step": m["launches"], "stage_ms": m["stage_ms"],
+                                 "tuning": m["tuning"]},
+            "latency_ms": {"batched_p50": float(np.percentile(m["batched_ms"], 50)),
+                           "batched_p99": float(np.percentile(m["batched_ms"], 99)),
+                           "plain_p50": float(np.percentile(m["plain_ms"], 50)),
+                           "plain_p99": float(np.percentile(m["plain_ms"], 99))},
+            "gpu_launches": m["launches"] * args.steps,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": None, "kernel": "batched step (frame transforms + labels)",
-                         "algorithmic_bytes_per_launch": bytes_step,
+                         "algorithmic_bytes_per_launch": m["bytes_step"],
                          "peak_source": "measured" if peaks else "fallback"},
-            "clocks": clk, "setup_s": {"generate": t_gen},
+            "clocks": m["clk"], "setup_s": {"generate": t_gen},
         }
         print(json.dumps(line), flush=True)
-    L.lbl_batch_free(b)
-    for r in rms:
-        L.lbl_roadmap_free(r)
 
 
-def run_serving(args, rank, world, local, dist, torch, L):
-    """Poisson request stream against 8 resident roadmaps; the same stream is
-    served with continuous batching and with one request per launch."""
-    import threading
-    rates = [float(x) for x in args.rates.split(",")]
-    rate = rates[0]
-    sizes = [20_000, 35_000, 61_000, 107_000, 187_000, 327_000, 572_000, 1_000_000]
-    t_gen = time.perf_counter()
-    rng = np.random.default_rng(rank_seed(args.seed, rank))
+SERVING_SIZES = [20_000, 35_000, 61_000, 107_000, 187_000, 327_000, 572_000, 1_000_000]
+
+
+def serving_setup(torch, L, seed: int, n_max: int, algo: str, sizes=SERVING_SIZES):
+    """Resident roadmaps (prefixes of one pool of arcs on a 256x256 grid), eight
+    32-proposition world plane sets in pinned memory, and the seeded request
+    stream (unit gaps, roadmap and plane-set choice, pose per request)."""
+    rng = np.random.default_rng(seed)
     agent = synth.agent_grid(256, 0.25, synth.MORTON)
     wgrid = synth.world_grid(256, 256, 0.25)
     arcs = synth.sample_arcs(rng, sizes[-1], agent, (-0.3, 0.3), (5.0, 40.0))
     rowptr, colidx = synth.sweep_csr(arcs, 1.2, agent, cpu_cores())
     P = 32
     plane_sets = [torch.from_numpy(synth.planes_mixed(rng, P, wgrid)).pin_memory() for _ in range(8)]
-    t_gen = time.perf_counter() - t_gen
-    quad = args.algo in ("quad", "auto")
+    quad = algo in ("quad", "auto")
     rms = [L.lbl_roadmap_upload(agent, rowptr[: n + 1], colidx[: int(rowptr[n])],
                                 flags=L.LBL_UPLOAD_QUAD if quad else 0) for n in sizes]
-    n_max = args.requests
-    unit_gaps = rng.exponential(1.0, size=n_max)  # scaled by 1/rate per run
-    which = rng.integers(0, len(sizes), size=n_max)
-    sets = rng.integers(0, len(plane_sets), size=n_max)
-    poses = [synth.random_pose(rng, wgrid) for _ in range(n_max)]
-    ring = 256
-    outs = [torch.empty(sizes[-1], dtype=torch.uint64).pin_memory() for _ in range(ring)]
+    req = {"unit_gaps": rng.exponential(1.0, size=n_max), "which": rng.integers(0, len(sizes), size=n_max),
+           "sets": rng.integers(0, len(plane_sets), size=n_max),
+           "poses": [synth.random_pose(rng, wgrid) for _ in range(n_max)]}
+    return {"sizes": sizes, "P": P, "wgrid": wgrid, "plane_sets": plane_sets, "rms": rms, "req": req, "quad": quad,
+            "nnz_largest": int(rowptr[-1]),
+            "outs": [torch.empty(sizes[-1], dtype=torch.uint64).pin_memory() for _ in range(256)]}
 
-    def serve(max_batch, rate, n_req):
-        warm = min(args.warmup * 100, n_req // 10)
-        gaps = unit_gaps[:n_req] / rate
-        srv = L.lbl_server_create(rms, [P] * len(sizes), None, lanes=2, mem_budget=4 << 30, max_batch=max_batch)
-        tickets = [None] * n_req
-        lat = np.zeros(n_req)
-        done_t = np.zeros(n_req)
-        submitted = threading.Semaphore(0)
 
-        def waiter():
-            for i in range(n_req):
-                submitted.acquire()
-                lat[i] = L.lbl_server_wait(srv, tickets[i], 60000) / 1e6
-                done_t[i] = time.monotonic_ns()
+def serve(L, st: dict, max_batch: int, rate: float, n_req: int, warm: int) -> dict:
+    """Replay the first n_req requests of the stream at `rate` from a host
+    thread; latency = scheduled arrival -> labels in host memory."""
+    import threading
+    sizes, P, req, outs = st["sizes"], st["P"], st["req"], st["outs"]
+    ring = len(outs)
+    gaps = req["unit_gaps"][:n_req] / rate
+    srv = L.lbl_server_create(st["rms"], [P] * len(sizes), None, lanes=2, mem_budget=4 << 30, max_batch=max_batch)
+    tickets = [None] * n_req
+    lat = np.zeros(n_req)
+    done_t = np.zeros(n_req)
+    submitted = threading.Semaphore(0)
 
-        th = threading.Thread(target=waiter)
-        th.start()
-        t0 = time.monotonic_ns() + 20_000_000
-        arrival = t0 + np.cumsum(gaps * 1e9).astype(np.int64)
+    def waiter():
         for i in range(n_req):
-            while time.monotonic_ns() < arrival[i]:
-                pass
-            if i >= ring:  # the output buffer of request i - ring is free again
-                while done_t[i - ring] == 0:
-                    time.sleep(0)
-            k = int(which[i])
-            tickets[i] = L.lbl_server_submit(srv, k, wgrid, plane_sets[int(sets[i])], poses[i],
-                                             outs[i % ring][: sizes[k]], arrival_ns=int(arrival[i]))
-            submitted.release()
-        th.join()
-        st = L.lbl_server_stats(srv)
-        L.lbl_server_free(srv)
-        sel = slice(warm, n_req)
-        span_s = (done_t[n_req - 1] - arrival[warm]) / 1e9
-        labels = float(sum(sizes[int(k)] for k in which[sel])) * P
-        return {"rate_req_s": rate, "requests": n_req, "warmup": warm,
-                "labels_per_s": labels / span_s, "p50_ms": float(np.percentile(lat[sel], 50)),
-                "p99_ms": float(np.percentile(lat[sel], 99)), "p999_ms": float(np.percentile(lat[sel], 99.9)),
-                "mean_ms": float(lat[sel].mean()), "achieved_req_per_s": (n_req - warm) / span_s,
-                "batches": st["batches"], "mean_batch": n_req / max(st["batches"], 1), "max_batch": st["max_batch"]}
+            submitted.acquire()
+            lat[i] = L.lbl_server_wait(srv, tickets[i], 60000) / 1e6
+            done_t[i] = time.monotonic_ns()
 
+    th = threading.Thread(target=waiter)
+    th.start()
+    t0 = time.monotonic_ns() + 20_000_000
+    arrival = t0 + np.cumsum(gaps * 1e9).astype(np.int64)
+    for i in range(n_req):
+        while time.monotonic_ns() < arrival[i]:
+            pass
+        if i >= ring:  # the output buffer of request i - ring is free again
+            while done_t[i - ring] == 0:
+                time.sleep(0)
+        k = int(req["which"][i])
+        tickets[i] = L.lbl_server_submit(srv, k, st["wgrid"], st["plane_sets"][int(req["sets"][i])],
+                                         req["poses"][i], outs[i % ring][: sizes[k]], arrival_ns=int(arrival[i]))
+        submitted.release()
+    th.join()
+    stats = L.lbl_server_stats(srv)
+    L.lbl_server_free(srv)
+    sel = slice(warm, n_req)
+    span_s = (done_t[n_req - 1] - arrival[warm]) / 1e9
+    labels = float(sum(sizes[int(k)] for k in req["which"][warm:n_req])) * P
+    return {"rate_req_s": rate, "requests": n_req, "warmup": warm,
+            "labels_per_s": labels / span_s, "p50_ms": float(np.percentile(lat[sel], 50)),
+            "p99_ms": float(np.percentile(lat[sel], 99)), "p999_ms": float(np.percentile(lat[sel], 99.9)),
+            "mean_ms": float(lat[sel].mean()), "achieved_req_per_s": (n_req - warm) / span_s,
+            "batches": stats["batches"], "mean_batch": n_req / max(stats["batches"], 1),
+            "max_batch": stats["max_batch"]}
+
+
+def run_serving(args, rank, world, local, dist, torch, L):
+    """Poisson request stream against 8 resident roadmaps; the same stream is
+    served with continuous batching and with one request per launch."""
+    rates = [float(x) for x in args.rates.split(",")]
+    rate = rates[0]
+    n_max = args.requests
+    t_gen = time.perf_counter()
+    st = serving_setup(torch, L, rank_seed(args.seed, rank), n_max, args.algo)
+    t_gen = time.perf_counter() - t_gen
+    warm = min(args.warmup * 100, n_max // 10)
     clocks = ClockSampler(local, enabled=not args.no_clocks and rank == 0)
     t0 = time.time()
-    cont = serve(128, rate, n_max)
+    cont = serve(L, st, 128, rate, n_max, warm)
     t1 = time.time()
     clk = clocks.stop(t0, t1)
-    plain = serve(1, rate, n_max)
+    plain = serve(L, st, 1, rate, n_max, warm)
     sweep = []
     for r in rates[1:]:
         n = min(n_max, 10_000)
-        c, p = serve(128, r, n), serve(1, r, n)
+        c, p = serve(L, st, 128, r, n, min(warm, n // 10)), serve(L, st, 1, r, n, min(warm, n // 10))
         sweep.append({"rate_req_s": r, "continuous_batching": c, "one_request_per_launch": p,
                       "throughput_gain": c["labels_per_s"] / p["labels_per_s"], "p99_gain": p["p99_ms"] / c["p99_ms"]})
     value = cont["labels_per_s"]
+    sizes, P, wgrid, which = st["sizes"], st["P"], st["wgrid"], st["req"]["which"]
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": n_max, "warmup": cont["warmup"],
             "ms_per_step": cont["mean_ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "u64", "data": "synthetic",
             "config": {"workload": WORKLOADS["serving"], "name": "serving", "requests": n_max, "rate_req_s": rate,
-                       "roadmap_edges": sizes, "nnz_largest": int(rowptr[-1]), "props": P,
-                       "algo": "quad" if quad else "csr", "parallelism": f"replicas x{world}"},
-            "gpu_launches": int(cont["batches"]) * (3 if quad else 2),
+                       "roadmap_edges": sizes, "nnz_largest": st["nnz_largest"], "props": P,
+                       "parallelism": f"replicas x{world}"},
+            "path": {"algo": "quad" if st["quad"] else "csr"},
+            "gpu_launches": int(cont["batches"]) * (3 if st["quad"] else 2),
             "serving": {"continuous_batching": cont, "one_request_per_launch": plain,
                         "p99_gain": plain["p99_ms"] / cont["p99_ms"], "saturation_sweep": sweep},
             "latency_ms": {"p50": cont["p50_ms"], "p99": cont["p99_ms"]},
@@ -798,8 +904,38 @@ def run_serving(args, rank, world, local, dist, torch, L):
             "clocks": clk, "setup_s": {"generate": t_gen},
         }
         print(json.dumps(line), flush=True)
-    for r in rms:
+    for r in st["rms"]:
         L.lbl_roadmap_free(r)
+
+
+def extras(args, rank, torch, L) -> dict:
+    """Reduced batched and serving measurements for the default line: 16 frames
+    of 10k-200k edges (one graph replay vs 16 call pairs, 200 steps), and 2 s of
+    Poisson arrivals at 2,000 req/s against the 8 resident roadmaps
+    (continuous batching vs one request per launch)."""
+    out = {}
+    t = time.perf_counter()
+    frames = synth.make_batch(seed=rank_seed(args.seed, rank) + 17, frames=16, edges=(10_000, 200_000),
+                              threads=cpu_cores())
+    m = measure_batched(torch, L, frames, 200, 5, "quad")
+    out["batched"] = batched_summary(m, frames, 200)
+    out["batched"]["workload"] = ("16 frames/agents, roadmaps of log-uniform 10k-200k edges on 128^2-512^2 z-order "
+                                  "grids at 0.25 m, 8-64 propositions; one CUDA-graph replay of the batched launches "
+                                  "vs 16 frame-by-frame transform+label call pairs; L2 flushed before every step")
+    n_req, rate = 4000, 2000.0
+    st = serving_setup(torch, L, rank_seed(args.seed, rank) + 29, n_req, "quad")
+    cont = serve(L, st, 128, rate, n_req, 400)
+    plain = serve(L, st, 1, rate, n_req, 400)
+    for r in st["rms"]:
+        L.lbl_roadmap_free(r)
+    out["serving"] = {"workload": f"{n_req} requests (2 s) of Poisson arrivals at {rate:.0f} req/s, each a random "
+                                  "pose + 32 world planes (256x256 at 0.25 m) against one of 8 resident roadmaps of "
+                                  "20k-1M edges; 2 lanes; latency = scheduled arrival to labels in host memory",
+                      "continuous_batching": cont, "one_request_per_launch": plain,
+                      "p99_gain": plain["p99_ms"] / cont["p99_ms"],
+                      "throughput_gain": cont["labels_per_s"] / plain["labels_per_s"]}
+    out["extras_s"] = time.perf_counter() - t
+    return out
 
 
 if __name__ == "__main__":
