@@ -68,7 +68,7 @@ def parse():
     ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS))
     ap.add_argument("--requests", type=int, default=20_000, help="serving: requests at the first rate")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--algo", default="quad", choices=["auto", "csr", "bittile", "sector", "quad"],
+    ap.add_argument("--algo", default="quad", choices=["auto", "csr", "bittile", "sector", "quad", "mma"],
                     help="labeling form; auto = measure every form on the first frame and keep the fastest")
     ap.add_argument("--lanes", type=int, default=0)
     ap.add_argument("--early-exit", type=int, default=-1)
@@ -216,10 +216,18 @@ def label_bytes(wl, algo: str, n_bt: int | None, with_monitor: bool, n_sec: int 
                 + 2 * pyramid_word_bytes(wl.P) * pyramid_words(wl.agent.cells) + out)
     if algo == "sector":
         return 4 * n_sec + 8 * (E + 1) + 8 * wl.agent.cells + out
+    if algo == "mma":  # tile-block bits and ids, tile offsets, row order; per frame O read, B written and read
+        n_mma, tiles = n_qd
+        return (2048 + 4) * n_mma + 8 * (tiles + 1) + 4 * E + 8 * wl.agent.cells + 2 * mma_n(wl.P) * wl.agent.cells + out
     if algo == "bittile":
         blocks = (wl.agent.cells + 63) // 64
         return 12 * n_bt + 8 * (E + 1) + 8 * wl.agent.cells + 8 * wl.P * blocks + out
     return 4 * wl.nnz + 8 * (E + 1) + 8 * wl.agent.cells + out
+
+
+def mma_n(P: int) -> int:
+    """Columns of the tensor-core form's B operand for P propositions."""
+    return 16 if P <= 16 else 32 if P <= 32 else 64
 
 
 def committed_traffic(kernel_src: str, workload: str, algo: str):
@@ -245,6 +253,22 @@ def workload_config(args, wl, world: int) -> dict:
             "l2": f"flushed before every step (256 MiB write); CSR {(4 * wl.nnz) / 1e9:.3f} GB "
                   + ("> L2" if 4 * wl.nnz > (129 << 20) else "< L2 (each step starts with a flushed L2)"),
             "parallelism": f"replicas x{world}"}
+
+
+def mma_roofline(wl, form, label_s: float, peaks, hbm_achieved: float, hbm_peak: float, lb: int) -> dict:
+    """The tensor-core form against the fp8 tensor peak: 2 x 128 x N x 128
+    flops per (tile, 128-cell block) pair.  The fp8 peak is the measured bf16
+    burst peak times the nominal fp8/bf16 ratio of 2."""
+    n_mma, tiles = form
+    flops = 2.0 * 128 * mma_n(wl.P) * 128 * n_mma
+    bf16 = (peaks or {}).get("bf16_tflops") or 1900.0
+    peak = 2.0 * bf16
+    achieved = flops / label_s / 1e12
+    return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "label_mma", "flops_per_launch": flops, "tile_blocks": n_mma, "tiles": tiles,
+            "peak_source": ("measured bf16 x 2 (fp8 nominal ratio)" if peaks else "fallback bf16 x 2"),
+            "hbm": {"achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_achieved / hbm_peak,
+                    "algorithmic_bytes_per_launch": lb}}
 
 
 def l1_roofline(kernel_src: str, workload: str, algo: str, E: int, label_s: float, clk, peaks):
@@ -419,10 +443,11 @@ def main():
         wl = synth.make(args.workload, seed=rank_seed(args.seed, rank), edges=args.edges, threads=cpu_cores())
     t_gen = time.perf_counter() - t_gen
     algo = {"auto": L.LBL_ALGO_AUTO, "csr": L.LBL_ALGO_CSR, "bittile": L.LBL_ALGO_BITTILE,
-            "sector": L.LBL_ALGO_SECTOR, "quad": L.LBL_ALGO_QUAD}[args.algo]
+            "sector": L.LBL_ALGO_SECTOR, "quad": L.LBL_ALGO_QUAD, "mma": L.LBL_ALGO_MMA}[args.algo]
     flags = ((L.LBL_UPLOAD_BITTILE if args.algo in ("auto", "bittile") else 0)
              | (L.LBL_UPLOAD_SECTOR if args.algo in ("auto", "sector") else 0)
-             | (L.LBL_UPLOAD_QUAD if args.algo in ("auto", "quad") else 0))
+             | (L.LBL_UPLOAD_QUAD if args.algo in ("auto", "quad") else 0)
+             | (L.LBL_UPLOAD_MMA if args.algo == "mma" else 0))
     stream = torch.cuda.Stream()
     rm = L.lbl_roadmap_upload(wl.agent, wl.rowptr, wl.colidx, flags=flags, stream=stream)
     mon = None
@@ -462,10 +487,10 @@ def main():
         transform()
         tuned = L.lbl_roadmap_autotune(rm, d_O, P, d_L, mon, d_next, d_viol, reps=5, stream=stream)
         used = {L.LBL_ALGO_BITTILE: "bittile", L.LBL_ALGO_SECTOR: "sector",
-                L.LBL_ALGO_QUAD: "quad"}.get(tuned["algo"], "csr")
+                L.LBL_ALGO_QUAD: "quad", L.LBL_ALGO_MMA: "mma"}.get(tuned["algo"], "csr")
     else:
         used = args.algo
-    launches_per_step = (2 + (1 if used in ("bittile", "quad") else 0)  # + planes / pyramid kernel
+    launches_per_step = (2 + (1 if used in ("bittile", "quad", "mma") else 0)  # + planes / pyramid / B kernel
                          + (1 if args.transform == "packed" else 0))   # + packing kernel
 
     # ---- warm-up
@@ -573,7 +598,8 @@ def main():
 
     # ---- roofline of the dominant kernel (labeling)
     info = L.lbl_roadmap_info(rm)
-    lb = label_bytes(wl, used, info[2], mon is not None, info[3], info[4])
+    qd_or_mma = L.lbl_roadmap_form_info(rm, L.LBL_ALGO_MMA) if used == "mma" else info[4]
+    lb = label_bytes(wl, used, info[2], mon is not None, info[3], qd_or_mma)
     label_avg_s = float(label_ms.mean()) / 1e3
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
@@ -609,7 +635,9 @@ def main():
                     "mode": "lbl_session_run frames back to back from pinned host memory; each frame's "
                             "H2D planes and D2H labels/monitor outputs inside the timed region"},
             "gpu_launches": launches_per_step * args.steps,
-            "roofline": {"bound": "l1" if l1 else "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "mma_probe": mma_probe(L) if used == "mma" else None,
+            "roofline": mma_roofline(wl, qd_or_mma, label_avg_s, peaks, achieved, peak, lb) if used == "mma" else
+                        {"bound": "l1" if l1 else "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": f"label_{used}", "algorithmic_bytes_per_launch": lb,
                          "csr_equivalent_gbs": label_bytes(wl, "csr", None, mon is not None) / label_avg_s / 1e9,
@@ -934,8 +962,21 @@ def extras(args, rank, torch, L) -> dict:
                       "continuous_batching": cont, "one_request_per_launch": plain,
                       "p99_gain": plain["p99_ms"] / cont["p99_ms"],
                       "throughput_gain": cont["labels_per_s"] / plain["labels_per_s"]}
+    out["mma_probe"] = mma_probe(L)
     out["extras_s"] = time.perf_counter() - t
     return out
+
+
+def mma_probe(L) -> dict:
+    """Measured tcgen05 rates behind the tensor-core form (lbl_mma_probe): e4m3
+    (the form's kind::f8f6f4) at the form's widths and bf16 for comparison; the
+    int8 kind does not exist on sm_103a."""
+    res = {}
+    for kind, n, name in ((0, 64, "e4m3_n64"), (0, 128, "e4m3_n128"), (0, 16, "e4m3_n16"), (1, 64, "bf16_n64")):
+        r = L.lbl_mma_probe(kind, n, reps=4000, ctas_per_sm=4)
+        res[name] = {"tflops": r["tflops"], "exact": r["exact"]}
+    res["int8"] = "tcgen05.mma kind::i8 is rejected by ptxas for sm_103a; the form multiplies 0/1 in e4m3 instead"
+    return res
 
 
 if __name__ == "__main__":

@@ -99,6 +99,12 @@ typedef struct {
                               over every such block (a pyramid of ~4/3 words per
                               cell) and each edge ORs one word per block.  Exact:
                               OR is associative and idempotent */
+#define LBL_ALGO_MMA 5     /* the dense product of eq. 8-10 on the tensor cores:
+                              tiles of 128 edges (in locality order) times
+                              K-blocks of 128 cells, each touched tile-block a
+                              0/1 matrix multiplied with O's 0/1 bits as e4m3
+                              (tcgen05.mma kind::f8f6f4, fp32 counts in tensor
+                              memory, exact); label bit p = count > 0 */
 
 typedef struct {
   int32_t algo;           /* LBL_ALGO_* */
@@ -162,6 +168,11 @@ int lbl_version(void);
 #define LBL_UPLOAD_KEEP_ORDER 16u /* with LBL_UPLOAD_QUAD: keep the caller's edge order
                                      for the quadtree rows (for roadmaps already ordered
                                      for locality) */
+#define LBL_UPLOAD_MMA 32u        /* also derive the tensor-core form used by LBL_ALGO_MMA
+                                     (grids of at most 2^22 cells): the edges sorted by
+                                     the z-order of their middle cell, in tiles of 128;
+                                     per tile the 128-cell blocks its rows touch, 2 KiB
+                                     each; 8 KiB of working memory per 128 cells */
 
 /*
  * lbl_roadmap_upload — make a roadmap resident on the device.
@@ -205,11 +216,22 @@ int lbl_roadmap_free(lbl_roadmap rm);
 
 /*
  * lbl_roadmap_status — synchronise `s`, then report whether any labeling kernel
- * on this roadmap gave up a bounded wait (its index stream did not arrive
- * within 2 s): LBL_ETIMEOUT if so (the labels of that call are incomplete; the
- * flag is cleared), LBL_OK otherwise.  Kernels never spin without a bound.
+ * on this roadmap gave up a bounded wait (the bulk-copy index stream of
+ * LBL_PIPE_BULK or the tensor-core form's MMA completion did not arrive within
+ * the roadmap's wait limit): LBL_ETIMEOUT if so (the labels of that call are
+ * incomplete; the flag is cleared), LBL_OK otherwise.  Kernels never spin
+ * without a bound; after giving up, a kernel still waits (at most 2 s) for
+ * the copies and MMAs it has in flight before it returns.
  */
 int lbl_roadmap_status(lbl_roadmap rm, lbl_stream s);
+
+/*
+ * lbl_roadmap_set_wait_limit — the limit of those waits for later launches on
+ * this roadmap, in nanoseconds (default 2,000,000,000; 0..60e9).  0 tests the
+ * awaited phase once without waiting, which makes a launch give up at its
+ * first wait whose data has not arrived: a way to exercise the failure path.
+ */
+int lbl_roadmap_set_wait_limit(lbl_roadmap rm, int64_t limit_ns);
 
 /* Shape of a roadmap: edges, nonzeros, (block, mask) entries of the block form
    (0 without LBL_UPLOAD_BITTILE), entries of the sector form (0 without
@@ -217,6 +239,14 @@ int lbl_roadmap_status(lbl_roadmap rm, lbl_stream s);
    and device bytes held.  Any out pointer may be NULL. */
 int lbl_roadmap_info(lbl_roadmap rm, int64_t *n_edges, int64_t *nnz, int64_t *n_block_entries,
                      int64_t *n_sector_entries, int64_t *n_qdadic_entries, int64_t *device_bytes);
+
+/* Size of one labeling form of a roadmap: *entries = what its kernels stream
+   per frame (LBL_ALGO_CSR: nonzeros; LBL_ALGO_BITTILE: (block, mask) entries;
+   LBL_ALGO_SECTOR: sector entries; LBL_ALGO_QUAD: quadtree entries;
+   LBL_ALGO_MMA: (tile of 128 edges, 128-cell block) pairs, 2 KiB each), 0 when
+   the roadmap lacks the form; *tiles (LBL_ALGO_MMA: tiles of 128 edges, else
+   0).  Either pointer may be NULL.  LBL_EINVAL for an unknown algo. */
+int lbl_roadmap_form_info(lbl_roadmap rm, int32_t algo, int64_t *entries, int64_t *tiles);
 
 /* ------------------------------------------------------- frame transform */
 
@@ -311,8 +341,9 @@ int lbl_monitor_step(lbl_monitor mon, const uint64_t *d_L, int64_t n, uint64_t *
  *   n_props  0..64
  *   d_L      uint64[n_edges]
  *   cfg      NULL = defaults (LBL_ALGO_AUTO)
- * LBL_ALGO_BITTILE / LBL_ALGO_SECTOR / LBL_ALGO_QUAD need a roadmap uploaded
- * with LBL_UPLOAD_BITTILE / LBL_UPLOAD_SECTOR / LBL_UPLOAD_QUAD
+ * LBL_ALGO_BITTILE / LBL_ALGO_SECTOR / LBL_ALGO_QUAD / LBL_ALGO_MMA need a
+ * roadmap uploaded with LBL_UPLOAD_BITTILE / LBL_UPLOAD_SECTOR /
+ * LBL_UPLOAD_QUAD / LBL_UPLOAD_MMA
  * (LBL_EUNSUPPORTED otherwise).  LBL_ALGO_AUTO takes the form
  * lbl_roadmap_autotune chose for n_props, else the quadtree form when the roadmap
  * has it, else the block form for n_props <= 8 when present, else CSR.  The
@@ -358,6 +389,21 @@ int lbl_label(lbl_roadmap rm, const uint64_t *d_O, int32_t n_props, uint64_t *d_
 int lbl_label_blocks_noalloc(const int64_t *d_block_rowptr, const uint32_t *d_block_id, const uint64_t *d_block_mask,
                              int64_t n_edges, const uint64_t *d_O, int64_t n_cells, int32_t n_props, uint64_t *d_L,
                              lbl_stream s);
+
+/*
+ * lbl_mma_probe — the tensor-core rate behind LBL_ALGO_MMA, measured on the
+ * current device.  Every CTA (ctas_per_sm per SM, 1..4) keeps one 128 x K
+ * 0/1 tile of A and one n x K tile of B in shared memory and accumulates
+ * their product `reps` times with tcgen05.mma into fp32 tensor memory:
+ * kind 0 = kind::f8f6f4 with e4m3 operands (K = 128; n 16, 64 or 128), the
+ * form LBL_ALGO_MMA uses; kind 1 = kind::f16 with bf16 operands (K = 64; n
+ * 16 or 64), for comparison.  *tflops = 2 x 128 x n x K x reps x CTAs / time
+ * (CUDA events around one launch); *exact = 1 iff every accumulated count of
+ * one CTA equals reps x (A.B^T) computed on the host.  The paper has no
+ * counterpart: it bounds what the dense form of eq. 8-10 can reach.
+ * Synchronises the device; allocates and frees its own small buffers.
+ */
+int lbl_mma_probe(int32_t kind, int32_t n, int32_t reps, int32_t ctas_per_sm, double *tflops, int32_t *exact);
 
 /*
  * lbl_roadmap_autotune — pick the labeling form of this roadmap by measurement

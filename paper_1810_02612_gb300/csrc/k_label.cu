@@ -31,29 +31,6 @@ __device__ __forceinline__ uint64_t warp_or(uint64_t v) {
   return (static_cast<uint64_t>(hi) << 32) | lo;
 }
 
-struct EpiSmem {
-  uint64_t T[256];
-  uint16_t V[256];
-};
-
-__device__ __forceinline__ void load_tables(const MonitorTables &mon, EpiSmem &sm) {
-  const int letters = 1 << mon.m;
-  for (int i = threadIdx.x; i < letters; i += blockDim.x) {
-    sm.T[i] = mon.T[i];
-    sm.V[i] = mon.V[i];
-  }
-  __syncthreads();
-}
-
-__device__ __forceinline__ void epilogue(const MonitorTables &mon, const EpiSmem &sm, int64_t e, uint64_t w) {
-  uint32_t letter = 0;
-#pragma unroll
-  for (int j = 0; j < 8; ++j)
-    if (j < mon.m) letter |= static_cast<uint32_t>((w >> mon.rel[j]) & 1u) << j;
-  mon.next[e] = sm.T[letter];
-  mon.viol[e] = sm.V[letter];
-}
-
 // Index load that bypasses L1 and asks L2 to evict the line first: the column
 // indices are streamed exactly once, O should keep its L2 residency.
 __device__ __forceinline__ uint64_t evict_first_policy() {
@@ -509,7 +486,7 @@ __global__ void __launch_bounds__(kThreads) k_quad_pyramid_batch(const __grid_co
 // waits on gathers and needs no registers for prefetching.
 constexpr int kStages = 6;
 constexpr int kChunk = 256;                   // indices per chunk (1 KiB)
-constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s bound on any wait
+constexpr unsigned long long kWaitNs = 2000000000ull;  // bound on the drain after a wait gave up
 
 __device__ __forceinline__ uint64_t global_ns() {
   uint64_t t;
@@ -535,10 +512,22 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
   return ok != 0;
 }
 
+__device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(static_cast<uint32_t>(__cvta_generic_to_shared(bar))), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
 // Bounded wait for the phase with the given parity, by every lane of the warp
 // (each lane's own acquire makes the copied bytes visible to it).  The timer
-// is read only when a try_wait returns without the phase.  False after kWaitNs.
-__device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, int lane) {
+// is read only when a try_wait returns without the phase.  False after
+// limit_ns; a limit of 0 only tests the phase once, without waiting.
+__device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, int lane, uint64_t limit_ns) {
+  if (limit_ns == 0) return __all_sync(kFull, mbar_test_wait(bar, parity));
   bool ok = mbar_try_wait(bar, parity);
   if (__all_sync(kFull, ok)) return true;
   const uint64_t t0 = global_ns();
@@ -546,7 +535,7 @@ __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, int la
     if (!ok) ok = mbar_try_wait(bar, parity);
     if (__all_sync(kFull, ok)) return true;
     const uint64_t t = __shfl_sync(kFull, global_ns(), 0);
-    if (t - t0 > kWaitNs) return false;
+    if (t - t0 > limit_ns) return false;
   }
   return false;
 }
@@ -569,7 +558,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_label_tma(const int64_t *__rest
                                                            const uint64_t *__restrict__ O,
                                                            const int64_t *__restrict__ part, uint64_t mask,
                                                            uint64_t *__restrict__ L, MonitorTables mon,
-                                                           int *__restrict__ err) {
+                                                           int *__restrict__ err, uint64_t wait_ns) {
   constexpr int W = kThreads / 32;
   constexpr int J = kChunk / 32;
   __shared__ __align__(128) int32_t ring[W][kStages][kChunk];
@@ -624,11 +613,12 @@ __global__ void __launch_bounds__(kThreads, 4) k_label_tma(const int64_t *__rest
     for (int64_t i = 0; i < kStages && i < n_chunks; ++i) issue(i);
   for (int64_t i = 0; i < n_chunks; ++i) {
     const int st = static_cast<int>(i % kStages);
-    if (!warp_wait(&bars[wid][st], static_cast<uint32_t>((i / kStages) & 1), lane)) {
-      // give up: record it, let the copies still in flight land, leave
+    if (!warp_wait(&bars[wid][st], static_cast<uint32_t>((i / kStages) & 1), lane, wait_ns)) {
+      // give up: record it, let the copies still in flight (chunks i to
+      // i + kStages - 1) land, leave
       if (lane == 0) {
         atomicExch(err, 1);
-        for (int64_t j = i + 1; j < n_chunks && j < i + kStages; ++j) {
+        for (int64_t j = i; j < n_chunks && j < i + kStages; ++j) {
           const uint64_t t0 = global_ns();
           while (!mbar_try_wait(&bars[wid][j % kStages], static_cast<uint32_t>((j / kStages) & 1)) &&
                  global_ns() - t0 < kWaitNs) {
@@ -1065,9 +1055,11 @@ cudaError_t launch_label_tma(const Roadmap &rm, const uint64_t *O, int32_t P, ui
   const unsigned grid = static_cast<unsigned>(rm.num_sms * rm.part_ctas);
   MonitorTables none{};
   if (mon)
-    k_label_tma<true><<<grid, kThreads, 0, s>>>(rm.rowptr, rm.colidx, O, rm.part, mask, L, *mon, rm.err);
+    k_label_tma<true><<<grid, kThreads, 0, s>>>(rm.rowptr, rm.colidx, O, rm.part, mask, L, *mon, rm.err,
+                                                 static_cast<uint64_t>(rm.wait_ns));
   else
-    k_label_tma<false><<<grid, kThreads, 0, s>>>(rm.rowptr, rm.colidx, O, rm.part, mask, L, none, rm.err);
+    k_label_tma<false><<<grid, kThreads, 0, s>>>(rm.rowptr, rm.colidx, O, rm.part, mask, L, none, rm.err,
+                                                  static_cast<uint64_t>(rm.wait_ns));
   return cudaGetLastError();
 }
 

@@ -103,6 +103,11 @@ void free_roadmap(Roadmap *rm) {
   cudaFree(rm->qd_idx);
   cudaFree(rm->qd_part);
   cudaFree(rm->pyr);
+  cudaFree(rm->mma_perm);
+  cudaFree(rm->mma_tptr);
+  cudaFree(rm->mma_tblk);
+  cudaFree(rm->mma_bits);
+  cudaFree(rm->mma_b);
   delete rm;
 }
 
@@ -422,6 +427,60 @@ int roadmap_finish(lbl_roadmap_s *rm, uint32_t flags, cudaStream_t st) {
       return fail(cuda_fail(e, "roadmap: quadtree partition"));
     rm->has_qd = true;
   }
+  if ((flags & LBL_UPLOAD_MMA) && n_edges > 0) {
+    if (rm->cells > (int64_t{1} << 22) || n_edges >= (int64_t{1} << 31)) {
+      set_error("roadmap: the tensor-core form needs at most 2^22 cells and fewer than 2^31 edges");
+      return fail(LBL_EINVAL);
+    }
+    rm->mma_nkb = static_cast<int32_t>((rm->cells + 127) / 128);
+    rm->mma_T = (n_edges + 127) / 128;
+    // tiles of 128 edges in locality order: the whole roadmap sorted by the
+    // z-order of each row's middle cell
+    std::vector<uint32_t> key(static_cast<size_t>(n_edges));
+    std::vector<int32_t> perm(static_cast<size_t>(n_edges));
+    uint32_t *d_key = nullptr;
+    if ((e = dev_alloc(&d_key, static_cast<size_t>(n_edges), nullptr)) != cudaSuccess ||
+        (e = launch_row_keys(rm->rowptr, rm->colidx, n_edges, rm->agent.order, rm->agent.w, d_key, st)) !=
+            cudaSuccess ||
+        (e = cudaMemcpyAsync(key.data(), d_key, sizeof(uint32_t) * n_edges, cudaMemcpyDeviceToHost, st)) !=
+            cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess) {
+      cudaFree(d_key);
+      return fail(cuda_fail(e, "roadmap: tensor-core form order"));
+    }
+    cudaFree(d_key);
+    sort_range_by_key(key.data(), 0, n_edges, perm.data());
+    std::vector<int64_t> cnt(static_cast<size_t>(rm->mma_T)), tptr(static_cast<size_t>(rm->mma_T + 1));
+    int64_t *d_cnt64 = nullptr;
+    if ((e = dev_alloc(&rm->mma_perm, static_cast<size_t>(n_edges), &rm->bytes)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(rm->mma_perm, perm.data(), sizeof(int32_t) * n_edges, cudaMemcpyHostToDevice, st)) !=
+            cudaSuccess ||
+        (e = dev_alloc(&d_cnt64, static_cast<size_t>(rm->mma_T), nullptr)) != cudaSuccess ||
+        (e = launch_mma_count(rm->rowptr, rm->colidx, rm->mma_perm, n_edges, rm->mma_nkb, d_cnt64, st)) !=
+            cudaSuccess ||
+        (e = cudaMemcpyAsync(cnt.data(), d_cnt64, sizeof(int64_t) * rm->mma_T, cudaMemcpyDeviceToHost, st)) !=
+            cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess) {
+      cudaFree(d_cnt64);
+      return fail(cuda_fail(e, "roadmap: tensor-core form"));
+    }
+    cudaFree(d_cnt64);
+    tptr[0] = 0;
+    for (int64_t t = 0; t < rm->mma_T; ++t) tptr[t + 1] = tptr[t] + cnt[t];
+    rm->n_mma = tptr[rm->mma_T];
+    if ((e = dev_alloc(&rm->mma_tptr, static_cast<size_t>(rm->mma_T + 1), &rm->bytes)) != cudaSuccess ||
+        (e = dev_alloc(&rm->mma_tblk, static_cast<size_t>(rm->n_mma), &rm->bytes)) != cudaSuccess ||
+        (e = dev_alloc(&rm->mma_bits, static_cast<size_t>(rm->n_mma) * 128 * 4, &rm->bytes)) != cudaSuccess ||
+        (e = dev_alloc(&rm->mma_b, static_cast<size_t>(rm->mma_nkb) * 64 * 128, &rm->bytes)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(rm->mma_tptr, tptr.data(), sizeof(int64_t) * (rm->mma_T + 1), cudaMemcpyHostToDevice,
+                             st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(rm->mma_bits, 0, sizeof(uint32_t) * 128 * 4 * static_cast<size_t>(rm->n_mma), st)) !=
+            cudaSuccess ||
+        (e = launch_mma_fill(rm->rowptr, rm->colidx, rm->mma_perm, n_edges, rm->mma_nkb, rm->mma_tptr, rm->mma_tblk,
+                             rm->mma_bits, st)) != cudaSuccess)
+      return fail(cuda_fail(e, "roadmap: tensor-core form"));
+    rm->has_mma = true;
+  }
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(cuda_fail(e, "roadmap"));
   cudaFree(d_bad);
   cudaFree(d_cnt);
@@ -454,7 +513,7 @@ int lbl_roadmap_upload(const lbl_grid *agent, const int64_t *rowptr, const int32
     return LBL_EINVAL;
   }
   if (flags & ~(LBL_UPLOAD_DEVICE_PTRS | LBL_UPLOAD_BITTILE | LBL_UPLOAD_SECTOR | LBL_UPLOAD_QUAD |
-                LBL_UPLOAD_KEEP_ORDER)) {
+                LBL_UPLOAD_KEEP_ORDER | LBL_UPLOAD_MMA)) {
     set_error("roadmap upload: unknown flags 0x%x", flags);
     return LBL_EINVAL;
   }
@@ -480,6 +539,41 @@ int lbl_roadmap_free(lbl_roadmap rm) {
   if (!rm) return LBL_OK;
   cudaDeviceSynchronize();
   free_roadmap(rm);
+  return LBL_OK;
+}
+
+int lbl_roadmap_set_wait_limit(lbl_roadmap rm, int64_t limit_ns) {
+  g_err.clear();
+  if (!rm || limit_ns < 0 || limit_ns > 60000000000LL) {
+    set_error("roadmap wait limit: NULL roadmap or a limit outside 0..60e9 ns");
+    return LBL_EINVAL;
+  }
+  rm->wait_ns = limit_ns;
+  return LBL_OK;
+}
+
+int lbl_roadmap_form_info(lbl_roadmap rm, int32_t algo, int64_t *entries, int64_t *tiles) {
+  g_err.clear();
+  if (!rm) {
+    set_error("roadmap form info: NULL roadmap");
+    return LBL_EINVAL;
+  }
+  int64_t n = 0, t = 0;
+  switch (algo) {
+    case LBL_ALGO_CSR: n = rm->nnz; break;
+    case LBL_ALGO_BITTILE: n = rm->has_bt ? rm->n_bt : 0; break;
+    case LBL_ALGO_SECTOR: n = rm->has_sec ? rm->n_sec : 0; break;
+    case LBL_ALGO_QUAD: n = rm->has_qd ? rm->n_qd : 0; break;
+    case LBL_ALGO_MMA:
+      n = rm->has_mma ? rm->n_mma : 0;
+      t = rm->has_mma ? rm->mma_T : 0;
+      break;
+    default:
+      set_error("roadmap form info: unknown algo %d", algo);
+      return LBL_EINVAL;
+  }
+  if (entries) *entries = n;
+  if (tiles) *tiles = t;
   return LBL_OK;
 }
 
@@ -746,7 +840,7 @@ int label_impl(lbl_roadmap rm, const uint64_t *d_O, int32_t n_props, uint64_t *d
     return LBL_EINVAL;
   }
   int algo = cfg ? cfg->algo : LBL_ALGO_AUTO;
-  if (algo < LBL_ALGO_AUTO || algo > LBL_ALGO_QUAD) {
+  if (algo < LBL_ALGO_AUTO || algo > LBL_ALGO_MMA) {
     set_error("label: unknown algo %d", algo);
     return LBL_EINVAL;
   }
@@ -760,6 +854,10 @@ int label_impl(lbl_roadmap rm, const uint64_t *d_O, int32_t n_props, uint64_t *d
   }
   if (algo == LBL_ALGO_QUAD && !rm->has_qd) {
     set_error("label: LBL_ALGO_QUAD needs a roadmap uploaded with LBL_UPLOAD_QUAD");
+    return LBL_EUNSUPPORTED;
+  }
+  if (algo == LBL_ALGO_MMA && !rm->has_mma) {
+    set_error("label: LBL_ALGO_MMA needs a roadmap uploaded with LBL_UPLOAD_MMA");
     return LBL_EUNSUPPORTED;
   }
   if (algo == LBL_ALGO_SECTOR && rm->E > 0 && (reinterpret_cast<uintptr_t>(d_O) & 31u)) {
@@ -781,7 +879,9 @@ int label_impl(lbl_roadmap rm, const uint64_t *d_O, int32_t n_props, uint64_t *d
   MonitorTables t{};
   if (mon) t = tables_of(*mon, d_next, d_viol);
   cudaError_t e;
-  if (algo == LBL_ALGO_BITTILE) {
+  if (algo == LBL_ALGO_MMA) {
+    e = launch_label_mma(*rm, d_O, n_props, d_L, mon ? &t : nullptr, st);
+  } else if (algo == LBL_ALGO_BITTILE) {
     e = launch_label_bittile(*rm, d_O, n_props, d_L, mon ? &t : nullptr, early, ctas, st);
   } else if (algo == LBL_ALGO_SECTOR) {
     const int depth = (cfg && cfg->depth == 8) ? 8 : 4;
@@ -874,9 +974,11 @@ int lbl_roadmap_autotune(lbl_roadmap rm, const uint64_t *d_O, int32_t n_props, l
   if (rm->has_bt) cand.push_back(lbl_config{LBL_ALGO_BITTILE, 0, 0, 0, 0, 0});
   if (rm->has_sec && !(reinterpret_cast<uintptr_t>(d_O) & 31u))
     for (int depth : {4, 8}) cand.push_back(lbl_config{LBL_ALGO_SECTOR, 0, 0, 0, 0, depth});
-  if (rm->has_qd)
+  if (rm->has_qd) {
     for (int depth : {8, 12}) cand.push_back(lbl_config{LBL_ALGO_QUAD, 0, 0, 0, LBL_PIPE_REGISTERS, depth});
     cand.push_back(lbl_config{LBL_ALGO_QUAD, 0, 0, 0, LBL_PIPE_FRONT, 8});
+  }
+  if (rm->has_mma) cand.push_back(lbl_config{LBL_ALGO_MMA, 0, 0, 0, 0, 0});
   cudaEvent_t t0, t1;
   cudaError_t e = cudaEventCreate(&t0);
   if (e == cudaSuccess) e = cudaEventCreate(&t1);

@@ -44,6 +44,32 @@ struct MonitorTables {
   uint8_t rel[8];
 };
 
+// The fused safety-monitor epilogue (Sec. 3.2) of the labeling kernels: the
+// monitor's next-state and violation tables staged in shared memory, and per
+// edge the letter formed from the label's relevant bits.
+struct EpiSmem {
+  uint64_t T[256];
+  uint16_t V[256];
+};
+
+__device__ __forceinline__ void load_tables(const MonitorTables &mon, EpiSmem &sm) {
+  const int letters = 1 << mon.m;
+  for (int i = threadIdx.x; i < letters; i += blockDim.x) {
+    sm.T[i] = mon.T[i];
+    sm.V[i] = mon.V[i];
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ void epilogue(const MonitorTables &mon, const EpiSmem &sm, int64_t e, uint64_t w) {
+  uint32_t letter = 0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+    if (j < mon.m) letter |= static_cast<uint32_t>((w >> mon.rel[j]) & 1u) << j;
+  mon.next[e] = sm.T[letter];
+  mon.viol[e] = sm.V[letter];
+}
+
 // One roadmap's share of a batched labeling launch (device table entry).
 struct BatchItem {
   const int64_t *rowptr;
@@ -200,11 +226,24 @@ struct Roadmap {
   QuadOffsets qd_off{};
   int64_t pyr_words = 0;
   uint64_t *pyr = nullptr;      // per-frame pyramid (working memory)
+  // dense tensor-core form (optional): edges in locality order in tiles of 128,
+  // per tile the K-blocks of 128 cells its rows touch, as 128 x 128 bit
+  // matrices (16 bytes per row); per-frame B operand as working memory
+  bool has_mma = false;
+  int64_t mma_T = 0;             // tiles
+  int64_t n_mma = 0;             // (tile, K-block) pairs
+  int32_t mma_nkb = 0;           // K-blocks of the grid
+  int32_t *mma_perm = nullptr;   // sorted position -> the caller's edge
+  int64_t *mma_tptr = nullptr;   // tile t's K-blocks: [mma_tptr[t], mma_tptr[t+1])
+  int32_t *mma_tblk = nullptr;   // K-block ids, ascending per tile
+  uint32_t *mma_bits = nullptr;  // n_mma x 128 rows x 4 words
+  uint8_t *mma_b = nullptr;      // mma_nkb x 64 x 128 e4m3 bytes
   // edge partition of the streaming CSR kernel: warp w owns [part[w], part[w+1])
   int64_t *part = nullptr;
   int64_t part_cap = 0;  // entries allocated
   int part_ctas = 0;     // CTAs per SM the partition was made for
   int *err = nullptr;    // device flag: a bounded wait in a kernel ran out
+  int64_t wait_ns = 2000000000;  // limit of those waits (lbl_roadmap_set_wait_limit)
   // AUTO choice per proposition count, set by lbl_roadmap_autotune
   bool tuned_valid[65] = {false};
   lbl_config tuned[65] = {};
@@ -282,6 +321,13 @@ cudaError_t launch_label_rows(const StreamRows &r, const void *base, int word_by
 // quadtree form: pyramid of O, then the stream over the quadtree rows
 // pyramid word width for n_props propositions: 1, 2, 4 or 8 bytes
 int quad_word_bytes(const Roadmap &rm, int32_t P);
+int mma_n_of(int32_t P);
+cudaError_t launch_mma_count(const int64_t *rowptr, const int32_t *colidx, const int32_t *perm, int64_t E,
+                             int32_t nkb, int64_t *count, cudaStream_t s);
+cudaError_t launch_mma_fill(const int64_t *rowptr, const int32_t *colidx, const int32_t *perm, int64_t E,
+                            int32_t nkb, const int64_t *tptr, int32_t *tblk, uint32_t *bits, cudaStream_t s);
+cudaError_t launch_label_mma(const Roadmap &rm, const uint64_t *O, int32_t P, uint64_t *L, const MonitorTables *mon,
+                             cudaStream_t s);
 int front_chunk_for(int64_t E, int num_sms);
 // pyramid of O into `pyr` (rm.pyr, or a buffer of rm.pyr_words 64-bit words owned elsewhere)
 cudaError_t launch_quad_pyramid(const Roadmap &rm, const uint64_t *O, int word_bytes, void *pyr, cudaStream_t s);

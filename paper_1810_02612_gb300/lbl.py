@@ -31,6 +31,7 @@ LBL_ALGO_CSR = 1
 LBL_ALGO_BITTILE = 2
 LBL_ALGO_SECTOR = 3
 LBL_ALGO_QUAD = 4
+LBL_ALGO_MMA = 5
 
 LBL_PIPE_REGISTERS = 1
 LBL_PIPE_BULK = 2
@@ -47,15 +48,17 @@ LBL_UPLOAD_BITTILE = 2
 LBL_UPLOAD_SECTOR = 4
 LBL_UPLOAD_QUAD = 8
 LBL_UPLOAD_KEEP_ORDER = 16
+LBL_UPLOAD_MMA = 32
 
 # every entry point declared in include/lbl.h
 EXPORTS = (
     "lbl_last_error", "lbl_version",
     "lbl_roadmap_upload", "lbl_roadmap_rasterize", "lbl_roadmap_rows", "lbl_roadmap_free", "lbl_roadmap_info",
+    "lbl_roadmap_form_info", "lbl_roadmap_set_wait_limit",
     "lbl_roadmap_status",
     "lbl_frame_transform", "lbl_pack_planes", "lbl_frame_transform_words",
     "lbl_monitor_create", "lbl_monitor_free", "lbl_monitor_step",
-    "lbl_label", "lbl_label_blocks_noalloc", "lbl_roadmap_autotune",
+    "lbl_label", "lbl_label_blocks_noalloc", "lbl_roadmap_autotune", "lbl_mma_probe",
     "lbl_session_create", "lbl_session_run", "lbl_session_free",
     "lbl_batch_create", "lbl_batch_set_frames", "lbl_batch_launch", "lbl_batch_free", "lbl_batch_autotune",
     "lbl_server_create", "lbl_server_submit", "lbl_server_wait", "lbl_server_stats", "lbl_server_free",
@@ -126,6 +129,8 @@ def load(build_if_needed: bool = True):
         "lbl_roadmap_rows": (ctypes.c_int, [p, p, p, p]),
         "lbl_roadmap_free": (ctypes.c_int, [p]),
         "lbl_roadmap_info": (ctypes.c_int, [p, p, p, p, p, p, p]),
+        "lbl_roadmap_form_info": (ctypes.c_int, [p, i32, p, p]),
+        "lbl_roadmap_set_wait_limit": (ctypes.c_int, [p, i64]),
         "lbl_roadmap_status": (ctypes.c_int, [p, p]),
         "lbl_frame_transform": (ctypes.c_int, [G, p, i32, lbl_pose, G, p, p]),
         "lbl_pack_planes": (ctypes.c_int, [G, p, i32, p, p]),
@@ -136,6 +141,7 @@ def load(build_if_needed: bool = True):
         "lbl_label": (ctypes.c_int, [p, p, i32, p, p, p, p, ctypes.POINTER(lbl_config), p]),
         "lbl_label_blocks_noalloc": (ctypes.c_int, [p, p, p, i64, p, i64, i32, p, p]),
         "lbl_roadmap_autotune": (ctypes.c_int, [p, p, i32, p, p, p, p, i32, ctypes.POINTER(lbl_config), p]),
+        "lbl_mma_probe": (ctypes.c_int, [i32, i32, i32, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32)]),
         "lbl_session_create": (ctypes.c_int, [p, G, i32, p, ctypes.POINTER(lbl_config), ctypes.POINTER(p)]),
         "lbl_session_run": (ctypes.c_int, [p, p, lbl_pose, p, p, p, p]),
         "lbl_session_free": (ctypes.c_int, [p]),
@@ -291,6 +297,17 @@ def lbl_roadmap_info(rm):
     return tuple(x.value for x in v)
 
 
+def lbl_roadmap_form_info(rm, algo: int):
+    """(entries, tiles) of one labeling form of the roadmap."""
+    n, t = ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(load().lbl_roadmap_form_info(rm, int(algo), ctypes.byref(n), ctypes.byref(t)))
+    return n.value, t.value
+
+
+def lbl_roadmap_set_wait_limit(rm, limit_ns: int) -> None:
+    _check(load().lbl_roadmap_set_wait_limit(rm, int(limit_ns)))
+
+
 def lbl_roadmap_status(rm, stream=None) -> None:
     """Synchronise the stream; raise LblError(LBL_ETIMEOUT) if a labeling kernel
     on this roadmap gave up a bounded wait since the last check."""
@@ -376,6 +393,13 @@ def lbl_label_blocks_noalloc(d_block_rowptr, d_block_id, d_block_mask, n_edges: 
                                            _dev(d_block_mask, "uint64", "block_mask"), int(n_edges),
                                            _dev(d_O, "uint64", "O"), int(n_cells), int(n_props),
                                            _dev(d_L, "uint64", "L"), _stream(stream)))
+
+
+def lbl_mma_probe(kind: int = 0, n: int = 64, reps: int = 4000, ctas_per_sm: int = 4):
+    """Measured tcgen05 rate (TFLOP/s) and exactness of the accumulated counts."""
+    t, ex = ctypes.c_double(0.0), ctypes.c_int32(0)
+    _check(load().lbl_mma_probe(int(kind), int(n), int(reps), int(ctas_per_sm), ctypes.byref(t), ctypes.byref(ex)))
+    return {"tflops": t.value, "exact": bool(ex.value)}
 
 
 def lbl_roadmap_autotune(rm, d_O, n_props: int, d_L, mon=None, d_next=None, d_viol=None, reps: int = 5,

@@ -61,14 +61,15 @@ def test_frame_transform3_odd_world_and_static_world():
 
 def test_labels3_all_forms_match_oracle(p3):
     wl = p3
-    rm = L.lbl_roadmap_upload(wl.agent, wl.rowptr, wl.colidx, flags=L.LBL_UPLOAD_BITTILE | L.LBL_UPLOAD_SECTOR | L.LBL_UPLOAD_QUAD)
+    rm = L.lbl_roadmap_upload(wl.agent, wl.rowptr, wl.colidx,
+                              flags=L.LBL_UPLOAD_BITTILE | L.LBL_UPLOAD_SECTOR | L.LBL_UPLOAD_QUAD | L.LBL_UPLOAD_MMA)
     try:
         O = _O(wl.world, wl.planes, wl.pose, wl.agent)
         want = oracle.label(wl.rowptr, wl.colidx, O.cpu().numpy(), wl.P, threads=8)
         assert (want != 0).any()
         for cfg in (dict(algo=L.LBL_ALGO_CSR), dict(algo=L.LBL_ALGO_CSR, lanes_per_edge=16),
                     dict(algo=L.LBL_ALGO_BITTILE), dict(algo=L.LBL_ALGO_SECTOR), dict(algo=L.LBL_ALGO_QUAD),
-                    dict(algo=L.LBL_ALGO_CSR, pipeline=L.LBL_PIPE_BULK)):
+                    dict(algo=L.LBL_ALGO_CSR, pipeline=L.LBL_PIPE_BULK), dict(algo=L.LBL_ALGO_MMA)):
             out = torch.empty(wl.n_edges, dtype=torch.uint64, device="cuda")
             L.lbl_label(rm, O, wl.P, out, cfg=cfg)
             torch.cuda.synchronize()

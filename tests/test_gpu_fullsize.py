@@ -40,7 +40,8 @@ QUAD_CFGS = [dict(algo=L.LBL_ALGO_QUAD), dict(algo=L.LBL_ALGO_QUAD, pipeline=L.L
 
 def _check_workload(wl, cfgs):
     E, P = wl.n_edges, wl.P
-    flags = L.LBL_UPLOAD_QUAD | (L.LBL_UPLOAD_BITTILE if any(c["algo"] == L.LBL_ALGO_BITTILE for c in cfgs) else 0)
+    flags = (L.LBL_UPLOAD_QUAD | (L.LBL_UPLOAD_BITTILE if any(c["algo"] == L.LBL_ALGO_BITTILE for c in cfgs) else 0)
+             | (L.LBL_UPLOAD_MMA if any(c["algo"] == L.LBL_ALGO_MMA for c in cfgs) else 0))
     rm = L.lbl_roadmap_upload(wl.agent, wl.rowptr, wl.colidx, flags=flags)
     mh = None
     try:
@@ -78,7 +79,7 @@ def _check_workload(wl, cfgs):
 def test_large_1m_edges_64_props_with_monitor():
     wl = synth.make("large", seed=0, threads=0)
     assert wl.n_edges == 1_000_000 and wl.P == 64 and wl.monitor is not None
-    _check_workload(wl, QUAD_CFGS + [dict(algo=L.LBL_ALGO_CSR)])
+    _check_workload(wl, QUAD_CFGS + [dict(algo=L.LBL_ALGO_CSR), dict(algo=L.LBL_ALGO_MMA)])
 
 
 def test_driving_100k_edges_all_rows():
@@ -98,7 +99,8 @@ def test_driving_100k_edges_all_rows():
 def test_paper_2d_2pow21_cells():
     wl = synth.make("paper", seed=0, threads=0)
     assert wl.agent.cells == 1 << 21
-    _check_workload(wl, QUAD_CFGS + [dict(algo=L.LBL_ALGO_CSR), dict(algo=L.LBL_ALGO_BITTILE)])
+    _check_workload(wl, QUAD_CFGS + [dict(algo=L.LBL_ALGO_CSR), dict(algo=L.LBL_ALGO_BITTILE),
+                                     dict(algo=L.LBL_ALGO_MMA)])
 
 
 def test_paper_time_augmented_2pow21_cells():

@@ -36,7 +36,7 @@ def empty_u16(n):
 class Roadmap:
     def __init__(self, agent, rowptr, colidx, bittile=False):
         self.E = rowptr.shape[0] - 1
-        every_form = L.LBL_UPLOAD_BITTILE | L.LBL_UPLOAD_SECTOR | L.LBL_UPLOAD_QUAD
+        every_form = L.LBL_UPLOAD_BITTILE | L.LBL_UPLOAD_SECTOR | L.LBL_UPLOAD_QUAD | L.LBL_UPLOAD_MMA
         self.h = L.lbl_roadmap_upload(agent, rowptr, colidx, flags=every_form if bittile else 0)
 
     def __del__(self):
@@ -85,6 +85,7 @@ CFGS = [
     dict(algo=L.LBL_ALGO_QUAD, ctas_per_sm=1),
     dict(algo=L.LBL_ALGO_QUAD, pipeline=L.LBL_PIPE_FRONT),      # moving front, whatever the size
     dict(algo=L.LBL_ALGO_QUAD, pipeline=L.LBL_PIPE_REGISTERS),  # fixed per-warp ranges
+    dict(algo=L.LBL_ALGO_MMA),                                  # tensor cores
     dict(algo=L.LBL_ALGO_AUTO),
 ]
 
@@ -458,6 +459,17 @@ def test_quad_rejects_csr_pipelines(plain):
         assert ei.value.code == L.LBL_EINVAL
 
 
+def test_mma_needs_its_upload_flag_and_a_grid_of_at_most_2pow22_cells(plain):
+    rm = Roadmap(plain.agent, plain.rowptr, plain.colidx, bittile=False)
+    with pytest.raises(L.LblError) as ei:
+        gpu_label(rm, gpu_O(plain), plain.P, dict(algo=L.LBL_ALGO_MMA))
+    assert ei.value.code == L.LBL_EUNSUPPORTED
+    big = synth.Grid(4096, 2048, 0.1, 0.0, 0.0, synth.ROWMAJOR)  # 2^23 cells
+    with pytest.raises(L.LblError) as ei:
+        L.lbl_roadmap_upload(big, np.array([0, 1], np.int64), np.array([5], np.int32), flags=L.LBL_UPLOAD_MMA)
+    assert ei.value.code == L.LBL_EINVAL
+
+
 def test_quad_needs_its_upload_flag(plain):
     rm = Roadmap(plain.agent, plain.rowptr, plain.colidx, bittile=False)
     with pytest.raises(L.LblError) as ei:
@@ -593,11 +605,22 @@ def test_autotune_choice_is_exact_and_sticks(driving_small):
     want = oracle.label(wl.rowptr, wl.colidx, host(O), wl.P, threads=8)
     out = empty_u64(rm.E)
     chosen = L.lbl_roadmap_autotune(rm.h, O, wl.P, out, reps=2)
-    assert chosen["algo"] in (L.LBL_ALGO_CSR, L.LBL_ALGO_BITTILE, L.LBL_ALGO_SECTOR, L.LBL_ALGO_QUAD)
+    assert chosen["algo"] in (L.LBL_ALGO_CSR, L.LBL_ALGO_BITTILE, L.LBL_ALGO_SECTOR, L.LBL_ALGO_QUAD, L.LBL_ALGO_MMA)
     assert np.array_equal(host(out), want)
     assert np.array_equal(gpu_label(rm, O, wl.P, dict(algo=L.LBL_ALGO_AUTO)), want)
     assert np.array_equal(gpu_label(rm, O, wl.P, None), want)
     L.lbl_roadmap_status(rm.h)
+
+
+def test_autotune_on_a_roadmap_without_derived_forms(driving_small):
+    """A CSR-only roadmap: the tuner tries only the forms the roadmap has."""
+    wl = driving_small
+    rm = Roadmap(wl.agent, wl.rowptr, wl.colidx, bittile=False)
+    O = gpu_O(wl)
+    out = empty_u64(rm.E)
+    chosen = L.lbl_roadmap_autotune(rm.h, O, wl.P, out, reps=1)
+    assert chosen["algo"] == L.LBL_ALGO_CSR
+    assert np.array_equal(host(out), oracle.label(wl.rowptr, wl.colidx, host(O), wl.P, threads=8))
 
 
 @pytest.mark.parametrize("order", [synth.MORTON, synth.ROWMAJOR])

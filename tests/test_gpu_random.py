@@ -16,12 +16,13 @@ pytestmark = pytest.mark.gpu
 
 import paper_1810_02612_gb300 as L  # noqa: E402
 
-FLAGS = L.LBL_UPLOAD_BITTILE | L.LBL_UPLOAD_SECTOR | L.LBL_UPLOAD_QUAD
+FLAGS = L.LBL_UPLOAD_BITTILE | L.LBL_UPLOAD_SECTOR | L.LBL_UPLOAD_QUAD | L.LBL_UPLOAD_MMA
 FORMS = [dict(algo=L.LBL_ALGO_CSR), dict(algo=L.LBL_ALGO_CSR, lanes_per_edge=8, early_exit=1),
          dict(algo=L.LBL_ALGO_CSR, pipeline=L.LBL_PIPE_BULK), dict(algo=L.LBL_ALGO_CSR, pipeline=L.LBL_PIPE_ASYNC),
          dict(algo=L.LBL_ALGO_BITTILE), dict(algo=L.LBL_ALGO_SECTOR), dict(algo=L.LBL_ALGO_QUAD),
          dict(algo=L.LBL_ALGO_QUAD, depth=8), dict(algo=L.LBL_ALGO_QUAD, depth=16),
-         dict(algo=L.LBL_ALGO_QUAD, pipeline=L.LBL_PIPE_FRONT), dict(algo=L.LBL_ALGO_AUTO)]
+         dict(algo=L.LBL_ALGO_QUAD, pipeline=L.LBL_PIPE_FRONT), dict(algo=L.LBL_ALGO_MMA),
+         dict(algo=L.LBL_ALGO_AUTO)]
 PROPS = [0, 1, 2, 5, 8, 9, 16, 17, 31, 32, 33, 63, 64]
 
 
