@@ -211,7 +211,17 @@ int lbl_roadmap_rasterize(const lbl_grid *agent, const double *h_arcs, int64_t n
    caller device buffers d_rowptr int64[E+1], d_colidx int32[nnz], on `s`. */
 int lbl_roadmap_rows(lbl_roadmap rm, int64_t *d_rowptr, int32_t *d_colidx, lbl_stream s);
 
-/* Release a roadmap (synchronises the device first). NULL is accepted. */
+/*
+ * Release a roadmap.  NULL is accepted.  Its device memory is freed in stream
+ * order after the work the library enqueued with it (lbl_label and the calls
+ * built on it, lbl_roadmap_rows, sessions, batch launches) has run; the call
+ * itself waits for nothing on the device and stalls no other stream.  Work a
+ * caller captured into a CUDA graph is not tracked: free a roadmap only after
+ * the replays that use it have completed, and free the sessions, batches and
+ * servers that hold it first.  The same holds for lbl_monitor_free,
+ * lbl_session_free and lbl_batch_free; lbl_server_free waits for the server's
+ * own lanes only.
+ */
 int lbl_roadmap_free(lbl_roadmap rm);
 
 /*
@@ -401,7 +411,8 @@ int lbl_label_blocks_noalloc(const int64_t *d_block_rowptr, const uint32_t *d_bl
  * (CUDA events around one launch); *exact = 1 iff every accumulated count of
  * one CTA equals reps x (A.B^T) computed on the host.  The paper has no
  * counterpart: it bounds what the dense form of eq. 8-10 can reach.
- * Synchronises the device; allocates and frees its own small buffers.
+ * Runs on the legacy default stream and synchronises it; allocates and frees
+ * its own small buffers.
  */
 int lbl_mma_probe(int32_t kind, int32_t n, int32_t reps, int32_t ctas_per_sm, double *tflops, int32_t *exact);
 

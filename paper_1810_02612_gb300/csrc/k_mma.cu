@@ -520,7 +520,7 @@ extern "C" int lbl_mma_probe(int32_t kind, int32_t n, int32_t reps, int32_t ctas
   };
   const unsigned grid = static_cast<unsigned>(sms * ctas_per_sm);
   float ms = 0.0f;
-  if ((e = launch(1, 3)) != cudaSuccess || (e = cudaDeviceSynchronize()) != cudaSuccess ||
+  if ((e = launch(1, 3)) != cudaSuccess || (e = cudaStreamSynchronize(nullptr)) != cudaSuccess ||
       (e = cudaEventRecord(t0)) != cudaSuccess || (e = launch(grid, reps)) != cudaSuccess ||
       (e = cudaEventRecord(t1)) != cudaSuccess || (e = cudaEventSynchronize(t1)) != cudaSuccess ||
       (e = cudaEventElapsedTime(&ms, t0, t1)) != cudaSuccess) {

@@ -85,29 +85,74 @@ bool same_device(int dev) {
   return true;
 }
 
+// One stream per device on which objects' memory is released (created on first
+// use, kept for the life of the process).
+cudaStream_t release_stream(int device) {
+  static std::mutex mu;
+  static cudaStream_t streams[64] = {};
+  std::lock_guard<std::mutex> lock(mu);
+  if (device < 0 || device >= 64) return nullptr;
+  if (!streams[device] && cudaStreamCreateWithFlags(&streams[device], cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    streams[device] = nullptr;
+  }
+  return streams[device];
+}
+
+void UseLog::note(cudaStream_t s) {
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    return;  // e.g. the legacy stream while another stream captures
+  }
+  if (cap != cudaStreamCaptureStatusNone) return;
+  std::lock_guard<std::mutex> lock(mu);
+  cudaEvent_t e = nullptr;
+  for (auto &u : ev)
+    if (u.first == s) e = u.second;
+  if (!e) {
+    if (ev.size() >= 16) {  // many streams: wait for the oldest uses here rather than keep every event
+      for (auto &u : ev) {
+        cudaEventSynchronize(u.second);
+        cudaEventDestroy(u.second);
+      }
+      ev.clear();
+    }
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      cudaStreamSynchronize(s);  // no event: make the use complete now instead
+      return;
+    }
+    ev.emplace_back(s, e);
+  }
+  cudaEventRecord(e, s);
+}
+
+void UseLog::release(int device, const std::vector<void *> &ptrs) {
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (cur != device) cudaSetDevice(device);
+  cudaStream_t rs = release_stream(device);
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    for (auto &u : ev) {
+      if (!rs || cudaStreamWaitEvent(rs, u.second, 0) != cudaSuccess) cudaEventSynchronize(u.second);
+      cudaEventDestroy(u.second);
+    }
+    ev.clear();
+  }
+  for (void *p : ptrs)
+    if (p) cudaFreeAsync(p, rs);  // rs NULL: the legacy stream, after the host waits above
+  cudaGetLastError();
+  if (cur >= 0 && cur != device) cudaSetDevice(cur);
+}
+
 void free_roadmap(Roadmap *rm) {
   if (!rm) return;
-  cudaFree(rm->rowptr);
-  cudaFree(rm->colidx);
-  cudaFree(rm->bt_rowptr);
-  cudaFree(rm->bt_block);
-  cudaFree(rm->bt_mask);
-  cudaFree(rm->planes);
-  cudaFree(rm->part);
-  cudaFree(rm->err);
-  cudaFree(rm->sec_rowptr);
-  cudaFree(rm->sec);
-  cudaFree(rm->sec_part);
-  cudaFree(rm->qd_rowptr);
-  cudaFree(rm->qd_perm);
-  cudaFree(rm->qd_idx);
-  cudaFree(rm->qd_part);
-  cudaFree(rm->pyr);
-  cudaFree(rm->mma_perm);
-  cudaFree(rm->mma_tptr);
-  cudaFree(rm->mma_tblk);
-  cudaFree(rm->mma_bits);
-  cudaFree(rm->mma_b);
+  rm->uses->release(rm->device, {rm->rowptr, rm->colidx, rm->bt_rowptr, rm->bt_block, rm->bt_mask, rm->planes,
+                                 rm->part, rm->err, rm->sec_rowptr, rm->sec, rm->sec_part, rm->qd_rowptr,
+                                 rm->qd_perm, rm->qd_idx, rm->qd_part, rm->pyr, rm->mma_perm, rm->mma_tptr,
+                                 rm->mma_tblk, rm->mma_bits, rm->mma_b});
   delete rm;
 }
 
@@ -236,8 +281,8 @@ int roadmap_new(const lbl_grid &agent, int64_t n_edges, int64_t nnz, lbl_roadmap
   rm->nnz = nnz;
   rm->cells = grid_cells(agent);
   const int64_t padded = ((nnz + 3) / 4) * 4 + 4;
-  if ((e = dev_alloc(&rm->rowptr, static_cast<size_t>(n_edges + 1), &rm->bytes)) != cudaSuccess ||
-      (e = dev_alloc(&rm->colidx, static_cast<size_t>(padded), &rm->bytes)) != cudaSuccess ||
+  if ((e = obj_alloc(&rm->rowptr, static_cast<size_t>(n_edges + 1), &rm->bytes)) != cudaSuccess ||
+      (e = obj_alloc(&rm->colidx, static_cast<size_t>(padded), &rm->bytes)) != cudaSuccess ||
       (e = cudaMemset(rm->colidx + nnz, 0, sizeof(int32_t) * (padded - nnz))) != cudaSuccess) {
     free_roadmap(rm);
     return cuda_fail(e, "roadmap: CSR arrays");
@@ -274,7 +319,7 @@ int roadmap_finish(lbl_roadmap_s *rm, uint32_t flags, cudaStream_t st) {
     return fail(LBL_EINVAL);
   }
   const bool want_bt = flags & LBL_UPLOAD_BITTILE;
-  if ((e = dev_alloc(&rm->err, 1, &rm->bytes)) != cudaSuccess ||
+  if ((e = obj_alloc(&rm->err, 1, &rm->bytes)) != cudaSuccess ||
       (e = cudaMemsetAsync(rm->err, 0, sizeof(int), st)) != cudaSuccess)
     return fail(cuda_fail(e, "roadmap: error flag"));
   if ((e = dev_alloc(&d_bad, 1, nullptr)) != cudaSuccess) return fail(cuda_fail(e, "roadmap: scratch"));
@@ -296,7 +341,7 @@ int roadmap_finish(lbl_roadmap_s *rm, uint32_t flags, cudaStream_t st) {
   if (n_edges > 0) {
     // edge partition of the streaming CSR kernel, for its default grid
     rm->part_cap = static_cast<int64_t>(rm->num_sms) * kMaxCtasPerSm * (kThreads / 32) + 1;
-    if ((e = dev_alloc(&rm->part, static_cast<size_t>(rm->part_cap), &rm->bytes)) != cudaSuccess)
+    if ((e = obj_alloc(&rm->part, static_cast<size_t>(rm->part_cap), &rm->bytes)) != cudaSuccess)
       return fail(cuda_fail(e, "roadmap: partition"));
     rm->part_ctas = stream_ctas_per_sm(8);
     if ((e = launch_partition(*rm, rm->part_ctas, st)) != cudaSuccess)
@@ -314,10 +359,10 @@ int roadmap_finish(lbl_roadmap_s *rm, uint32_t flags, cudaStream_t st) {
     for (int64_t i = 0; i < n_edges; ++i) brow[i + 1] = brow[i] + cnt[i];
     rm->n_bt = brow[n_edges];
     rm->n_blocks = (rm->cells + 63) / 64;
-    if ((e = dev_alloc(&rm->bt_rowptr, static_cast<size_t>(n_edges + 1), &rm->bytes)) != cudaSuccess ||
-        (e = dev_alloc(&rm->bt_block, static_cast<size_t>(rm->n_bt), &rm->bytes)) != cudaSuccess ||
-        (e = dev_alloc(&rm->bt_mask, static_cast<size_t>(rm->n_bt), &rm->bytes)) != cudaSuccess ||
-        (e = dev_alloc(&rm->planes, static_cast<size_t>(rm->n_blocks * 64), &rm->bytes)) != cudaSuccess)
+    if ((e = obj_alloc(&rm->bt_rowptr, static_cast<size_t>(n_edges + 1), &rm->bytes)) != cudaSuccess ||
+        (e = obj_alloc(&rm->bt_block, static_cast<size_t>(rm->n_bt), &rm->bytes)) != cudaSuccess ||
+        (e = obj_alloc(&rm->bt_mask, static_cast<size_t>(rm->n_bt), &rm->bytes)) != cudaSuccess ||
+        (e = obj_alloc(&rm->planes, static_cast<size_t>(rm->n_blocks * 64), &rm->bytes)) != cudaSuccess)
       return fail(cuda_fail(e, "roadmap: block form"));
     if ((e = cudaMemcpyAsync(rm->bt_rowptr, brow.data(), sizeof(int64_t) * (n_edges + 1), cudaMemcpyHostToDevice,
                              st)) != cudaSuccess ||
@@ -347,9 +392,9 @@ int roadmap_finish(lbl_roadmap_s *rm, uint32_t flags, cudaStream_t st) {
     srow[0] = 0;
     for (int64_t i = 0; i < n_edges; ++i) srow[i + 1] = srow[i] + cnt[i];
     rm->n_sec = srow[n_edges];
-    if ((e = dev_alloc(&rm->sec_rowptr, static_cast<size_t>(n_edges + 1), &rm->bytes)) != cudaSuccess ||
-        (e = dev_alloc(&rm->sec, static_cast<size_t>(rm->n_sec), &rm->bytes)) != cudaSuccess ||
-        (e = dev_alloc(&rm->sec_part, static_cast<size_t>(rm->part_cap), &rm->bytes)) != cudaSuccess ||
+    if ((e = obj_alloc(&rm->sec_rowptr, static_cast<size_t>(n_edges + 1), &rm->bytes)) != cudaSuccess ||
+        (e = obj_alloc(&rm->sec, static_cast<size_t>(rm->n_sec), &rm->bytes)) != cudaSuccess ||
+        (e = obj_alloc(&rm->sec_part, static_cast<size_t>(rm->part_cap), &rm->bytes)) != cudaSuccess ||
         (e = cudaMemcpyAsync(rm->sec_rowptr, srow.data(), sizeof(int64_t) * (n_edges + 1), cudaMemcpyHostToDevice,
                              st)) != cudaSuccess ||
         (e = launch_sector_fill(rm->rowptr, rm->colidx, n_edges, rm->sec_rowptr, rm->sec, st)) != cudaSuccess)
@@ -391,7 +436,7 @@ int roadmap_finish(lbl_roadmap_s *rm, uint32_t flags, cudaStream_t st) {
       std::vector<int32_t> perm(static_cast<size_t>(n_edges));
       for (int c = 0; c < kSessionChunks; ++c)
         sort_range_by_key(key.data(), n_edges * c / kSessionChunks, n_edges * (c + 1) / kSessionChunks, perm.data());
-      if ((e = dev_alloc(&rm->qd_perm, static_cast<size_t>(n_edges), &rm->bytes)) != cudaSuccess ||
+      if ((e = obj_alloc(&rm->qd_perm, static_cast<size_t>(n_edges), &rm->bytes)) != cudaSuccess ||
           (e = cudaMemcpyAsync(rm->qd_perm, perm.data(), sizeof(int32_t) * n_edges, cudaMemcpyHostToDevice, st)) !=
               cudaSuccess ||
           (e = cudaStreamSynchronize(st)) != cudaSuccess)
@@ -412,10 +457,10 @@ int roadmap_finish(lbl_roadmap_s *rm, uint32_t flags, cudaStream_t st) {
     drow[0] = 0;
     for (int64_t i = 0; i < n_edges; ++i) drow[i + 1] = drow[i] + cnt[i];
     rm->n_qd = drow[n_edges];
-    if ((e = dev_alloc(&rm->qd_rowptr, static_cast<size_t>(n_edges + 1), &rm->bytes)) != cudaSuccess ||
-        (e = dev_alloc(&rm->qd_idx, static_cast<size_t>(rm->n_qd + 4), &rm->bytes)) != cudaSuccess ||
-        (e = dev_alloc(&rm->qd_part, static_cast<size_t>(rm->part_cap), &rm->bytes)) != cudaSuccess ||
-        (e = dev_alloc(&rm->pyr, static_cast<size_t>(words), &rm->bytes)) != cudaSuccess ||
+    if ((e = obj_alloc(&rm->qd_rowptr, static_cast<size_t>(n_edges + 1), &rm->bytes)) != cudaSuccess ||
+        (e = obj_alloc(&rm->qd_idx, static_cast<size_t>(rm->n_qd + 4), &rm->bytes)) != cudaSuccess ||
+        (e = obj_alloc(&rm->qd_part, static_cast<size_t>(rm->part_cap), &rm->bytes)) != cudaSuccess ||
+        (e = obj_alloc(&rm->pyr, static_cast<size_t>(words), &rm->bytes)) != cudaSuccess ||
         (e = cudaMemcpyAsync(rm->qd_rowptr, drow.data(), sizeof(int64_t) * (n_edges + 1), cudaMemcpyHostToDevice,
                              st)) != cudaSuccess ||
         (e = launch_quad_fill(rm->rowptr, rm->colidx, n_edges, rm->qd_perm, rm->qd_off, rm->qd_rowptr, rm->qd_idx,
@@ -452,7 +497,7 @@ int roadmap_finish(lbl_roadmap_s *rm, uint32_t flags, cudaStream_t st) {
     sort_range_by_key(key.data(), 0, n_edges, perm.data());
     std::vector<int64_t> cnt(static_cast<size_t>(rm->mma_T)), tptr(static_cast<size_t>(rm->mma_T + 1));
     int64_t *d_cnt64 = nullptr;
-    if ((e = dev_alloc(&rm->mma_perm, static_cast<size_t>(n_edges), &rm->bytes)) != cudaSuccess ||
+    if ((e = obj_alloc(&rm->mma_perm, static_cast<size_t>(n_edges), &rm->bytes)) != cudaSuccess ||
         (e = cudaMemcpyAsync(rm->mma_perm, perm.data(), sizeof(int32_t) * n_edges, cudaMemcpyHostToDevice, st)) !=
             cudaSuccess ||
         (e = dev_alloc(&d_cnt64, static_cast<size_t>(rm->mma_T), nullptr)) != cudaSuccess ||
@@ -468,10 +513,10 @@ int roadmap_finish(lbl_roadmap_s *rm, uint32_t flags, cudaStream_t st) {
     tptr[0] = 0;
     for (int64_t t = 0; t < rm->mma_T; ++t) tptr[t + 1] = tptr[t] + cnt[t];
     rm->n_mma = tptr[rm->mma_T];
-    if ((e = dev_alloc(&rm->mma_tptr, static_cast<size_t>(rm->mma_T + 1), &rm->bytes)) != cudaSuccess ||
-        (e = dev_alloc(&rm->mma_tblk, static_cast<size_t>(rm->n_mma), &rm->bytes)) != cudaSuccess ||
-        (e = dev_alloc(&rm->mma_bits, static_cast<size_t>(rm->n_mma) * 128 * 4, &rm->bytes)) != cudaSuccess ||
-        (e = dev_alloc(&rm->mma_b, static_cast<size_t>(rm->mma_nkb) * 64 * 128, &rm->bytes)) != cudaSuccess ||
+    if ((e = obj_alloc(&rm->mma_tptr, static_cast<size_t>(rm->mma_T + 1), &rm->bytes)) != cudaSuccess ||
+        (e = obj_alloc(&rm->mma_tblk, static_cast<size_t>(rm->n_mma), &rm->bytes)) != cudaSuccess ||
+        (e = obj_alloc(&rm->mma_bits, static_cast<size_t>(rm->n_mma) * 128 * 4, &rm->bytes)) != cudaSuccess ||
+        (e = obj_alloc(&rm->mma_b, static_cast<size_t>(rm->mma_nkb) * 64 * 128, &rm->bytes)) != cudaSuccess ||
         (e = cudaMemcpyAsync(rm->mma_tptr, tptr.data(), sizeof(int64_t) * (rm->mma_T + 1), cudaMemcpyHostToDevice,
                              st)) != cudaSuccess ||
         (e = cudaMemsetAsync(rm->mma_bits, 0, sizeof(uint32_t) * 128 * 4 * static_cast<size_t>(rm->n_mma), st)) !=
@@ -537,8 +582,7 @@ int lbl_roadmap_upload(const lbl_grid *agent, const int64_t *rowptr, const int32
 int lbl_roadmap_free(lbl_roadmap rm) {
   g_err.clear();
   if (!rm) return LBL_OK;
-  cudaDeviceSynchronize();
-  free_roadmap(rm);
+  free_roadmap(rm);  // released in stream order after the roadmap's last logged use
   return LBL_OK;
 }
 
@@ -605,6 +649,7 @@ int lbl_roadmap_rows(lbl_roadmap rm, int64_t *d_rowptr, int32_t *d_colidx, lbl_s
   if (e == cudaSuccess && rm->nnz > 0)
     e = cudaMemcpyAsync(d_colidx, rm->colidx, sizeof(int32_t) * rm->nnz, cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) return cuda_fail(e, "roadmap rows");
+  rm->uses->note(st);
   return LBL_OK;
 }
 
@@ -755,13 +800,12 @@ int lbl_monitor_create(int32_t n_states, int32_t m, const uint8_t *relbits, cons
     mon->hV[letter] = v;
   }
   cudaError_t e = cudaGetDevice(&mon->device);
-  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&mon->T), sizeof(mon->hT));
-  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&mon->V), sizeof(mon->hV));
+  if (e == cudaSuccess) e = obj_alloc(&mon->T, 256, nullptr);
+  if (e == cudaSuccess) e = obj_alloc(&mon->V, 256, nullptr);
   if (e == cudaSuccess) e = cudaMemcpy(mon->T, mon->hT, sizeof(mon->hT), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(mon->V, mon->hV, sizeof(mon->hV), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
-    cudaFree(mon->T);
-    cudaFree(mon->V);
+    mon->uses->release(mon->device, {mon->T, mon->V});
     delete mon;
     return cuda_fail(e, "monitor create");
   }
@@ -772,9 +816,7 @@ int lbl_monitor_create(int32_t n_states, int32_t m, const uint8_t *relbits, cons
 int lbl_monitor_free(lbl_monitor mon) {
   g_err.clear();
   if (!mon) return LBL_OK;
-  cudaDeviceSynchronize();
-  cudaFree(mon->T);
-  cudaFree(mon->V);
+  mon->uses->release(mon->device, {mon->T, mon->V});  // after the monitor's last logged use
   delete mon;
   return LBL_OK;
 }
@@ -809,6 +851,7 @@ int lbl_monitor_step(lbl_monitor mon, const uint64_t *d_L, int64_t n, uint64_t *
   MonitorTables t = tables_of(*mon, d_next, d_viol);
   cudaError_t e = launch_monitor_step(t, d_L, n, device_sms(mon->device), reinterpret_cast<cudaStream_t>(s));
   if (e != cudaSuccess) return cuda_fail(e, "monitor step: launch");
+  mon->uses->note(reinterpret_cast<cudaStream_t>(s));
   return LBL_OK;
 }
 
@@ -946,6 +989,8 @@ int label_impl(lbl_roadmap rm, const uint64_t *d_O, int32_t n_props, uint64_t *d
                                  : launch_label_stream(*rm, d_O, n_props, d_L, mt, depth, st);
   }
   if (e != cudaSuccess) return cuda_fail(e, "label: launch");
+  rm->uses->note(st);
+  if (mon) mon->uses->note(st);
   return LBL_OK;
 }
 

@@ -9,6 +9,7 @@
 using namespace lbl;
 
 struct lbl_batch_s {
+  std::shared_ptr<UseLog> uses = std::make_shared<UseLog>();
   int device = 0;
   int num_sms = 1;
   int32_t n = 0;
@@ -74,7 +75,7 @@ cudaError_t plan_class(const lbl_batch_s *b, int c, int ctas, int upw, BatchTabl
     off[i + 1] = off[i] + (b->cls[i] == c ? W[i] + 1 : 0);
   }
   int64_t *part = nullptr;
-  cudaError_t e = dev_alloc(&part, static_cast<size_t>(std::max<int64_t>(off[b->n], 1)), nullptr);
+  cudaError_t e = obj_alloc(&part, static_cast<size_t>(std::max<int64_t>(off[b->n], 1)), nullptr);
   if (e != cudaSuccess) return e;
   tab->total = 0;
   for (int i = 0; i < b->n && e == cudaSuccess; ++i) {
@@ -90,7 +91,7 @@ cudaError_t plan_class(const lbl_batch_s *b, int c, int ctas, int upw, BatchTabl
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);  // the partitions, made on the legacy stream
   if (e != cudaSuccess) {
-    cudaFree(part);
+    obj_free_now(part);
     return e;
   }
   *part_out = part;
@@ -173,9 +174,9 @@ int lbl_batch_create(int32_t n, const lbl_roadmap *rms, const int32_t *n_props, 
     }
     off[i + 1] = off[i] + W[i] + 1;
   }
-  cudaError_t e = dev_alloc(&b->part, static_cast<size_t>(off[n]), nullptr);
-  if (e == cudaSuccess) e = dev_alloc(&b->counter, kWordClasses, nullptr);
-  if (e == cudaSuccess && pyr_words > 0) e = dev_alloc(&b->pyr, static_cast<size_t>(pyr_words), nullptr);
+  cudaError_t e = obj_alloc(&b->part, static_cast<size_t>(off[n]), nullptr);
+  if (e == cudaSuccess) e = obj_alloc(&b->counter, kWordClasses, nullptr);
+  if (e == cudaSuccess && pyr_words > 0) e = obj_alloc(&b->pyr, static_cast<size_t>(pyr_words), nullptr);
   b->pyr_slot.assign(n, -1);
   b->cls.assign(n, kWordClasses - 1);
   b->slot.assign(n, 0);
@@ -223,9 +224,7 @@ int lbl_batch_create(int32_t n, const lbl_roadmap *rms, const int32_t *n_props, 
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
   if (e != cudaSuccess) {
-    cudaFree(b->part);
-    cudaFree(b->counter);
-    cudaFree(b->pyr);
+    b->uses->release(b->device, {b->part, b->counter, b->pyr});
     delete b;
     return cuda_fail(e, "batch create: partitions");
   }
@@ -278,7 +277,7 @@ int lbl_batch_set_frames(lbl_batch b, const lbl_frame *frames) {
   }
   if (need > b->words_cap) {
     uint64_t *w = nullptr;
-    cudaError_t e = dev_alloc(&w, static_cast<size_t>(need), nullptr);
+    cudaError_t e = obj_alloc(&w, static_cast<size_t>(need), nullptr);
     if (e != cudaSuccess) return cuda_fail(e, "batch frames: packed words");
     if (b->words) b->retired.push_back(b->words);
     b->words = w;
@@ -323,19 +322,24 @@ int lbl_batch_launch(lbl_batch b, uint32_t stages, lbl_stream s) {
       if (b->tabs[c].n > 0) e = launch_label_batch(b->tabs[c], b->counter + c, b->num_sms, b->ctas_c[c], st);
   }
   if (e != cudaSuccess) return cuda_fail(e, "batch launch");
+  // the batch's memory, and its roadmaps' rows and monitors' tables, are in use
+  // until this launch ends (not logged while the stream is being captured)
+  b->uses->note(st);
+  for (int i = 0; i < b->n; ++i) {
+    if (i == 0 || b->rms[i] != b->rms[i - 1]) b->rms[i]->uses->note(st);
+    if (b->mons[i]) b->mons[i]->uses->note(st);
+  }
   return LBL_OK;
 }
 
 int lbl_batch_free(lbl_batch b) {
   clear_error();
   if (!b) return LBL_OK;
-  cudaDeviceSynchronize();
-  cudaFree(b->part);
-  cudaFree(b->counter);
-  cudaFree(b->pyr);
-  cudaFree(b->words);
-  for (uint64_t *w : b->retired) cudaFree(w);
-  for (int64_t *q : b->tuned_parts) cudaFree(q);
+  // released after the batch's last logged launch, without waiting for the device
+  std::vector<void *> mem = {b->part, b->counter, b->pyr, b->words};
+  for (uint64_t *w : b->retired) mem.push_back(w);
+  for (int64_t *q : b->tuned_parts) mem.push_back(q);
+  b->uses->release(b->device, mem);
   delete b;
   return LBL_OK;
 }
@@ -399,7 +403,7 @@ int lbl_batch_autotune(lbl_batch b, int32_t reps, lbl_stream s, lbl_batch_tuning
             best_tab = tab;
             std::swap(best_part, part);
           }
-          if (part) cudaFree(part);
+          obj_free_now(part);  // its timed launches have completed
           if (e != cudaSuccess) break;
         }
       }
@@ -411,7 +415,7 @@ int lbl_batch_autotune(lbl_batch b, int32_t reps, lbl_stream s, lbl_batch_tuning
       b->tuned_parts.push_back(best_part);
       best_part = nullptr;
     }
-    if (best_part) cudaFree(best_part);
+    obj_free_now(best_part);
     res.depth = best_depth;
     res.ctas_per_sm = best_ctas;
     res.units_per_warp = best_upw;

@@ -22,7 +22,11 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <memory>
+#include <mutex>
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "../../include/lbl.h"
 
@@ -188,7 +192,23 @@ struct StreamRows {
   int front_chunk = -1;  // moving front over chunks of this many edges; 0 = per-warp stream, -1 = by range size
 };
 
+// Memory owned by the library's objects (roadmaps, monitors, sessions,
+// batches, servers) comes from the stream-ordered allocator.  Each object logs
+// the last piece of work it enqueued on every stream it used (an event per
+// stream); its *_free makes a library stream wait for those events and frees
+// the memory there with cudaFreeAsync, so releasing one object neither waits
+// for nor stalls work of others on the device.  Work a CUDA graph replays is
+// not logged: the caller frees an object only after the replays that use it.
+struct UseLog {
+  std::mutex mu;
+  std::vector<std::pair<cudaStream_t, cudaEvent_t>> ev;
+  void note(cudaStream_t s);  // record the object's latest work on s (skipped while s is capturing)
+  // free `ptrs` in stream order after every logged use (the device must be the object's)
+  void release(int device, const std::vector<void *> &ptrs);
+};
+
 struct Roadmap {
+  std::shared_ptr<UseLog> uses = std::make_shared<UseLog>();
   int device = 0;
   int num_sms = 0;
   lbl_grid agent{};
@@ -251,6 +271,7 @@ struct Roadmap {
 };
 
 struct Monitor {
+  std::shared_ptr<UseLog> uses = std::make_shared<UseLog>();
   int device = 0;
   int32_t n_states = 0, m = 0, reject = -1;
   uint8_t rel[8] = {0};
@@ -391,6 +412,23 @@ int label_impl(lbl_roadmap rm, const uint64_t *d_O, int32_t n_props, uint64_t *d
                uint64_t *d_next, uint16_t *d_viol, const lbl_config *cfg, cudaStream_t st);
 
 // cudaMalloc of `count` elements (at least 16 bytes), adding the bytes to *bytes if given
+// Object-owned memory (see UseLog): stream-ordered allocation on the legacy
+// stream, which is then synchronised so any stream may use it at once.
+template <typename T>
+cudaError_t obj_alloc(T **p, size_t count, int64_t *bytes) {
+  const size_t b = count * sizeof(T);
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(p), b ? b : 16, nullptr);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
+  if (e == cudaSuccess && bytes) *bytes += static_cast<int64_t>(b);
+  return e;
+}
+
+// Free object memory whose uses the host has already waited for.
+inline void obj_free_now(void *p) {
+  if (p) cudaFreeAsync(p, nullptr);
+}
+
+// Temporary device memory of one call, freed with cudaFree before it returns.
 template <typename T>
 cudaError_t dev_alloc(T **p, size_t count, int64_t *bytes) {
   const size_t b = count * sizeof(T);

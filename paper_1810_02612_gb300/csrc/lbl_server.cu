@@ -371,13 +371,14 @@ int lbl_server_create(int32_t n, const lbl_roadmap *rms, const int32_t *n_props,
   // fixed work-unit size: 32k nonzero-equivalents (a unit takes a warp ~10 us)
   constexpr double kUnitCost = 32768.0;
   auto cleanup = [&](int code) {
-    for (Resident &R : S->res) cudaFree(R.part);
+    cudaStreamSynchronize(nullptr);  // the partitions were made there
+    for (Resident &R : S->res) lbl::obj_free_now(R.part);
     for (Lane &l : S->lanes) {
       if (l.s) cudaStreamDestroy(l.s);
       if (l.done) cudaEventDestroy(l.done);
-      cudaFree(l.counter);
+      lbl::obj_free_now(l.counter);
     }
-    cudaFree(S->arena_base);
+    lbl::obj_free_now(S->arena_base);
     delete S;
     return code;
   };
@@ -391,7 +392,7 @@ int lbl_server_create(int32_t n, const lbl_roadmap *rms, const int32_t *n_props,
     const double cost = static_cast<double>((R.quad ? rm.n_qd : rm.nnz) + lbl::kEdgeCost * rm.E);
     R.units = rm.E > 0 ? std::min<int64_t>(rm.E, std::max<int64_t>(1, static_cast<int64_t>(std::ceil(cost / kUnitCost))))
                        : 0;
-    e = cudaMalloc(reinterpret_cast<void **>(&R.part), sizeof(int64_t) * (R.units + 1));
+    e = lbl::obj_alloc(&R.part, static_cast<size_t>(R.units + 1), nullptr);
     if (e == cudaSuccess)
       e = lbl::launch_partition_into(R.quad ? rm.qd_rowptr : rm.rowptr, rm.E, R.units, R.part, nullptr);
   }
@@ -400,14 +401,14 @@ int lbl_server_create(int32_t n, const lbl_roadmap *rms, const int32_t *n_props,
   for (const Resident &R : S->res) all_quad = all_quad && (R.quad || R.rm->E == 0);
   S->depth = all_quad ? lbl::kQuadDepth : 8;
   S->ctas = lbl::batch_ctas_per_sm(S->depth);
-  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&S->arena_base), static_cast<size_t>(mem_budget));
+  if (e == cudaSuccess) e = lbl::obj_alloc(&S->arena_base, static_cast<size_t>(mem_budget), nullptr);
   if (e != cudaSuccess) return cleanup(lbl::cuda_fail(e, "server create: resident state"));
   S->arena.init(static_cast<size_t>(mem_budget));
   S->lanes.resize(lanes);
   for (Lane &l : S->lanes) {
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&l.s, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&l.done, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&l.counter), sizeof(unsigned long long));
+    if (e == cudaSuccess) e = lbl::obj_alloc(&l.counter, 1, nullptr);
   }
   if (e != cudaSuccess) return cleanup(lbl::cuda_fail(e, "server create: lanes"));
   try {
@@ -514,14 +515,16 @@ int lbl_server_free(lbl_server S) {
   }
   S->cv_work.notify_all();
   if (S->th.joinable()) S->th.join();
-  cudaDeviceSynchronize();
-  for (Resident &R : S->res) cudaFree(R.part);
+  // the server's work is all on its own lanes: wait for those alone, then free
+  // its memory in stream order (no device-wide synchronisation)
+  for (Lane &l : S->lanes) cudaStreamSynchronize(l.s);
+  for (Resident &R : S->res) lbl::obj_free_now(R.part);
   for (Lane &l : S->lanes) {
     cudaStreamDestroy(l.s);
     cudaEventDestroy(l.done);
-    cudaFree(l.counter);
+    lbl::obj_free_now(l.counter);
   }
-  cudaFree(S->arena_base);
+  lbl::obj_free_now(S->arena_base);
   delete S;
   return LBL_OK;
 }

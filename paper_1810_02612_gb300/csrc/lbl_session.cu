@@ -9,6 +9,7 @@
 using namespace lbl;
 
 struct lbl_session_s {
+  std::shared_ptr<UseLog> uses = std::make_shared<UseLog>();  // the caller's streams the session's work waited on
   int device = 0;
   lbl_roadmap rm = nullptr;
   lbl_monitor mon = nullptr;
@@ -87,7 +88,7 @@ int lbl_session_create(lbl_roadmap rm, const lbl_grid *world, int32_t n_props, l
     ss->has_cfg = true;
   }
   const size_t plane_bytes = static_cast<size_t>(n_props) * grid_cells(*world);
-  cudaError_t e = dev_alloc(&ss->planes, 2 * plane_bytes, nullptr);
+  cudaError_t e = obj_alloc(&ss->planes, 2 * plane_bytes, nullptr);
   ss->slot[0] = ss->planes;
   ss->slot[1] = ss->planes + plane_bytes;
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ss->cin, cudaStreamNonBlocking);
@@ -95,13 +96,13 @@ int lbl_session_create(lbl_roadmap rm, const lbl_grid *world, int32_t n_props, l
     e = cudaEventCreateWithFlags(&ss->ev_in[k], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ss->ev_free[k], cudaEventDisableTiming);
   }
-  if (e == cudaSuccess) e = dev_alloc(&ss->O, static_cast<size_t>(rm->cells), nullptr);
+  if (e == cudaSuccess) e = obj_alloc(&ss->O, static_cast<size_t>(rm->cells), nullptr);
   if (e == cudaSuccess && static_cast<int64_t>(plane_bytes) >= kPackedMinPlaneBytes &&
       grid_cells(*world) <= kPackedWorldRatio * rm->cells)
-    e = dev_alloc(&ss->words, static_cast<size_t>(grid_cells(*world)) * packed_word_bytes(n_props), nullptr);
-  if (e == cudaSuccess) e = dev_alloc(&ss->L, static_cast<size_t>(2 * rm->E), nullptr);
-  if (e == cudaSuccess && mon) e = dev_alloc(&ss->next, static_cast<size_t>(2 * rm->E), nullptr);
-  if (e == cudaSuccess && mon) e = dev_alloc(&ss->viol, static_cast<size_t>(2 * rm->E), nullptr);
+    e = obj_alloc(&ss->words, static_cast<size_t>(grid_cells(*world)) * packed_word_bytes(n_props), nullptr);
+  if (e == cudaSuccess) e = obj_alloc(&ss->L, static_cast<size_t>(2 * rm->E), nullptr);
+  if (e == cudaSuccess && mon) e = obj_alloc(&ss->next, static_cast<size_t>(2 * rm->E), nullptr);
+  if (e == cudaSuccess && mon) e = obj_alloc(&ss->viol, static_cast<size_t>(2 * rm->E), nullptr);
   for (int k = 0; k < 2; ++k) {
     ss->Ls[k] = ss->L ? ss->L + k * rm->E : nullptr;
     ss->Ns[k] = ss->next ? ss->next + k * rm->E : nullptr;
@@ -124,14 +125,14 @@ int lbl_session_create(lbl_roadmap rm, const lbl_grid *world, int32_t n_props, l
   if (e == cudaSuccess && stream_form && rm->E >= kSessionChunkMinEdges) {
     ss->chunked = true;
     ss->quad = c.algo == LBL_ALGO_QUAD;
-    if (ss->quad) e = dev_alloc(&ss->pyr, static_cast<size_t>(rm->pyr_words), nullptr);
+    if (ss->quad) e = obj_alloc(&ss->pyr, static_cast<size_t>(rm->pyr_words), nullptr);
     ss->depth = c.depth ? c.depth : (ss->quad ? kQuadDepth : 8);
     const int occ = stream_ctas_per_sm(ss->depth);
     ss->ctas = c.ctas_per_sm > 0 ? std::min(c.ctas_per_sm, occ) : occ;
     ss->warps = static_cast<int64_t>(rm->num_sms) * ss->ctas * (kThreads / 32);
     for (int c = 0; c <= kSessionChunks; ++c) ss->edge0[c] = rm->E * c / kSessionChunks;
     const int64_t *rows = ss->quad ? rm->qd_rowptr : rm->rowptr;
-    e = dev_alloc(&ss->cpart, static_cast<size_t>(kSessionChunks * (ss->warps + 1)), nullptr);
+    e = obj_alloc(&ss->cpart, static_cast<size_t>(kSessionChunks * (ss->warps + 1)), nullptr);
     for (int c = 0; c < kSessionChunks && e == cudaSuccess; ++c)
       e = launch_partition_into(rows + ss->edge0[c], ss->edge0[c + 1] - ss->edge0[c], ss->warps,
                                 ss->cpart + c * (ss->warps + 1), nullptr);
@@ -238,26 +239,26 @@ int lbl_session_run(lbl_session ss, const uint8_t *h_planes, lbl_pose pose, uint
   if ((e = cudaEventRecord(ss->ev_out[k], ss->cs)) != cudaSuccess ||
       (e = cudaStreamWaitEvent(st, ss->ev_out[k], 0)) != cudaSuccess)
     return cuda_fail(e, "session run: join");
+  rm.uses->note(cc);  // the roadmap's and monitor's rows and tables were read on the session's streams
+  if (ss->mon) ss->mon->uses->note(cc);
+  ss->uses->note(st);
   return LBL_OK;
 }
 
 int lbl_session_free(lbl_session ss) {
   clear_error();
   if (!ss) return LBL_OK;
-  cudaDeviceSynchronize();
-  cudaFree(ss->planes);
-  cudaFree(ss->O);
-  cudaFree(ss->L);
-  cudaFree(ss->next);
-  cudaFree(ss->viol);
-  cudaFree(ss->cpart);
-  if (ss->cs) cudaStreamDestroy(ss->cs);
+  // the session's own streams hold all its work (with the caller's streams it
+  // waited on, logged by lbl_session_run): its memory is released after that,
+  // without waiting for the rest of the device
+  for (cudaStream_t q : {ss->cin, ss->cc, ss->cs})
+    if (q) ss->uses->note(q);
+  ss->uses->release(ss->device, {ss->planes, ss->O, ss->L, ss->next, ss->viol, ss->cpart, ss->pyr, ss->words});
+  if (ss->cs) cudaStreamDestroy(ss->cs);  // destroyed once their work is done
   if (ss->cin) cudaStreamDestroy(ss->cin);
   if (ss->cc) cudaStreamDestroy(ss->cc);
   for (int k = 0; k < 2; ++k)
     if (ss->ev_out[k]) cudaEventDestroy(ss->ev_out[k]);
-  cudaFree(ss->pyr);
-  cudaFree(ss->words);
   for (cudaEvent_t ev : ss->ev)
     if (ev) cudaEventDestroy(ev);
   for (int k = 0; k < 2; ++k) {
