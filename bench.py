@@ -149,6 +149,11 @@ class ClockSampler:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={CLOCK_FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
+            # the sampler's start-up (its first query of the GPU) happens before
+            # the timed region: wait, at most 1.5 s, for its first sample
+            t_end = time.time() + 1.5
+            while time.time() < t_end and self.proc.poll() is None and os.path.getsize(self.path) == 0:
+                time.sleep(0.01)
         except (OSError, FileNotFoundError):
             self.proc = None
 
@@ -506,6 +511,8 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     t0 = time.time()
+    with torch.cuda.stream(stream):
+        flush.fill_(255)  # untimed: keeps the device busy while the host enqueues the first step
     for i in range(args.steps):
         with torch.cuda.stream(stream):
             flush.fill_(i & 255)

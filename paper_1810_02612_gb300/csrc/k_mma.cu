@@ -32,6 +32,9 @@ constexpr int kCoreRow = 16; // bytes per core-matrix row (8 rows x 16 bytes per
 constexpr int kSbo = (kMmaK / kCoreRow) * 128;  // bytes between 8-row groups of an operand tile
 constexpr int kLbo = 128;                       // bytes between K-adjacent core matrices
 constexpr unsigned long long kMmaWaitNs = 2000000000ull;
+// CTAs per SM of the labeling kernel: each holds 64 tensor-memory columns at
+// most (6 x 64 <= 512) and ~27 KB of shared memory.
+constexpr int kMmaCtasPerSm = 6;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -204,7 +207,7 @@ __global__ void __launch_bounds__(256) k_mma_bexpand(const uint64_t *__restrict_
 }
 
 template <int N, bool EPI>
-__global__ void __launch_bounds__(kMmaM, 4) k_label_mma(const int64_t *__restrict__ tptr,
+__global__ void __launch_bounds__(kMmaM, kMmaCtasPerSm) k_label_mma(const int64_t *__restrict__ tptr,
                                                         const int32_t *__restrict__ tblk,
                                                         const uint4 *__restrict__ bits, const uint8_t *__restrict__ B,
                                                         int64_t T, int64_t E, const int32_t *__restrict__ perm,
@@ -235,11 +238,21 @@ __global__ void __launch_bounds__(kMmaM, 4) k_label_mma(const int64_t *__restric
   const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
   uint32_t phase = 0;
   bool ok = true;
+  constexpr int BV = N * kMmaK / 16 / kMmaM;  // 16-byte pieces of a B block per thread
   for (int64_t t = blockIdx.x; t < T && ok; t += gridDim.x) {
     const int64_t k0 = tptr[t], k1 = tptr[t + 1];
+    // the next block's row bits and B matrix are loaded into registers while
+    // the current block's MMAs run
+    uint4 w = make_uint4(0, 0, 0, 0), bq[BV];
+    auto fetch = [&](int64_t i) {
+      w = __ldg(bits + i * kMmaM + tid);
+      const uint4 *src = reinterpret_cast<const uint4 *>(B + static_cast<int64_t>(__ldg(tblk + i)) * (N * kMmaK));
+#pragma unroll
+      for (int j = 0; j < BV; ++j) bq[j] = __ldg(src + tid + j * kMmaM);
+    };
+    if (k1 > k0) fetch(k0);
     for (int64_t i = k0; i < k1; ++i) {
       // A: this thread's row bits -> 128 e4m3 bytes, 16 per core matrix
-      const uint4 w = __ldg(bits + i * kMmaM + tid);
       const uint32_t words[4] = {w.x, w.y, w.z, w.w};
       uint8_t *arow = sA + (tid / 8) * kSbo + (tid % 8) * kCoreRow;
 #pragma unroll
@@ -250,9 +263,8 @@ __global__ void __launch_bounds__(kMmaM, 4) k_label_mma(const int64_t *__restric
                        nibble_bytes(h >> 12));
       }
       // B: the block's matrix, already in the operand layout
-      const uint4 *src = reinterpret_cast<const uint4 *>(B + static_cast<int64_t>(__ldg(tblk + i)) * (N * kMmaK));
 #pragma unroll
-      for (int j = tid; j < N * kMmaK / 16; j += kMmaM) reinterpret_cast<uint4 *>(sB)[j] = __ldg(src + j);
+      for (int j = 0; j < BV; ++j) reinterpret_cast<uint4 *>(sB)[tid + j * kMmaM] = bq[j];
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic-proxy writes -> the MMA's reads
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncthreads();
@@ -273,6 +285,7 @@ __global__ void __launch_bounds__(kMmaM, 4) k_label_mma(const int64_t *__restric
                      : "memory");
       }
       __syncwarp();
+      if (i + 1 < k1) fetch(i + 1);
       // every thread waits for the MMAs before shared memory is refilled
       ok = mbar_wait_bounded(&bar, phase & 1u, wait_ns);
       ++phase;
@@ -418,7 +431,7 @@ unsigned grid_of(int64_t n, int per) { return static_cast<unsigned>((n + per - 1
 
 template <int N>
 cudaError_t run_mma(const Roadmap &rm, uint64_t mask, uint64_t *L, const MonitorTables *mon, cudaStream_t s) {
-  const int64_t g = std::min<int64_t>(rm.mma_T, static_cast<int64_t>(rm.num_sms) * 4);
+  const int64_t g = std::min<int64_t>(rm.mma_T, static_cast<int64_t>(rm.num_sms) * kMmaCtasPerSm);
   MonitorTables none{};
   if (mon)
     k_label_mma<N, true><<<static_cast<unsigned>(g), kMmaM, 0, s>>>(
