@@ -82,6 +82,39 @@ def test_large_1m_edges_64_props_with_monitor():
     _check_workload(wl, QUAD_CFGS + [dict(algo=L.LBL_ALGO_CSR), dict(algo=L.LBL_ALGO_MMA)])
 
 
+def test_large_1m_edges_session_frames_back_to_back():
+    """The e2e path of bench.py: 1M-edge frames from pinned host memory through
+    lbl_session_run (one moving-front launch per frame at this size), two frames
+    at different poses enqueued back to back; every edge's label, next states
+    and violations equal the oracle."""
+    wl = synth.make("large", seed=0, threads=0)
+    m = wl.monitor
+    rm = L.lbl_roadmap_upload(wl.agent, wl.rowptr, wl.colidx, flags=L.LBL_UPLOAD_QUAD)
+    hm = L.lbl_monitor_create(m.n_states, m.m, m.relbits, m.delta, m.reject)
+    ss = L.lbl_session_create(rm, wl.world, wl.P, hm)
+    try:
+        planes = torch.from_numpy(wl.planes).pin_memory()
+        rng = np.random.default_rng(71)
+        poses = [wl.pose] + [synth.random_pose(rng, wl.world)]
+        outs = [(torch.empty(wl.n_edges, dtype=torch.uint64).pin_memory(),
+                 torch.empty(wl.n_edges, dtype=torch.uint64).pin_memory(),
+                 torch.empty(wl.n_edges, dtype=torch.uint16).pin_memory()) for _ in poses]
+        s = torch.cuda.Stream()
+        for pose, (oL, oN, oV) in zip(poses, outs):
+            L.lbl_session_run(ss, planes, pose, oL, oN, oV, stream=s)
+        s.synchronize()
+        for pose, (oL, oN, oV) in zip(poses, outs):
+            O = oracle.frame_transform(wl.world, wl.planes, pose[:3], wl.agent)
+            want = oracle.label(wl.rowptr, wl.colidx, O, wl.P, threads=THREADS)
+            wn, wv = oracle.monitor(m.n_states, m.m, m.relbits, m.delta, m.reject, want)
+            assert np.array_equal(oL.numpy(), want)
+            assert np.array_equal(oN.numpy(), wn) and np.array_equal(oV.numpy(), wv)
+    finally:
+        L.lbl_session_free(ss)
+        L.lbl_monitor_free(hm)
+        L.lbl_roadmap_free(rm)
+
+
 def test_driving_100k_edges_all_rows():
     wl = synth.make("driving", seed=0, threads=0)
     rm = L.lbl_roadmap_upload(wl.agent, wl.rowptr, wl.colidx, flags=L.LBL_UPLOAD_QUAD)

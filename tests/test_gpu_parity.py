@@ -530,15 +530,18 @@ def test_session_run_from_host_memory(large_small):
         L.lbl_monitor_free(hm)
 
 
-@pytest.mark.parametrize("flags", [0, "quad"])
+@pytest.mark.parametrize("flags", [0, "quad", "front"])
 def test_session_chunked_copies_match_oracle(flags):
     """Roadmaps of 2^16 edges or more: the session labels them in edge ranges
-    and copies each range to the host while the next is labeled."""
+    and copies each range to the host while the next is labeled; with the
+    moving front (forced here; chosen by size on large roadmaps) in one range
+    after one front launch."""
     wl = synth.make("large", seed=14, edges=90_000)
     rm = L.lbl_roadmap_upload(wl.agent, wl.rowptr, wl.colidx, flags=L.LBL_UPLOAD_QUAD if flags else 0)
     mon = wl.monitor
     hm = L.lbl_monitor_create(mon.n_states, mon.m, mon.relbits, mon.delta, mon.reject)
-    ss = L.lbl_session_create(rm, wl.world, wl.P, hm)
+    cfg = dict(algo=L.LBL_ALGO_QUAD, pipeline=L.LBL_PIPE_FRONT) if flags == "front" else None
+    ss = L.lbl_session_create(rm, wl.world, wl.P, hm, cfg)
     try:
         planes = torch.from_numpy(wl.planes).pin_memory()
         outL = torch.full((wl.n_edges,), 7, dtype=torch.int64).view(torch.uint64).pin_memory()
