@@ -454,7 +454,9 @@ def main():
              | (L.LBL_UPLOAD_QUAD if args.algo in ("auto", "quad") else 0)
              | (L.LBL_UPLOAD_MMA if args.algo == "mma" else 0))
     stream = torch.cuda.Stream()
+    t_up = time.perf_counter()
     rm = L.lbl_roadmap_upload(wl.agent, wl.rowptr, wl.colidx, flags=flags, stream=stream)
+    t_up = time.perf_counter() - t_up
     mon = None
     if wl.monitor is not None:
         m = wl.monitor
@@ -652,7 +654,7 @@ def main():
             "roofline_csr_form": csr_line,
             "cpu_baseline": cpu,
             "clocks": clk,
-            "setup_s": {"generate": t_gen},
+            "setup_s": {"generate": t_gen, "upload": t_up},
         }
         line.update(more)
         print(json.dumps(line), flush=True)
