@@ -116,6 +116,8 @@ __device__ __forceinline__ uint64_t frame_word(const FrameItem &f, uint32_t idx)
 // a 4 x 8 tile and its O stores coalesce).
 template <int WB>
 __global__ void __launch_bounds__(256) k_frame_z(const __grid_constant__ FrameItem f, uint32_t n) {
+  pdl_wait();
+  pdl_trigger();
   const uint32_t idx = blockIdx.x * 256u + threadIdx.x;
   if (idx < n) f.O[idx] = frame_word<WB>(f, idx);
 }
@@ -126,6 +128,8 @@ __global__ void __launch_bounds__(256) k_frame_z(const __grid_constant__ FrameIt
 // rows); the tile's O stores are four 64-byte runs.
 template <int WB>
 __global__ void __launch_bounds__(256) k_frame_tiles(const __grid_constant__ FrameItem f) {
+  pdl_wait();
+  pdl_trigger();
   const uint32_t xt = blockIdx.x * 8u + (threadIdx.x >> 5), lane = threadIdx.x & 31u;
   const uint32_t ix = 8u * xt + (lane & 7u), iy = 4u * blockIdx.y + (lane >> 3), it = blockIdx.z;
   if (ix >= static_cast<uint32_t>(f.aw) || iy >= static_cast<uint32_t>(f.ah)) return;
@@ -223,6 +227,8 @@ __device__ __forceinline__ void pack_lane(const PackItem &it, int64_t lane) {
 
 template <int WB, bool VEC>
 __global__ void __launch_bounds__(256) k_pack_planes(const __grid_constant__ PackItem it) {
+  pdl_wait();
+  pdl_trigger();
   pack_lane<WB, VEC>(it, static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x);
 }
 
@@ -271,11 +277,11 @@ template <int WB>
 static void transform_launch(const FrameItem &f, cudaStream_t s) {
   const uint32_t n = static_cast<uint32_t>(f.aw) * static_cast<uint32_t>(f.ah) * static_cast<uint32_t>(f.ad);
   if (f.order == LBL_ORDER_MORTON) {
-    k_frame_z<WB><<<(n + 255u) / 256u, 256, 0, s>>>(f, n);
+    pdl_launch(k_frame_z<WB>, dim3((n + 255u) / 256u), dim3(256), s, f, n);
   } else {  // at most 32768 / 4 tile rows and 32768 slabs: within the grid's y and z limits
     const dim3 grid((static_cast<unsigned>(f.aw) + 63u) / 64u, (static_cast<unsigned>(f.ah) + 3u) / 4u,
                     static_cast<unsigned>(f.ad));
-    k_frame_tiles<WB><<<grid, 256, 0, s>>>(f);
+    pdl_launch(k_frame_tiles<WB>, grid, dim3(256), s, f);
   }
 }
 
@@ -297,9 +303,9 @@ cudaError_t launch_frame_transform(const FrameItem &f, cudaStream_t s) {
 template <int WB>
 static void pack_launch(const PackItem &it, bool vec, unsigned blocks, cudaStream_t s) {
   if (vec)
-    k_pack_planes<WB, true><<<blocks, 256, 0, s>>>(it);
+    pdl_launch(k_pack_planes<WB, true>, dim3(blocks), dim3(256), s, it);
   else
-    k_pack_planes<WB, false><<<blocks, 256, 0, s>>>(it);
+    pdl_launch(k_pack_planes<WB, false>, dim3(blocks), dim3(256), s, it);
 }
 
 // vector loads and stores: 4-byte aligned planes, whole lanes, words aligned to the lane's store

@@ -293,6 +293,7 @@ __global__ void __launch_bounds__(kFrontWarps * 32, 1) k_label_front(const int64
                                                                     const int32_t *__restrict__ perm) {
   __shared__ EpiSmem sm;
   __shared__ int next_chunk;
+  pdl_wait();
   if (threadIdx.x == 0) next_chunk = 0;
   if (EPI)
     load_tables(mon, sm);  // contains __syncthreads
@@ -462,6 +463,8 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads) k_quad_pyramid(const uint64_t *__restrict__ O, int64_t cells,
                                                            QuadOffsets off, T *__restrict__ pyr) {
   __shared__ uint64_t wsum[kThreads / 32];
+  pdl_wait();
+  pdl_trigger();
   quad_pyramid_block<T>(O, cells, off, pyr, blockIdx.x, wsum);
 }
 
@@ -1186,12 +1189,13 @@ void front_launch(const StreamRows &r, const T *base, uint64_t mask, uint64_t *L
   const int small = std::min(chunk, kFrontTailChunk);
   const int tail = 2 * kFrontWarps * small;
   MonitorTables none{};
+  const dim3 g(grid), b(kFrontWarps * 32);
   if (mon)
-    k_label_front<8, true, T><<<grid, kFrontWarps * 32, 0, s>>>(r.rowptr, r.idx, base, r.part, stride, chunk, tail,
-                                                                 small, mask, L, *mon, r.perm);
+    pdl_launch(k_label_front<8, true, T>, g, b, s, r.rowptr, r.idx, base, r.part, stride, chunk, tail, small, mask, L,
+               *mon, r.perm);
   else
-    k_label_front<8, false, T><<<grid, kFrontWarps * 32, 0, s>>>(r.rowptr, r.idx, base, r.part, stride, chunk, tail,
-                                                                  small, mask, L, none, r.perm);
+    pdl_launch(k_label_front<8, false, T>, g, b, s, r.rowptr, r.idx, base, r.part, stride, chunk, tail, small, mask,
+               L, none, r.perm);
 }
 
 template <typename T>
@@ -1244,13 +1248,13 @@ int quad_word_bytes(const Roadmap &rm, int32_t P) {
 cudaError_t launch_quad_pyramid(const Roadmap &rm, const uint64_t *O, int word_bytes, void *pyr, cudaStream_t s) {
   if (rm.cells == 0) return cudaSuccess;
   const unsigned grid = static_cast<unsigned>((rm.cells + kThreads - 1) / kThreads);
-  switch (word_bytes) {
-    case 1: k_quad_pyramid<uint8_t><<<grid, kThreads, 0, s>>>(O, rm.cells, rm.qd_off, static_cast<uint8_t *>(pyr)); break;
-    case 2: k_quad_pyramid<uint16_t><<<grid, kThreads, 0, s>>>(O, rm.cells, rm.qd_off, static_cast<uint16_t *>(pyr)); break;
-    case 4: k_quad_pyramid<uint32_t><<<grid, kThreads, 0, s>>>(O, rm.cells, rm.qd_off, static_cast<uint32_t *>(pyr)); break;
-    default: k_quad_pyramid<uint64_t><<<grid, kThreads, 0, s>>>(O, rm.cells, rm.qd_off, static_cast<uint64_t *>(pyr)); break;
+  const dim3 g(grid), b(kThreads);
+  switch (word_bytes) {  // launched dependent on the frame transform before it
+    case 1: return pdl_launch(k_quad_pyramid<uint8_t>, g, b, s, O, rm.cells, rm.qd_off, static_cast<uint8_t *>(pyr));
+    case 2: return pdl_launch(k_quad_pyramid<uint16_t>, g, b, s, O, rm.cells, rm.qd_off, static_cast<uint16_t *>(pyr));
+    case 4: return pdl_launch(k_quad_pyramid<uint32_t>, g, b, s, O, rm.cells, rm.qd_off, static_cast<uint32_t *>(pyr));
+    default: return pdl_launch(k_quad_pyramid<uint64_t>, g, b, s, O, rm.cells, rm.qd_off, static_cast<uint64_t *>(pyr));
   }
-  return cudaGetLastError();
 }
 
 cudaError_t launch_quad_pyramid_batch(const PyrTable &tab, cudaStream_t s) {

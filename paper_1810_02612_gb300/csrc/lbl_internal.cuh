@@ -74,6 +74,32 @@ __device__ __forceinline__ void epilogue(const MonitorTables &mon, const EpiSmem
   mon.viol[e] = sm.V[letter];
 }
 
+// Programmatic dependent launch.  The kernels of one frame (plane packing,
+// frame transform, pyramid, labels) each depend on the one before; launched
+// with pdl_launch, a kernel's CTAs are placed on the SMs while the kernel
+// before it finishes (that kernel lets them in with pdl_trigger at its start),
+// so the launch gap between the two shrinks.  A kernel launched this way calls
+// pdl_wait first: it returns once the kernel before has completed and its
+// writes are visible, so nothing is read or written early.  Launched the usual
+// way, pdl_wait returns at once.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t pdl_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, Args &&...args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 // One roadmap's share of a batched labeling launch (device table entry).
 struct BatchItem {
   const int64_t *rowptr;
