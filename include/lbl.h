@@ -585,10 +585,9 @@ int lbl_server_free(lbl_server srv);
  * kernels: the planes go in on the session's own copy stream into one of two
  * device buffers (frame i+1's copy runs while frame i is labeled), and on
  * roadmaps of 2^16 edges or more labeled by a streamed form (quadtree, or CSR
- * without lane groups) the labels leave on a second copy stream: in four edge
- * ranges, each while the next range is labeled, or, on quadtree roadmaps
- * large enough for the moving front (about 3,000 edges per SM), in one range
- * after a single front launch over the whole frame.  Such a session keeps its own
+ * without lane groups) the labels leave on a second copy stream once the
+ * frame's single labeling launch (the moving front on quadtree roadmaps of
+ * about 3,000 edges per SM or more, else the per-warp stream) has ended.  Such a session keeps its own
  * pyramid and output buffers (two sets), runs its kernels on its own stream
  * and only makes `s` wait for each frame's end, so frame i+1 is computed while
  * frame i is still being copied out; it reads nothing on the device that the

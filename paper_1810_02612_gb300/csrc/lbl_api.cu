@@ -418,7 +418,7 @@ int roadmap_finish(lbl_roadmap_s *rm, uint32_t flags, cudaStream_t st) {
     }
     rm->pyr_words = words;
     if (n_edges > 1 && n_edges < (1LL << 31) && !(flags & LBL_UPLOAD_KEEP_ORDER) && grid_depth(rm->agent) == 1) {
-      // locality order: inside each session edge range, rows by the z-order of
+      // locality order: inside each of kOrderRanges edge ranges, rows by the z-order of
       // their middle cell's (x, y); time-augmented grids keep the caller's
       // order, which measured faster than every key tried there
       std::vector<uint32_t> key(static_cast<size_t>(n_edges));
@@ -434,8 +434,8 @@ int roadmap_finish(lbl_roadmap_s *rm, uint32_t flags, cudaStream_t st) {
       }
       cudaFree(d_key);
       std::vector<int32_t> perm(static_cast<size_t>(n_edges));
-      for (int c = 0; c < kSessionChunks; ++c)
-        sort_range_by_key(key.data(), n_edges * c / kSessionChunks, n_edges * (c + 1) / kSessionChunks, perm.data());
+      for (int c = 0; c < kOrderRanges; ++c)
+        sort_range_by_key(key.data(), n_edges * c / kOrderRanges, n_edges * (c + 1) / kOrderRanges, perm.data());
       if ((e = obj_alloc(&rm->qd_perm, static_cast<size_t>(n_edges), &rm->bytes)) != cudaSuccess ||
           (e = cudaMemcpyAsync(rm->qd_perm, perm.data(), sizeof(int32_t) * n_edges, cudaMemcpyHostToDevice, st)) !=
               cudaSuccess ||

@@ -180,9 +180,12 @@ constexpr int kQuadLevels = 4;
 // gathers hit L1, and four CTAs per SM at depth 8 beat three at depth 12
 // (and five or six at depths 6 or 4) on every single-frame workload.
 constexpr int kQuadDepth = 8;
-// Host-buffer sessions label big roadmaps in this many edge ranges and copy
-// each range's results to the host while the next one is labeled.
-constexpr int kSessionChunks = 4;
+// The locality order sorts the quadtree rows inside each of this many equal
+// ranges of the caller's edges, not across the whole roadmap (with the moving
+// front: 0.2528 vs 0.2618 ms on the 1M-edge call, rows pre-sorted).
+constexpr int kOrderRanges = 4;
+// Host-buffer sessions label roadmaps of at least this many edges on their own
+// stream, pyramid and partition.
 constexpr int64_t kSessionChunkMinEdges = 1 << 16;
 struct QuadOffsets {
   int64_t at[kQuadLevels + 1];  // first pyramid word of each level
@@ -262,7 +265,7 @@ struct Roadmap {
   int64_t *qd_rowptr = nullptr;
   int32_t *qd_idx = nullptr;    // n_qd entries, padded like colidx
   // Quadtree row i is the caller's edge qd_perm[i]: inside each of the
-  // kSessionChunks edge ranges the rows of a 2-D grid are sorted by the z-order
+  // kOrderRanges edge ranges the rows of a 2-D grid are sorted by the z-order
   // of their middle cell's (x, y), so a CTA's edges lie close together and
   // share pyramid lines in L1; NULL keeps the caller's order (time-augmented
   // grids, LBL_UPLOAD_KEEP_ORDER, roadmaps of 2^31 edges or more)

@@ -40,23 +40,23 @@ struct lbl_session_s {
   // kPackedMinPlaneBytes on a world of at most kPackedWorldRatio times the
   // agent's cells, so packing reads little the transform would not.
   uint8_t *words = nullptr;
-  // Chunked labeling: the edges in `ranges` ranges (kSessionChunks, or one),
-  // each labeled by the whole grid; a range's results go to the host on `cs`
-  // while the next range is labeled.  Used with the default form (quadtree,
-  // else streaming CSR).  A quadtree roadmap large enough for the moving front
-  // is labeled as one range: the front over the whole roadmap is faster than
-  // the per-warp stream over four quarters (1M edges: 0.262 vs 4 x 0.073 ms),
-  // and frames run back to back still overlap one frame's copies with the
-  // next frame's kernels through the two output sets.
+  // Own-stream labeling (`chunked`, with the default form: quadtree, else
+  // streaming CSR, on roadmaps of kSessionChunkMinEdges edges or more): the
+  // session's own pyramid and partition, its kernels on `cc`, the results
+  // copied to the host on `cs`.  The whole roadmap is one range, labeled by the
+  // moving front or the per-warp stream as lbl_label chooses by size; frames
+  // run back to back overlap one frame's copies with the next frame's kernels
+  // through the two output sets.  (Four ranges, each copied out while the next
+  // was labeled, measured slower at every size: 100k edges 0.055 vs 0.036 ms
+  // per frame, 250k 0.117 vs 0.089, 400k 0.155 vs 0.129, 1M 0.29 vs 0.26.)
   bool chunked = false;
-  int ranges = lbl::kSessionChunks;
   bool quad = false;
   int depth = 8, ctas = 0;
-  int64_t edge0[lbl::kSessionChunks + 1] = {0};
-  int64_t *cpart = nullptr;  // kSessionChunks partitions of warps + 1 entries
+  int64_t *cpart = nullptr;  // the warps' partition: warps + 1 entries
   int64_t warps = 0;
+  int front_chunk = -1;  // quadtree: -1 = the moving front by size (as lbl_label), 0 = per-warp stream, > 0 = front
   cudaStream_t cs = nullptr;
-  cudaEvent_t ev[lbl::kSessionChunks + 1] = {nullptr};
+  cudaEvent_t ev = nullptr;  // labels done: the copies on `cs` may start
 };
 
 extern "C" {
@@ -136,21 +136,15 @@ int lbl_session_create(lbl_roadmap rm, const lbl_grid *world, int32_t n_props, l
     const int occ = stream_ctas_per_sm(ss->depth);
     ss->ctas = c.ctas_per_sm > 0 ? std::min(c.ctas_per_sm, occ) : occ;
     ss->warps = static_cast<int64_t>(rm->num_sms) * ss->ctas * (kThreads / 32);
-    const int pipe = c.pipeline;
-    if (ss->quad && ss->depth == 8 && pipe != LBL_PIPE_REGISTERS &&
-        (front_chunk_for(rm->E, rm->num_sms) > 0 || pipe == LBL_PIPE_FRONT))
-      ss->ranges = 1;
-    for (int r = 0; r <= ss->ranges; ++r) ss->edge0[r] = rm->E * r / ss->ranges;
+    if (ss->quad && c.pipeline == LBL_PIPE_FRONT) ss->front_chunk = std::max(front_chunk_for(rm->E, rm->num_sms), 8);
+    if (!ss->quad || c.pipeline == LBL_PIPE_REGISTERS) ss->front_chunk = 0;
     const int64_t *rows = ss->quad ? rm->qd_rowptr : rm->rowptr;
-    e = obj_alloc(&ss->cpart, static_cast<size_t>(ss->ranges * (ss->warps + 1)), nullptr);
-    for (int c = 0; c < ss->ranges && e == cudaSuccess; ++c)
-      e = launch_partition_into(rows + ss->edge0[c], ss->edge0[c + 1] - ss->edge0[c], ss->warps,
-                                ss->cpart + c * (ss->warps + 1), nullptr);
+    e = obj_alloc(&ss->cpart, static_cast<size_t>(ss->warps + 1), nullptr);
+    if (e == cudaSuccess) e = launch_partition_into(rows, rm->E, ss->warps, ss->cpart, nullptr);
     if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
   }
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ss->cs, cudaStreamNonBlocking);
-  for (int c = 0; c <= kSessionChunks && e == cudaSuccess; ++c)
-    e = cudaEventCreateWithFlags(&ss->ev[c], cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ss->ev, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     lbl_session_free(ss);
     return cuda_fail(e, "session create");
@@ -220,27 +214,20 @@ int lbl_session_run(lbl_session ss, const uint8_t *h_planes, lbl_pose pose, uint
         return cuda_fail(e, "session run: pyramid");
       base = ss->pyr;
     }
-    for (int c = 0; c < ss->ranges; ++c) {
-      const int64_t e0 = ss->edge0[c], n = ss->edge0[c + 1] - e0;
-      if (n == 0) continue;
-      // quadtree rows in locality order write to the caller's edges of the
-      // same range: the outputs are addressed from their start, not from e0
-      const int32_t *perm = ss->quad && rm.qd_perm ? rm.qd_perm + e0 : nullptr;
-      const int64_t o0 = perm ? 0 : e0;
-      const StreamRows r{(ss->quad ? rm.qd_rowptr : rm.rowptr) + e0, ss->quad ? rm.qd_idx : rm.colidx,
-                         ss->cpart + c * (ss->warps + 1), ss->ctas, n, ss->quad ? rm.n_qd : rm.nnz, perm};
-      MonitorTables t{};
-      if (ss->mon) t = tables_of(*ss->mon, dN + o0, dV + o0);
-      e = launch_label_rows(r, base, wb, ss->P, dL + o0, ss->mon ? &t : nullptr, ss->depth, rm.num_sms, cc);
-      if (e == cudaSuccess) e = cudaEventRecord(ss->ev[c], cc);
-      if (e == cudaSuccess) e = cudaStreamWaitEvent(ss->cs, ss->ev[c], 0);
-      if (e == cudaSuccess) e = copy_out(e0, n);
-      if (e != cudaSuccess) return cuda_fail(e, "session run: chunk");
-    }
+    StreamRows r{ss->quad ? rm.qd_rowptr : rm.rowptr, ss->quad ? rm.qd_idx : rm.colidx, ss->cpart, ss->ctas, rm.E,
+                 ss->quad ? rm.n_qd : rm.nnz, ss->quad ? rm.qd_perm : nullptr};
+    r.front_chunk = ss->front_chunk;
+    MonitorTables t{};
+    if (ss->mon) t = tables_of(*ss->mon, dN, dV);
+    e = launch_label_rows(r, base, wb, ss->P, dL, ss->mon ? &t : nullptr, ss->depth, rm.num_sms, cc);
+    if (e == cudaSuccess) e = cudaEventRecord(ss->ev, cc);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ss->cs, ss->ev, 0);
+    if (e == cudaSuccess) e = copy_out(0, rm.E);
+    if (e != cudaSuccess) return cuda_fail(e, "session run: labels");
   } else {
     rc = label_impl(ss->rm, ss->O, ss->P, dL, ss->mon, dN, dV, ss->has_cfg ? &ss->cfg : nullptr, cc);
     if (rc != LBL_OK) return rc;
-    if ((e = cudaEventRecord(ss->ev[0], cc)) != cudaSuccess || (e = cudaStreamWaitEvent(ss->cs, ss->ev[0], 0)) != cudaSuccess ||
+    if ((e = cudaEventRecord(ss->ev, cc)) != cudaSuccess || (e = cudaStreamWaitEvent(ss->cs, ss->ev, 0)) != cudaSuccess ||
         (rm.E > 0 && (e = copy_out(0, rm.E)) != cudaSuccess))
       return cuda_fail(e, "session run: copy results");
   }
@@ -269,8 +256,7 @@ int lbl_session_free(lbl_session ss) {
   if (ss->cc) cudaStreamDestroy(ss->cc);
   for (int k = 0; k < 2; ++k)
     if (ss->ev_out[k]) cudaEventDestroy(ss->ev_out[k]);
-  for (cudaEvent_t ev : ss->ev)
-    if (ev) cudaEventDestroy(ev);
+  if (ss->ev) cudaEventDestroy(ss->ev);
   for (int k = 0; k < 2; ++k) {
     if (ss->ev_in[k]) cudaEventDestroy(ss->ev_in[k]);
     if (ss->ev_free[k]) cudaEventDestroy(ss->ev_free[k]);

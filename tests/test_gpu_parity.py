@@ -532,10 +532,10 @@ def test_session_run_from_host_memory(large_small):
 
 @pytest.mark.parametrize("flags", [0, "quad", "front"])
 def test_session_chunked_copies_match_oracle(flags):
-    """Roadmaps of 2^16 edges or more: the session labels them in edge ranges
-    and copies each range to the host while the next is labeled; with the
-    moving front (forced here; chosen by size on large roadmaps) in one range
-    after one front launch."""
+    """Roadmaps of 2^16 edges or more: the session labels them on its own
+    stream with its own pyramid and partition, then copies the results to the
+    host; by the per-warp stream (the size rule at 90k edges) or the moving
+    front (forced here; chosen by size on large roadmaps)."""
     wl = synth.make("large", seed=14, edges=90_000)
     rm = L.lbl_roadmap_upload(wl.agent, wl.rowptr, wl.colidx, flags=L.LBL_UPLOAD_QUAD if flags else 0)
     mon = wl.monitor
