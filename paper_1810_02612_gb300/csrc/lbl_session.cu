@@ -117,7 +117,7 @@ int lbl_session_create(lbl_roadmap rm, const lbl_grid *world, int32_t n_props, l
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ss->cc, cudaStreamNonBlocking);
   for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&ss->ev_out[k], cudaEventDisableTiming);
 
-  // Chunked labeling when the configuration resolves to a register-pipelined
+  // Own-stream labeling when the configuration resolves to a register-pipelined
   // stream (quadtree, or CSR without lane groups, early exit or copy rings) on
   // a roadmap big enough to pay.
   lbl_config c{};
