@@ -21,6 +21,7 @@ sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import gc
 import hashlib
 import json
 import math
@@ -512,6 +513,7 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    gc.disable()  # no collector pause while the host enqueues the timed steps
     t0 = time.time()
     with torch.cuda.stream(stream):
         flush.fill_(255)  # untimed: keeps the device busy while the host enqueues the first step
@@ -525,6 +527,7 @@ def main():
         ev[i][2].record(stream)
     torch.cuda.synchronize()
     t1 = time.time()
+    gc.enable()
     if dist:
         dist.barrier()
     step_ms = np.array([a.elapsed_time(c) for a, b, c in ev])
@@ -594,11 +597,13 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     t_a, t_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    gc.disable()
     t_a.record(stream)
     for i in range(args.steps):
         L.lbl_session_run(ss, h_planes, wl.pose, h_L, h_next, h_viol, stream=stream)
     t_b.record(stream)
     torch.cuda.synchronize()
+    gc.enable()
     e2e_ms = max_over_ranks(float(t_a.elapsed_time(t_b)), dist, "cuda")
     e2e_value = job_throughput(world, E, P, args.steps, e2e_ms)
     h2d = int(wl.planes.nbytes)

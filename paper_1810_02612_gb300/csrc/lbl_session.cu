@@ -22,7 +22,8 @@ struct lbl_session_s {
   uint16_t *viol = nullptr;
   // Two plane buffers, filled on `cin` in turn: frame i+1's planes go to the
   // device while frame i is transformed and labeled.  ev_in[k]: slot k filled;
-  // ev_free[k]: the transform that read slot k is done.
+  // ev_free[k]: the frame that read slot k is done (recorded after its labels,
+  // so no event separates the frame's kernels).
   uint8_t *slot[2] = {nullptr, nullptr};
   cudaStream_t cin = nullptr;
   cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
@@ -183,6 +184,9 @@ int lbl_session_run(lbl_session ss, const uint8_t *h_planes, lbl_pose pose, uint
     e = cudaMemcpyAsync(ss->slot[k], h_planes, plane_bytes, cudaMemcpyHostToDevice, ss->cin);
   if (e == cudaSuccess) e = cudaEventRecord(ss->ev_in[k], ss->cin);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(cc, ss->ev_in[k], 0);
+  // output set k copied out (frame i-2) before this frame's kernels, so no
+  // event sits between them and each is launched while the one before ends
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(cc, ss->ev_out[k], 0);
   if (e != cudaSuccess) return cuda_fail(e, "session run: copy planes");
   int rc = LBL_OK;
   if (ss->words) {
@@ -193,9 +197,6 @@ int lbl_session_run(lbl_session ss, const uint8_t *h_planes, lbl_pose pose, uint
     rc = lbl_frame_transform(&ss->world, ss->slot[k], ss->P, pose, &rm.agent, ss->O, reinterpret_cast<lbl_stream>(cc));
   }
   if (rc != LBL_OK) return rc;
-  if ((e = cudaEventRecord(ss->ev_free[k], cc)) != cudaSuccess ||
-      (e = cudaStreamWaitEvent(cc, ss->ev_out[k], 0)) != cudaSuccess)  // output set k copied out (frame i-2)
-    return cuda_fail(e, "session run: event");
   ++ss->frame;
   auto copy_out = [&](int64_t e0, int64_t n) {
     cudaError_t r = cudaMemcpyAsync(h_L + e0, dL + e0, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost, ss->cs);
@@ -220,6 +221,7 @@ int lbl_session_run(lbl_session ss, const uint8_t *h_planes, lbl_pose pose, uint
     MonitorTables t{};
     if (ss->mon) t = tables_of(*ss->mon, dN, dV);
     e = launch_label_rows(r, base, wb, ss->P, dL, ss->mon ? &t : nullptr, ss->depth, rm.num_sms, cc);
+    if (e == cudaSuccess) e = cudaEventRecord(ss->ev_free[k], cc);  // plane slot k free (read before the labels)
     if (e == cudaSuccess) e = cudaEventRecord(ss->ev, cc);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(ss->cs, ss->ev, 0);
     if (e == cudaSuccess) e = copy_out(0, rm.E);
@@ -227,7 +229,8 @@ int lbl_session_run(lbl_session ss, const uint8_t *h_planes, lbl_pose pose, uint
   } else {
     rc = label_impl(ss->rm, ss->O, ss->P, dL, ss->mon, dN, dV, ss->has_cfg ? &ss->cfg : nullptr, cc);
     if (rc != LBL_OK) return rc;
-    if ((e = cudaEventRecord(ss->ev, cc)) != cudaSuccess || (e = cudaStreamWaitEvent(ss->cs, ss->ev, 0)) != cudaSuccess ||
+    if ((e = cudaEventRecord(ss->ev_free[k], cc)) != cudaSuccess || (e = cudaEventRecord(ss->ev, cc)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(ss->cs, ss->ev, 0)) != cudaSuccess ||
         (rm.E > 0 && (e = copy_out(0, rm.E)) != cudaSuccess))
       return cuda_fail(e, "session run: copy results");
   }
