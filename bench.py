@@ -122,6 +122,47 @@ def dist_env():
     return rank, world, local
 
 
+# ---------------------------------------------------------------- enqueue gate
+
+class Gate:
+    """Timed steps are enqueued in blocks, each behind a fixed-length spin
+    kernel (torch.cuda._sleep) on the timing stream, with the device idle
+    before it.  The host then queues the whole block while the device spins,
+    so a host pause inside the block (pauses of 40-55 ms were seen on the GPU
+    hosts, longer than the ~46 ms of work the driver queue holds) cannot
+    leave the device idle between a step's events.  The spin and the idle
+    time between blocks are outside every timed interval.  `late` counts the
+    blocks whose host enqueue took longer than the spin (0 = no step can have
+    waited for the host)."""
+
+    def __init__(self, torch, stream, block: int = 64, ms: float = 20.0):
+        self.torch, self.stream, self.block, self.ms = torch, stream, block, ms
+        self.host_ms = []
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        cal = 2_000_000
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            a.record(stream)
+            torch.cuda._sleep(cal)
+            b.record(stream)
+        torch.cuda.synchronize()
+        self.cycles = int(cal * ms / max(a.elapsed_time(b), 1e-3))
+
+    def blocks(self, n: int):
+        for b0 in range(0, n, self.block):
+            self.torch.cuda.synchronize()
+            with self.torch.cuda.stream(self.stream):
+                self.torch.cuda._sleep(self.cycles)
+            t = time.perf_counter()
+            yield range(b0, min(n, b0 + self.block))
+            self.host_ms.append((time.perf_counter() - t) * 1e3)
+
+    def summary(self) -> dict:
+        return {"block_steps": self.block, "gate_ms": self.ms, "blocks": len(self.host_ms),
+                "host_enqueue_ms_max": max(self.host_ms) if self.host_ms else 0.0,
+                "late": sum(h > self.ms for h in self.host_ms)}
+
+
 # --------------------------------------------------------------------- clocks
 
 CLOCK_FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -501,8 +542,11 @@ def main():
     launches_per_step = (2 + (1 if used in ("bittile", "quad", "mma") else 0)  # + planes / pyramid / B kernel
                          + (1 if args.transform == "packed" else 0))   # + packing kernel
 
-    # ---- warm-up
-    for _ in range(args.warmup):
+    # ---- warm-up (the flush fills too: a kernel's first launch in the process
+    # loads its module and can wait for the device)
+    for w in range(args.warmup):
+        with torch.cuda.stream(stream):
+            flush.fill_(w & 255)
         step()
     torch.cuda.synchronize()
 
@@ -513,21 +557,22 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    gate = Gate(torch, stream)
     gc.disable()  # no collector pause while the host enqueues the timed steps
     t0 = time.time()
-    with torch.cuda.stream(stream):
-        flush.fill_(255)  # untimed: keeps the device busy while the host enqueues the first step
-    for i in range(args.steps):
-        with torch.cuda.stream(stream):
-            flush.fill_(i & 255)
-        ev[i][0].record(stream)
-        transform()
-        ev[i][1].record(stream)
-        L.lbl_label(rm, d_O, P, d_L, mon, d_next, d_viol, cfg, stream=stream)
-        ev[i][2].record(stream)
+    for blk in gate.blocks(args.steps):
+        for i in blk:
+            with torch.cuda.stream(stream):
+                flush.fill_(i & 255)
+            ev[i][0].record(stream)
+            transform()
+            ev[i][1].record(stream)
+            L.lbl_label(rm, d_O, P, d_L, mon, d_next, d_viol, cfg, stream=stream)
+            ev[i][2].record(stream)
     torch.cuda.synchronize()
     t1 = time.time()
     gc.enable()
+    gates = {"steps": gate.summary()}
     if dist:
         dist.barrier()
     step_ms = np.array([a.elapsed_time(c) for a, b, c in ev])
@@ -549,13 +594,16 @@ def main():
         cev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_csr)]
         for _ in range(3):
             L.lbl_label(rm, d_O, P, d_L, mon, d_next, d_viol, csr_cfg, stream=stream)
-        for i in range(n_csr):
-            with torch.cuda.stream(stream):
-                flush.fill_(i & 255)
-            cev[i][0].record(stream)
-            L.lbl_label(rm, d_O, P, d_L, mon, d_next, d_viol, csr_cfg, stream=stream)
-            cev[i][1].record(stream)
+        cgate = Gate(torch, stream)
+        for blk in cgate.blocks(n_csr):
+            for i in blk:
+                with torch.cuda.stream(stream):
+                    flush.fill_(i & 255)
+                cev[i][0].record(stream)
+                L.lbl_label(rm, d_O, P, d_L, mon, d_next, d_viol, csr_cfg, stream=stream)
+                cev[i][1].record(stream)
         torch.cuda.synchronize()
+        gates["csr_form"] = cgate.summary()
         csr_s = float(np.mean([a.elapsed_time(b) for a, b in cev])) / 1e3
         csr_b = label_bytes(wl, "csr", None, mon is not None)
         peaks0 = measured_peaks()
@@ -596,15 +644,19 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    t_a, t_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    egate = Gate(torch, stream)
+    n_blk = (args.steps + egate.block - 1) // egate.block
+    t_ab = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_blk)]
     gc.disable()
-    t_a.record(stream)
-    for i in range(args.steps):
-        L.lbl_session_run(ss, h_planes, wl.pose, h_L, h_next, h_viol, stream=stream)
-    t_b.record(stream)
+    for j, blk in enumerate(egate.blocks(args.steps)):
+        t_ab[j][0].record(stream)
+        for i in blk:
+            L.lbl_session_run(ss, h_planes, wl.pose, h_L, h_next, h_viol, stream=stream)
+        t_ab[j][1].record(stream)
     torch.cuda.synchronize()
     gc.enable()
-    e2e_ms = max_over_ranks(float(t_a.elapsed_time(t_b)), dist, "cuda")
+    gates["e2e"] = egate.summary()
+    e2e_ms = max_over_ranks(float(sum(a.elapsed_time(b) for a, b in t_ab)), dist, "cuda")
     e2e_value = job_throughput(world, E, P, args.steps, e2e_ms)
     h2d = int(wl.planes.nbytes)
     d2h = 8 * E + ((8 + 2) * E if mon else 0)
@@ -659,6 +711,7 @@ def main():
             "roofline_csr_form": csr_line,
             "cpu_baseline": cpu,
             "clocks": clk,
+            "enqueue_gates": gates,
             "setup_s": {"generate": t_gen, "upload": t_up},
         }
         line.update(more)
@@ -723,18 +776,27 @@ def measure_batched(torch, L, frames, steps: int, warmup: int, algo: str, dist=N
     with torch.cuda.graph(g, stream=stream):
         L.lbl_batch_launch(b, stream=torch.cuda.current_stream())
 
-    def timed(fn, n):
+    gates = {}
+
+    def timed(fn, n, name="", cmds=4, ms=20.0):
+        # cmds: commands one step queues; a gated block holds at most ~800
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
-        for i in range(n):
-            with torch.cuda.stream(stream):
-                flush.fill_(i & 255)
-            ev[i][0].record(stream)
-            fn()
-            ev[i][1].record(stream)
+        gate = Gate(torch, stream, block=max(1, min(64, 800 // cmds)), ms=ms)
+        for blk in gate.blocks(n):
+            for i in blk:
+                with torch.cuda.stream(stream):
+                    flush.fill_(i & 255)
+                ev[i][0].record(stream)
+                fn()
+                ev[i][1].record(stream)
         torch.cuda.synchronize()
+        if name:
+            gates[name] = gate.summary()
         return np.array([a.elapsed_time(c) for a, c in ev])
 
-    for _ in range(warmup):
+    for w in range(warmup):
+        with torch.cuda.stream(stream):
+            flush.fill_(w & 255)
         plain_step()
         g.replay()
     torch.cuda.synchronize()
@@ -742,18 +804,19 @@ def measure_batched(torch, L, frames, steps: int, warmup: int, algo: str, dist=N
         dist.barrier()
     t0 = time.time()
     with torch.cuda.stream(stream):
-        batched_ms = timed(lambda: g.replay(), steps)
+        batched_ms = timed(lambda: g.replay(), steps, "batched")
     t1 = time.time()
     clk = clocks.stop(t0, t1) if clocks else None
-    plain_ms = timed(plain_step, steps)
+    nf = len(frames)
+    plain_ms = timed(plain_step, steps, "plain", cmds=3 + 4 * nf, ms=50.0)
     # where the time goes: each stage alone, batched and frame by frame
     n_br = max(5, steps // 5)
     with torch.cuda.stream(stream):
-        b_tr = timed(lambda: L.lbl_batch_launch(b, L.LBL_STAGE_TRANSFORM, stream=stream), n_br)
-        b_lb = timed(lambda: L.lbl_batch_launch(b, L.LBL_STAGE_LABEL, stream=stream), n_br)
-    p_tr = timed(lambda: [frame_transform(f, d) for f, d in zip(frames, fr)], n_br)
+        b_tr = timed(lambda: L.lbl_batch_launch(b, L.LBL_STAGE_TRANSFORM, stream=stream), n_br, cmds=6)
+        b_lb = timed(lambda: L.lbl_batch_launch(b, L.LBL_STAGE_LABEL, stream=stream), n_br, cmds=8)
+    p_tr = timed(lambda: [frame_transform(f, d) for f, d in zip(frames, fr)], n_br, cmds=3 + nf, ms=50.0)
     p_lb = timed(lambda: [L.lbl_label(r, d["d_O"], f.P, d["d_L"], stream=stream)
-                          for f, r, d in zip(frames, rms, fr)], n_br)
+                          for f, r, d in zip(frames, rms, fr)], n_br, cmds=3 + 3 * nf, ms=50.0)
     entries = [L.lbl_roadmap_info(r)[4] if quad else f.nnz for f, r in zip(frames, rms)]
     L.lbl_batch_free(b)
     for r in rms:
@@ -764,6 +827,7 @@ def measure_batched(torch, L, frames, steps: int, warmup: int, algo: str, dist=N
                      + (2 * pyramid_word_bytes(f.P) * pyramid_words(f.agent.cells) if quad else 0)
                      for f, n in zip(frames, entries))
     return {"batched_ms": batched_ms, "plain_ms": plain_ms, "match": bool(match), "clk": clk, "tuning": tuning,
+            "gates": gates,
             "units": sum(f.n_edges * f.P for f in frames), "entries": int(sum(entries)), "bytes_step": bytes_step,
             "launches": 1 + int(packs) + int(quad) + label_classes,  # (pack,) transform, (pyramid,) labels
             "plain_launches": len(frames) * (3 if quad else 2),  # transform, (pyramid,) label per frame
@@ -784,7 +848,7 @@ def batched_summary(m: dict, frames, steps: int) -> dict:
             "plain_p50_ms": float(np.percentile(m["plain_ms"], 50)),
             "plain_p99_ms": float(np.percentile(m["plain_ms"], 99)),
             "batched_launches_per_step": m["launches"], "plain_launches_per_step": m["plain_launches"],
-            "stage_ms": m["stage_ms"], "tuning": m["tuning"]}
+            "stage_ms": m["stage_ms"], "tuning": m["tuning"], "enqueue_gates": m["gates"]}
 
 
 def run_batched(args, rank, world, local, dist, torch, L):
