@@ -364,6 +364,44 @@ int lbl_label(lbl_roadmap rm, const uint64_t *d_O, int32_t n_props, uint64_t *d_
               uint16_t *d_viol, const lbl_config *cfg, lbl_stream s);
 
 /*
+ * lbl_frame_transform_pyramid — lbl_frame_transform_words (Sec. 5, eq. 13)
+ * for the roadmap's agent grid that also builds, from the words it computes,
+ * the roadmap's per-frame quadtree pyramid: for every aligned block of 4^k
+ * consecutive cells (k <= 4) the OR of their words, i.e. eq. 10 over that
+ * block, which the quadtree rows gather (LBL_ALGO_QUAD).  On a z-order agent
+ * grid the pyramid is built inside the transform kernel (one launch, O not
+ * read back); on a row-major grid the transform and the pyramid are two
+ * launches.  lbl_label_pyramid then labels the frame from it.
+ *   rm       uploaded with LBL_UPLOAD_QUAD (LBL_EUNSUPPORTED otherwise, unless
+ *            the roadmap has no edges: then only O is written)
+ *   d_words  packed world words of lbl_pack_planes (LBL_PACKED_WORD_BYTES(n_props) each)
+ *   d_O      uint64[agent cells], written as by lbl_frame_transform_words;
+ *            may be NULL on a z-order agent grid (the words then exist only as
+ *            the pyramid's level 0)
+ * Same errors as lbl_frame_transform_words.  The pyramid is the roadmap's
+ * working memory: a quadtree lbl_label or another lbl_frame_transform_pyramid
+ * on this roadmap overwrites it, and calls on one roadmap must not overlap on
+ * the device.  Asynchronous on `s`.
+ */
+int lbl_frame_transform_pyramid(lbl_roadmap rm, const lbl_grid *world, const void *d_words, int32_t n_props,
+                                lbl_pose pose, uint64_t *d_O, lbl_stream s);
+
+/*
+ * lbl_label_pyramid — lbl_label's quadtree form (eq. 10 over each row's
+ * maximal quadtree blocks) gathering from the pyramid the last
+ * lbl_frame_transform_pyramid (or quadtree lbl_label) enqueued on this roadmap,
+ * so a frame is labeled without a pyramid launch.  Outputs, the fused monitor
+ * and `cfg` as in lbl_label; cfg->algo must be LBL_ALGO_AUTO or LBL_ALGO_QUAD
+ * (AUTO takes the quadtree configuration lbl_roadmap_autotune measured, if it
+ * chose the quadtree form).  LBL_EINVAL when no pyramid for n_props'
+ * word width (1, 2, 4 or 8 bytes) was enqueued on this roadmap.  The pyramid
+ * is read as the stream finds it: order this call after the transform that
+ * built it, on the same stream or behind an event.
+ */
+int lbl_label_pyramid(lbl_roadmap rm, int32_t n_props, uint64_t *d_L, lbl_monitor mon, uint64_t *d_next,
+                      uint16_t *d_viol, const lbl_config *cfg, lbl_stream s);
+
+/*
  * lbl_label_blocks_noalloc — the block-form labeling of lbl_label
  * (LBL_ALGO_BITTILE) for callers that cannot allocate device memory: planning
  * loops under real-time or safety rules that forbid allocation once the system

@@ -122,6 +122,22 @@ __global__ void __launch_bounds__(256) k_frame_z(const __grid_constant__ FrameIt
   if (idx < n) f.O[idx] = frame_word<WB>(f, idx);
 }
 
+// z-order grids with the quadtree pyramid: a CTA's 256 cells are one block
+// of the pyramid's top level, so the words each thread computes go to O (when
+// asked for) and to the pyramid's level 0, and the CTA ORs levels 1-4 from the
+// same registers: no O re-read and no pyramid launch before the labels.
+template <int WB, typename T>
+__global__ void __launch_bounds__(256) k_frame_z_pyramid(const __grid_constant__ FrameItem f, uint32_t n,
+                                                         const __grid_constant__ QuadOffsets off, T *__restrict__ pyr) {
+  __shared__ uint64_t wsum[kThreads / 32];
+  pdl_wait();
+  pdl_trigger();
+  const uint32_t idx = blockIdx.x * 256u + threadIdx.x;
+  const uint64_t v = idx < n ? frame_word<WB>(f, idx) : 0ull;
+  if (f.O && idx < n) f.O[idx] = v;
+  quad_pyramid_of<T>(v, n, off, pyr, blockIdx.x, wsum);
+}
+
 // Row-major grids: a warp per 8 x 4 tile of one slab (grid: x tiles / 8, y
 // tiles, slabs), so under any rotation a warp's world reads stay within a few
 // rows (a warp along one row would read a rotated line of up to 32 world
@@ -298,6 +314,38 @@ cudaError_t launch_frame_transform(const FrameItem &f, cudaStream_t s) {
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
+}
+
+template <int WB, typename T>
+static cudaError_t transform_pyramid_launch(const FrameItem &f, const QuadOffsets &off, void *pyr, cudaStream_t s) {
+  const uint32_t n = static_cast<uint32_t>(f.aw) * static_cast<uint32_t>(f.ah) * static_cast<uint32_t>(f.ad);
+  return pdl_launch(k_frame_z_pyramid<WB, T>, dim3((n + 255u) / 256u), dim3(256), s, f, n, off, static_cast<T *>(pyr));
+}
+
+template <int WB>
+static cudaError_t transform_pyramid_width(const FrameItem &f, const QuadOffsets &off, int pyr_bytes, void *pyr,
+                                           cudaStream_t s) {
+  using W = typename WordOf<WB>::T;
+  if (pyr_bytes == WB) return transform_pyramid_launch<WB, W>(f, off, pyr, s);
+  if (pyr_bytes == 8) return transform_pyramid_launch<WB, uint64_t>(f, off, pyr, s);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_frame_transform_pyramid(const FrameItem &f, const QuadOffsets &off, int pyr_bytes, void *pyr,
+                                           cudaStream_t s) {
+  const int64_t n = static_cast<int64_t>(f.aw) * f.ah * f.ad;
+  if (n == 0) return cudaSuccess;
+  if (n >= (1ll << 31) || f.plane_cells >= (1ll << 31)) return cudaErrorInvalidValue;  // grids are checked on the host
+  if (f.order != LBL_ORDER_MORTON || !f.words) return cudaErrorInvalidValue;
+  cudaError_t e;
+  switch (f.word_bytes) {
+    case 1: e = transform_pyramid_width<1>(f, off, pyr_bytes, pyr, s); break;
+    case 2: e = transform_pyramid_width<2>(f, off, pyr_bytes, pyr, s); break;
+    case 4: e = transform_pyramid_width<4>(f, off, pyr_bytes, pyr, s); break;
+    case 8: e = transform_pyramid_width<8>(f, off, pyr_bytes, pyr, s); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <int WB>

@@ -293,12 +293,15 @@ __global__ void __launch_bounds__(kFrontWarps * 32, 1) k_label_front(const int64
                                                                     const int32_t *__restrict__ perm) {
   __shared__ EpiSmem sm;
   __shared__ int next_chunk;
-  pdl_wait();
+  // The monitor tables are written once, when the monitor is created, so
+  // they are loaded before waiting for the kernel before (the frame
+  // transform), while its last CTAs run.
   if (threadIdx.x == 0) next_chunk = 0;
   if (EPI)
     load_tables(mon, sm);  // contains __syncthreads
   else
     __syncthreads();
+  pdl_wait();
   const uint64_t pol = evict_first_policy();
   const int lane = threadIdx.x & 31;
   const int64_t r0 = __ldg(part + static_cast<int64_t>(blockIdx.x) * stride);
@@ -424,39 +427,14 @@ __global__ void __launch_bounds__(kThreads, stream_min_blocks<U>()) k_label_batc
   }
 }
 
-// Quadtree pyramid of O for the quadtree form (compressed A): level k holds,
-// for every block of 4^k consecutive cells in the grid's cell order that lies
-// wholly inside the grid, the OR of their words; level 0 is O itself.  Word of
-// block b at level k: pyr[off.at[k] + b].  One CTA covers the 256 consecutive
-// cells of top-level block `blk`: levels 1-2 (4 and 16 cells) by butterfly
-// shuffles inside each warp, levels 3-4 (64 and 256 cells) from the eight
-// 32-cell warp words.
+// Quadtree pyramid of O (quad_pyramid_of): one CTA per 256-cell block of the
+// top level, each thread loading the word of its cell.
 template <typename T>
 __device__ __forceinline__ void quad_pyramid_block(const uint64_t *__restrict__ O, int64_t cells,
                                                    const QuadOffsets &off, T *__restrict__ pyr, int64_t blk,
                                                    uint64_t *wsum) {
-  static_assert(kThreads == 256 && kQuadLevels == 4, "one CTA = one block of the top level");
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t i = blk * kThreads + threadIdx.x;
-  uint64_t v = i < cells ? __ldg(O + i) : 0ull;
-  if (i < cells) pyr[i] = static_cast<T>(v);
-  v = or_xor(or_xor(v, 1), 2);  // every lane: OR of its aligned 4-cell block
-  if ((lane & 3) == 0 && (i >> 2) < (cells >> 2)) pyr[off.at[1] + (i >> 2)] = static_cast<T>(v);
-  v = or_xor(or_xor(v, 4), 8);  // 16-cell block
-  if ((lane & 15) == 0 && (i >> 4) < (cells >> 4)) pyr[off.at[2] + (i >> 4)] = static_cast<T>(v);
-  v = or_xor(v, 16);  // the warp's 32 cells
-  if (lane == 0) wsum[wid] = v;
-  __syncthreads();
-  if (threadIdx.x < 4) {  // 64-cell blocks: warps (2t, 2t+1)
-    const int t = threadIdx.x;
-    const int64_t b = blk * 4 + t;
-    if (b < (cells >> 6)) pyr[off.at[3] + b] = static_cast<T>(wsum[2 * t] | wsum[2 * t + 1]);
-  } else if (threadIdx.x == 4) {  // the 256-cell block
-    uint64_t a = 0;
-#pragma unroll
-    for (int w = 0; w < kThreads / 32; ++w) a |= wsum[w];
-    if (blk < (cells >> 8)) pyr[off.at[4] + blk] = static_cast<T>(a);
-  }
+  quad_pyramid_of<T>(i < cells ? __ldg(O + i) : 0ull, cells, off, pyr, blk, wsum);
 }
 
 template <typename T>
@@ -1267,8 +1245,10 @@ cudaError_t launch_label_quad(const Roadmap &rm, const uint64_t *O, int32_t P, u
                               const MonitorTables *mon, int depth, cudaStream_t s, int front_chunk) {
   if (rm.E == 0) return cudaSuccess;
   const int wb = quad_word_bytes(rm, P);
-  cudaError_t e = launch_quad_pyramid(rm, O, wb, rm.pyr, s);
-  if (e != cudaSuccess) return e;
+  if (O) {
+    cudaError_t e = launch_quad_pyramid(rm, O, wb, rm.pyr, s);
+    if (e != cudaSuccess) return e;
+  }
   StreamRows r{rm.qd_rowptr, rm.qd_idx, rm.qd_part, rm.qd_part_ctas, rm.E, rm.n_qd, rm.qd_perm};
   r.front_chunk = front_chunk;
   return launch_label_rows(r, rm.pyr, wb, P, L, mon, depth, rm.num_sms, s);

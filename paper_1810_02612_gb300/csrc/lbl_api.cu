@@ -534,6 +534,46 @@ int roadmap_finish(lbl_roadmap_s *rm, uint32_t flags, cudaStream_t st) {
 
 }  // namespace lbl
 
+namespace lbl {
+
+int transform_pyramid(const lbl_grid *world, const void *d_words, int32_t n_props, lbl_pose pose, const Roadmap &rm,
+                      uint64_t *d_O, void *pyr, cudaStream_t st) {
+  const lbl_grid *agent = &rm.agent;
+  if (!valid_grid(world, "frame transform (world)", false)) return LBL_EINVAL;
+  if (n_props < 0 || n_props > 64) {
+    set_error("frame transform (pyramid): n_props = %d outside 0..64", n_props);
+    return LBL_EINVAL;
+  }
+  const bool z = agent->order == LBL_ORDER_MORTON;
+  if (!d_words || (!d_O && !z)) {
+    set_error("frame transform (pyramid): NULL buffer (row-major agent grids need O)");
+    return LBL_EINVAL;
+  }
+  if (reinterpret_cast<uintptr_t>(d_words) % static_cast<uintptr_t>(packed_word_bytes(n_props)) ||
+      reinterpret_cast<uintptr_t>(d_O) % 8u) {
+    set_error("frame transform (pyramid): words or O not aligned to their width");
+    return LBL_EINVAL;
+  }
+  FrameMap m;
+  if (!frame_map(*world, *agent, pose, &m)) return LBL_EINVAL;
+  FrameItem f = frame_item(m, *world, *agent, nullptr, n_props, d_O, 0);
+  f.words = d_words;
+  f.word_bytes = packed_word_bytes(n_props);
+  f.wmask = n_props >= 64 ? ~0ull : ((1ull << n_props) - 1ull);
+  const int wb = quad_word_bytes(rm, n_props);
+  cudaError_t e;
+  if (z) {
+    e = launch_frame_transform_pyramid(f, rm.qd_off, wb, pyr, st);
+  } else {  // row-major cells: the pyramid's blocks are row runs, not the transform's tiles
+    e = launch_frame_transform(f, st);
+    if (e == cudaSuccess) e = launch_quad_pyramid(rm, d_O, wb, pyr, st);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "frame transform (pyramid): launch");
+  return LBL_OK;
+}
+
+}  // namespace lbl
+
 extern "C" {
 
 const char *lbl_last_error(void) { return g_err.c_str(); }
@@ -750,6 +790,83 @@ int lbl_frame_transform_words(const lbl_grid *world, const void *d_words, int32_
   return LBL_OK;
 }
 
+int lbl_frame_transform_pyramid(lbl_roadmap rm, const lbl_grid *world, const void *d_words, int32_t n_props,
+                                lbl_pose pose, uint64_t *d_O, lbl_stream s) {
+  g_err.clear();
+  if (!rm) {
+    set_error("frame transform (pyramid): NULL roadmap");
+    return LBL_EINVAL;
+  }
+  if (!same_device(rm->device)) return LBL_EINVAL;
+  if (rm->E > 0 && !rm->has_qd) {
+    set_error("frame transform (pyramid): the roadmap has no quadtree form (LBL_UPLOAD_QUAD)");
+    return LBL_EUNSUPPORTED;
+  }
+  const cudaStream_t st = reinterpret_cast<cudaStream_t>(s);
+  if (rm->E == 0) {  // no rows, no pyramid: the transform alone, if O is wanted
+    if (!d_O) return valid_grid(world, "frame transform (world)", false) ? LBL_OK : LBL_EINVAL;
+    return lbl_frame_transform_words(world, d_words, n_props, pose, &rm->agent, d_O, s);
+  }
+  const int rc = transform_pyramid(world, d_words, n_props, pose, *rm, d_O, rm->pyr, st);
+  if (rc != LBL_OK) return rc;
+  rm->pyr_built_bytes = quad_word_bytes(*rm, n_props);
+  rm->uses->note(st);
+  return LBL_OK;
+}
+
+int lbl_label_pyramid(lbl_roadmap rm, int32_t n_props, uint64_t *d_L, lbl_monitor mon, uint64_t *d_next,
+                      uint16_t *d_viol, const lbl_config *cfg, lbl_stream s) {
+  g_err.clear();
+  if (!rm) {
+    set_error("label (pyramid): NULL roadmap");
+    return LBL_EINVAL;
+  }
+  if (n_props < 0 || n_props > 64) {
+    set_error("label (pyramid): n_props = %d outside 0..64", n_props);
+    return LBL_EINVAL;
+  }
+  if (rm->E > 0 && !d_L) {
+    set_error("label (pyramid): NULL L");
+    return LBL_EINVAL;
+  }
+  if (mon && rm->E > 0 && (!d_next || !d_viol)) {
+    set_error("label (pyramid): monitor given but next/viol is NULL");
+    return LBL_EINVAL;
+  }
+  if (!same_device(rm->device)) return LBL_EINVAL;
+  if (mon && mon->device != rm->device) {
+    set_error("label (pyramid): monitor and roadmap live on different devices");
+    return LBL_EINVAL;
+  }
+  const int algo = cfg ? cfg->algo : LBL_ALGO_AUTO;
+  if (algo != LBL_ALGO_AUTO && algo != LBL_ALGO_QUAD) {
+    set_error("label (pyramid): labels from the pyramid are the quadtree form (algo %d asked)", algo);
+    return LBL_EINVAL;
+  }
+  if (rm->E == 0) return LBL_OK;
+  if (rm->pyr_built_bytes == 0 || rm->pyr_built_bytes != quad_word_bytes(*rm, n_props)) {
+    set_error("label (pyramid): no pyramid for %d propositions on this roadmap (lbl_frame_transform_pyramid first)",
+              n_props);
+    return LBL_EINVAL;
+  }
+  lbl_config tuned_cfg;
+  if (algo == LBL_ALGO_AUTO) {  // the measured quadtree configuration, else the form's defaults
+    cfg = nullptr;
+    if (rm->tuned_valid[n_props] && rm->tuned[n_props].algo == LBL_ALGO_QUAD) {
+      tuned_cfg = rm->tuned[n_props];
+      cfg = &tuned_cfg;
+    }
+  }
+  MonitorTables t{};
+  if (mon) t = tables_of(*mon, d_next, d_viol);
+  const cudaStream_t st = reinterpret_cast<cudaStream_t>(s);
+  const int rc = quad_label(rm, nullptr, n_props, d_L, mon ? &t : nullptr, cfg, st);
+  if (rc != LBL_OK) return rc;
+  rm->uses->note(st);
+  if (mon) mon->uses->note(st);
+  return LBL_OK;
+}
+
 int lbl_monitor_create(int32_t n_states, int32_t m, const uint8_t *relbits, const uint8_t *delta, int32_t reject,
                        lbl_monitor *out) {
   g_err.clear();
@@ -859,6 +976,39 @@ int lbl_monitor_step(lbl_monitor mon, const uint64_t *d_L, int64_t n, uint64_t *
 
 namespace lbl {
 
+// The quadtree form's launch (lbl_label, lbl_label_pyramid): the partition
+// for the requested grid, the pyramid of d_O (none when d_O is NULL: the rows
+// gather from the pyramid the frame transform built), then the stream over
+// the quadtree rows.
+int quad_label(lbl_roadmap rm, const uint64_t *d_O, int32_t n_props, uint64_t *d_L, const MonitorTables *mt,
+               const lbl_config *cfg, cudaStream_t st) {
+  const int ctas = cfg ? cfg->ctas_per_sm : 0;
+  const int qpipe = cfg ? cfg->pipeline : 0;
+  if (qpipe != 0 && qpipe != LBL_PIPE_REGISTERS && qpipe != LBL_PIPE_FRONT) {
+    set_error("label: pipeline %d does not apply to the quadtree form", qpipe);
+    return LBL_EINVAL;
+  }
+  const int depth = (cfg && cfg->depth) ? cfg->depth : kQuadDepth;
+  cudaError_t e;
+  if (rm->E > 0) {
+    const int occ = stream_ctas_per_sm(depth);
+    const int want = ctas > 0 ? std::min(ctas, occ) : occ;
+    if (want != rm->qd_part_ctas) {
+      const int64_t W = static_cast<int64_t>(rm->num_sms) * want * (kThreads / 32);
+      if ((e = launch_partition_into(rm->qd_rowptr, rm->E, W, rm->qd_part, st)) != cudaSuccess)
+        return cuda_fail(e, "label: quadtree partition");
+      rm->qd_part_ctas = want;
+    }
+  }
+  // pipeline: 0 = the moving front on large roadmaps (by size), LBL_PIPE_FRONT
+  // = the front whatever the size, anything else = the per-warp stream
+  const int fchunk = qpipe == 0 ? -1 : qpipe == LBL_PIPE_FRONT ? std::max(front_chunk_for(rm->E, rm->num_sms), 8) : 0;
+  e = launch_label_quad(*rm, d_O, n_props, d_L, mt, depth, st, fchunk);
+  if (e != cudaSuccess) return cuda_fail(e, "label: launch");
+  if (d_O && rm->E > 0) rm->pyr_built_bytes = quad_word_bytes(*rm, n_props);
+  return LBL_OK;
+}
+
 int label_impl(lbl_roadmap rm, const uint64_t *d_O, int32_t n_props, uint64_t *d_L, lbl_monitor mon,
                uint64_t *d_next, uint16_t *d_viol, const lbl_config *cfg, cudaStream_t st) {
   if (!rm) {
@@ -940,27 +1090,9 @@ int label_impl(lbl_roadmap rm, const uint64_t *d_O, int32_t n_props, uint64_t *d
     }
     e = launch_label_sector(*rm, d_O, n_props, d_L, mon ? &t : nullptr, depth, st);
   } else if (algo == LBL_ALGO_QUAD) {
-    const int qpipe = cfg ? cfg->pipeline : 0;
-    if (qpipe != 0 && qpipe != LBL_PIPE_REGISTERS && qpipe != LBL_PIPE_FRONT) {
-      set_error("label: pipeline %d does not apply to the quadtree form", qpipe);
-      return LBL_EINVAL;
-    }
-    const int depth = (cfg && cfg->depth) ? cfg->depth : kQuadDepth;
-    if (rm->E > 0) {
-      const int occ = stream_ctas_per_sm(depth);
-      const int want = ctas > 0 ? std::min(ctas, occ) : occ;
-      if (want != rm->qd_part_ctas) {
-        const int64_t W = static_cast<int64_t>(rm->num_sms) * want * (kThreads / 32);
-        if ((e = launch_partition_into(rm->qd_rowptr, rm->E, W, rm->qd_part, st)) != cudaSuccess)
-          return cuda_fail(e, "label: quadtree partition");
-        rm->qd_part_ctas = want;
-      }
-    }
-    // pipeline: 0 = the moving front on large roadmaps (by size), LBL_PIPE_FRONT
-    // = the front whatever the size, anything else = the per-warp stream
-    const int pipe = cfg ? cfg->pipeline : 0;
-    const int fchunk = pipe == 0 ? -1 : pipe == LBL_PIPE_FRONT ? std::max(front_chunk_for(rm->E, rm->num_sms), 8) : 0;
-    e = launch_label_quad(*rm, d_O, n_props, d_L, mon ? &t : nullptr, depth, st, fchunk);
+    const int rc = quad_label(rm, d_O, n_props, d_L, mon ? &t : nullptr, cfg, st);
+    if (rc != LBL_OK) return rc;
+    e = cudaSuccess;
   } else if (early || lpe > 0) {
     // lanes-per-edge form (one edge per lane group; supports early exit)
     e = launch_label_csr(*rm, d_O, n_props, d_L, mon ? &t : nullptr, resolve_lpe(*rm, cfg), early, ctas, st);

@@ -191,6 +191,45 @@ struct QuadOffsets {
   int64_t at[kQuadLevels + 1];  // first pyramid word of each level
 };
 
+// Quadtree pyramid of O (compressed A): level k holds, for every block of 4^k
+// consecutive cells in the grid's cell order that lies wholly inside the
+// grid, the OR of their words; level 0 is O itself.  Word of block b at level
+// k: pyr[off.at[k] + b].  One CTA of kThreads covers the 256 consecutive
+// cells of top-level block `blk`, thread t holding v = the word of cell
+// blk * 256 + t (0 past the grid): levels 1-2 (4 and 16 cells) by butterfly
+// shuffles inside each warp, levels 3-4 (64 and 256 cells) from the eight
+// 32-cell warp words in `wsum`.  Used by the pyramid kernels (which read v
+// from O) and by the frame transform that builds the pyramid of the words it
+// computes.
+template <typename T>
+__device__ __forceinline__ void quad_pyramid_of(uint64_t v, int64_t cells, const QuadOffsets &off,
+                                                T *__restrict__ pyr, int64_t blk, uint64_t *wsum) {
+  static_assert(kThreads == 256 && kQuadLevels == 4, "one CTA = one block of the top level");
+  constexpr unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t i = blk * kThreads + threadIdx.x;
+  if (i < cells) pyr[i] = static_cast<T>(v);
+  v |= __shfl_xor_sync(full, v, 1);
+  v |= __shfl_xor_sync(full, v, 2);  // every lane: OR of its aligned 4-cell block
+  if ((lane & 3) == 0 && (i >> 2) < (cells >> 2)) pyr[off.at[1] + (i >> 2)] = static_cast<T>(v);
+  v |= __shfl_xor_sync(full, v, 4);
+  v |= __shfl_xor_sync(full, v, 8);  // 16-cell block
+  if ((lane & 15) == 0 && (i >> 4) < (cells >> 4)) pyr[off.at[2] + (i >> 4)] = static_cast<T>(v);
+  v |= __shfl_xor_sync(full, v, 16);  // the warp's 32 cells
+  if (lane == 0) wsum[wid] = v;
+  __syncthreads();
+  if (threadIdx.x < 4) {  // 64-cell blocks: warps (2t, 2t+1)
+    const int t = threadIdx.x;
+    const int64_t b = blk * 4 + t;
+    if (b < (cells >> 6)) pyr[off.at[3] + b] = static_cast<T>(wsum[2 * t] | wsum[2 * t + 1]);
+  } else if (threadIdx.x == 4) {  // the 256-cell block
+    uint64_t a = 0;
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; ++w) a |= wsum[w];
+    if (blk < (cells >> 8)) pyr[off.at[4] + blk] = static_cast<T>(a);
+  }
+}
+
 // One item of a batched pyramid launch: O of a frame -> that frame's pyramid.
 struct PyrItem {
   const uint64_t *O;
@@ -275,6 +314,7 @@ struct Roadmap {
   QuadOffsets qd_off{};
   int64_t pyr_words = 0;
   uint64_t *pyr = nullptr;      // per-frame pyramid (working memory)
+  int pyr_built_bytes = 0;      // word width of the pyramid last enqueued into `pyr` (0: none yet)
   // dense tensor-core form (optional): edges in locality order in tiles of 128,
   // per tile the K-blocks of 128 cells its rows touch, as 128 x 128 bit
   // matrices (16 bytes per row); per-frame B operand as working memory
@@ -346,6 +386,11 @@ FrameItem frame_item(const FrameMap &m, const lbl_grid &W, const lbl_grid &A, co
                      uint64_t *O, int64_t cell0);
 
 cudaError_t launch_frame_transform(const FrameItem &f, cudaStream_t s);
+// z-order agent grids, packed world words: the transform (O written unless
+// f.O is NULL) and the quadtree pyramid of its words (pyr_bytes-wide words at
+// `off`) in one kernel
+cudaError_t launch_frame_transform_pyramid(const FrameItem &f, const QuadOffsets &off, int pyr_bytes, void *pyr,
+                                           cudaStream_t s);
 cudaError_t launch_pack_planes(const PackItem &it, cudaStream_t s);
 cudaError_t launch_pack_batch(const PackTable &tab, cudaStream_t s);
 bool pack_vec_ok(const PackItem &it);
@@ -381,6 +426,7 @@ cudaError_t launch_label_mma(const Roadmap &rm, const uint64_t *O, int32_t P, ui
 int front_chunk_for(int64_t E, int num_sms);
 // pyramid of O into `pyr` (rm.pyr, or a buffer of rm.pyr_words 64-bit words owned elsewhere)
 cudaError_t launch_quad_pyramid(const Roadmap &rm, const uint64_t *O, int word_bytes, void *pyr, cudaStream_t s);
+// O NULL: label from rm.pyr as it stands (built by the frame transform)
 cudaError_t launch_label_quad(const Roadmap &rm, const uint64_t *O, int32_t P, uint64_t *L,
                                 const MonitorTables *mon, int depth, cudaStream_t s, int front_chunk = -1);
 cudaError_t launch_quad_pyramid_batch(const PyrTable &tab, cudaStream_t s);
@@ -434,8 +480,15 @@ void free_roadmap(Roadmap *rm);
 bool valid_grid(const lbl_grid *g, const char *name, bool need_order);
 int device_sms(int dev);    // SM count (cached per device)
 bool same_device(int dev);  // the current device is `dev` (else sets the error)
+// lbl_frame_transform_pyramid into an explicit pyramid buffer (a roadmap's or
+// a session's, pyr_words of rm): status code; O may be NULL on z-order grids
+int transform_pyramid(const lbl_grid *world, const void *d_words, int32_t n_props, lbl_pose pose, const Roadmap &rm,
+                      uint64_t *d_O, void *pyr, cudaStream_t st);
 void clear_error();         // empty lbl_last_error at the start of an entry point
 MonitorTables tables_of(const Monitor &mon, uint64_t *next, uint16_t *viol);
+// the quadtree form's labeling (d_O NULL: from the pyramid already built)
+int quad_label(lbl_roadmap_s *rm, const uint64_t *d_O, int32_t n_props, uint64_t *d_L, const MonitorTables *mt,
+               const lbl_config *cfg, cudaStream_t st);
 // lbl_label's body: argument checks, form resolution, re-partitioning, launch
 int label_impl(lbl_roadmap rm, const uint64_t *d_O, int32_t n_props, uint64_t *d_L, lbl_monitor mon,
                uint64_t *d_next, uint16_t *d_viol, const lbl_config *cfg, cudaStream_t st);

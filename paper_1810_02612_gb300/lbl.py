@@ -58,7 +58,8 @@ EXPORTS = (
     "lbl_roadmap_status",
     "lbl_frame_transform", "lbl_pack_planes", "lbl_frame_transform_words",
     "lbl_monitor_create", "lbl_monitor_free", "lbl_monitor_step",
-    "lbl_label", "lbl_label_blocks_noalloc", "lbl_roadmap_autotune", "lbl_mma_probe",
+    "lbl_label", "lbl_frame_transform_pyramid", "lbl_label_pyramid", "lbl_label_blocks_noalloc",
+    "lbl_roadmap_autotune", "lbl_mma_probe",
     "lbl_session_create", "lbl_session_run", "lbl_session_free",
     "lbl_batch_create", "lbl_batch_set_frames", "lbl_batch_launch", "lbl_batch_free", "lbl_batch_autotune",
     "lbl_server_create", "lbl_server_submit", "lbl_server_wait", "lbl_server_stats", "lbl_server_free",
@@ -139,6 +140,8 @@ def load(build_if_needed: bool = True):
         "lbl_monitor_free": (ctypes.c_int, [p]),
         "lbl_monitor_step": (ctypes.c_int, [p, p, i64, p, p, p]),
         "lbl_label": (ctypes.c_int, [p, p, i32, p, p, p, p, ctypes.POINTER(lbl_config), p]),
+        "lbl_frame_transform_pyramid": (ctypes.c_int, [p, G, p, i32, lbl_pose, p, p]),
+        "lbl_label_pyramid": (ctypes.c_int, [p, i32, p, p, p, p, ctypes.POINTER(lbl_config), p]),
         "lbl_label_blocks_noalloc": (ctypes.c_int, [p, p, p, i64, p, i64, i32, p, p]),
         "lbl_roadmap_autotune": (ctypes.c_int, [p, p, i32, p, p, p, p, i32, ctypes.POINTER(lbl_config), p]),
         "lbl_mma_probe": (ctypes.c_int, [i32, i32, i32, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32)]),
@@ -382,6 +385,20 @@ def lbl_label(rm, d_O, n_props: int, d_L, mon=None, d_next=None, d_viol=None, cf
     _check(load().lbl_label(rm, _dev(d_O, "uint64", "O"), int(n_props), _dev(d_L, "uint64", "L"), mon,
                             _dev(d_next, "uint64", "next"), _dev(d_viol, "uint16", "viol"), _cfg(cfg),
                             _stream(stream)))
+
+
+def lbl_frame_transform_pyramid(rm, world, d_words, n_props: int, pose, d_O=None, stream=None) -> None:
+    """The packed-word frame transform that also builds the roadmap's quadtree
+    pyramid of its words (d_O may be None on z-order agent grids)."""
+    w = _grid(world)
+    _check(load().lbl_frame_transform_pyramid(rm, ctypes.byref(w), _words(d_words, n_props, "words"), int(n_props),
+                                              _pose(pose), _dev(d_O, "uint64", "O"), _stream(stream)))
+
+
+def lbl_label_pyramid(rm, n_props: int, d_L, mon=None, d_next=None, d_viol=None, cfg=None, stream=None) -> None:
+    """Quadtree-form labels from the pyramid lbl_frame_transform_pyramid built."""
+    _check(load().lbl_label_pyramid(rm, int(n_props), _dev(d_L, "uint64", "L"), mon, _dev(d_next, "uint64", "next"),
+                                    _dev(d_viol, "uint16", "viol"), _cfg(cfg), _stream(stream)))
 
 
 def lbl_label_blocks_noalloc(d_block_rowptr, d_block_id, d_block_mask, n_edges: int, d_O, n_cells: int,
