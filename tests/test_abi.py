@@ -95,6 +95,17 @@ def test_null_handles_are_rejected_or_ignored():
         L.lbl_label(None, 0, 1, 0, stream=0)
 
 
+def test_pyramid_entry_points_refuse_a_null_roadmap():
+    """The transform that builds the pyramid and the labels from it need a
+    roadmap; both refuse NULL with LBL_EINVAL before any device work."""
+    world = B.lbl_grid(4, 4, 0.3, 0.0, 0.0, 0)
+    for call in (lambda: L.lbl_frame_transform_pyramid(None, world, 8192, 4, (0.0, 0.0, 0.0), 4096, stream=0),
+                 lambda: L.lbl_label_pyramid(None, 4, 8192, stream=0)):
+        with pytest.raises(L.LblError) as ei:
+            call()
+        assert ei.value.code == L.LBL_EINVAL and "NULL roadmap" in L.lbl_last_error()
+
+
 def test_binding_refuses_host_arrays_for_device_arguments():
     g = B.lbl_grid(8, 8, 1.0, 0.0, 0.0, 0)
     with pytest.raises(TypeError):
