@@ -1,6 +1,7 @@
 """Parity at full size, in the configuration bench.py times: the 1M-edge,
-64-proposition workload with the fused monitor through the quadtree form (and
-the CSR form), the 2^21-cell 2-D and (x, y, tau) workloads, the 100k-edge
+64-proposition workload with the fused monitor through the quadtree form (the
+transform building the pyramid and the labels from it, as timed, and through
+lbl_label; and the CSR form), the 2^21-cell 2-D and (x, y, tau) workloads, the 100k-edge
 driving workload and the 64-frame batch, all with the bench's seeds.
 
 Every edge of every case is compared with the oracle, element by element: the
@@ -80,6 +81,37 @@ def test_large_1m_edges_64_props_with_monitor():
     wl = synth.make("large", seed=0, threads=0)
     assert wl.n_edges == 1_000_000 and wl.P == 64 and wl.monitor is not None
     _check_workload(wl, QUAD_CFGS + [dict(algo=L.LBL_ALGO_CSR), dict(algo=L.LBL_ALGO_MMA)])
+
+
+def test_large_1m_edges_transform_building_the_pyramid():
+    """The step bench.py times on this workload: packed planes, the frame
+    transform that builds the quadtree pyramid, and the moving front gathering
+    from it with the fused monitor, at two poses; the transform's O and every
+    edge's label, next states and violations equal the oracle."""
+    wl = synth.make("large", seed=0, threads=0)
+    m = wl.monitor
+    rm = L.lbl_roadmap_upload(wl.agent, wl.rowptr, wl.colidx, flags=L.LBL_UPLOAD_QUAD)
+    hm = L.lbl_monitor_create(m.n_states, m.m, m.relbits, m.delta, m.reject)
+    try:
+        words = torch.empty(wl.world.cells, dtype=getattr(torch, L.packed_word_dtype(wl.P)), device="cuda")
+        L.lbl_pack_planes(wl.world, torch.from_numpy(wl.planes).cuda(), wl.P, words)
+        O = torch.empty(wl.agent.cells, dtype=torch.uint64, device="cuda")
+        out = torch.empty(wl.n_edges, dtype=torch.uint64, device="cuda")
+        nxt = torch.empty(wl.n_edges, dtype=torch.uint64, device="cuda")
+        viol = torch.empty(wl.n_edges, dtype=torch.uint16, device="cuda")
+        for pose in (wl.pose, synth.random_pose(np.random.default_rng(72), wl.world)):
+            L.lbl_frame_transform_pyramid(rm, wl.world, words, wl.P, pose, O)
+            L.lbl_label_pyramid(rm, wl.P, out, hm, nxt, viol)
+            torch.cuda.synchronize()
+            want_O = oracle.frame_transform(wl.world, wl.planes, pose, wl.agent)
+            assert np.array_equal(O.cpu().numpy(), want_O)
+            want = oracle.label(wl.rowptr, wl.colidx, want_O, wl.P, threads=THREADS)
+            wn, wv = oracle.monitor(m.n_states, m.m, m.relbits, m.delta, m.reject, want)
+            assert np.array_equal(out.cpu().numpy(), want)
+            assert np.array_equal(nxt.cpu().numpy(), wn) and np.array_equal(viol.cpu().numpy(), wv)
+    finally:
+        L.lbl_monitor_free(hm)
+        L.lbl_roadmap_free(rm)
 
 
 def test_large_1m_edges_session_frames_back_to_back():
