@@ -292,7 +292,10 @@ __global__ void __launch_bounds__(kThreads, stream_min_blocks<U>()) k_label_stre
 // own entries instead 0.2650 ms.  With 1-byte pyramid words (the paper frames,
 // ~10 KB chunks) it was neutral (2^21-cell 2-D frame 0.2528 vs 0.2525-0.2534
 // ms) or slower ((x, y, tau) frame 0.3034 vs 0.3065-0.3098 ms), so only 8-byte
-// pyramid words prefetch.
+// pyramid words prefetch.  The same warp also asks L2 for the next chunk's
+// entries of the row order (`perm`, read when a window of labels is written
+// out): 1M-edge call 0.2464 -> 0.2459 ms, paper frame unchanged.  (The
+// next chunk's last row pointer, likewise: no change, 0.2457 ms.)
 constexpr int kFrontWarps = 32;
 constexpr int kFrontTailChunk = 8;
 constexpr int kFrontPrefetchBytes = 10240;
@@ -336,6 +339,10 @@ __global__ void __launch_bounds__(kFrontWarps * 32, 1) k_label_front(const int64
     }
     if (e_beg >= r1) return;  // warp-uniform
     const int64_t p0 = __ldg(rowptr + e_beg), p1 = __ldg(rowptr + e_end);
+    if (perm && lane < 2) {  // the next chunk's caller-order indices into L2 (its first and last)
+      const int32_t *q = perm + min(e_end + lane * (e_end - e_beg), r1 - 1);
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(q));
+    }
     if (pf_bytes > 0 && lane == 0) {  // the start of the next chunk's index stream into L2
       const int64_t a = (p1 * 4 + 15) & ~static_cast<int64_t>(15);
       const int64_t b = min(p1 * 4 + pf_bytes, idx_bytes) & ~static_cast<int64_t>(15);
