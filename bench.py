@@ -567,10 +567,14 @@ def main():
                 L.LBL_ALGO_QUAD: "quad", L.LBL_ALGO_MMA: "mma"}.get(tuned["algo"], "csr")
     else:
         used = args.algo
-    if auto_transform and used == "quad" and wl.agent.order == synth.MORTON and P > 0:
+    # the transform builds the pyramid in one launch on z-order grids and on 2-D
+    # row-major grids of whole 16 x 16 tiles (the quadtree form's tiled order)
+    one_launch = (wl.agent.order == synth.MORTON
+                  or (wl.agent.d <= 1 and wl.agent.w % 16 == 0 and wl.agent.h % 16 == 0))
+    if auto_transform and used == "quad" and one_launch and P > 0:
         args.transform = "pyramid"  # measured at least as fast as either transform + pyramid launch
-    if args.transform == "pyramid" and (used != "quad" or wl.agent.order != synth.MORTON):
-        raise SystemExit("--transform pyramid needs the quadtree form on a z-order agent grid")
+    if args.transform == "pyramid" and (used != "quad" or not one_launch):
+        raise SystemExit("--transform pyramid needs the quadtree form on a z-order or tiled row-major agent grid")
     launches_per_step = (2 + (1 if used in ("bittile", "quad", "mma") and args.transform != "pyramid" else 0)
                          + (1 if args.transform in ("packed", "pyramid") else 0))  # + planes / pyramid / B, packing
 

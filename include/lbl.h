@@ -94,8 +94,12 @@ typedef struct {
                               (compressed A): a row is the union of blocks of 4^k
                               consecutive cells of the cell order (k <= 4) that
                               start at a multiple of 4^k (in z-order: the
-                              2^k x 2^k squares of the quadtree; in row-major
-                              order: aligned runs).  Per frame the library ORs O
+                              2^k x 2^k squares of the quadtree).  On a 2-D
+                              row-major grid whose sides are multiples of 16
+                              the blocks follow a tiled order (16 x 16 tiles in
+                              row-major order, z-order inside each tile), so
+                              they are squares too; other row-major grids use
+                              aligned runs of a grid row.  Per frame the library ORs O
                               over every such block (a pyramid of ~4/3 words per
                               cell) and each edge ORs one word per block.  Exact:
                               OR is associative and idempotent */
@@ -369,15 +373,17 @@ int lbl_label(lbl_roadmap rm, const uint64_t *d_O, int32_t n_props, uint64_t *d_
  * the roadmap's per-frame quadtree pyramid: for every aligned block of 4^k
  * consecutive cells (k <= 4) the OR of their words, i.e. eq. 10 over that
  * block, which the quadtree rows gather (LBL_ALGO_QUAD).  On a z-order agent
- * grid the pyramid is built inside the transform kernel (one launch, O not
- * read back); on a row-major grid the transform and the pyramid are two
- * launches.  lbl_label_pyramid then labels the frame from it.
+ * grid, and on a 2-D row-major grid whose sides are multiples of 16 (the
+ * quadtree form's tiled order), the pyramid is built inside the transform
+ * kernel (one launch, O not read back); on other row-major grids the
+ * transform and the pyramid are two launches.  lbl_label_pyramid then labels
+ * the frame from it.
  *   rm       uploaded with LBL_UPLOAD_QUAD (LBL_EUNSUPPORTED otherwise, unless
  *            the roadmap has no edges: then only O is written)
  *   d_words  packed world words of lbl_pack_planes (LBL_PACKED_WORD_BYTES(n_props) each)
  *   d_O      uint64[agent cells], written as by lbl_frame_transform_words;
- *            may be NULL on a z-order agent grid (the words then exist only as
- *            the pyramid's level 0)
+ *            may be NULL where the pyramid is built in one launch (the words
+ *            then exist only as the pyramid's level 0)
  * Same errors as lbl_frame_transform_words.  The pyramid is the roadmap's
  * working memory: a quadtree lbl_label or another lbl_frame_transform_pyramid
  * on this roadmap overwrites it, and calls on one roadmap must not overlap on

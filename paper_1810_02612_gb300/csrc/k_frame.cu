@@ -126,15 +126,27 @@ __global__ void __launch_bounds__(256) k_frame_z(const __grid_constant__ FrameIt
 // of the pyramid's top level, so the words each thread computes go to O (when
 // asked for) and to the pyramid's level 0, and the CTA ORs levels 1-4 from the
 // same registers: no O re-read and no pyramid launch before the labels.
+// On a row-major 2-D grid in the quadtree form's tiled order (tiled_w > 0) a
+// CTA is one 16 x 16 tile: its words go to the tile's cells of the row-major O
+// and, in the tile's z-order, to the pyramid.
 template <int WB, typename T>
 __global__ void __launch_bounds__(256) k_frame_z_pyramid(const __grid_constant__ FrameItem f, uint32_t n,
-                                                         const __grid_constant__ QuadOffsets off, T *__restrict__ pyr) {
+                                                         const __grid_constant__ QuadOffsets off, T *__restrict__ pyr,
+                                                         int32_t tiled_w) {
   __shared__ uint64_t wsum[kThreads / 32];
   pdl_wait();
   pdl_trigger();
   const uint32_t idx = blockIdx.x * 256u + threadIdx.x;
-  const uint64_t v = idx < n ? frame_word<WB>(f, idx) : 0ull;
-  if (f.O && idx < n) f.O[idx] = v;
+  uint64_t v = 0;
+  if (tiled_w > 0) {  // n is a multiple of 256: every thread has a cell
+    uint32_t ix, iy;
+    tiled_cell(tiled_w, blockIdx.x, threadIdx.x, ix, iy);
+    v = world_word<WB>(f, ix, iy, 0);
+    if (f.O) f.O[iy * static_cast<uint32_t>(f.aw) + ix] = v;
+  } else if (idx < n) {
+    v = frame_word<WB>(f, idx);
+    if (f.O) f.O[idx] = v;
+  }
   quad_pyramid_of<T>(v, n, off, pyr, blockIdx.x, wsum);
 }
 
@@ -317,32 +329,40 @@ cudaError_t launch_frame_transform(const FrameItem &f, cudaStream_t s) {
 }
 
 template <int WB, typename T>
-static cudaError_t transform_pyramid_launch(const FrameItem &f, const QuadOffsets &off, void *pyr, cudaStream_t s) {
+static cudaError_t transform_pyramid_launch(const FrameItem &f, const QuadOffsets &off, void *pyr, int32_t tiled_w,
+                                            cudaStream_t s) {
   const uint32_t n = static_cast<uint32_t>(f.aw) * static_cast<uint32_t>(f.ah) * static_cast<uint32_t>(f.ad);
-  return pdl_launch(k_frame_z_pyramid<WB, T>, dim3((n + 255u) / 256u), dim3(256), s, f, n, off, static_cast<T *>(pyr));
+  return pdl_launch(k_frame_z_pyramid<WB, T>, dim3((n + 255u) / 256u), dim3(256), s, f, n, off, static_cast<T *>(pyr),
+                    tiled_w);
 }
 
 template <int WB>
 static cudaError_t transform_pyramid_width(const FrameItem &f, const QuadOffsets &off, int pyr_bytes, void *pyr,
-                                           cudaStream_t s) {
+                                           int32_t tiled_w, cudaStream_t s) {
   using W = typename WordOf<WB>::T;
-  if (pyr_bytes == WB) return transform_pyramid_launch<WB, W>(f, off, pyr, s);
-  if (pyr_bytes == 8) return transform_pyramid_launch<WB, uint64_t>(f, off, pyr, s);
+  if (pyr_bytes == WB) return transform_pyramid_launch<WB, W>(f, off, pyr, tiled_w, s);
+  if (pyr_bytes == 8) return transform_pyramid_launch<WB, uint64_t>(f, off, pyr, tiled_w, s);
   return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_frame_transform_pyramid(const FrameItem &f, const QuadOffsets &off, int pyr_bytes, void *pyr,
-                                           cudaStream_t s) {
+                                           int32_t tiled_w, cudaStream_t s) {
   const int64_t n = static_cast<int64_t>(f.aw) * f.ah * f.ad;
   if (n == 0) return cudaSuccess;
   if (n >= (1ll << 31) || f.plane_cells >= (1ll << 31)) return cudaErrorInvalidValue;  // grids are checked on the host
-  if (f.order != LBL_ORDER_MORTON || !f.words) return cudaErrorInvalidValue;
+  if (!f.words) return cudaErrorInvalidValue;
+  if (tiled_w > 0) {  // a row-major 2-D grid of whole 16 x 16 tiles
+    if (f.order != LBL_ORDER_ROWMAJOR || f.ad != 1 || f.aw != tiled_w || f.aw % 16 || f.ah % 16)
+      return cudaErrorInvalidValue;
+  } else if (f.order != LBL_ORDER_MORTON) {
+    return cudaErrorInvalidValue;
+  }
   cudaError_t e;
   switch (f.word_bytes) {
-    case 1: e = transform_pyramid_width<1>(f, off, pyr_bytes, pyr, s); break;
-    case 2: e = transform_pyramid_width<2>(f, off, pyr_bytes, pyr, s); break;
-    case 4: e = transform_pyramid_width<4>(f, off, pyr_bytes, pyr, s); break;
-    case 8: e = transform_pyramid_width<8>(f, off, pyr_bytes, pyr, s); break;
+    case 1: e = transform_pyramid_width<1>(f, off, pyr_bytes, pyr, tiled_w, s); break;
+    case 2: e = transform_pyramid_width<2>(f, off, pyr_bytes, pyr, tiled_w, s); break;
+    case 4: e = transform_pyramid_width<4>(f, off, pyr_bytes, pyr, tiled_w, s); break;
+    case 8: e = transform_pyramid_width<8>(f, off, pyr_bytes, pyr, tiled_w, s); break;
     default: return cudaErrorInvalidValue;
   }
   return e != cudaSuccess ? e : cudaGetLastError();

@@ -460,21 +460,29 @@ __global__ void __launch_bounds__(kThreads, stream_min_blocks<U>()) k_label_batc
 
 // Quadtree pyramid of O (quad_pyramid_of): one CTA per 256-cell block of the
 // top level, each thread loading the word of its cell.
+// In the tiled order (tiled_w > 0) the CTA's block is one 16 x 16 tile, read
+// from the row-major O.
 template <typename T>
 __device__ __forceinline__ void quad_pyramid_block(const uint64_t *__restrict__ O, int64_t cells,
                                                    const QuadOffsets &off, T *__restrict__ pyr, int64_t blk,
-                                                   uint64_t *wsum) {
+                                                   uint64_t *wsum, int32_t tiled_w) {
   const int64_t i = blk * kThreads + threadIdx.x;
-  quad_pyramid_of<T>(i < cells ? __ldg(O + i) : 0ull, cells, off, pyr, blk, wsum);
+  int64_t src = i;
+  if (tiled_w > 0) {
+    uint32_t x, y;
+    tiled_cell(tiled_w, blk, threadIdx.x, x, y);
+    src = static_cast<int64_t>(y) * tiled_w + x;
+  }
+  quad_pyramid_of<T>(i < cells ? __ldg(O + src) : 0ull, cells, off, pyr, blk, wsum);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_quad_pyramid(const uint64_t *__restrict__ O, int64_t cells,
-                                                           QuadOffsets off, T *__restrict__ pyr) {
+                                                           QuadOffsets off, T *__restrict__ pyr, int32_t tiled_w) {
   __shared__ uint64_t wsum[kThreads / 32];
   pdl_wait();
   pdl_trigger();
-  quad_pyramid_block<T>(O, cells, off, pyr, blockIdx.x, wsum);
+  quad_pyramid_block<T>(O, cells, off, pyr, blockIdx.x, wsum, tiled_w);
 }
 
 // The same for many frames in one launch: CTA b finds its item (the last with
@@ -493,10 +501,17 @@ __global__ void __launch_bounds__(kThreads) k_quad_pyramid_batch(const __grid_co
   const PyrItem &it = tab.items[lo];
   const int64_t blk = b - it.block0;
   switch (it.word_bytes) {  // CTA-uniform
-    case 1: quad_pyramid_block<uint8_t>(it.O, it.cells, it.off, static_cast<uint8_t *>(it.pyr), blk, wsum); break;
-    case 2: quad_pyramid_block<uint16_t>(it.O, it.cells, it.off, static_cast<uint16_t *>(it.pyr), blk, wsum); break;
-    case 4: quad_pyramid_block<uint32_t>(it.O, it.cells, it.off, static_cast<uint32_t *>(it.pyr), blk, wsum); break;
-    default: quad_pyramid_block<uint64_t>(it.O, it.cells, it.off, static_cast<uint64_t *>(it.pyr), blk, wsum);
+    case 1:
+      quad_pyramid_block<uint8_t>(it.O, it.cells, it.off, static_cast<uint8_t *>(it.pyr), blk, wsum, it.tiled_w);
+      break;
+    case 2:
+      quad_pyramid_block<uint16_t>(it.O, it.cells, it.off, static_cast<uint16_t *>(it.pyr), blk, wsum, it.tiled_w);
+      break;
+    case 4:
+      quad_pyramid_block<uint32_t>(it.O, it.cells, it.off, static_cast<uint32_t *>(it.pyr), blk, wsum, it.tiled_w);
+      break;
+    default:
+      quad_pyramid_block<uint64_t>(it.O, it.cells, it.off, static_cast<uint64_t *>(it.pyr), blk, wsum, it.tiled_w);
   }
 }
 
@@ -1261,10 +1276,14 @@ cudaError_t launch_quad_pyramid(const Roadmap &rm, const uint64_t *O, int word_b
   const unsigned grid = static_cast<unsigned>((rm.cells + kThreads - 1) / kThreads);
   const dim3 g(grid), b(kThreads);
   switch (word_bytes) {  // launched dependent on the frame transform before it
-    case 1: return pdl_launch(k_quad_pyramid<uint8_t>, g, b, s, O, rm.cells, rm.qd_off, static_cast<uint8_t *>(pyr));
-    case 2: return pdl_launch(k_quad_pyramid<uint16_t>, g, b, s, O, rm.cells, rm.qd_off, static_cast<uint16_t *>(pyr));
-    case 4: return pdl_launch(k_quad_pyramid<uint32_t>, g, b, s, O, rm.cells, rm.qd_off, static_cast<uint32_t *>(pyr));
-    default: return pdl_launch(k_quad_pyramid<uint64_t>, g, b, s, O, rm.cells, rm.qd_off, static_cast<uint64_t *>(pyr));
+    case 1: return pdl_launch(k_quad_pyramid<uint8_t>, g, b, s, O, rm.cells, rm.qd_off, static_cast<uint8_t *>(pyr),
+                              rm.qd_tiled_w);
+    case 2: return pdl_launch(k_quad_pyramid<uint16_t>, g, b, s, O, rm.cells, rm.qd_off, static_cast<uint16_t *>(pyr),
+                               rm.qd_tiled_w);
+    case 4: return pdl_launch(k_quad_pyramid<uint32_t>, g, b, s, O, rm.cells, rm.qd_off, static_cast<uint32_t *>(pyr),
+                               rm.qd_tiled_w);
+    default: return pdl_launch(k_quad_pyramid<uint64_t>, g, b, s, O, rm.cells, rm.qd_off, static_cast<uint64_t *>(pyr),
+                               rm.qd_tiled_w);
   }
 }
 

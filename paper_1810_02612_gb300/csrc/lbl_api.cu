@@ -417,6 +417,11 @@ int roadmap_finish(lbl_roadmap_s *rm, uint32_t flags, cudaStream_t st) {
       words += rm->cells >> (2 * k);
     }
     rm->pyr_words = words;
+    // row-major 2-D grids whose sides are multiples of 16 take the tiled order
+    // (square blocks); other row-major grids keep runs of a grid row
+    if (rm->agent.order == LBL_ORDER_ROWMAJOR && grid_depth(rm->agent) == 1 && rm->agent.w % 16 == 0 &&
+        rm->agent.h % 16 == 0)
+      rm->qd_tiled_w = rm->agent.w;
     if (n_edges > 1 && n_edges < (1LL << 31) && !(flags & LBL_UPLOAD_KEEP_ORDER) && grid_depth(rm->agent) == 1) {
       // locality order: inside each of kOrderRanges edge ranges, rows by the z-order of
       // their middle cell's (x, y); time-augmented grids keep the caller's
@@ -446,7 +451,8 @@ int roadmap_finish(lbl_roadmap_s *rm, uint32_t flags, cudaStream_t st) {
     std::vector<int64_t> drow(static_cast<size_t>(n_edges + 1));
     int32_t *d_dc = nullptr;
     if ((e = dev_alloc(&d_dc, static_cast<size_t>(n_edges), nullptr)) != cudaSuccess ||
-        (e = launch_quad_count(rm->rowptr, rm->colidx, n_edges, rm->qd_perm, d_dc, st)) != cudaSuccess ||
+        (e = launch_quad_count(rm->rowptr, rm->colidx, n_edges, rm->qd_perm, rm->qd_tiled_w, d_dc, st)) !=
+            cudaSuccess ||
         (e = cudaMemcpyAsync(cnt.data(), d_dc, sizeof(int32_t) * n_edges, cudaMemcpyDeviceToHost, st)) !=
             cudaSuccess ||
         (e = cudaStreamSynchronize(st)) != cudaSuccess) {
@@ -463,7 +469,8 @@ int roadmap_finish(lbl_roadmap_s *rm, uint32_t flags, cudaStream_t st) {
         (e = obj_alloc(&rm->pyr, static_cast<size_t>(words), &rm->bytes)) != cudaSuccess ||
         (e = cudaMemcpyAsync(rm->qd_rowptr, drow.data(), sizeof(int64_t) * (n_edges + 1), cudaMemcpyHostToDevice,
                              st)) != cudaSuccess ||
-        (e = launch_quad_fill(rm->rowptr, rm->colidx, n_edges, rm->qd_perm, rm->qd_off, rm->qd_rowptr, rm->qd_idx,
+        (e = launch_quad_fill(rm->rowptr, rm->colidx, n_edges, rm->qd_perm, rm->qd_tiled_w, rm->qd_off, rm->qd_rowptr,
+                              rm->qd_idx,
                               st)) != cudaSuccess)
       return fail(cuda_fail(e, "roadmap: quadtree form"));
     rm->qd_part_ctas = stream_ctas_per_sm(kQuadDepth);
@@ -544,9 +551,12 @@ int transform_pyramid(const lbl_grid *world, const void *d_words, int32_t n_prop
     set_error("frame transform (pyramid): n_props = %d outside 0..64", n_props);
     return LBL_EINVAL;
   }
-  const bool z = agent->order == LBL_ORDER_MORTON;
-  if (!d_words || (!d_O && !z)) {
-    set_error("frame transform (pyramid): NULL buffer (row-major agent grids need O)");
+  // z-order grids, and row-major grids in the tiled order, build the pyramid
+  // inside the transform and need no O
+  const bool one_launch = agent->order == LBL_ORDER_MORTON || rm.qd_tiled_w > 0;
+  if (!d_words || (!d_O && !one_launch)) {
+    set_error("frame transform (pyramid): NULL buffer (row-major agent grids need O unless their sides are "
+              "multiples of 16)");
     return LBL_EINVAL;
   }
   if (reinterpret_cast<uintptr_t>(d_words) % static_cast<uintptr_t>(packed_word_bytes(n_props)) ||
@@ -562,9 +572,9 @@ int transform_pyramid(const lbl_grid *world, const void *d_words, int32_t n_prop
   f.wmask = n_props >= 64 ? ~0ull : ((1ull << n_props) - 1ull);
   const int wb = quad_word_bytes(rm, n_props);
   cudaError_t e;
-  if (z) {
-    e = launch_frame_transform_pyramid(f, rm.qd_off, wb, pyr, st);
-  } else {  // row-major cells: the pyramid's blocks are row runs, not the transform's tiles
+  if (one_launch) {
+    e = launch_frame_transform_pyramid(f, rm.qd_off, wb, pyr, rm.qd_tiled_w, st);
+  } else {  // other row-major grids: the pyramid's blocks are row runs, not the transform's tiles
     e = launch_frame_transform(f, st);
     if (e == cudaSuccess) e = launch_quad_pyramid(rm, d_O, wb, pyr, st);
   }

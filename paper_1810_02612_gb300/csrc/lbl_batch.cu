@@ -204,6 +204,7 @@ int lbl_batch_create(int32_t n, const lbl_roadmap *rms, const int32_t *n_props, 
       pi.block0 = block0;
       pi.off = r.qd_off;
       pi.word_bytes = wb;
+      pi.tiled_w = r.qd_tiled_w;
       it.O = pi.pyr;
       b->pyr_slot[i] = b->ptab.n++;
       pyr0 += r.pyr_words;

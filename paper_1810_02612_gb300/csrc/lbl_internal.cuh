@@ -191,6 +191,21 @@ struct QuadOffsets {
   int64_t at[kQuadLevels + 1];  // first pyramid word of each level
 };
 
+// Cell (x, y) of a row-major grid tiled_w cells wide that tiled index
+// 256 * tile + t stands for: tiles of 16 x 16 cells in row-major order, t the
+// z-order index inside the tile (x in the odd bits, y in the even bits).
+__device__ __forceinline__ void tiled_cell(int32_t tiled_w, int64_t tile, uint32_t t, uint32_t &x, uint32_t &y) {
+  const int64_t tw = tiled_w >> 4;
+  uint32_t lx = 0, ly = 0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    lx |= ((t >> (2 * i + 1)) & 1u) << i;
+    ly |= ((t >> (2 * i)) & 1u) << i;
+  }
+  x = static_cast<uint32_t>((tile % tw) * 16) + lx;
+  y = static_cast<uint32_t>((tile / tw) * 16) + ly;
+}
+
 // Quadtree pyramid of O (compressed A): level k holds, for every block of 4^k
 // consecutive cells in the grid's cell order that lies wholly inside the
 // grid, the OR of their words; level 0 is O itself.  Word of block b at level
@@ -238,6 +253,7 @@ struct PyrItem {
   int64_t block0;  // first 256-cell block of this item in the launch
   QuadOffsets off;
   int32_t word_bytes;  // 1, 2, 4 or 8
+  int32_t tiled_w;     // > 0: the pyramid is in the tiled order of a row-major grid this wide
 };
 // Batched label launches group their items by gathered word width.
 constexpr int kWordClasses = 4;  // 1, 2, 4, 8 bytes
@@ -313,6 +329,9 @@ struct Roadmap {
   int qd_part_ctas = 0;
   QuadOffsets qd_off{};
   int64_t pyr_words = 0;
+  // > 0: the quadtree rows and the pyramid use the tiled order of this
+  // row-major 2-D grid (its width; sides multiples of 16), 0: the cell order
+  int32_t qd_tiled_w = 0;
   uint64_t *pyr = nullptr;      // per-frame pyramid (working memory)
   int pyr_built_bytes = 0;      // word width of the pyramid last enqueued into `pyr` (0: none yet)
   // dense tensor-core form (optional): edges in locality order in tiles of 128,
@@ -386,11 +405,12 @@ FrameItem frame_item(const FrameMap &m, const lbl_grid &W, const lbl_grid &A, co
                      uint64_t *O, int64_t cell0);
 
 cudaError_t launch_frame_transform(const FrameItem &f, cudaStream_t s);
-// z-order agent grids, packed world words: the transform (O written unless
+// z-order agent grids, or row-major 2-D grids in the quadtree form's tiled
+// order (tiled_w > 0), packed world words: the transform (O written unless
 // f.O is NULL) and the quadtree pyramid of its words (pyr_bytes-wide words at
 // `off`) in one kernel
 cudaError_t launch_frame_transform_pyramid(const FrameItem &f, const QuadOffsets &off, int pyr_bytes, void *pyr,
-                                           cudaStream_t s);
+                                           int32_t tiled_w, cudaStream_t s);
 cudaError_t launch_pack_planes(const PackItem &it, cudaStream_t s);
 cudaError_t launch_pack_batch(const PackTable &tab, cudaStream_t s);
 bool pack_vec_ok(const PackItem &it);
@@ -434,10 +454,12 @@ cudaError_t launch_quad_pyramid_batch(const PyrTable &tab, cudaStream_t s);
 // of the (x, y) of row e's middle cell (2-D grids of w columns in `order`)
 cudaError_t launch_row_keys(const int64_t *rowptr, const int32_t *colidx, int64_t E, int32_t order, int32_t w,
                             uint32_t *key, cudaStream_t s);
+// tiled_w > 0: rows in the tiled order of a row-major grid tiled_w cells wide
+// (16 x 16 tiles in row-major order, z-order inside a tile), else in the cell order
 cudaError_t launch_quad_count(const int64_t *rowptr, const int32_t *colidx, int64_t E, const int32_t *rowmap,
-                                int32_t *count, cudaStream_t s);
+                                int32_t tiled_w, int32_t *count, cudaStream_t s);
 cudaError_t launch_quad_fill(const int64_t *rowptr, const int32_t *colidx, int64_t E, const int32_t *rowmap,
-                               QuadOffsets off, const int64_t *drow, int32_t *idx, cudaStream_t s);
+                               int32_t tiled_w, QuadOffsets off, const int64_t *drow, int32_t *idx, cudaStream_t s);
 
 cudaError_t launch_label_bittile(const Roadmap &rm, const uint64_t *O, int32_t P, uint64_t *L,
                                  const MonitorTables *mon, bool early_exit, int ctas_per_sm, cudaStream_t s);

@@ -207,6 +207,7 @@ cudaError_t launch_group(lbl_server_s &S, Lane &lane, std::vector<Request *> &gr
       pi.cells = rm.cells;
       pi.block0 = block0;
       pi.off = rm.qd_off;
+      pi.tiled_w = rm.qd_tiled_w;
       block0 += (rm.cells + lbl::kThreads - 1) / lbl::kThreads;
       it.O = r.d_pyr;
     }

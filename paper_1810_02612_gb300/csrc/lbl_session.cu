@@ -133,10 +133,11 @@ int lbl_session_create(lbl_roadmap rm, const lbl_grid *world, int32_t n_props, l
     ss->chunked = true;
     ss->quad = c.algo == LBL_ALGO_QUAD;
     if (ss->quad) e = obj_alloc(&ss->pyr, static_cast<size_t>(rm->pyr_words), nullptr);
-    // z-order quadtree sessions always pack the planes: the transform then
-    // builds the pyramid itself (device step 0.0393 -> 0.0376 ms on the
+    // quadtree sessions on z-order (or tiled row-major) grids always pack the
+    // planes: the transform then builds the pyramid itself (device step 0.0393 -> 0.0376 ms on the
     // 100k-edge frame with 2 MiB of planes)
-    if (e == cudaSuccess && ss->quad && !ss->words && n_props > 0 && rm->agent.order == LBL_ORDER_MORTON &&
+    if (e == cudaSuccess && ss->quad && !ss->words && n_props > 0 &&
+        (rm->agent.order == LBL_ORDER_MORTON || rm->qd_tiled_w > 0) &&
         grid_cells(*world) <= kPackedWorldRatio * rm->cells)
       e = obj_alloc(&ss->words, static_cast<size_t>(grid_cells(*world)) * packed_word_bytes(n_props), nullptr);
     ss->depth = c.depth ? c.depth : (ss->quad ? kQuadDepth : 8);
@@ -195,9 +196,10 @@ int lbl_session_run(lbl_session ss, const uint8_t *h_planes, lbl_pose pose, uint
   if (e == cudaSuccess) e = cudaStreamWaitEvent(cc, ss->ev_out[k], 0);
   if (e != cudaSuccess) return cuda_fail(e, "session run: copy planes");
   int rc = LBL_OK;
-  // z-order quadtree sessions build the pyramid inside the transform (the
-  // words are needed only as its level 0, so O is not written)
-  const bool fused = ss->words && ss->chunked && ss->quad && rm.agent.order == LBL_ORDER_MORTON;
+  // quadtree sessions on z-order (or tiled row-major) grids build the pyramid
+  // inside the transform (the words are needed only as its level 0, so O is
+  // not written)
+  const bool fused = ss->words && ss->chunked && ss->quad && (rm.agent.order == LBL_ORDER_MORTON || rm.qd_tiled_w > 0);
   if (ss->words) {
     const PackItem it{ss->slot[k], ss->words, grid_cells(ss->world), ss->P, packed_word_bytes(ss->P)};
     if ((e = launch_pack_planes(it, cc)) != cudaSuccess) return cuda_fail(e, "session run: pack planes");

@@ -3,7 +3,8 @@ and of labels gathered from that pyramid (lbl_label_pyramid): the agent words,
 the labels and the fused monitor's outputs equal the oracle bit for bit
 (eq. 13, eq. 10, Sec. 3.2).  Covers every pyramid word width, z-order grids
 whose cell count is below one 256-cell block or not a whole number of blocks
-per level, the row-major fallback, (x, y, tau) z-order grids, the moving front
+per level, row-major grids in the tiled order and the row-major fallback,
+(x, y, tau) z-order grids, the moving front
 and the per-warp stream, and the calls' refusals."""
 import numpy as np
 import pytest
@@ -87,9 +88,18 @@ def test_pyramid_path_grids_below_and_around_one_block(n):
 
 
 def test_pyramid_path_row_major_grid_and_larger_roadmap():
-    """Row-major agent grid (transform and pyramid as two launches) and a
-    z-order 256 x 256 roadmap of 20k edges (many chunks of the front)."""
+    """Row-major agent grids of whole 16 x 16 tiles (the tiled order: one
+    launch, also without O) and of partial tiles (transform and pyramid as two
+    launches), and a z-order 256 x 256 roadmap of 20k edges (many chunks of
+    the front)."""
+    tiled = synth.make("plain", seed=56, edges=700, order=synth.ROWMAJOR, n=80, h=48, P=12)
+    rm = L.lbl_roadmap_upload(tiled.agent, tiled.rowptr, tiled.colidx, flags=L.LBL_UPLOAD_QUAD)
+    try:
+        check_frame(tiled, 12, rm, with_O=False)
+    finally:
+        L.lbl_roadmap_free(rm)
     for wl, P in ((synth.make("plain", seed=50, edges=700, order=synth.ROWMAJOR, P=12), 12),
+                  (synth.make("plain", seed=57, edges=700, order=synth.ROWMAJOR, n=72, h=40, P=12), 12),
                   (synth.make("driving", seed=51, edges=20_000), 32)):
         rm = L.lbl_roadmap_upload(wl.agent, wl.rowptr, wl.colidx, flags=L.LBL_UPLOAD_QUAD)
         try:
@@ -149,7 +159,7 @@ def test_pyramid_calls_refuse_what_they_cannot_do():
             L.lbl_label_pyramid(rm, 6, out, cfg=dict(algo=L.LBL_ALGO_CSR))
         with pytest.raises(L.LblError, match="LBL_UPLOAD_QUAD"):
             L.lbl_frame_transform_pyramid(plain, wl.world, words, 6, wl.pose)
-        row = synth.make("plain", seed=55, edges=50, order=synth.ROWMAJOR, P=6)
+        row = synth.make("plain", seed=55, edges=50, order=synth.ROWMAJOR, n=72, h=40, P=6)  # not whole tiles
         rrm = L.lbl_roadmap_upload(row.agent, row.rowptr, row.colidx, flags=L.LBL_UPLOAD_QUAD)
         try:
             with pytest.raises(L.LblError, match="row-major agent grids need O"):
