@@ -289,10 +289,13 @@ __global__ void __launch_bounds__(kThreads, stream_min_blocks<U>()) k_label_stre
 // DRAM.  Measured on the 1M-edge call (64-bit pyramid words, chunks of 24 edges
 // of ~23 KB of indices): no prefetch 0.2539 ms, 2 / 4 / 6 / 8 / 10 / 12 / 16 KB
 // 0.2536 / 0.2507 / 0.2484 / 0.2469 / 0.2460 / 0.2463 / 0.2485 ms; the chunk's
-// own entries instead 0.2650 ms.  With 1-byte pyramid words (the paper frames,
-// ~10 KB chunks) it was neutral (2^21-cell 2-D frame 0.2528 vs 0.2525-0.2534
-// ms) or slower ((x, y, tau) frame 0.3034 vs 0.3065-0.3098 ms), so only 8-byte
-// pyramid words prefetch.  The same warp also asks L2 for the next chunk's
+// own entries instead 0.2650 ms.  The 2^21-cell 2-D frame (1-byte words, rows
+// in the tiled order and sorted for locality): 0.1560 ms without, 2 / 4 / 8 /
+// 10 / 12 / 16 / 24 KB 0.1557 / 0.1535 / 0.1517 / 0.1513 / 0.1509 / 0.1514 /
+// 0.1518 ms.  The (x, y, tau) frame, whose rows keep the caller's order (the
+// chunks of a CTA are not neighbours in space): 0.3035 ms without, 4 / 8 KB
+// 0.3095 / 0.3065 ms.  So the front prefetches only rows the library put in
+// locality order.  The same warp also asks L2 for the next chunk's
 // entries of the row order (`perm`, read when a window of labels is written
 // out): 1M-edge call 0.2464 -> 0.2459 ms, paper frame unchanged.  (The
 // next chunk's last row pointer, likewise: no change, 0.2457 ms.)
@@ -1212,7 +1215,7 @@ void front_launch(const StreamRows &r, const T *base, uint64_t mask, uint64_t *L
   const unsigned grid = static_cast<unsigned>(num_sms);
   const int small = std::min(chunk, kFrontTailChunk);
   const int tail = 2 * kFrontWarps * small;
-  const int pf = sizeof(T) == 8 ? kFrontPrefetchBytes : 0;
+  const int pf = r.perm ? kFrontPrefetchBytes : 0;  // rows in the library's locality order
   const int64_t idx_bytes = r.entries * 4;  // prefetches stay inside the rows' entries
   MonitorTables none{};
   const dim3 g(grid), b(kFrontWarps * 32);
