@@ -168,6 +168,43 @@ def test_paper_2d_2pow21_cells():
                                      dict(algo=L.LBL_ALGO_MMA)])
 
 
+def test_paper_2d_transform_pyramid_and_session_frames():
+    """The paper frame's quadtree rows are in the tiled order (2048 x 1024 is
+    whole 16 x 16 tiles): the transform building the pyramid with the labels
+    from it, as bench.py times them, and host-buffer session frames back to
+    back (which take the same kernels), at two poses; the transform's O and
+    every edge's label equal the oracle."""
+    wl = synth.make("paper", seed=0, threads=0)
+    rm = L.lbl_roadmap_upload(wl.agent, wl.rowptr, wl.colidx, flags=L.LBL_UPLOAD_QUAD)
+    ss = L.lbl_session_create(rm, wl.world, wl.P)
+    try:
+        poses = [wl.pose, synth.random_pose(np.random.default_rng(73), wl.world)]
+        wants = [oracle.frame_transform(wl.world, wl.planes, pose, wl.agent) for pose in poses]
+        words = torch.empty(wl.world.cells, dtype=getattr(torch, L.packed_word_dtype(wl.P)), device="cuda")
+        L.lbl_pack_planes(wl.world, torch.from_numpy(wl.planes).cuda(), wl.P, words)
+        O = torch.empty(wl.agent.cells, dtype=torch.uint64, device="cuda")
+        out = torch.empty(wl.n_edges, dtype=torch.uint64, device="cuda")
+        labels = []
+        for pose, want_O in zip(poses, wants):
+            L.lbl_frame_transform_pyramid(rm, wl.world, words, wl.P, pose, O)
+            L.lbl_label_pyramid(rm, wl.P, out)
+            torch.cuda.synchronize()
+            assert np.array_equal(O.cpu().numpy(), want_O)
+            labels.append(oracle.label(wl.rowptr, wl.colidx, want_O, wl.P, threads=THREADS))
+            assert np.array_equal(out.cpu().numpy(), labels[-1])
+        planes = torch.from_numpy(wl.planes).pin_memory()
+        outs = [torch.empty(wl.n_edges, dtype=torch.uint64).pin_memory() for _ in poses]
+        s = torch.cuda.Stream()
+        for pose, o in zip(poses, outs):
+            L.lbl_session_run(ss, planes, pose, o, stream=s)
+        s.synchronize()
+        for o, want in zip(outs, labels):
+            assert np.array_equal(o.numpy(), want)
+    finally:
+        L.lbl_session_free(ss)
+        L.lbl_roadmap_free(rm)
+
+
 def test_paper_time_augmented_2pow21_cells():
     wl = synth.make_paper3d(seed=0, threads=0)
     assert wl.agent.cells == 1 << 21 and wl.agent.d == 128
