@@ -740,7 +740,8 @@ def main():
             "gpu_launches": launches_per_step * args.steps,
             "mma_probe": mma_probe(L) if used == "mma" else None,
             "roofline": mma_roofline(wl, qd_or_mma, label_avg_s, peaks, achieved, peak, lb) if used == "mma" else
-                        {"bound": "l1" if l1 else "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        {"bound": "l1" if l1 and l1["frac"] >= achieved / peak else "hbm",  # the fuller one
+                         "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": f"label_{used}", "algorithmic_bytes_per_launch": lb,
                          "csr_equivalent_gbs": label_bytes(wl, "csr", None, mon is not None) / label_avg_s / 1e9,
