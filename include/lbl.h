@@ -150,7 +150,8 @@ typedef struct lbl_server_s *lbl_server;
    The pointer stays valid until the thread's next lbl_* call. */
 const char *lbl_last_error(void);
 
-/* ABI version of this header (major * 10000 + minor * 100 + patch). */
+/* ABI version of this header (major * 10000 + minor * 100 + patch): 1.1.0
+   (1.0.0 plus lbl_frame_transform_pyramid and lbl_label_pyramid). */
 int lbl_version(void);
 
 /* --------------------------------------------------------------- roadmap */

@@ -588,7 +588,7 @@ extern "C" {
 
 const char *lbl_last_error(void) { return g_err.c_str(); }
 
-int lbl_version(void) { return 10000; }
+int lbl_version(void) { return 10100; }
 
 int lbl_roadmap_upload(const lbl_grid *agent, const int64_t *rowptr, const int32_t *colidx, int64_t n_edges,
                        int64_t nnz, uint32_t flags, lbl_stream s, lbl_roadmap *out) {

@@ -48,7 +48,7 @@ def test_struct_layouts_match_the_header():
 
 
 def test_version_and_empty_error():
-    assert L.lbl_version() == 10000
+    assert L.lbl_version() == 10100  # 1.1.0: the transform building the pyramid, labels from it
     assert L.lbl_last_error() == ""
 
 
